@@ -1,0 +1,86 @@
+"""The pins catch plausible oracle mistakes.
+
+Each case copies the oracle's C source, plants one mistake (a dropped term, a
+wrong index or operand, an off-by-one, a strict instead of inclusive test, a
+missing reset), compiles it into a temporary library and runs the pin suite
+against it: at least one pin must fail.  Everything happens on the CPU.
+"""
+import ctypes
+import os
+import subprocess
+
+import pytest
+
+import oracle
+import test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "localgd.c")
+
+MUTANTS = {
+    "ppr_x_drops_alpha": ("x[u] = x[u] + alpha * rho[i];", "x[u] = x[u] + rho[i];"),
+    "ppr_share_not_divided_by_degree": ("double w = (one_minus_alpha * rho[i]) / (double)d;",
+                                        "double w = (one_minus_alpha * rho[i]);"),
+    "ppr_share_uses_alpha": ("const double one_minus_alpha = 1.0 - alpha;",
+                             "const double one_minus_alpha = alpha;"),
+    "strict_threshold": ("fabs(r[u]) >= thr) active", "fabs(r[u]) > thr) active"),
+    "threshold_without_degree": ("double thr = eps_theta * (double)deg_of(off, u);",
+                                 "double thr = eps_theta;"),
+    "active_not_zeroed": ("        r[u] = 0.0;\n        vol +=", "        vol +="),
+    "katz_share_divided_by_degree": ("double w = beta * rho[i];",
+                                     "double w = beta * rho[i] / (double)(deg_of(off, u) + 1);"),
+    "hk_coef_off_by_one": ("const double coef = tau / (double)(t + 1);",
+                           "const double coef = tau / (double)(t + 2);"),
+    "hk_theta_without_psi": ("exp(tau) / ((double)(N + 1) * oracle_hk_psi(tau, N, t))",
+                             "exp(tau) / ((double)(N + 1))"),
+    "hk_terms_one_short": ("if (tail <= tol) best = N; else break;",
+                           "if (tail <= tol) best = N - 1; else break;"),
+    "hk_psi_wrong_factorial": ("term = term * (tau / (double)(k + j));",
+                               "term = term * (tau / (double)(j));"),
+}
+
+PIN_CASES = [
+    (pins.test_ppr_edge2_rounds, dict(alpha=0.15)),
+    (pins.test_ppr_star_rounds_from_center, dict(k=3)),
+    (pins.test_katz_star_closed_form, dict(k=4, beta=0.3)),
+    (pins.test_hk_star_closed_form, dict(k=5, tau=3.0)),
+    (pins.test_ppr_error_bound_dense, dict(gi=4, alpha=0.15, eps=1e-4)),
+    (pins.test_hk_dense, dict(gi=4, tau=5.0)),
+    (pins.test_ppr_round_invariants, dict(gi=4)),
+    (pins.test_threshold_is_inclusive, {}),
+    (pins.test_hk_terms_against_poisson_tail, {}),
+    (pins.test_hk_psi_definition, {}),
+    (pins.test_hk_weighted_mass_and_layer_invariant, {}),
+]
+
+
+def build_mutant(tmp_path, name):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor for {name} not unique"
+    path = tmp_path / f"{name}.c"
+    path.write_text(src.replace(old, new))
+    so = tmp_path / f"{name}.so"
+    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+                           "-std=c11", "-o", str(so), str(path), "-lm"])
+    return str(so)
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(tmp_path, monkeypatch, name):
+    so = build_mutant(tmp_path, name)
+    good = oracle._load()
+    bad = ctypes.CDLL(so)
+    # same signatures as the real library
+    for sym in ("oracle_ppr_round", "oracle_katz_round", "oracle_hk_round", "oracle_hk_terms",
+                "oracle_hk_psi", "oracle_hk_theta", "oracle_localgd_solve",
+                "oracle_localgd_solve_many", "oracle_push_fifo"):
+        f, g = getattr(bad, sym), getattr(good, sym)
+        f.argtypes, f.restype = g.argtypes, g.restype
+    monkeypatch.setattr(oracle, "_lib", bad)
+    caught = []
+    for fn, kw in PIN_CASES:
+        try:
+            fn(**kw)
+        except AssertionError:
+            caught.append(fn.__name__)
+    assert caught, f"no pin caught mutant {name}"
