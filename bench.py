@@ -1,0 +1,382 @@
+#!/usr/bin/env python3
+"""Benchmark: batched FP32 LocalGD on R-MAT scale 24 (GTEPS and seeds/s at eps=1e-7).
+
+One step = one batched solve of the whole hot path (seed init, every LocalGD round of
+every seed in one persistent launch, per-seed top-64) for 1024 PPR sources (512 uniform
++ 512 top-1% hubs), alpha=0.1, eps=1e-7, on the synthetic R-MAT 24 graph (edge factor
+16, symmetrised, deduplicated).  Reports seeds/s (value), GTEPS, the plain FP64
+one-seed-per-launch path on the same GPU, the roofline of the persistent round kernel,
+an end-to-end figure through host buffers, and the FP64 oracle on the host's cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank solves its own 1024 seeds on a replica of the graph
+(seed sharding, no collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "GTEPS & seeds/s at eps=1e-7, % HBM peak; batched FP32 vs plain FP64 on same GPU"
+ALPHA, EPS, TOPK = 0.1, 1e-7, 64
+# algorithmic bytes of the persistent round kernel (hash accumulators, FP32):
+# per pushed edge: column id 4 + slot word read 8 + residual write 4 + threshold 4
+BYTES_PER_EDGE = 20
+# per pushed node: candidate 4 + slot word 8 + residual zero 4 + x read/write 8 + threshold 4
+# + row offsets 16 + degree-bin entry written and read 2*20 + candidate append 4
+BYTES_PER_PUSH = 88
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gde", choices=["gde", "reference"])
+    ap.add_argument("--graph", default="rmat24", help="named synthetic workload graph")
+    ap.add_argument("--seeds", type=int, default=1024)
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--budget-gb", type=float, default=0.0,
+                    help="hash accumulator budget (0: the library default)")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_inputs(graph_name, nseeds, rank):
+    import synth
+    t0 = time.time()
+    g = synth.workload_graph(graph_name)
+    half = nseeds // 2
+    seeds = synth.seeds_mixed(g, nseeds - half, half, seed=4 + 1000 * rank)
+    log(f"[bench] graph {g.summary()} generated in {time.time() - t0:.1f}s")
+    return g, seeds
+
+
+def workload_config(g, nseeds, n_gpus):
+    return {
+        "workload": f"batched PPR top-{TOPK}, R-MAT scale 24 (edge factor 16, a=0.57 b=0.19 c=0.19, "
+                    f"symmetrised, deduplicated, int32 CSR), {nseeds} seeds/GPU (half uniform, "
+                    f"half top-1% degree), alpha={ALPHA}, eps={EPS}, FP32 hash accumulators"
+                    if g.name == "rmat24" else f"batched PPR top-{TOPK} on {g.name}, {nseeds} seeds",
+        "graph": g.name, "n": int(g.n), "nnz": int(g.nnz), "max_degree": int(g.degrees().max()),
+        "seeds_per_gpu": nseeds, "alpha": ALPHA, "eps": EPS, "topk": TOPK,
+        "global_batch": nseeds * n_gpus,
+        "parallelism": f"seed-sharded replicas x{n_gpus}",
+        "l2": "inputs larger than L2: CSR 2.1 GB read in place, accumulator pool rewritten every step",
+    }
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def cpu_baseline(g, seeds, budget_s=12.0):
+    """The FP64 oracle (as it stands) on a bounded sample of the same seed mix, one seed per
+    host thread."""
+    import numpy as np
+
+    import oracle
+    import synth
+    cores = synth.num_threads()
+    half = len(seeds) // 2
+    # equal numbers of uniform and hub seeds, one round of `cores` seeds first to size the sample
+    k = max(2, cores)
+    pick = np.concatenate([seeds[: k // 2], seeds[half: half + k - k // 2]])
+    t0 = time.time()
+    oracle.localgd_many(g, "ppr", ALPHA, EPS, pick)
+    dt = time.time() - t0
+    reps = max(1, min(8, int(budget_s / max(dt, 1e-3))))
+    if reps > 1:
+        pick2 = np.concatenate([seeds[: reps * k // 2], seeds[half: half + reps * (k - k // 2)]])
+        t0 = time.time()
+        oracle.localgd_many(g, "ppr", ALPHA, EPS, pick2)
+        dt = time.time() - t0
+        pick = pick2
+    return {"value": len(pick) / dt, "unit": "seeds/s", "cores": cores, "kind": "oracle",
+            "sample": f"{len(pick)} of the {len(seeds)} seeds ({len(pick) // 2} uniform + "
+                      f"{len(pick) - len(pick) // 2} hubs), FP64 LocalGD oracle, one seed per thread, "
+                      f"{dt:.1f}s wall"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    g, seeds = make_inputs(args.graph, args.seeds, 0)
+    import numpy as np
+
+    import oracle
+    import synth
+    cores = synth.num_threads()
+    k = max(2, cores)
+    half = len(seeds) // 2
+    per_step = np.concatenate([seeds[: k // 2], seeds[half: half + k - k // 2]])
+    for _ in range(args.warmup):
+        oracle.localgd_many(g, "ppr", ALPHA, EPS, per_step[: max(2, k // 4)])
+    times = []
+    for s in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.localgd_many(g, "ppr", ALPHA, EPS, per_step)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = len(per_step) * args.steps / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "seeds/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(g, args.seeds, args.gpus),
+        "cpu_baseline": {"value": value, "unit": "seeds/s", "cores": cores, "kind": "oracle",
+                         "sample": f"each step {len(per_step)} of the {len(seeds)} seeds (half uniform, "
+                                   f"half hubs), FP64 LocalGD oracle, one seed per host thread"},
+        "e2e": {"value": value, "unit": "seeds/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws != args.gpus:
+        log(f"[bench] warning: --gpus {args.gpus} but WORLD_SIZE {ws}")
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+
+    import paper_2410_21634_gb300 as gde
+    gde.load()
+    g, seeds_np = make_inputs(args.graph, args.seeds, rank)
+    G = gde.Graph.from_synth(g)
+    nseeds = len(seeds_np)
+    dev = torch.device("cuda", local)
+    seeds = torch.from_numpy(seeds_np).to(dev)
+    ids = torch.zeros((nseeds, TOPK), dtype=torch.int32, device=dev)
+    vals = torch.zeros((nseeds, TOPK), dtype=torch.float32, device=dev)
+
+    budget = int(args.budget_gb * (1 << 30))
+
+    def step():
+        return gde.solve(G, "ppr", ALPHA, EPS, seeds, vals, ids, precision="fp32", topk=TOPK, batched=1,
+                         mem_budget_bytes=budget)
+
+    for _ in range(max(args.warmup, 3)):
+        st, stats = step()
+    overflow = sum(1 for s in stats if s["status"] == gde.ENOMEM)
+    torch.cuda.synchronize()
+    G.profile_enable(True)
+    stream = torch.cuda.current_stream()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        start.record(stream)
+        for _ in range(args.steps):
+            st, stats = step()
+        stop.record(stream)
+        torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    ms = start.elapsed_time(stop)
+    prof = G.profile_read()
+    G.profile_enable(False)
+    t_max = ms
+    edges_step = prof["edges"] / args.steps
+    if pg:
+        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        t_max = float(tt.item())
+        ee = torch.tensor([prof["edges"]], device=dev, dtype=torch.float64)
+        pg.all_reduce(ee, op=pg.ReduceOp.SUM)
+        edges_total = float(ee.item())
+    else:
+        edges_total = float(prof["edges"])
+    sec = t_max / 1e3
+    value = nseeds * ws * args.steps / sec
+    gteps = edges_total / sec / 1e9
+    clk = clocks.summary()
+
+    # roofline of the persistent round kernel (its own CUDA events, on the launching stream)
+    peak, peak_kind = measured_peaks()
+    launches = max(prof["batch_launches"], 1)
+    k_ms = prof["batch_rounds_ms"] / launches
+    alg_bytes = (BYTES_PER_EDGE * prof["edges"] + BYTES_PER_PUSH * prof["pushes"]) / launches
+    achieved = alg_bytes / (k_ms / 1e3) / 1e9
+    traffic = None
+    tp = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tp):
+        # DRAM bytes per launch from an ncu capture; only valid for the kernel source it was taken on
+        import hashlib
+        tj = json.load(open(tp))
+        src = open(os.path.join(ROOT, "paper_2410_21634_gb300", "csrc", "batched.cu"), "rb").read()
+        if (tj.get("kernel") == "k_batch_rounds" and tj.get("graph") == g.name and tj.get("seeds") == nseeds
+                and tj.get("source_sha256") == hashlib.sha256(src).hexdigest()):
+            traffic = tj.get("bytes_per_launch")
+    roofline = {"bound": "hbm", "kernel": "k_batch_rounds", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
+                "kernel_ms": k_ms, "alg_bytes_per_launch": alg_bytes,
+                "share_of_step": prof["batch_rounds_ms"] / ms if ms > 0 else None}
+
+    # end to end through the public API with host buffers (seeds in, top-k out)
+    seeds_host = torch.from_numpy(seeds_np).pin_memory()
+    ids_h = torch.zeros((nseeds, TOPK), dtype=torch.int32).pin_memory()
+    vals_h = torch.zeros((nseeds, TOPK), dtype=torch.float32).pin_memory()
+    ids_hn, vals_hn, seeds_hn = ids_h.numpy(), vals_h.numpy(), seeds_host.numpy()
+    e2e_steps = max(3, min(args.steps, 10))
+    gde.solve(G, "ppr", ALPHA, EPS, seeds_hn, vals_hn, ids_hn, precision="fp32", topk=TOPK, batched=1,
+              mem_budget_bytes=budget)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        gde.solve(G, "ppr", ALPHA, EPS, seeds_hn, vals_hn, ids_hn, precision="fp32", topk=TOPK, batched=1,
+                  mem_budget_bytes=budget)
+    e2e_sec = (time.perf_counter() - t0) / e2e_steps
+    e2e = {"value": nseeds * ws / e2e_sec, "unit": "seeds/s", "h2d_bytes_per_step": 4 * nseeds,
+           "d2h_bytes_per_step": 8 * nseeds * TOPK,
+           "note": "host seed ids in, host top-k ids+values out, through gde_solve with host pointers"}
+
+    # the plain FP64 local GD, one seed per launch, on the same GPU and seed mix
+    plain = None
+    if not args.no_plain and rank == 0:
+        out = torch.zeros((1, g.n), dtype=torch.float64, device=dev)
+        half = nseeds // 2
+        sample = np.concatenate([seeds_np[:128], seeds_np[half:half + 128]])
+        for s in sample[:4]:
+            gde.solve(G, "ppr", ALPHA, EPS, torch.tensor([s], dtype=torch.int32, device=dev), out)
+        torch.cuda.synchronize()
+        vol = 0
+        t0 = time.perf_counter()
+        for s in sample:
+            _, st1 = gde.solve(G, "ppr", ALPHA, EPS, torch.tensor([s], dtype=torch.int32, device=dev), out)
+            vol += st1[0]["active_volume"]
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        plain = {"value": len(sample) / dt, "unit": "seeds/s", "gteps": vol / dt / 1e9,
+                 "sample": f"{len(sample)} of the {nseeds} seeds (128 uniform + 128 hubs), one gde_solve "
+                           f"per seed, dense FP64 x and r, output x written per seed",
+                 "dtype": "f64"}
+
+    cpu = None
+    if not args.no_cpu and rank == 0 and ws == 1:
+        cpu = cpu_baseline(g, seeds_np)
+
+    launches_per_step = 4  # pool clear, seed init, persistent rounds, top-k
+    gpu_launches = launches_per_step * args.steps + 3 * prof["dense_rounds"]
+    line = {
+        "metric": METRIC, "value": value, "unit": "seeds/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config(g, nseeds, ws),
+        "gteps": gteps,
+        "plain_fp64_one_seed_per_launch": plain,
+        "speedup_vs_plain_fp64": (value / ws) / plain["value"] if plain else None,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": gpu_launches,
+        "clocks": clk,
+        "hash_overflow_seeds": overflow,
+        "edges_per_step": edges_step,
+        "rounds_per_step": prof["rounds"] / launches,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    G.close()
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

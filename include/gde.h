@@ -1,0 +1,178 @@
+/*
+ * gde.h — C ABI of the GB300 local graph-diffusion solver.
+ *
+ * Computes approximate graph diffusion vectors f = sum_k c_k M^k s (Eq. 1 of
+ * "Faster Local Solvers for Graph Diffusion Equations", arXiv 2410.21634) for
+ * three equations of Table 1, by the parallel local diffusion process LocalGD
+ * (Eq. local-gd, Section 3.3):
+ *
+ *   GDE_PPR   personalized PageRank, M = A D^-1, c_k = alpha (1-alpha)^k   (Eq. f-ppr)
+ *   GDE_KATZ  Katz, (I - beta A) x = e_s; the Katz vector is x - e_s      (Eq. f-katz)
+ *   GDE_HK    heat kernel exp(-tau (I - A D^-1)) e_s via its Taylor layers (Section 2)
+ *
+ * Each round t takes the active set S_t = { u : r_u != 0, |r_u| >= theta_t eps d_u }
+ * (Definition 3.1; theta_t = 1 for PPR and Katz), moves r_S into x and scatters
+ * M r_S back into the residual.  The source has unit mass (r0 = e_s):
+ *   PPR : x_u += alpha r_u, r_v += ((1-alpha) r_u)/d_u          (v in N(u))
+ *   Katz: x_u += r_u,       r_v += beta r_u
+ *   HK  : layer-t node u:  x_u += r_u, r_{t+1,v} += ((tau/(t+1)) r_u)/d_u; the last
+ *         Taylor layer N (tail mass <= hk_tol) only moves its residual into x.
+ * Degree-0 nodes scatter nothing.  All work runs in this library's CUDA kernels
+ * (sm_103a); there is no CPU fallback.
+ *
+ * Conventions for every entry point:
+ *   - Return GDE_OK or an error status; gde_last_error() then describes the
+ *     failure (thread-local, valid until the thread's next call).
+ *   - No output is written on failure, except per-seed stats where stated.
+ *   - Pointers are host pointers unless GDE_DEVICE_PTRS is set in the relevant
+ *     flags; device pointers must be on the device that was current when the graph
+ *     was created.  Inputs are copied; outputs are caller-allocated.
+ *   - Calls on one graph are serialised by the library (a per-graph lock); use one
+ *     graph per host thread for concurrency.
+ */
+#ifndef GDE_H
+#define GDE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gde_graph gde_graph;
+typedef struct gde_session gde_session;
+
+typedef enum { GDE_PPR = 0, GDE_KATZ = 1, GDE_HK = 2 } gde_kind;
+
+typedef enum {
+    GDE_OK = 0,
+    GDE_EINVAL = 1,    /* bad argument or malformed CSR */
+    GDE_ENOMEM = 2,    /* device or host allocation failed, or the memory budget is too small */
+    GDE_ECUDA = 3,     /* a CUDA runtime error */
+    GDE_ENOTCONV = 4,  /* the round cap was reached before S_t became empty */
+    GDE_ETIMEOUT = 5   /* a bounded device-side wait gave up */
+} gde_status;
+
+enum {
+    GDE_DEVICE_PTRS = 0x1u,      /* pointer arguments are device pointers */
+    GDE_CHECK_SYMMETRIC = 0x2u   /* gde_graph_create: also verify that A = A^T */
+};
+
+enum { GDE_FP64 = 0, GDE_FP32 = 1 };
+
+/* Solve options; gde_solve_opts_init() fills the defaults. */
+typedef struct {
+    int32_t precision;       /* GDE_FP64 (default) or GDE_FP32: storage and arithmetic of x and r.
+                                Threshold tests and all reductions are FP64 in both. */
+    int32_t deterministic;   /* 1: scatter by sort + segmented reduce (bitwise reproducible);
+                                0 (default): atomic scatter */
+    int32_t topk;            /* 0 (default): dense output; k > 0: the k largest x per seed */
+    int32_t hk_threshold;    /* HK only.  0 (default): theta_t = e^tau/((N+1) psi_t(tau)) with
+                                psi_t = sum_{j<=N-t} tau^j t!/(t+j)!, which bounds
+                                0 <= f_N - e^-tau x <= eps d_u; 1: theta_t = 1 */
+    int32_t batched;         /* 1: all seeds in one persistent launch with per-seed hash
+                                accumulators (PPR/Katz, FP32, topk > 0); 0 (default): one
+                                seed at a time with dense x and r */
+    uint32_t flags;          /* GDE_DEVICE_PTRS: seeds and outputs are device pointers */
+    int64_t max_rounds;      /* round cap; 0 (default) means 1,000,000 */
+    int64_t mem_budget_bytes;/* batched: bytes for the hash accumulators; 0 = automatic */
+    double hk_tol;           /* HK Taylor tail tolerance; 0 (default) means 1e-12 */
+    void *cuda_stream;       /* borrowed cudaStream_t to run on; NULL = the graph's stream */
+} gde_solve_opts;
+
+/* Per-seed result statistics (Definition 3.1 and Theorem 3.5). */
+typedef struct {
+    int64_t rounds;          /* T: number of rounds with a non-empty S_t */
+    int64_t active_volume;   /* sum_t vol(S_t): the operation count of the paper */
+    int64_t pushes;          /* sum_t |S_t| */
+    double resid_l1;         /* ||r^(T)||_1 (HK: summed over all Taylor layers) */
+    double mass_l1;          /* ||x^(T)||_1 before any output scaling */
+    int32_t status;          /* gde_status of this seed */
+    int32_t reserved;
+} gde_stats;
+
+void gde_solve_opts_init(gde_solve_opts *opts);
+
+/*
+ * Upload an undirected simple graph in CSR form and keep it resident in HBM.
+ *   n        number of nodes (0 <= n < 2^31)
+ *   offsets  n+1 int64 row offsets, offsets[0] = 0, non-decreasing
+ *   cols     offsets[n] int32 column ids, each row strictly increasing, in [0, n),
+ *            without self-loops (the paper assumes P_uu = 0)
+ *   flags    GDE_DEVICE_PTRS, GDE_CHECK_SYMMETRIC
+ * The arrays are copied and validated on the device; a violation returns
+ * GDE_EINVAL.  *out receives the handle, to be released with gde_graph_destroy.
+ */
+gde_status gde_graph_create(int64_t n, const int64_t *offsets, const int32_t *cols,
+                            uint32_t flags, gde_graph **out);
+
+gde_status gde_graph_destroy(gde_graph *g);
+
+/* n, number of CSR entries and maximum degree of a graph (any pointer may be NULL). */
+gde_status gde_graph_info(const gde_graph *g, int64_t *n, int64_t *nnz, int32_t *max_degree);
+
+/*
+ * Approximate diffusion vectors for nseeds independent unit sources.
+ *   kind, param  GDE_PPR with alpha in (0,1); GDE_KATZ with beta > 0 (LocalGD terminates
+ *                when beta lambda_max(A) < 1); GDE_HK with tau > 0
+ *   eps          tolerance > 0 of the active-set test
+ *   seeds        nseeds source node ids in [0, n)
+ *   out_x        topk == 0: nseeds x n values, row-major (double for GDE_FP64, float for
+ *                GDE_FP32): x for PPR, x = (I - beta A)^-1 e_s approximately for Katz,
+ *                e^-tau x (the heat-kernel vector) for HK.
+ *                topk == k: nseeds x k values, largest first (ties: lower id first), and
+ *                out_ids receives the matching nseeds x k node ids (-1 pads seeds whose
+ *                support is smaller than k)
+ *   stats        NULL or nseeds gde_stats
+ * Returns GDE_ENOTCONV if some seed hit max_rounds (its output is still written).
+ */
+gde_status gde_solve(gde_graph *g, gde_kind kind, double param, double eps,
+                     const int32_t *seeds, int32_t nseeds, const gde_solve_opts *opts,
+                     void *out_x, int32_t *out_ids, gde_stats *stats);
+
+/*
+ * Kernel timing, for benchmarks.  While enabled on a graph, every solve on it records CUDA
+ * events on its stream around the round kernels; gde_profile_read synchronises, sums the
+ * elapsed times and the work counters since the last gde_profile_enable, and resets nothing.
+ */
+typedef struct {
+    double batch_rounds_ms;      /* persistent batched round kernel (frontier + scatter) */
+    double batch_clear_ms;       /* batched: accumulator pool reset */
+    double batch_topk_ms;        /* batched: per-seed top-k */
+    double dense_frontier_ms;    /* single-seed frontier kernels */
+    double dense_push_ms;        /* single-seed push/scatter kernels */
+    int64_t batch_launches;      /* persistent launches timed */
+    int64_t dense_rounds;        /* single-seed rounds timed */
+    int64_t edges;               /* sum of vol(S_t) over the timed work */
+    int64_t pushes;              /* sum of |S_t| over the timed work */
+    int64_t inserts;             /* batched: new hash keys */
+    int64_t rounds;              /* batched: rounds of the persistent loop */
+} gde_profile;
+
+gde_status gde_profile_enable(gde_graph *g, int enable);
+gde_status gde_profile_read(gde_graph *g, gde_profile *out);
+
+/* Thread-local description of the last failure of this thread ("" if none). */
+const char *gde_last_error(void);
+
+/*
+ * Stepping interface (one LocalGD round per call), used to compare the device state
+ * with the CPU oracle round by round.  Dense state, one seed, opts->precision honoured.
+ *   gde_session_begin   x = 0, r = e_seed (HK: layer 0)
+ *   gde_session_step    runs round t; *n_active receives |S_t| (0: converged, nothing done)
+ *   gde_session_read    copies x (n values), r (n values: the current residual, for HK the
+ *                       current layer) and S_t of the last step (ascending ids, *n_active
+ *                       entries; active may hold n ints) into host buffers, or device
+ *                       buffers if opts->flags had GDE_DEVICE_PTRS; any pointer may be NULL
+ */
+gde_status gde_session_begin(gde_graph *g, gde_kind kind, double param, double eps, int32_t seed,
+                             const gde_solve_opts *opts, gde_session **out);
+gde_status gde_session_step(gde_session *s, int64_t *n_active);
+gde_status gde_session_read(gde_session *s, void *x, void *r, int32_t *active, int64_t *n_active);
+gde_status gde_session_end(gde_session *s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GDE_H */

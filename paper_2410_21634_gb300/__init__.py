@@ -1,0 +1,278 @@
+"""Python binding of the GB300 local graph-diffusion library (include/gde.h).
+
+Argument marshalling only: every step of the solver runs in the CUDA library
+``_build/libgde.so`` (built by ``_build.build()``).  The binding refuses to work
+when that library is missing — there is no CPU fallback.
+
+Arrays may be numpy arrays (host) or CUDA tensors (device pointers are passed with
+``GDE_DEVICE_PTRS``).  PyTorch is only used, when present, to read a tensor's data
+pointer and current stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+PPR, KATZ, HK = 0, 1, 2
+KINDS = {"ppr": PPR, "katz": KATZ, "hk": HK}
+FP64, FP32 = 0, 1
+DEVICE_PTRS = 0x1
+CHECK_SYMMETRIC = 0x2
+OK, EINVAL, ENOMEM, ECUDA, ENOTCONV, ETIMEOUT = range(6)
+STATUS_NAMES = {0: "GDE_OK", 1: "GDE_EINVAL", 2: "GDE_ENOMEM", 3: "GDE_ECUDA",
+                4: "GDE_ENOTCONV", 5: "GDE_ETIMEOUT"}
+
+EXPORTED = ["gde_solve_opts_init", "gde_graph_create", "gde_graph_destroy", "gde_graph_info",
+            "gde_solve", "gde_last_error", "gde_session_begin", "gde_session_step",
+            "gde_session_read", "gde_session_end", "gde_profile_enable", "gde_profile_read"]
+
+
+class GdeError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("deterministic", ctypes.c_int32),
+                ("topk", ctypes.c_int32), ("hk_threshold", ctypes.c_int32),
+                ("batched", ctypes.c_int32), ("flags", ctypes.c_uint32),
+                ("max_rounds", ctypes.c_int64), ("mem_budget_bytes", ctypes.c_int64),
+                ("hk_tol", ctypes.c_double), ("cuda_stream", ctypes.c_void_p)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int64), ("active_volume", ctypes.c_int64),
+                ("pushes", ctypes.c_int64), ("resid_l1", ctypes.c_double),
+                ("mass_l1", ctypes.c_double), ("status", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("batch_rounds_ms", ctypes.c_double), ("batch_clear_ms", ctypes.c_double),
+                ("batch_topk_ms", ctypes.c_double), ("dense_frontier_ms", ctypes.c_double),
+                ("dense_push_ms", ctypes.c_double), ("batch_launches", ctypes.c_int64),
+                ("dense_rounds", ctypes.c_int64), ("edges", ctypes.c_int64),
+                ("pushes", ctypes.c_int64), ("inserts", ctypes.c_int64), ("rounds", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load libgde.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or _build.LIB
+    if not os.path.exists(p):
+        raise ImportError(f"CUDA library {p} is missing: run paper_2410_21634_gb300._build.build()")
+    lib = ctypes.CDLL(p)
+    vp, I64, I32, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+    lib.gde_solve_opts_init.argtypes = [ctypes.POINTER(SolveOpts)]
+    lib.gde_solve_opts_init.restype = None
+    lib.gde_graph_create.argtypes = [I64, vp, vp, ctypes.c_uint32, ctypes.POINTER(vp)]
+    lib.gde_graph_destroy.argtypes = [vp]
+    lib.gde_graph_info.argtypes = [vp, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I32)]
+    lib.gde_solve.argtypes = [vp, ctypes.c_int, D, D, vp, I32, ctypes.POINTER(SolveOpts), vp, vp, vp]
+    lib.gde_last_error.argtypes = []
+    lib.gde_last_error.restype = ctypes.c_char_p
+    lib.gde_session_begin.argtypes = [vp, ctypes.c_int, D, D, I32, ctypes.POINTER(SolveOpts),
+                                      ctypes.POINTER(vp)]
+    lib.gde_session_step.argtypes = [vp, ctypes.POINTER(I64)]
+    lib.gde_session_read.argtypes = [vp, vp, vp, vp, ctypes.POINTER(I64)]
+    lib.gde_session_end.argtypes = [vp]
+    lib.gde_profile_enable.argtypes = [vp, ctypes.c_int]
+    lib.gde_profile_read.argtypes = [vp, ctypes.POINTER(Profile)]
+    for name in ("gde_graph_create", "gde_graph_destroy", "gde_graph_info", "gde_solve",
+                 "gde_session_begin", "gde_session_step", "gde_session_read", "gde_session_end",
+                 "gde_profile_enable", "gde_profile_read"):
+        getattr(lib, name).restype = ctypes.c_int
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def last_error() -> str:
+    return load().gde_last_error().decode()
+
+
+def _check(st: int):
+    if st != OK:
+        raise GdeError(st, last_error())
+
+
+def _kind(kind) -> int:
+    return KINDS[kind] if isinstance(kind, str) else int(kind)
+
+
+def _is_cuda_tensor(a) -> bool:
+    return hasattr(a, "is_cuda") and bool(a.is_cuda)
+
+
+def _ptr(a):
+    """(pointer, is_device) of a numpy array or a CUDA tensor (must be contiguous)."""
+    if a is None:
+        return None, False
+    if _is_cuda_tensor(a):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), True
+    if not isinstance(a, np.ndarray) or not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("expected a C-contiguous numpy array or a CUDA tensor")
+    return a.ctypes.data, False
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:
+        pass
+    return None
+
+
+def make_opts(precision=FP64, topk=0, hk_threshold=0, batched=0, deterministic=0, flags=0,
+              max_rounds=0, mem_budget_bytes=0, hk_tol=0.0, stream=None) -> SolveOpts:
+    o = SolveOpts()
+    load().gde_solve_opts_init(ctypes.byref(o))
+    o.precision = FP32 if precision in (FP32, "fp32", "float32") else FP64
+    o.topk, o.hk_threshold, o.batched, o.deterministic = topk, hk_threshold, batched, deterministic
+    o.flags, o.max_rounds, o.mem_budget_bytes, o.hk_tol = flags, max_rounds, mem_budget_bytes, hk_tol
+    o.cuda_stream = stream
+    return o
+
+
+class Graph:
+    """A CSR graph resident in HBM (gde_graph_create / gde_graph_destroy)."""
+
+    def __init__(self, n: int, offsets, cols, check_symmetric: bool = False):
+        lib = load()
+        po, do = _ptr(offsets)
+        pc, dc = _ptr(cols)
+        if do != dc:
+            raise ValueError("offsets and cols must both be host arrays or both CUDA tensors")
+        flags = (DEVICE_PTRS if do else 0) | (CHECK_SYMMETRIC if check_symmetric else 0)
+        h = ctypes.c_void_p()
+        _check(lib.gde_graph_create(int(n), po, pc, flags, ctypes.byref(h)))
+        self._h = h
+        self.n = int(n)
+
+    @classmethod
+    def from_synth(cls, g, **kw):
+        return cls(g.n, np.ascontiguousarray(g.offsets, dtype=np.int64),
+                   np.ascontiguousarray(g.cols, dtype=np.int32), **kw)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self):
+        n, nnz, md = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        _check(load().gde_graph_info(self._h, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(md)))
+        return {"n": n.value, "nnz": nnz.value, "max_degree": md.value}
+
+    def profile_enable(self, enable: bool = True):
+        _check(load().gde_profile_enable(self._h, int(enable)))
+
+    def profile_read(self) -> dict:
+        p = Profile()
+        _check(load().gde_profile_read(self._h, ctypes.byref(p)))
+        return p.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().gde_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def solve(graph: Graph, kind, param: float, eps: float, seeds, out_x, out_ids=None,
+          stats: bool = True, **opt_kw):
+    """gde_solve.  seeds/out_x/out_ids: numpy arrays (host) or CUDA tensors (device).
+    Returns (status, list of per-seed stats dicts)."""
+    lib = load()
+    ps, ds = _ptr(seeds)
+    px, dx = _ptr(out_x)
+    pi, di = _ptr(out_ids)
+    if ds != dx or (out_ids is not None and di != dx):
+        raise ValueError("seeds and outputs must all be host arrays or all CUDA tensors")
+    nseeds = int(seeds.shape[0])
+    flags = opt_kw.pop("flags", 0) | (DEVICE_PTRS if dx else 0)
+    if dx and "stream" not in opt_kw:
+        opt_kw["stream"] = _current_stream()
+    o = make_opts(flags=flags, **opt_kw)
+    st_arr = (Stats * max(nseeds, 1))() if stats else None
+    st = lib.gde_solve(graph.handle, _kind(kind), float(param), float(eps), ps, nseeds,
+                       ctypes.byref(o), px, pi, ctypes.cast(st_arr, ctypes.c_void_p) if stats else None)
+    if st not in (OK, ENOTCONV):
+        _check(st)
+    return st, ([st_arr[i].as_dict() for i in range(nseeds)] if stats else [])
+
+
+class Session:
+    """Stepping interface: one LocalGD round per step() (gde_session_*)."""
+
+    def __init__(self, graph: Graph, kind, param: float, eps: float, seed: int, **opt_kw):
+        lib = load()
+        self.graph = graph
+        self.precision = FP32 if opt_kw.get("precision", FP64) in (FP32, "fp32") else FP64
+        o = make_opts(**opt_kw)
+        h = ctypes.c_void_p()
+        _check(lib.gde_session_begin(graph.handle, _kind(kind), float(param), float(eps), int(seed),
+                                     ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+
+    def step(self) -> int:
+        k = ctypes.c_int64()
+        _check(load().gde_session_step(self._h, ctypes.byref(k)))
+        return k.value
+
+    def read(self):
+        """(x, r, active S_t of the last step (unordered)) as host numpy arrays."""
+        n = self.graph.n
+        dt = np.float64 if self.precision == FP64 else np.float32
+        x = np.empty(n, dtype=dt)
+        r = np.empty(n, dtype=dt)
+        act = np.empty(max(n, 1), dtype=np.int32)
+        k = ctypes.c_int64()
+        _check(load().gde_session_read(self._h, x.ctypes.data, r.ctypes.data, act.ctypes.data,
+                                       ctypes.byref(k)))
+        return x, r, act[:k.value].copy()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().gde_session_end(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

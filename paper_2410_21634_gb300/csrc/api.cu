@@ -1,0 +1,448 @@
+// C ABI entry points (include/gde.h): argument checks, graph store lifetime, the
+// single-seed solve loop and the stepping interface.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace gde {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+void clear_error() { g_last_error.clear(); }
+
+void *dmalloc(size_t bytes, const char *what) {
+    void *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();  // clear the sticky-free allocation error
+        char buf[256];
+        snprintf(buf, sizeof(buf), "cudaMalloc(%zu bytes) for %s failed: %s", bytes, what,
+                 cudaGetErrorString(e));
+        set_error(buf);
+        throw Fail{e == cudaErrorMemoryAllocation ? GDE_ENOMEM : GDE_ECUDA};
+    }
+    return p;
+}
+
+void dfree(void *p) {
+    if (p) cudaFree(p);
+}
+
+// -------------------------------------------------------------- profiler --
+
+int Profiler::start(int kind, cudaStream_t s) {
+    if (!enabled) return -1;
+    cudaEvent_t a, b;
+    GDE_CUDA(cudaEventCreate(&a));
+    GDE_CUDA(cudaEventCreate(&b));
+    GDE_CUDA(cudaEventRecord(a, s));
+    marks.push_back({kind, {a, b}});
+    return (int)marks.size() - 1;
+}
+
+void Profiler::stop(int idx, cudaStream_t s) {
+    if (idx < 0) return;
+    GDE_CUDA(cudaEventRecord(marks[(size_t)idx].second.second, s));
+}
+
+void Profiler::reset() {
+    for (auto &m : marks) {
+        cudaEventDestroy(m.second.first);
+        cudaEventDestroy(m.second.second);
+    }
+    marks.clear();
+    counters = gde_profile{};
+}
+
+void Profiler::read(gde_profile *out) {
+    gde_profile p = counters;
+    for (auto &m : marks) {
+        GDE_CUDA(cudaEventSynchronize(m.second.second));
+        float ms = 0.0f;
+        GDE_CUDA(cudaEventElapsedTime(&ms, m.second.first, m.second.second));
+        switch (m.first) {
+            case kProfBatchRounds: p.batch_rounds_ms += ms; break;
+            case kProfBatchClear: p.batch_clear_ms += ms; break;
+            case kProfBatchTopk: p.batch_topk_ms += ms; break;
+            case kProfDenseFrontier: p.dense_frontier_ms += ms; break;
+            case kProfDensePush: p.dense_push_ms += ms; break;
+            default: break;
+        }
+    }
+    *out = p;
+}
+
+// ----------------------------------------------------------- heat kernel --
+
+// Smallest N with e^-tau sum_{k>N} tau^k/k! <= tol: the Poisson(tau) tail, summed from its
+// small end (terms p_k = e^-tau tau^k/k! by the ratio p_{k+1} = p_k tau/(k+1)).
+int64_t hk_terms(double tau, double tol) {
+    const int64_t kmax = (int64_t)(10.0 * tau) + 200;
+    std::vector<double> p((size_t)kmax + 2);
+    p[0] = std::exp(-tau);
+    for (int64_t k = 0; k < kmax; k++) p[k + 1] = p[k] * tau / (double)(k + 1);
+    double tail = 0.0;
+    int64_t best = kmax;
+    for (int64_t N = kmax - 1; N >= 0; N--) {
+        tail += p[N + 1];
+        if (tail <= tol) best = N; else break;
+    }
+    return best;
+}
+
+// theta_t = e^tau / ((N+1) psi_t(tau)), psi_t = sum_{j=0}^{N-t} tau^j t!/(t+j)!  (mode 0);
+// 1 (mode 1).  Weighting each layer's leftover residual by psi_t and splitting eps evenly over
+// the N+1 layers bounds the error of e^-tau x by eps d_u.
+double hk_theta(double tau, int64_t N, int64_t t, int mode) {
+    if (mode == 1) return 1.0;
+    double psi = 0.0, term = 1.0;
+    for (int64_t j = 0; j <= N - t; j++) {
+        if (j > 0) term = term * (tau / (double)(t + j));
+        psi += term;
+    }
+    return std::exp(tau) / ((double)(N + 1) * psi);
+}
+
+static SolveParams make_params(Graph &g, gde_kind kind, double param, double eps,
+                               const gde_solve_opts &o) {
+    GDE_REQUIRE(kind == GDE_PPR || kind == GDE_KATZ || kind == GDE_HK, GDE_EINVAL, "unknown kind");
+    GDE_REQUIRE(std::isfinite(param) && std::isfinite(eps), GDE_EINVAL, "param and eps must be finite");
+    GDE_REQUIRE(eps > 0.0, GDE_EINVAL, "eps must be > 0");
+    if (kind == GDE_PPR) GDE_REQUIRE(param > 0.0 && param < 1.0, GDE_EINVAL, "PPR alpha must be in (0,1)");
+    if (kind == GDE_KATZ) GDE_REQUIRE(param > 0.0, GDE_EINVAL, "Katz beta must be > 0");
+    if (kind == GDE_HK) GDE_REQUIRE(param > 0.0 && param < 700.0, GDE_EINVAL, "HK tau must be in (0,700)");
+    GDE_REQUIRE(o.precision == GDE_FP64 || o.precision == GDE_FP32, GDE_EINVAL, "bad precision");
+    GDE_REQUIRE(o.hk_threshold == 0 || o.hk_threshold == 1, GDE_EINVAL, "bad hk_threshold");
+    GDE_REQUIRE(o.max_rounds >= 0, GDE_EINVAL, "max_rounds must be >= 0");
+    GDE_REQUIRE(o.topk >= 0, GDE_EINVAL, "topk must be >= 0");
+    GDE_REQUIRE(o.hk_tol >= 0.0 && o.hk_tol < 1.0, GDE_EINVAL, "hk_tol must be in [0,1)");
+    SolveParams p{};
+    p.kind = kind;
+    p.param = param;
+    p.eps = eps;
+    p.precision = o.precision;
+    p.hk_mode = o.hk_threshold;
+    p.hk_tol = o.hk_tol > 0.0 ? o.hk_tol : 1e-12;
+    p.max_rounds = o.max_rounds > 0 ? o.max_rounds : 1000000;
+    p.hk_N = kind == GDE_HK ? hk_terms(param, p.hk_tol) : 0;
+    p.stream = o.cuda_stream ? (cudaStream_t)o.cuda_stream : g.stream;
+    return p;
+}
+
+static DenseWork *dense_for(Graph &g, int precision) {
+    int k = precision == GDE_FP64 ? 0 : 1;
+    if (!g.dense[k]) g.dense[k] = dense_work_create(g, precision);
+    return g.dense[k];
+}
+
+}  // namespace gde
+
+using namespace gde;
+
+struct gde_session {
+    gde_graph *graph = nullptr;
+    SolveParams p{};
+    DenseWork *w = nullptr;
+    uint32_t flags = 0;
+};
+
+#define API_BEGIN try { clear_error();
+#define API_END                                                                 \
+    }                                                                           \
+    catch (const Fail &f) { return f.st; }                                      \
+    catch (const std::bad_alloc &) { set_error("host allocation failed"); return GDE_ENOMEM; } \
+    catch (...) { set_error("unexpected C++ exception"); return GDE_ECUDA; }    \
+    return GDE_OK;
+
+extern "C" {
+
+void gde_solve_opts_init(gde_solve_opts *o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->precision = GDE_FP64;
+}
+
+const char *gde_last_error(void) { return g_last_error.c_str(); }
+
+gde_status gde_graph_create(int64_t n, const int64_t *offsets, const int32_t *cols, uint32_t flags,
+                            gde_graph **out) {
+    API_BEGIN
+    GDE_REQUIRE(out != nullptr, GDE_EINVAL, "out is NULL");
+    *out = nullptr;
+    GDE_REQUIRE(n >= 0 && n < ((int64_t)1 << 31), GDE_EINVAL, "n must be in [0, 2^31)");
+    GDE_REQUIRE(offsets != nullptr, GDE_EINVAL, "offsets is NULL");
+    const bool dev = (flags & GDE_DEVICE_PTRS) != 0;
+    int64_t nnz = 0;
+    if (dev) {
+        GDE_CUDA(cudaMemcpy(&nnz, offsets + n, sizeof(int64_t), cudaMemcpyDeviceToHost));
+    } else {
+        nnz = offsets[n];
+    }
+    GDE_REQUIRE(nnz >= 0 && nnz < ((int64_t)1 << 40), GDE_EINVAL, "offsets[n] out of range");
+    GDE_REQUIRE(nnz == 0 || cols != nullptr, GDE_EINVAL, "cols is NULL");
+    gde_graph *h = new gde_graph();
+    Graph &g = h->g;
+    try {
+        g.n = n;
+        g.nnz = nnz;
+        GDE_CUDA(cudaGetDevice(&g.device));
+        GDE_CUDA(cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking));
+        g.off = (int64_t *)dmalloc(sizeof(int64_t) * (size_t)(n + 1), "CSR offsets");
+        g.col = (int32_t *)dmalloc(sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1), "CSR columns");
+        g.deg = (int32_t *)dmalloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1), "degrees");
+        const cudaMemcpyKind k = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        GDE_CUDA(cudaMemcpyAsync(g.off, offsets, sizeof(int64_t) * (size_t)(n + 1), k, g.stream));
+        if (nnz > 0)
+            GDE_CUDA(cudaMemcpyAsync(g.col, cols, sizeof(int32_t) * (size_t)nnz, k, g.stream));
+        unsigned bits = 0;
+        graph_validate(g, (flags & GDE_CHECK_SYMMETRIC) != 0, &bits);
+        if (bits) {
+            std::string m = "invalid CSR:";
+            if (bits & kBadOffsets) m += " offsets not monotone or not starting at 0;";
+            if (bits & kBadColRange) m += " column id out of range;";
+            if (bits & kUnsorted) m += " row not strictly increasing (unsorted or duplicate);";
+            if (bits & kSelfLoop) m += " self-loop;";
+            if (bits & kAsymmetric) m += " not symmetric;";
+            set_error(m);
+            throw Fail{GDE_EINVAL};
+        }
+    } catch (...) {
+        gde_graph_destroy(h);
+        throw;
+    }
+    *out = h;
+    API_END
+}
+
+gde_status gde_graph_destroy(gde_graph *h) {
+    if (!h) return GDE_OK;
+    Graph &g = h->g;
+    if (g.stream) cudaStreamSynchronize(g.stream);
+    for (int k = 0; k < 2; k++) dense_work_destroy(g.dense[k]);
+    batch_work_destroy(g.batch);
+    g.prof.reset();
+    dfree(g.off);
+    dfree(g.col);
+    dfree(g.deg);
+    if (g.stream) cudaStreamDestroy(g.stream);
+    delete h;
+    return GDE_OK;
+}
+
+gde_status gde_graph_info(const gde_graph *h, int64_t *n, int64_t *nnz, int32_t *max_degree) {
+    API_BEGIN
+    GDE_REQUIRE(h != nullptr, GDE_EINVAL, "graph is NULL");
+    if (n) *n = h->g.n;
+    if (nnz) *nnz = h->g.nnz;
+    if (max_degree) *max_degree = h->g.max_degree;
+    API_END
+}
+
+gde_status gde_solve(gde_graph *h, gde_kind kind, double param, double eps, const int32_t *seeds,
+                     int32_t nseeds, const gde_solve_opts *opts, void *out_x, int32_t *out_ids,
+                     gde_stats *stats) {
+    API_BEGIN
+    GDE_REQUIRE(h != nullptr, GDE_EINVAL, "graph is NULL");
+    gde_solve_opts o;
+    gde_solve_opts_init(&o);
+    if (opts) o = *opts;
+    Graph &g = h->g;
+    std::lock_guard<std::mutex> lock(g.mu);
+    SolveParams p = make_params(g, kind, param, eps, o);
+    GDE_REQUIRE(nseeds >= 0, GDE_EINVAL, "nseeds must be >= 0");
+    if (nseeds == 0) return GDE_OK;
+    GDE_REQUIRE(seeds != nullptr && out_x != nullptr, GDE_EINVAL, "seeds or out_x is NULL");
+    GDE_REQUIRE(o.topk == 0 || out_ids != nullptr, GDE_EINVAL, "topk output needs out_ids");
+    GDE_REQUIRE(o.topk <= 64, GDE_EINVAL, "topk must be <= 64");
+    GDE_REQUIRE(o.topk == 0 || o.precision == GDE_FP32, GDE_EINVAL, "topk output is FP32");
+    GDE_REQUIRE(o.batched == 0 || o.batched == 1, GDE_EINVAL, "bad batched flag");
+    GDE_REQUIRE(o.deterministic == 0, GDE_EINVAL, "deterministic mode is not available in this build");
+    const bool dev = (o.flags & GDE_DEVICE_PTRS) != 0;
+    std::vector<int32_t> hs((size_t)nseeds);
+    if (dev) {
+        GDE_CUDA(cudaMemcpyAsync(hs.data(), seeds, sizeof(int32_t) * (size_t)nseeds,
+                                 cudaMemcpyDeviceToHost, p.stream));
+        GDE_CUDA(cudaStreamSynchronize(p.stream));
+    } else {
+        memcpy(hs.data(), seeds, sizeof(int32_t) * (size_t)nseeds);
+    }
+    for (int32_t i = 0; i < nseeds; i++)
+        GDE_REQUIRE(hs[i] >= 0 && hs[i] < g.n, GDE_EINVAL, "seed id out of range");
+
+    const size_t rsz = p.precision == GDE_FP64 ? 8 : 4;
+    const int k = o.topk;
+    // device views of the outputs (staging buffers for host pointers)
+    std::vector<void *> owned;
+    auto stage = [&](size_t bytes, const char *what) {
+        void *q = dmalloc(bytes, what);
+        owned.push_back(q);
+        return q;
+    };
+    gde_status worst = GDE_OK;
+    try {
+        std::vector<gde_stats> st((size_t)nseeds);
+        std::vector<int32_t> todo;  // seeds solved one at a time with dense x and r
+        int32_t *ids_dev = nullptr;
+        float *vals_dev = nullptr;
+        if (k > 0) {
+            ids_dev = dev ? out_ids : (int32_t *)stage(4 * (size_t)nseeds * k, "top-k ids");
+            vals_dev = dev ? (float *)out_x : (float *)stage(4 * (size_t)nseeds * k, "top-k values");
+        }
+        if (o.batched) {
+            GDE_REQUIRE(k > 0, GDE_EINVAL, "batched mode returns top-k lists: set topk");
+            const int32_t *seeds_dev = seeds;
+            if (!dev) {
+                int32_t *sd = (int32_t *)stage(4 * (size_t)nseeds, "seeds");
+                GDE_CUDA(cudaMemcpyAsync(sd, hs.data(), 4 * (size_t)nseeds, cudaMemcpyHostToDevice, p.stream));
+                seeds_dev = sd;
+            }
+            std::vector<int32_t> of((size_t)nseeds);
+            int32_t nof = 0;
+            batch_solve(g, p, seeds_dev, nseeds, k, o.mem_budget_bytes, ids_dev, vals_dev, st.data(),
+                        of.data(), &nof);
+            for (int32_t i = 0; i < nof; i++) todo.push_back(of[i]);
+        } else {
+            for (int32_t i = 0; i < nseeds; i++) todo.push_back(i);
+        }
+        if (!todo.empty()) {
+            DenseWork *w = dense_for(g, p.precision);
+            void *vec = nullptr;
+            if (k > 0 || !dev) vec = stage(rsz * (size_t)(g.n > 0 ? g.n : 1), "output staging");
+            for (int32_t i : todo) {
+                dense_begin(g, w, p, hs[i]);
+                gde_stats one{};
+                double rl1 = 1.0, xl1 = 0.0;
+                int64_t rounds = 0;
+                bool converged = false;
+                while (rounds < p.max_rounds) {
+                    RoundInfo ri;
+                    int64_t na = dense_round(g, w, p, &ri);
+                    if (na == 0) { converged = true; break; }
+                    rounds++;
+                    one.active_volume += ri.vol;
+                    one.pushes += ri.n_active;
+                    xl1 += (kind == GDE_PPR ? param : 1.0) * ri.rS_l1;
+                    rl1 = rl1 - ri.rS_l1 + ri.scat;
+                }
+                if (!converged && !dense_pending(w)) converged = true;
+                one.rounds = rounds;
+                one.resid_l1 = rl1;
+                one.mass_l1 = xl1;
+                one.status = converged ? GDE_OK : GDE_ENOTCONV;
+                void *dst = vec ? vec : (char *)out_x + rsz * (size_t)g.n * i;
+                dense_output(g, w, p, dst);
+                if (k > 0) {
+                    topk_dense_f32((const float *)vec, g.n, k, ids_dev + (size_t)i * k,
+                                   vals_dev + (size_t)i * k, p.stream);
+                } else if (!dev && g.n > 0) {
+                    GDE_CUDA(cudaMemcpyAsync((char *)out_x + rsz * (size_t)g.n * i, vec, rsz * (size_t)g.n,
+                                             cudaMemcpyDeviceToHost, p.stream));
+                }
+                GDE_CUDA(cudaStreamSynchronize(p.stream));
+                st[(size_t)i] = one;
+            }
+        }
+        if (k > 0 && !dev) {
+            GDE_CUDA(cudaMemcpyAsync(out_ids, ids_dev, 4 * (size_t)nseeds * k, cudaMemcpyDeviceToHost, p.stream));
+            GDE_CUDA(cudaMemcpyAsync(out_x, vals_dev, 4 * (size_t)nseeds * k, cudaMemcpyDeviceToHost, p.stream));
+        }
+        GDE_CUDA(cudaStreamSynchronize(p.stream));
+        for (int32_t i = 0; i < nseeds; i++) {
+            if (st[(size_t)i].status != GDE_OK) worst = (gde_status)st[(size_t)i].status;
+            if (stats) stats[i] = st[(size_t)i];
+        }
+    } catch (...) {
+        for (void *q : owned) dfree(q);
+        throw;
+    }
+    for (void *q : owned) dfree(q);
+    if (worst != GDE_OK) {
+        set_error("round cap reached before the active set became empty");
+        return worst;
+    }
+    API_END
+}
+
+gde_status gde_profile_enable(gde_graph *h, int enable) {
+    API_BEGIN
+    GDE_REQUIRE(h != nullptr, GDE_EINVAL, "graph is NULL");
+    Graph &g = h->g;
+    std::lock_guard<std::mutex> lock(g.mu);
+    g.prof.reset();
+    g.prof.enabled = enable != 0;
+    API_END
+}
+
+gde_status gde_profile_read(gde_graph *h, gde_profile *out) {
+    API_BEGIN
+    GDE_REQUIRE(h != nullptr && out != nullptr, GDE_EINVAL, "graph or out is NULL");
+    Graph &g = h->g;
+    std::lock_guard<std::mutex> lock(g.mu);
+    g.prof.read(out);
+    API_END
+}
+
+gde_status gde_session_begin(gde_graph *h, gde_kind kind, double param, double eps, int32_t seed,
+                             const gde_solve_opts *opts, gde_session **out) {
+    API_BEGIN
+    GDE_REQUIRE(h != nullptr && out != nullptr, GDE_EINVAL, "graph or out is NULL");
+    *out = nullptr;
+    gde_solve_opts o;
+    gde_solve_opts_init(&o);
+    if (opts) o = *opts;
+    Graph &g = h->g;
+    std::lock_guard<std::mutex> lock(g.mu);
+    GDE_REQUIRE(seed >= 0 && seed < g.n, GDE_EINVAL, "seed id out of range");
+    gde_session *s = new gde_session();
+    try {
+        s->graph = h;
+        s->p = make_params(g, kind, param, eps, o);
+        s->flags = o.flags;
+        s->w = dense_work_create(g, s->p.precision);
+        dense_begin(g, s->w, s->p, seed);
+        GDE_CUDA(cudaStreamSynchronize(s->p.stream));
+    } catch (...) {
+        dense_work_destroy(s->w);
+        delete s;
+        throw;
+    }
+    *out = s;
+    API_END
+}
+
+gde_status gde_session_step(gde_session *s, int64_t *n_active) {
+    API_BEGIN
+    GDE_REQUIRE(s != nullptr, GDE_EINVAL, "session is NULL");
+    Graph &g = s->graph->g;
+    std::lock_guard<std::mutex> lock(g.mu);
+    int64_t k = dense_round(g, s->w, s->p, nullptr);
+    if (n_active) *n_active = k;
+    API_END
+}
+
+gde_status gde_session_read(gde_session *s, void *x, void *r, int32_t *active, int64_t *n_active) {
+    API_BEGIN
+    GDE_REQUIRE(s != nullptr, GDE_EINVAL, "session is NULL");
+    Graph &g = s->graph->g;
+    std::lock_guard<std::mutex> lock(g.mu);
+    dense_read(g, s->w, s->p, x, r, active, n_active, (s->flags & GDE_DEVICE_PTRS) != 0);
+    API_END
+}
+
+gde_status gde_session_end(gde_session *s) {
+    if (!s) return GDE_OK;
+    if (s->w) {
+        cudaStreamSynchronize(s->p.stream);
+        dense_work_destroy(s->w);
+    }
+    delete s;
+    return GDE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,889 @@
+// Batched LocalGD: many independent unit sources in one persistent launch (Eq. local-gd,
+// Section 3.3, run for every seed at once), FP32 x and r in per-seed open-addressed hash
+// tables in HBM, top-k output per seed.
+//
+// Layout (pool of P = nseeds * cap slots, cap a power of two):
+//   kr[slot]  64-bit word {low: node id (0xFFFFFFFF = empty), high: r as float bits}; key and
+//             residual share one 8-byte word, so a probe and the atomic add on r touch the
+//             same 32-byte sector (4 slots per sector)
+//   xs[slot]  float x of that node
+// seed j owns slots [j*cap, (j+1)*cap); a slot index therefore names its seed (slot >> log2cap).
+// thr32[v] = fl(eps d_v) rounded up to float (one array shared by all seeds).
+//
+// Rounds run inside one cooperative kernel: phase A builds S_t for every seed from the
+// candidate list (slots whose residual crossed its threshold in the previous round), zeroes
+// r on S_t, adds to x and bins the pushes by degree into lists pooled over all seeds; a grid
+// barrier; phase B scatters every push into its seed's table (insert-or-add) and appends
+// threshold crossings to the next candidate list; a grid barrier.  Every grid-barrier wait
+// is bounded by a time limit after which the kernel records GDE_ETIMEOUT and returns.
+#include <cooperative_groups.h>
+#include <cooperative_groups/scan.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace gde {
+
+constexpr uint32_t kEmpty = 0xFFFFFFFFu;
+constexpr int kTopMax = 64;
+constexpr int kBHubVolBits = 40;
+constexpr unsigned long long kBHubVolMask = (1ull << kBHubVolBits) - 1;
+constexpr unsigned long long kBarrierLimitNs = 20ull * 1000 * 1000 * 1000;  // 20 s
+
+enum : int { kSeedOk = 0, kSeedOverflow = 1 };
+
+struct BCtl {  // per-round counters (one set per round parity)
+    unsigned long long hub_packed;
+    unsigned int cnt_small;
+    unsigned int cnt_med;
+    unsigned int cand_out;
+    unsigned int n_active;
+    unsigned long long vol;
+    double rS_l1;
+    unsigned int overflow;
+    unsigned int pad;
+};
+
+struct BGlobal {
+    BCtl ctl[2];
+    unsigned int bar_count;
+    unsigned int bar_gen;
+    unsigned int error;       // 0, or a gde_status
+    unsigned int rounds;      // rounds executed
+    unsigned long long total_vol;
+    unsigned long long total_pushes;
+};
+
+struct RoundLog {
+    unsigned long long n_active;
+    unsigned long long vol;
+    double rS_l1;
+    unsigned long long ncand;
+};
+
+constexpr int kLogCap = 4096;
+
+struct BatchWork {
+    int64_t nseeds_cap = 0;
+    int64_t cap = 0;        // slots per seed
+    int log2cap = 0;
+    int64_t pool = 0;       // nseeds_cap * cap
+    int64_t list_cap = 0;   // candidate / bin capacity
+    unsigned long long *kr = nullptr;
+    float *xs = nullptr;
+    float *thr32 = nullptr;
+    int64_t thr_n = 0;
+    double thr_eps = -1.0;
+    uint32_t *cand[2] = {nullptr, nullptr};
+    int64_t *b_beg[3] = {nullptr, nullptr, nullptr};
+    int32_t *b_deg[3] = {nullptr, nullptr, nullptr};
+    float *b_w[3] = {nullptr, nullptr, nullptr};
+    int32_t *b_seed[3] = {nullptr, nullptr, nullptr};
+    int64_t *hub_vstart = nullptr;
+    int32_t *seeds = nullptr;        // device copy of the seed ids
+    int32_t *status = nullptr;       // per seed
+    unsigned *inserts = nullptr;     // per seed
+    unsigned long long *svol = nullptr;  // per seed
+    unsigned *spushes = nullptr;     // per seed
+    int32_t *slast = nullptr;        // per seed: last round with a push
+    double *sresid = nullptr;        // per seed
+    double *smass = nullptr;         // per seed
+    BGlobal *glob = nullptr;
+    RoundLog *log = nullptr;
+    int grid = 0;
+};
+
+// ------------------------------------------------------------- device bits --
+
+__device__ __forceinline__ uint32_t mix32(uint32_t v) {
+    // murmur3 finaliser
+    v ^= v >> 16;
+    v *= 0x85EBCA6Bu;
+    v ^= v >> 13;
+    v *= 0xC2B2AE35u;
+    v ^= v >> 16;
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ float *r_of(unsigned long long *kr, uint64_t slot) {
+    return reinterpret_cast<float *>(kr + slot) + 1;
+}
+
+// Grid-wide barrier for a cooperative launch (all blocks co-resident).  Returns false if the
+// wait exceeded the time limit or another block recorded an error; the caller then returns.
+__device__ bool grid_sync(BGlobal *g, unsigned nblocks) {
+    __syncthreads();
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned gen = ld_acquire_u32(&g->bar_gen);
+        __threadfence();
+        const unsigned arrived = atomicAdd(&g->bar_count, 1u);
+        if (arrived == nblocks - 1) {
+            atomicExch(&g->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&g->bar_gen, 1u);
+        } else {
+            const unsigned long long t0 = globaltimer();
+            while (ld_acquire_u32(&g->bar_gen) == gen) {
+                if (ld_acquire_u32(&g->error) != 0) { ok = 0; break; }
+                if (globaltimer() - t0 > kBarrierLimitNs) {
+                    atomicCAS(&g->error, 0u, (unsigned)GDE_ETIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        if (ld_acquire_u32(&g->error) != 0) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <typename T> __device__ __forceinline__ T bwarp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+struct BArgs {
+    const int64_t *off;
+    const int32_t *col;
+    const float *thr32;
+    unsigned long long *kr;
+    float *xs;
+    int log2cap;
+    uint32_t mask;
+    int32_t nseeds;
+    int32_t *status;
+    unsigned *inserts;
+    unsigned load_limit;
+    unsigned long long *svol;
+    unsigned *spushes;
+    int32_t *slast;
+    uint32_t *cand[2];
+    unsigned list_cap;
+    int64_t *b_beg[3];
+    int32_t *b_deg[3];
+    float *b_w[3];
+    int32_t *b_seed[3];
+    int64_t *hub_vstart;
+    BGlobal *glob;
+    RoundLog *log;
+    int kind;
+    double cx;    // x += cx * rho
+    double coef;  // PPR 1-alpha (share divided by d_u), Katz beta
+    int64_t max_rounds;
+    int32_t t1, t2, chunk;
+};
+
+__device__ __forceinline__ void bappend(unsigned *counter, uint32_t *list, uint32_t v, unsigned cap,
+                                        unsigned *overflow) {
+    cg::coalesced_group g = cg::coalesced_threads();
+    unsigned base = 0;
+    if (g.thread_rank() == 0) base = atomicAdd(counter, (unsigned)g.size());
+    const unsigned i = g.shfl(base, 0) + g.thread_rank();
+    if (i < cap) list[i] = v; else atomicOr(overflow, 1u);
+}
+
+// insert-or-add w into seed j's table at node v; appends the slot to the next candidate list
+// when the residual crosses fl(eps d_v)
+__device__ __forceinline__ void bscatter(const BArgs &a, BCtl *ctl, uint32_t *cand_out, int32_t j,
+                                         int32_t v, float w) {
+    const uint64_t base = (uint64_t)j << a.log2cap;
+    uint32_t h = mix32((uint32_t)v) & a.mask;
+    const float thr = a.thr32[v];
+    for (uint32_t probe = 0; probe <= a.mask; probe++) {
+        const uint64_t slot = base + h;
+        unsigned long long word = ld_relaxed_u64(a.kr + slot);
+        for (;;) {
+            const uint32_t key = (uint32_t)(word & 0xFFFFFFFFull);
+            if (key == (uint32_t)v) {
+                const float old = atomicAdd(r_of(a.kr, slot), w);
+                const float nv = __fadd_rn(old, w);
+                if (old < thr && nv >= thr) bappend(&ctl->cand_out, cand_out, (uint32_t)slot, a.list_cap, &ctl->overflow);
+                return;
+            }
+            if (key != kEmpty) break;  // another node: keep probing
+            const unsigned long long want =
+                ((unsigned long long)__float_as_uint(w) << 32) | (unsigned long long)(uint32_t)v;
+            const unsigned long long prev = atomicCAS(a.kr + slot, word, want);
+            if (prev == word) {
+                // new key with residual w (old value 0)
+                if (w >= thr) bappend(&ctl->cand_out, cand_out, (uint32_t)slot, a.list_cap, &ctl->overflow);
+                // count inserts per seed: one atomic per group of lanes with the same seed
+                const unsigned peers = __match_any_sync(__activemask(), j);
+                if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) {
+                    const unsigned c = atomicAdd(a.inserts + j, (unsigned)__popc(peers));
+                    if (c + (unsigned)__popc(peers) > a.load_limit) atomicExch(a.status + j, kSeedOverflow);
+                }
+                return;
+            }
+            word = prev;  // lost the race: look at what was written
+        }
+        h = (h + 1) & a.mask;
+    }
+    atomicExch(a.status + j, kSeedOverflow);  // table full
+}
+
+__global__ void __launch_bounds__(kThreads) k_batch_rounds(BArgs a) {
+    const unsigned nblocks = gridDim.x;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t gw = tid >> 5, nw = nthreads >> 5;
+    BGlobal *G = a.glob;
+    __shared__ double s_rs[kWarps];
+    __shared__ unsigned long long s_vol[kWarps];
+
+    for (int64_t t = 0; t < a.max_rounds; t++) {
+        const int p = (int)(t & 1);
+        BCtl *ctl = &G->ctl[p];
+        BCtl *prev = &G->ctl[p ^ 1];
+        const unsigned ncand = min(__ldcg(&prev->cand_out), a.list_cap);
+        const uint32_t *cand = a.cand[p];
+
+        // ---------------- phase A: S_t for every seed ----------------
+        double my_rs = 0.0;
+        unsigned long long my_vol = 0;
+        for (int64_t ci = tid; ci < ncand; ci += nthreads) {
+            const uint32_t slot = __ldcg(cand + ci);
+            const int32_t j = (int32_t)(slot >> a.log2cap);
+            if (__ldcg(a.status + j) != kSeedOk) continue;
+            const unsigned long long word = __ldcg(a.kr + slot);
+            const int32_t v = (int32_t)(word & 0xFFFFFFFFull);
+            const float rho = __uint_as_float((uint32_t)(word >> 32));
+            const float thr = a.thr32[v];
+            if (!(rho != 0.0f && fabsf(rho) >= thr)) continue;
+            __stcg(r_of(a.kr, slot), 0.0f);
+            const double rho64 = (double)rho;
+            const float xold = __ldcg(a.xs + slot);
+            if (a.kind == GDE_PPR)
+                __stcg(a.xs + slot, __fadd_rn(xold, __double2float_rn(__dmul_rn(a.cx, rho64))));
+            else
+                __stcg(a.xs + slot, __fadd_rn(xold, rho));
+            const int64_t beg = a.off[v];
+            const int32_t d = (int32_t)(a.off[v + 1] - beg);
+            my_rs += fabs(rho64);
+            my_vol += (unsigned long long)d;
+            {
+                // per-seed counters: one atomic per group of lanes with the same seed
+                const unsigned am = __activemask();
+                const unsigned peers = __match_any_sync(am, j);
+                const unsigned dsum = __reduce_add_sync(peers, (unsigned)d);
+                if (lane == __ffs(peers) - 1) {
+                    atomicAdd(a.svol + j, (unsigned long long)dsum);
+                    atomicAdd(a.spushes + j, (unsigned)__popc(peers));
+                    atomicMax(a.slast + j, (int)t);
+                }
+            }
+            if (d == 0) continue;
+            float w;
+            if (a.kind == GDE_KATZ)
+                w = __double2float_rn(__dmul_rn(a.coef, rho64));
+            else
+                w = __double2float_rn(__ddiv_rn(__dmul_rn(a.coef, rho64), (double)d));
+            if (d <= a.t2) {
+                // each bin gets its own coalesced group so a group never mixes two counters
+                const int bin = d <= a.t1 ? 0 : 1;
+                unsigned *counter = bin == 0 ? &ctl->cnt_small : &ctl->cnt_med;
+                unsigned i;
+                if (bin == 0) {
+                    cg::coalesced_group g = cg::coalesced_threads();
+                    unsigned base = 0;
+                    if (g.thread_rank() == 0) base = atomicAdd(counter, (unsigned)g.size());
+                    i = g.shfl(base, 0) + g.thread_rank();
+                } else {
+                    cg::coalesced_group g = cg::coalesced_threads();
+                    unsigned base = 0;
+                    if (g.thread_rank() == 0) base = atomicAdd(counter, (unsigned)g.size());
+                    i = g.shfl(base, 0) + g.thread_rank();
+                }
+                if (i < a.list_cap) {
+                    __stcg(a.b_beg[bin] + i, beg); __stcg(a.b_deg[bin] + i, d);
+                    __stcg(a.b_w[bin] + i, w); __stcg(a.b_seed[bin] + i, j);
+                } else {
+                    atomicOr(&ctl->overflow, 1u);
+                }
+            } else {
+                cg::coalesced_group g = cg::coalesced_threads();
+                const unsigned long long dv = (unsigned long long)d;
+                const unsigned long long excl = cg::exclusive_scan(g, dv);
+                const unsigned long long tot = g.shfl(excl + dv, g.size() - 1);
+                unsigned long long old = 0;
+                if (g.thread_rank() == 0)
+                    old = atomicAdd(&ctl->hub_packed, ((unsigned long long)g.size() << kBHubVolBits) + tot);
+                old = g.shfl(old, 0);
+                const unsigned long long i = (old >> kBHubVolBits) + g.thread_rank();
+                if (i < a.list_cap) {
+                    __stcg(a.b_beg[2] + i, beg); __stcg(a.b_deg[2] + i, d);
+                    __stcg(a.b_w[2] + i, w); __stcg(a.b_seed[2] + i, j);
+                    __stcg(a.hub_vstart + i, (int64_t)((old & kBHubVolMask) + excl));
+                } else {
+                    atomicOr(&ctl->overflow, 1u);
+                }
+            }
+        }
+        {
+            double rs = bwarp_sum(my_rs);
+            unsigned long long vv = bwarp_sum(my_vol);
+            if (lane == 0) { s_rs[wid] = rs; s_vol[wid] = vv; }
+            __syncthreads();
+            if (wid == 0) {
+                rs = lane < kWarps ? s_rs[lane] : 0.0;
+                vv = lane < kWarps ? s_vol[lane] : 0ull;
+                rs = bwarp_sum(rs);
+                vv = bwarp_sum(vv);
+                if (lane == 0 && vv + (rs != 0.0)) {
+                    atomicAdd(&ctl->rS_l1, rs);
+                    atomicAdd(&ctl->vol, vv);
+                }
+            }
+        }
+        if (!grid_sync(G, nblocks)) return;
+
+        // ---------------- phase B: scatter ----------------
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            // the other parity's counters were last read in phase A of this round
+            prev->hub_packed = 0; prev->cnt_small = 0; prev->cnt_med = 0; prev->cand_out = 0;
+            prev->n_active = 0; prev->vol = 0; prev->rS_l1 = 0.0; prev->overflow = 0;
+        }
+        uint32_t *cand_out = a.cand[p ^ 1];
+        if (__ldcg(&ctl->overflow)) {
+            if (tid == 0) atomicCAS(&G->error, 0u, (unsigned)GDE_ENOMEM);
+        } else {
+            const unsigned long long hp = __ldcg(&ctl->hub_packed);
+            const int64_t H = (int64_t)(hp >> kBHubVolBits);
+            const int64_t VH = (int64_t)(hp & kBHubVolMask);
+            if (VH > 0) {
+                const int64_t nchunks = (VH + a.chunk - 1) / a.chunk;
+                for (int64_t c = gw; c < nchunks; c += nw) {
+                    const int64_t e0 = c * a.chunk;
+                    const int64_t e1 = min(e0 + (int64_t)a.chunk, VH);
+                    int64_t lo = 0, hi = H;
+                    while (hi - lo > 1) {
+                        const int64_t mid = (lo + hi) >> 1;
+                        if (__ldcg(a.hub_vstart + mid) <= e0) lo = mid; else hi = mid;
+                    }
+                    int64_t h = lo;
+                    int64_t hs = __ldcg(a.hub_vstart + h);
+                    int64_t he = hs + __ldcg(a.b_deg[2] + h);
+                    int64_t hb = __ldcg(a.b_beg[2] + h);
+                    float hw = __ldcg(a.b_w[2] + h);
+                    int32_t hj = __ldcg(a.b_seed[2] + h);
+                    for (int64_t e = e0 + lane; e < e1; e += 32) {
+                        while (e >= he) {
+                            ++h;
+                            hs = __ldcg(a.hub_vstart + h);
+                            he = hs + __ldcg(a.b_deg[2] + h);
+                            hb = __ldcg(a.b_beg[2] + h);
+                            hw = __ldcg(a.b_w[2] + h);
+                            hj = __ldcg(a.b_seed[2] + h);
+                        }
+                        bscatter(a, ctl, cand_out, hj, a.col[hb + (e - hs)], hw);
+                    }
+                }
+            }
+            const unsigned nmed = min(__ldcg(&ctl->cnt_med), a.list_cap);
+            for (int64_t i = gw; i < nmed; i += nw) {
+                const int64_t b = __ldcg(a.b_beg[1] + i);
+                const int32_t d = __ldcg(a.b_deg[1] + i);
+                const float w = __ldcg(a.b_w[1] + i);
+                const int32_t j = __ldcg(a.b_seed[1] + i);
+                for (int32_t k = lane; k < d; k += 32) bscatter(a, ctl, cand_out, j, a.col[b + k], w);
+            }
+            const unsigned nsm = min(__ldcg(&ctl->cnt_small), a.list_cap);
+            for (int64_t i = tid; i < nsm; i += nthreads) {
+                const int64_t b = __ldcg(a.b_beg[0] + i);
+                const int32_t d = __ldcg(a.b_deg[0] + i);
+                const float w = __ldcg(a.b_w[0] + i);
+                const int32_t j = __ldcg(a.b_seed[0] + i);
+                for (int32_t k = 0; k < d; k++) bscatter(a, ctl, cand_out, j, a.col[b + k], w);
+            }
+        }
+        if (!grid_sync(G, nblocks)) return;
+        const unsigned next = __ldcg(&ctl->cand_out);
+        const unsigned ovf = __ldcg(&ctl->overflow);
+        if (tid == 0) {
+            G->rounds = (unsigned)(t + 1);
+            const unsigned long long rv = __ldcg(&ctl->vol);
+            G->total_vol += rv;
+            if (t < kLogCap) {
+                a.log[t].vol = rv;
+                a.log[t].rS_l1 = __ldcg(&ctl->rS_l1);
+                a.log[t].ncand = ncand;
+                a.log[t].n_active = next;
+            }
+            if (ovf || next > a.list_cap) atomicCAS(&G->error, 0u, (unsigned)GDE_ENOMEM);
+        }
+        if (next == 0 || next > a.list_cap || ovf) break;
+    }
+}
+
+// clear the pool and fill the per-node thresholds
+__global__ void k_batch_clear(int64_t pool, unsigned long long *kr, float *xs) {
+    const unsigned long long empty = (unsigned long long)kEmpty;  // r = 0.0f in the high half
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < pool;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        kr[i] = empty;
+        xs[i] = 0.0f;
+    }
+}
+
+__global__ void k_batch_thr(int64_t n, const int32_t *deg, float *thr32, double eps) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        thr32[i] = __double2float_ru(__dmul_rn(eps, (double)deg[i]));
+}
+
+__global__ void k_batch_seed(int32_t nseeds, const int32_t *seeds, unsigned long long *kr,
+                             uint32_t *cand0, int log2cap, uint32_t mask, BGlobal *G,
+                             int32_t *status, unsigned *inserts, unsigned long long *svol,
+                             unsigned *spushes, int32_t *slast) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j == 0) {
+        memset(G, 0, sizeof(BGlobal));
+        G->ctl[1].cand_out = (unsigned)nseeds;
+    }
+    if (j >= nseeds) return;
+    const int32_t s = seeds[j];
+    const uint64_t slot = ((uint64_t)j << log2cap) + (mix32((uint32_t)s) & mask);
+    kr[slot] = ((unsigned long long)__float_as_uint(1.0f) << 32) | (unsigned long long)(uint32_t)s;
+    cand0[j] = (uint32_t)slot;
+    status[j] = kSeedOk;
+    inserts[j] = 1;
+    svol[j] = 0;
+    spushes[j] = 0;
+    slast[j] = -1;
+}
+
+// ------------------------------------------------------------------- top-k --
+
+// bitonic helpers on 64-bit keys, one key per lane, descending order
+__device__ __forceinline__ unsigned long long cmpx(unsigned long long v, int partner_mask, bool keep_max) {
+    const unsigned long long o = __shfl_xor_sync(0xffffffffu, v, partner_mask);
+    return keep_max ? (v > o ? v : o) : (v < o ? v : o);
+}
+
+// sort 32 keys (one per lane) descending
+__device__ __forceinline__ unsigned long long sort32_desc(unsigned long long v, int lane) {
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const bool up = ((lane & k) == 0);       // this block sorted descending
+            const bool lower = ((lane & j) == 0);
+            v = cmpx(v, j, up == lower);
+        }
+    }
+    return v;
+}
+
+// bitonic sequence of 32 (one per lane) -> descending
+__device__ __forceinline__ unsigned long long merge32_desc(unsigned long long v, int lane) {
+#pragma unroll
+    for (int j = 16; j > 0; j >>= 1) v = cmpx(v, j, (lane & j) == 0);
+    return v;
+}
+
+// top-64 list held as a (positions 0..31) and b (32..63), both descending across lanes.
+// Insert a batch of 32 candidates c (one per lane, any order).
+__device__ __forceinline__ void top64_insert(unsigned long long &a, unsigned long long &b,
+                                             unsigned long long c, int lane) {
+    const unsigned long long lmin = __shfl_sync(0xffffffffu, b, 31);
+    if (!__any_sync(0xffffffffu, c > lmin)) return;
+    c = sort32_desc(c, lane);
+    // top 32 of (b U c): elementwise max of b and reversed c, then sort
+    const unsigned long long crev = __shfl_sync(0xffffffffu, c, 31 - lane);
+    unsigned long long m = b > crev ? b : crev;
+    m = merge32_desc(m, lane);
+    // merge a (desc) and m (desc): a followed by reversed m is bitonic
+    const unsigned long long mrev = __shfl_sync(0xffffffffu, m, 31 - lane);
+    const unsigned long long hi = a > mrev ? a : mrev;
+    const unsigned long long lo = a > mrev ? mrev : a;
+    a = merge32_desc(hi, lane);
+    b = merge32_desc(lo, lane);
+}
+
+struct TopkArgs {
+    const unsigned long long *kr;
+    const float *xs;
+    int log2cap;
+    int64_t cap;
+    int k;
+    int32_t *out_ids;
+    float *out_vals;
+    double *sresid;
+    double *smass;
+};
+
+// one block per seed: scan its table, keep the top-k of (x desc, id asc), and sum |r| and x in FP64
+__global__ void __launch_bounds__(kThreads) k_batch_topk(TopkArgs a) {
+    const int j = blockIdx.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint64_t base = (uint64_t)j << a.log2cap;
+    unsigned long long ta = 0, tb = 0;
+    double rsum = 0.0, xsum = 0.0;
+    for (int64_t i0 = (int64_t)wid * 32; i0 < a.cap; i0 += kThreads) {
+        const int64_t i = i0 + lane;
+        unsigned long long key = 0;
+        if (i < a.cap) {
+            const float x = a.xs[base + i];
+            const unsigned long long w = a.kr[base + i];
+            const uint32_t v = (uint32_t)(w & 0xFFFFFFFFull);
+            if (v != kEmpty) rsum += fabs((double)__uint_as_float((uint32_t)(w >> 32)));
+            if (x > 0.0f && v != kEmpty) {
+                xsum += (double)x;
+                key = ((unsigned long long)__float_as_uint(x) << 32) | (unsigned long long)(0xFFFFFFFFu - v);
+            }
+        }
+        top64_insert(ta, tb, key, lane);
+    }
+    __shared__ unsigned long long s_a[kWarps][32], s_b[kWarps][32];
+    __shared__ double s_r[kWarps], s_x[kWarps];
+    s_a[wid][lane] = ta;
+    s_b[wid][lane] = tb;
+    rsum = bwarp_sum(rsum);
+    xsum = bwarp_sum(xsum);
+    if (lane == 0) { s_r[wid] = rsum; s_x[wid] = xsum; }
+    __syncthreads();
+    if (wid == 0) {
+        for (int w = 1; w < kWarps; w++) {
+            top64_insert(ta, tb, s_a[w][lane], lane);
+            top64_insert(ta, tb, s_b[w][lane], lane);
+        }
+        double rr = lane < kWarps ? s_r[lane] : 0.0;
+        double xx = lane < kWarps ? s_x[lane] : 0.0;
+        rr = bwarp_sum(rr);
+        xx = bwarp_sum(xx);
+        if (lane == 0) { a.sresid[j] = rr; a.smass[j] = xx; }
+        const int k = a.k;
+        for (int half = 0; half < 2; half++) {
+            const int pos = half * 32 + lane;
+            const unsigned long long key = half ? tb : ta;
+            if (pos < k) {
+                const bool valid = key != 0;
+                a.out_ids[(int64_t)j * k + pos] = valid ? (int32_t)(0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFull)) : -1;
+                a.out_vals[(int64_t)j * k + pos] = valid ? __uint_as_float((uint32_t)(key >> 32)) : 0.0f;
+            }
+        }
+    }
+}
+
+// dense top-k over x[0..n) (float): partial top-64 per block, then one block merges
+__global__ void __launch_bounds__(kThreads) k_topk_dense_partial(int64_t n, const float *x,
+                                                                 unsigned long long *partial) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned long long ta = 0, tb = 0;
+    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t lo = (int64_t)blockIdx.x * per, hi = min(lo + per, n);
+    for (int64_t i0 = lo + (int64_t)wid * 32; i0 < hi; i0 += kThreads) {
+        const int64_t i = i0 + lane;
+        unsigned long long key = 0;
+        if (i < hi) {
+            const float v = x[i];
+            if (v > 0.0f) key = ((unsigned long long)__float_as_uint(v) << 32) | (unsigned long long)(0xFFFFFFFFu - (uint32_t)i);
+        }
+        top64_insert(ta, tb, key, lane);
+    }
+    __shared__ unsigned long long s_a[kWarps][32], s_b[kWarps][32];
+    s_a[wid][lane] = ta;
+    s_b[wid][lane] = tb;
+    __syncthreads();
+    if (wid == 0) {
+        for (int w = 1; w < kWarps; w++) {
+            top64_insert(ta, tb, s_a[w][lane], lane);
+            top64_insert(ta, tb, s_b[w][lane], lane);
+        }
+        partial[(int64_t)blockIdx.x * 64 + lane] = ta;
+        partial[(int64_t)blockIdx.x * 64 + 32 + lane] = tb;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_topk_dense_final(int64_t nparts, const unsigned long long *partial,
+                                                               int k, int32_t *ids, float *vals) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned long long ta = 0, tb = 0;
+    for (int64_t i0 = (int64_t)wid * 32; i0 < nparts * 64; i0 += kThreads) {
+        const int64_t i = i0 + lane;
+        top64_insert(ta, tb, i < nparts * 64 ? partial[i] : 0ull, lane);
+    }
+    __shared__ unsigned long long s_a[kWarps][32], s_b[kWarps][32];
+    s_a[wid][lane] = ta;
+    s_b[wid][lane] = tb;
+    __syncthreads();
+    if (wid == 0) {
+        for (int w = 1; w < kWarps; w++) {
+            top64_insert(ta, tb, s_a[w][lane], lane);
+            top64_insert(ta, tb, s_b[w][lane], lane);
+        }
+        for (int half = 0; half < 2; half++) {
+            const int pos = half * 32 + lane;
+            const unsigned long long key = half ? tb : ta;
+            if (pos < k) {
+                const bool valid = key != 0;
+                ids[pos] = valid ? (int32_t)(0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFull)) : -1;
+                vals[pos] = valid ? __uint_as_float((uint32_t)(key >> 32)) : 0.0f;
+            }
+        }
+    }
+}
+
+void topk_dense_f32(const float *x_dev, int64_t n, int k, int32_t *ids_dev, float *vals_dev,
+                    cudaStream_t s) {
+    GDE_REQUIRE(k >= 1 && k <= kTopMax, GDE_EINVAL, "topk must be in [1, 64]");
+    const int parts = kSMs * 2;
+    unsigned long long *partial = (unsigned long long *)dmalloc(8 * 64 * (size_t)parts, "top-k partials");
+    try {
+        k_topk_dense_partial<<<parts, kThreads, 0, s>>>(n, x_dev, partial);
+        GDE_CUDA(cudaGetLastError());
+        k_topk_dense_final<<<1, kThreads, 0, s>>>(parts, partial, k, ids_dev, vals_dev);
+        GDE_CUDA(cudaGetLastError());
+        GDE_CUDA(cudaStreamSynchronize(s));
+    } catch (...) {
+        dfree(partial);
+        throw;
+    }
+    dfree(partial);
+}
+
+// =============================================================== host ====
+
+static void batch_free(BatchWork *w) {
+    if (!w) return;
+    dfree(w->kr); dfree(w->xs); dfree(w->thr32);
+    for (int k = 0; k < 2; k++) dfree(w->cand[k]);
+    for (int b = 0; b < 3; b++) { dfree(w->b_beg[b]); dfree(w->b_deg[b]); dfree(w->b_w[b]); dfree(w->b_seed[b]); }
+    dfree(w->hub_vstart); dfree(w->seeds); dfree(w->status); dfree(w->inserts); dfree(w->svol);
+    dfree(w->spushes); dfree(w->slast); dfree(w->sresid); dfree(w->smass); dfree(w->glob); dfree(w->log);
+    delete w;
+}
+
+void batch_work_destroy(BatchWork *w) { batch_free(w); }
+
+static BatchWork *batch_work_get(Graph &g, int64_t nseeds, int64_t cap, int64_t list_cap) {
+    BatchWork *w = g.batch;
+    if (w && w->nseeds_cap >= nseeds && w->cap == cap && w->list_cap >= list_cap) return w;
+    if (w) { batch_free(w); g.batch = nullptr; }
+    w = new BatchWork();
+    try {
+        w->nseeds_cap = nseeds;
+        w->cap = cap;
+        w->log2cap = 0;
+        while (((int64_t)1 << w->log2cap) < cap) w->log2cap++;
+        w->pool = nseeds * cap;
+        w->list_cap = list_cap;
+        w->kr = (unsigned long long *)dmalloc(8 * (size_t)w->pool, "hash keys/residuals");
+        w->xs = (float *)dmalloc(4 * (size_t)w->pool, "hash x");
+        for (int k = 0; k < 2; k++) w->cand[k] = (uint32_t *)dmalloc(4 * (size_t)list_cap, "candidates");
+        for (int b = 0; b < 3; b++) {
+            w->b_beg[b] = (int64_t *)dmalloc(8 * (size_t)list_cap, "bins");
+            w->b_deg[b] = (int32_t *)dmalloc(4 * (size_t)list_cap, "bins");
+            w->b_w[b] = (float *)dmalloc(4 * (size_t)list_cap, "bins");
+            w->b_seed[b] = (int32_t *)dmalloc(4 * (size_t)list_cap, "bins");
+        }
+        w->hub_vstart = (int64_t *)dmalloc(8 * (size_t)list_cap, "hub offsets");
+        w->seeds = (int32_t *)dmalloc(4 * (size_t)nseeds, "seeds");
+        w->status = (int32_t *)dmalloc(4 * (size_t)nseeds, "seed status");
+        w->inserts = (unsigned *)dmalloc(4 * (size_t)nseeds, "seed inserts");
+        w->svol = (unsigned long long *)dmalloc(8 * (size_t)nseeds, "seed volume");
+        w->spushes = (unsigned *)dmalloc(4 * (size_t)nseeds, "seed pushes");
+        w->slast = (int32_t *)dmalloc(4 * (size_t)nseeds, "seed rounds");
+        w->sresid = (double *)dmalloc(8 * (size_t)nseeds, "seed residual");
+        w->smass = (double *)dmalloc(8 * (size_t)nseeds, "seed mass");
+        w->glob = (BGlobal *)dmalloc(sizeof(BGlobal), "batch control");
+        w->log = (RoundLog *)dmalloc(sizeof(RoundLog) * kLogCap, "round log");
+        int per_sm = 0;
+        GDE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_rounds, kThreads, 0));
+        int dev = 0, sms = 0;
+        GDE_CUDA(cudaGetDevice(&dev));
+        GDE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        GDE_REQUIRE(per_sm > 0, GDE_ECUDA, "batched kernel cannot be resident");
+        w->grid = sms * per_sm;
+    } catch (...) {
+        batch_free(w);
+        throw;
+    }
+    g.batch = w;
+    return w;
+}
+
+static inline int64_t floor_pow2(int64_t v) {
+    int64_t p = 1;
+    while (p * 2 <= v) p *= 2;
+    return p;
+}
+
+static inline int64_t ceil_pow2(int64_t v) {
+    int64_t p = 1;
+    while (p < v) p *= 2;
+    return p;
+}
+
+// Runs a batched PPR/Katz solve.  seeds_dev: device seed ids.  Outputs (device): ids[nseeds*k],
+// vals[nseeds*k] (float).  stats_host may be NULL.  Seeds whose table overflowed are reported
+// with status GDE_ENOMEM in stats and in *n_overflow; their outputs are not valid.
+void batch_solve(Graph &g, const SolveParams &p, const int32_t *seeds_dev, int32_t nseeds, int k,
+                 int64_t mem_budget, int32_t *ids_dev, float *vals_dev, gde_stats *stats_host,
+                 int32_t *overflow_seeds_host, int32_t *n_overflow) {
+    GDE_REQUIRE(k >= 1 && k <= kTopMax, GDE_EINVAL, "batched mode needs 1 <= topk <= 64");
+    GDE_REQUIRE(p.kind == GDE_PPR || p.kind == GDE_KATZ, GDE_EINVAL, "batched mode supports PPR and Katz");
+    GDE_REQUIRE(p.precision == GDE_FP32, GDE_EINVAL, "batched mode stores x and r in FP32");
+    GDE_REQUIRE(g.n < ((int64_t)1 << 31) - 1, GDE_EINVAL, "graph too large for 32-bit keys");
+    const int64_t budget = mem_budget > 0 ? mem_budget : ((int64_t)16 << 30);
+    int64_t cap = floor_pow2(budget / (12 * (int64_t)nseeds));
+    // a table of 2n slots never exceeds half load (at most n keys)
+    const int64_t cap_max = ceil_pow2(2 * (g.n > 0 ? g.n : 1));
+    if (cap > cap_max) cap = cap_max;
+    GDE_REQUIRE(cap >= 64 || cap == cap_max, GDE_ENOMEM, "memory budget too small for the batch");
+    GDE_REQUIRE((int64_t)nseeds * cap < ((int64_t)1 << 32), GDE_EINVAL, "batch pool exceeds 2^32 slots");
+    // candidate and bin lists: every slot can enter a list at most once per round, but the
+    // per-round frontier of all seeds together is far smaller than the pool; past this
+    // capacity the solve reports GDE_ENOMEM
+    int64_t list_cap = (int64_t)nseeds * cap;
+    const int64_t list_max = (int64_t)1 << 24;
+    if (list_cap > list_max) list_cap = list_max;
+    GDE_REQUIRE(nseeds <= list_cap, GDE_EINVAL, "too many seeds for one batch");
+    BatchWork *w = batch_work_get(g, nseeds, cap, list_cap);
+    cudaStream_t s = p.stream;
+    GDE_CUDA(cudaMemcpyAsync(w->seeds, seeds_dev, 4 * (size_t)nseeds, cudaMemcpyDeviceToDevice, s));
+    const int64_t pool = (int64_t)nseeds * cap;
+    const int pc = g.prof.start(kProfBatchClear, s);
+    k_batch_clear<<<kSMs * 8, kThreads, 0, s>>>(pool, w->kr, w->xs);
+    GDE_CUDA(cudaGetLastError());
+    g.prof.stop(pc, s);
+    if (w->thr_eps != p.eps || w->thr_n != g.n || !w->thr32) {
+        if (!w->thr32) w->thr32 = (float *)dmalloc(4 * (size_t)(g.n > 0 ? g.n : 1), "thresholds");
+        k_batch_thr<<<kSMs * 8, kThreads, 0, s>>>(g.n, g.deg, w->thr32, p.eps);
+        GDE_CUDA(cudaGetLastError());
+        w->thr_eps = p.eps;
+        w->thr_n = g.n;
+    }
+    k_batch_seed<<<(nseeds + kThreads - 1) / kThreads, kThreads, 0, s>>>(
+        nseeds, w->seeds, w->kr, w->cand[0], w->log2cap, (uint32_t)(cap - 1), w->glob, w->status,
+        w->inserts, w->svol, w->spushes, w->slast);
+    GDE_CUDA(cudaGetLastError());
+
+    BArgs a{};
+    a.off = g.off; a.col = g.col; a.thr32 = w->thr32; a.kr = w->kr; a.xs = w->xs;
+    a.log2cap = w->log2cap; a.mask = (uint32_t)(cap - 1); a.nseeds = nseeds;
+    a.status = w->status; a.inserts = w->inserts;
+    a.load_limit = (unsigned)(cap * 3 / 4);
+    a.svol = w->svol; a.spushes = w->spushes; a.slast = w->slast;
+    a.cand[0] = w->cand[0]; a.cand[1] = w->cand[1];
+    a.list_cap = (unsigned)list_cap;
+    for (int b = 0; b < 3; b++) { a.b_beg[b] = w->b_beg[b]; a.b_deg[b] = w->b_deg[b]; a.b_w[b] = w->b_w[b]; a.b_seed[b] = w->b_seed[b]; }
+    a.hub_vstart = w->hub_vstart;
+    a.glob = w->glob; a.log = w->log;
+    a.kind = p.kind;
+    a.cx = p.kind == GDE_PPR ? p.param : 1.0;
+    a.coef = p.kind == GDE_PPR ? 1.0 - p.param : p.param;
+    a.max_rounds = p.max_rounds;
+    Bins bins;
+    a.t1 = bins.t1; a.t2 = bins.t2; a.chunk = bins.chunk;
+
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)w->grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const int pr = g.prof.start(kProfBatchRounds, s);
+    GDE_CUDA(cudaLaunchKernelEx(&cfg, k_batch_rounds, a));
+    g.prof.stop(pr, s);
+
+    TopkArgs ta{};
+    ta.kr = w->kr; ta.xs = w->xs; ta.log2cap = w->log2cap; ta.cap = cap; ta.k = k;
+    ta.out_ids = ids_dev; ta.out_vals = vals_dev; ta.sresid = w->sresid; ta.smass = w->smass;
+    const int pt = g.prof.start(kProfBatchTopk, s);
+    k_batch_topk<<<nseeds, kThreads, 0, s>>>(ta);
+    GDE_CUDA(cudaGetLastError());
+    g.prof.stop(pt, s);
+
+    // per-seed results
+    BGlobal hg;
+    GDE_CUDA(cudaMemcpyAsync(&hg, w->glob, sizeof(BGlobal), cudaMemcpyDeviceToHost, s));
+    std::vector<int32_t> st(nseeds), last(nseeds);
+    std::vector<unsigned long long> vol(nseeds);
+    std::vector<unsigned> pushes(nseeds);
+    std::vector<double> resid(nseeds), mass(nseeds);
+    std::vector<unsigned> ins(nseeds);
+    GDE_CUDA(cudaMemcpyAsync(st.data(), w->status, 4 * (size_t)nseeds, cudaMemcpyDeviceToHost, s));
+    if (g.prof.enabled)
+        GDE_CUDA(cudaMemcpyAsync(ins.data(), w->inserts, 4 * (size_t)nseeds, cudaMemcpyDeviceToHost, s));
+    if (stats_host || g.prof.enabled) {
+        GDE_CUDA(cudaMemcpyAsync(last.data(), w->slast, 4 * (size_t)nseeds, cudaMemcpyDeviceToHost, s));
+        GDE_CUDA(cudaMemcpyAsync(vol.data(), w->svol, 8 * (size_t)nseeds, cudaMemcpyDeviceToHost, s));
+        GDE_CUDA(cudaMemcpyAsync(pushes.data(), w->spushes, 4 * (size_t)nseeds, cudaMemcpyDeviceToHost, s));
+        GDE_CUDA(cudaMemcpyAsync(resid.data(), w->sresid, 8 * (size_t)nseeds, cudaMemcpyDeviceToHost, s));
+        GDE_CUDA(cudaMemcpyAsync(mass.data(), w->smass, 8 * (size_t)nseeds, cudaMemcpyDeviceToHost, s));
+    }
+    GDE_CUDA(cudaStreamSynchronize(s));
+    if (hg.error == GDE_ETIMEOUT) {
+        set_error("batched solve: a grid barrier wait timed out");
+        throw Fail{GDE_ETIMEOUT};
+    }
+    if (hg.error != 0) {
+        set_error("batched solve: candidate or bin list capacity exceeded");
+        throw Fail{(gde_status)hg.error};
+    }
+    if (g.prof.enabled) {
+        g.prof.counters.batch_launches += 1;
+        g.prof.counters.rounds += hg.rounds;
+        for (int32_t j = 0; j < nseeds; j++) {
+            g.prof.counters.edges += (int64_t)vol[j];
+            g.prof.counters.pushes += pushes[j];
+            g.prof.counters.inserts += ins[j];
+        }
+    }
+    const bool capped = (int64_t)hg.rounds >= p.max_rounds;
+    int32_t nof = 0;
+    for (int32_t j = 0; j < nseeds; j++) {
+        const bool of = st[j] != kSeedOk;
+        if (of && overflow_seeds_host) overflow_seeds_host[nof] = j;
+        if (of) nof++;
+        if (stats_host) {
+            gde_stats &o = stats_host[j];
+            o.rounds = last[j] + 1;
+            o.active_volume = (int64_t)vol[j];
+            o.pushes = pushes[j];
+            o.resid_l1 = resid[j];
+            o.mass_l1 = mass[j];
+            o.status = of ? GDE_ENOMEM : ((capped && last[j] + 1 >= (int64_t)hg.rounds) ? GDE_ENOTCONV : GDE_OK);
+            o.reserved = 0;
+        }
+    }
+    if (n_overflow) *n_overflow = nof;
+}
+
+}  // namespace gde

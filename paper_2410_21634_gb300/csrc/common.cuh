@@ -1,0 +1,160 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "gde.h"
+
+namespace gde {
+
+// ------------------------------------------------------------------ errors --
+
+void set_error(const std::string &msg);
+void clear_error();
+
+struct Fail {
+    gde_status st;
+};
+
+#define GDE_CUDA(call)                                                              \
+    do {                                                                            \
+        cudaError_t e_ = (call);                                                    \
+        if (e_ != cudaSuccess) {                                                    \
+            ::gde::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));   \
+            throw ::gde::Fail{GDE_ECUDA};                                           \
+        }                                                                           \
+    } while (0)
+
+#define GDE_REQUIRE(cond, status, msg)                                              \
+    do {                                                                            \
+        if (!(cond)) {                                                              \
+            ::gde::set_error(msg);                                                  \
+            throw ::gde::Fail{status};                                              \
+        }                                                                           \
+    } while (0)
+
+// device allocation that throws GDE_ENOMEM
+void *dmalloc(size_t bytes, const char *what);
+void dfree(void *p);
+
+// ---------------------------------------------------------------- constants --
+
+constexpr int kSMs = 152;          // GB300: 2 dies x 76 SMs
+constexpr int kThreads = 256;      // block size of the round kernels
+constexpr int kWarps = kThreads / 32;
+
+// degree bins of the push (autotunable; these are the defaults)
+struct Bins {
+    int32_t t1 = 8;       // d <= t1: thread per node
+    int32_t t2 = 2048;    // t1 < d <= t2: warp per node; d > t2: hub merge-path chunks
+    int32_t chunk = 4096; // hub edges per warp work item
+};
+
+// ---------------------------------------------------------------- profiler --
+
+enum ProfKind { kProfBatchRounds = 0, kProfBatchClear, kProfBatchTopk, kProfDenseFrontier, kProfDensePush, kProfKinds };
+
+struct Profiler {
+    bool enabled = false;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> marks;
+    gde_profile counters{};
+    // record a start event; returns the index to close with stop()
+    int start(int kind, cudaStream_t s);
+    void stop(int idx, cudaStream_t s);
+    void reset();
+    void read(gde_profile *out);
+};
+
+// ------------------------------------------------------------------- graph --
+
+struct Graph {
+    int64_t n = 0;
+    int64_t nnz = 0;
+    int32_t max_degree = 0;
+    int device = 0;
+    int64_t *off = nullptr;   // n+1
+    int32_t *col = nullptr;   // nnz
+    int32_t *deg = nullptr;   // n
+    cudaStream_t stream = nullptr;
+    std::mutex mu;
+    struct DenseWork *dense[2] = {nullptr, nullptr};     // cached single-seed workspace per precision
+    struct BatchWork *batch = nullptr;                   // cached batched workspace
+    Profiler prof;
+};
+
+// row validation result bits
+enum : unsigned {
+    kBadOffsets = 1u, kBadColRange = 2u, kUnsorted = 4u, kSelfLoop = 8u, kAsymmetric = 16u
+};
+
+void graph_validate(Graph &g, bool check_symmetric, unsigned *bits_out);
+
+// ------------------------------------------------------------------- solve --
+
+struct SolveParams {
+    gde_kind kind;
+    double param;      // alpha | beta | tau
+    double eps;
+    int precision;     // GDE_FP64 / GDE_FP32
+    int hk_mode;       // 0 error-bound theta, 1 literal
+    double hk_tol;
+    int64_t max_rounds;
+    int64_t hk_N;      // Taylor layers - 1 (HK)
+    cudaStream_t stream;
+};
+
+// heat-kernel helpers (host)
+int64_t hk_terms(double tau, double tol);
+double hk_theta(double tau, int64_t N, int64_t t, int mode);
+
+// dense single-seed engine (dense.cu)
+struct DenseWork;
+DenseWork *dense_work_create(Graph &g, int precision);
+void dense_work_destroy(DenseWork *w);
+
+struct RoundInfo {
+    int64_t n_active;
+    int64_t vol;
+    double rS_l1;
+    double scat;     // sum over pushed nodes of d_u w_u (mass scattered)
+    double retired;  // HK: residual mass of the finished layer that was cleared
+};
+
+// begin a solve from `seed`; afterwards dense_round advances one round
+void dense_begin(Graph &g, DenseWork *w, const SolveParams &p, int32_t seed);
+// runs round t (w keeps t); returns |S_t| (0 = converged) and fills info
+int64_t dense_round(Graph &g, DenseWork *w, const SolveParams &p, RoundInfo *info);
+int64_t dense_round_index(const DenseWork *w);
+// true while another round may have a non-empty active set
+bool dense_pending(const DenseWork *w);
+// device pointers of the current state
+void *dense_x(DenseWork *w);
+void dense_read(Graph &g, DenseWork *w, const SolveParams &p, void *x, void *r, int32_t *active,
+                int64_t *n_active, bool device_ptrs);
+// write the output vector (HK scaled by e^-tau) into dst (device pointer, n values)
+void dense_output(Graph &g, DenseWork *w, const SolveParams &p, void *dst_dev);
+// top-k of the current x (scaled for HK) into device buffers ids[k], vals[k]
+void dense_topk(Graph &g, DenseWork *w, const SolveParams &p, int k, int32_t *ids_dev,
+                void *vals_dev);
+
+// batched engine (batched.cu)
+struct BatchWork;
+void batch_work_destroy(BatchWork *w);
+void batch_solve(Graph &g, const SolveParams &p, const int32_t *seeds_dev, int32_t nseeds, int k,
+                 int64_t mem_budget, int32_t *ids_dev, float *vals_dev, gde_stats *stats_host,
+                 int32_t *overflow_seeds_host, int32_t *n_overflow);
+// top-k (x desc, id asc) of a dense float vector on the device
+void topk_dense_f32(const float *x_dev, int64_t n, int k, int32_t *ids_dev, float *vals_dev,
+                    cudaStream_t s);
+
+}  // namespace gde
+
+struct gde_graph {
+    gde::Graph g;
+};

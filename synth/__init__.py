@@ -238,6 +238,8 @@ WORKLOADS = {
     "chung_lu_2p24": dict(gen="chung_lu", n=1 << 24, mean_deg=20.0, gamma=2.1, seed=3),
     # batched form: R-MAT scale 24, edge factor 16
     "rmat24": dict(gen="rmat", scale=24, edge_factor=16, seed=4),
+    # a smaller graph of the same family (profiling captures, quick checks)
+    "rmat20": dict(gen="rmat", scale=20, edge_factor=16, seed=4),
     # serving form: Chung-Lu n=2^23, mean degree 16, exponent 2.3
     "chung_lu_2p23": dict(gen="chung_lu", n=1 << 23, mean_deg=16.0, gamma=2.3, seed=5),
 }
