@@ -152,6 +152,33 @@ typedef struct {
 gde_status gde_profile_enable(gde_graph *g, int enable);
 gde_status gde_profile_read(gde_graph *g, gde_profile *out);
 
+/*
+ * Top-k of a dense float vector that allocates no device memory (no counterpart in the
+ * paper: an interface for callers that cannot allocate).  Some callers cannot call
+ * cudaMalloc: an application that has already handed all device memory to its own pool
+ * allocator, a serving loop that must not take the allocator's device-wide lock or
+ * implicit synchronisation between requests, or a host that only lets this library touch
+ * memory it was given.  This entry point runs the same two top-k kernels as gde_solve's
+ * topk output, with their per-block partial lists kept in a fixed scratch array inside the
+ * library (GDE_TOPK_NOALLOC_SCRATCH_BYTES = 256 KiB of device memory per GPU, held from the
+ * library's loading until process exit) instead of a buffer from cudaMalloc.
+ *   x          device pointer, n floats (n in [1, 2^31 - 1]); only entries > 0 are ranked
+ *   k          1 <= k <= 64 (GDE_TOPK_NOALLOC_MAX_K); other values return GDE_EINVAL
+ *   out_ids    device pointer, k ids: largest x first, ties by lower id, -1 past the support
+ *   out_vals   device pointer, k floats (0 past the support)
+ *   cuda_stream  cudaStream_t to launch on (NULL: the legacy default stream); the call does
+ *              not synchronise: results are ready when the stream reaches this point
+ * The first call on a device looks up that device's scratch address (cudaGetSymbolAddress)
+ * with the device current; make that first call before any stream capture.  All calls on a
+ * device share the one scratch array: calls whose kernels overlap on the GPU (other streams,
+ * other host threads) race and must be serialised by the caller.  Every call rewrites the
+ * scratch it reads, so nothing carries over from a previous call.
+ */
+#define GDE_TOPK_NOALLOC_MAX_K 64
+#define GDE_TOPK_NOALLOC_SCRATCH_BYTES (512 * 64 * 8)
+gde_status gde_topk_f32_noalloc(const float *x, int64_t n, int32_t k, int32_t *out_ids,
+                                float *out_vals, void *cuda_stream);
+
 /* Thread-local description of the last failure of this thread ("" if none). */
 const char *gde_last_error(void);
 

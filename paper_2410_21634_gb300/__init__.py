@@ -28,7 +28,8 @@ STATUS_NAMES = {0: "GDE_OK", 1: "GDE_EINVAL", 2: "GDE_ENOMEM", 3: "GDE_ECUDA",
 
 EXPORTED = ["gde_solve_opts_init", "gde_graph_create", "gde_graph_destroy", "gde_graph_info",
             "gde_solve", "gde_last_error", "gde_session_begin", "gde_session_step",
-            "gde_session_read", "gde_session_end", "gde_profile_enable", "gde_profile_read"]
+            "gde_session_read", "gde_session_end", "gde_profile_enable", "gde_profile_read",
+            "gde_topk_f32_noalloc"]
 
 
 class GdeError(RuntimeError):
@@ -96,6 +97,8 @@ def load(path: str | None = None):
     lib.gde_session_step.argtypes = [vp, ctypes.POINTER(I64)]
     lib.gde_session_read.argtypes = [vp, vp, vp, vp, ctypes.POINTER(I64)]
     lib.gde_session_end.argtypes = [vp]
+    lib.gde_topk_f32_noalloc.argtypes = [vp, I64, I32, vp, vp, vp]
+    lib.gde_topk_f32_noalloc.restype = ctypes.c_int
     lib.gde_profile_enable.argtypes = [vp, ctypes.c_int]
     lib.gde_profile_read.argtypes = [vp, ctypes.POINTER(Profile)]
     for name in ("gde_graph_create", "gde_graph_destroy", "gde_graph_info", "gde_solve",
@@ -234,6 +237,19 @@ def solve(graph: Graph, kind, param: float, eps: float, seeds, out_x, out_ids=No
     if st not in (OK, ENOTCONV):
         _check(st)
     return st, ([st_arr[i].as_dict() for i in range(nseeds)] if stats else [])
+
+
+def topk_noalloc(x, k: int, out_ids, out_vals, stream=None):
+    """gde_topk_f32_noalloc: top-k of a dense float CUDA vector without device allocation.
+    x, out_ids (int32, k) and out_vals (float32, k) must be contiguous CUDA tensors; the call
+    is asynchronous on `stream` (default: torch's current stream)."""
+    for a in (x, out_ids, out_vals):
+        if not _is_cuda_tensor(a):
+            raise ValueError("topk_noalloc takes CUDA tensors")
+    if stream is None:
+        stream = _current_stream()
+    _check(load().gde_topk_f32_noalloc(_ptr(x)[0], int(x.numel()), int(k), _ptr(out_ids)[0],
+                                       _ptr(out_vals)[0], stream))
 
 
 class Session:

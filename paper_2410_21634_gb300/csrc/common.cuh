@@ -152,6 +152,11 @@ void batch_solve(Graph &g, const SolveParams &p, const int32_t *seeds_dev, int32
 // top-k (x desc, id asc) of a dense float vector on the device
 void topk_dense_f32(const float *x_dev, int64_t n, int k, int32_t *ids_dev, float *vals_dev,
                     cudaStream_t s);
+// the two kernels of that top-k: per-block top-64 lists into `partial` (64 keys per block),
+// then one block merges gridDim-many lists into the first k entries
+__global__ void k_topk_dense_partial(int64_t n, const float *x, unsigned long long *partial);
+__global__ void k_topk_dense_final(int64_t nparts, const unsigned long long *partial, int k,
+                                   int32_t *ids, float *vals);
 
 }  // namespace gde
 
