@@ -153,6 +153,32 @@ gde_status gde_profile_enable(gde_graph *g, int enable);
 gde_status gde_profile_read(gde_graph *g, gde_profile *out);
 
 /*
+ * Per-round record of the last batched solve on g (Definition 3.1 per round, all seeds
+ * together): out receives up to cap rows of 7 doubles {candidates |C_t|, vol(S_t),
+ * ||r_S||_1, device ns from the start of the persistent launch to the end of the round,
+ * ns to the end of the round's frontier phase, the scatter phase's warp busy time summed
+ * over warps (ns), the longest warp's busy time (ns)}; *rounds receives the number of
+ * rounds (may exceed cap).
+ */
+gde_status gde_profile_rounds(gde_graph *g, double *out, int64_t cap, int64_t *rounds);
+
+/*
+ * Launch shape of the push (SURVEY-style degree bins): nodes with d <= t1 are pushed by one
+ * thread, t1 < d <= t2 by one warp, d > t2 in merge-path chunks of `chunk` edges over the
+ * concatenated hub adjacency; blocks_per_sm sets the persistent grid (0 = the occupancy
+ * limit).  Values <= 0 keep the current setting.  Applies to later solves on g.
+ */
+typedef struct {
+    int32_t t1;
+    int32_t t2;
+    int32_t chunk;
+    int32_t blocks_per_sm;
+} gde_tuning;
+
+gde_status gde_set_tuning(gde_graph *g, const gde_tuning *t);
+gde_status gde_get_tuning(const gde_graph *g, gde_tuning *t);
+
+/*
  * Top-k of a dense float vector that allocates no device memory (no counterpart in the
  * paper: an interface for callers that cannot allocate).  Some callers cannot call
  * cudaMalloc: an application that has already handed all device memory to its own pool

@@ -29,7 +29,7 @@ STATUS_NAMES = {0: "GDE_OK", 1: "GDE_EINVAL", 2: "GDE_ENOMEM", 3: "GDE_ECUDA",
 EXPORTED = ["gde_solve_opts_init", "gde_graph_create", "gde_graph_destroy", "gde_graph_info",
             "gde_solve", "gde_last_error", "gde_session_begin", "gde_session_step",
             "gde_session_read", "gde_session_end", "gde_profile_enable", "gde_profile_read",
-            "gde_topk_f32_noalloc"]
+            "gde_topk_f32_noalloc", "gde_profile_rounds", "gde_set_tuning", "gde_get_tuning"]
 
 
 class GdeError(RuntimeError):
@@ -67,6 +67,11 @@ class Profile(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("t1", ctypes.c_int32), ("t2", ctypes.c_int32), ("chunk", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32)]
+
+
 _lib = None
 
 
@@ -99,6 +104,11 @@ def load(path: str | None = None):
     lib.gde_session_end.argtypes = [vp]
     lib.gde_topk_f32_noalloc.argtypes = [vp, I64, I32, vp, vp, vp]
     lib.gde_topk_f32_noalloc.restype = ctypes.c_int
+    lib.gde_profile_rounds.argtypes = [vp, vp, I64, ctypes.POINTER(I64)]
+    lib.gde_set_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
+    lib.gde_get_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
+    for name in ("gde_profile_rounds", "gde_set_tuning", "gde_get_tuning"):
+        getattr(lib, name).restype = ctypes.c_int
     lib.gde_profile_enable.argtypes = [vp, ctypes.c_int]
     lib.gde_profile_read.argtypes = [vp, ctypes.POINTER(Profile)]
     for name in ("gde_graph_create", "gde_graph_destroy", "gde_graph_info", "gde_solve",
@@ -197,6 +207,23 @@ class Graph:
         p = Profile()
         _check(load().gde_profile_read(self._h, ctypes.byref(p)))
         return p.as_dict()
+
+    def profile_rounds(self, cap: int = 4096):
+        """per-round rows (candidates, volume, ||r_S||_1, ns at round end, ns at frontier end,
+        scatter busy ns summed over warps, longest warp ns) of the last batched solve"""
+        buf = np.zeros((cap, 7), dtype=np.float64)
+        r = ctypes.c_int64()
+        _check(load().gde_profile_rounds(self._h, buf.ctypes.data, cap, ctypes.byref(r)))
+        return buf[: min(r.value, cap)].copy()
+
+    def set_tuning(self, t1=0, t2=0, chunk=0, blocks_per_sm=0):
+        t = Tuning(t1, t2, chunk, blocks_per_sm)
+        _check(load().gde_set_tuning(self._h, ctypes.byref(t)))
+
+    def get_tuning(self) -> dict:
+        t = Tuning()
+        _check(load().gde_get_tuning(self._h, ctypes.byref(t)))
+        return {f: getattr(t, f) for f, _ in t._fields_}
 
     def close(self):
         if getattr(self, "_h", None):

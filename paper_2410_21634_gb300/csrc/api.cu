@@ -388,6 +388,45 @@ gde_status gde_profile_read(gde_graph *h, gde_profile *out) {
     API_END
 }
 
+gde_status gde_profile_rounds(gde_graph *h, double *out, int64_t cap, int64_t *rounds) {
+    API_BEGIN
+    GDE_REQUIRE(h != nullptr && rounds != nullptr, GDE_EINVAL, "graph or rounds is NULL");
+    GDE_REQUIRE(cap >= 0 && (cap == 0 || out != nullptr), GDE_EINVAL, "bad output buffer");
+    Graph &g = h->g;
+    std::lock_guard<std::mutex> lock(g.mu);
+    *rounds = batch_round_log(g, out, cap);
+    API_END
+}
+
+gde_status gde_set_tuning(gde_graph *h, const gde_tuning *t) {
+    API_BEGIN
+    GDE_REQUIRE(h != nullptr && t != nullptr, GDE_EINVAL, "graph or tuning is NULL");
+    Graph &g = h->g;
+    std::lock_guard<std::mutex> lock(g.mu);
+    Bins b = g.bins;
+    if (t->t1 > 0) b.t1 = t->t1;
+    if (t->t2 > 0) b.t2 = t->t2;
+    if (t->chunk > 0) b.chunk = t->chunk;
+    if (t->blocks_per_sm > 0) b.blocks_per_sm = t->blocks_per_sm;
+    GDE_REQUIRE(b.t1 <= b.t2, GDE_EINVAL, "tuning: t1 must be <= t2");
+    GDE_REQUIRE(b.chunk >= 32 && b.chunk <= (1 << 24), GDE_EINVAL, "tuning: chunk must be in [32, 2^24]");
+    GDE_REQUIRE(b.blocks_per_sm <= 32, GDE_EINVAL, "tuning: blocks_per_sm must be <= 32");
+    g.bins = b;
+    for (int k = 0; k < 2; k++)
+        if (g.dense[k]) { dense_work_destroy(g.dense[k]); g.dense[k] = nullptr; }
+    API_END
+}
+
+gde_status gde_get_tuning(const gde_graph *h, gde_tuning *t) {
+    API_BEGIN
+    GDE_REQUIRE(h != nullptr && t != nullptr, GDE_EINVAL, "graph or tuning is NULL");
+    t->t1 = h->g.bins.t1;
+    t->t2 = h->g.bins.t2;
+    t->chunk = h->g.bins.chunk;
+    t->blocks_per_sm = h->g.bins.blocks_per_sm;
+    API_END
+}
+
 gde_status gde_session_begin(gde_graph *h, gde_kind kind, double param, double eps, int32_t seed,
                              const gde_solve_opts *opts, gde_session **out) {
     API_BEGIN

@@ -19,6 +19,7 @@
 #include <cooperative_groups.h>
 #include <cooperative_groups/scan.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -64,6 +65,10 @@ struct RoundLog {
     unsigned long long vol;
     double rS_l1;
     unsigned long long ncand;
+    unsigned long long t_ns;   // device time at the end of the round
+    unsigned long long tA_ns;  // device time at the end of phase A (S_t built)
+    unsigned long long busy_sum_ns;  // phase B: sum over warps of their busy time
+    unsigned long long busy_max_ns;  // phase B: the longest warp
 };
 
 constexpr int kLogCap = 4096;
@@ -85,6 +90,18 @@ struct BatchWork {
     float *b_w[3] = {nullptr, nullptr, nullptr};
     int32_t *b_seed[3] = {nullptr, nullptr, nullptr};
     int64_t *hub_vstart = nullptr;
+    // per-candidate push record of the round (frontier phase -> placement phase)
+    int64_t *tmp_beg = nullptr;
+    int32_t *tmp_deg = nullptr;
+    float *tmp_w = nullptr;
+    uint32_t *tmp_jb = nullptr;      // seed | bin << 30
+    // per-(bin, seed) segment counts, offsets and cursors of the seed-ordered bins
+    unsigned *seg_cnt = nullptr;     // 3 * nseeds
+    unsigned *seg_off = nullptr;     // 3 * nseeds
+    unsigned *seg_cur = nullptr;     // 2 * nseeds
+    unsigned long long *seg_hvol = nullptr;  // nseeds: hub volume per seed
+    unsigned long long *vol_off = nullptr;   // nseeds
+    unsigned long long *seg_hcur = nullptr;  // nseeds: packed (count << 40) | volume cursor
     int32_t *seeds = nullptr;        // device copy of the seed ids
     int32_t *status = nullptr;       // per seed
     unsigned *inserts = nullptr;     // per seed
@@ -95,7 +112,9 @@ struct BatchWork {
     double *smass = nullptr;         // per seed
     BGlobal *glob = nullptr;
     RoundLog *log = nullptr;
-    int grid = 0;
+    int grid = 0;    // co-resident blocks of the persistent kernel
+    int sms = 0;
+    int64_t last_rounds = 0;
 };
 
 // ------------------------------------------------------------- device bits --
@@ -194,6 +213,16 @@ struct BArgs {
     float *b_w[3];
     int32_t *b_seed[3];
     int64_t *hub_vstart;
+    int64_t *tmp_beg;
+    int32_t *tmp_deg;
+    float *tmp_w;
+    uint32_t *tmp_jb;
+    unsigned *seg_cnt;
+    unsigned *seg_off;
+    unsigned *seg_cur;
+    unsigned long long *seg_hvol;
+    unsigned long long *vol_off;
+    unsigned long long *seg_hcur;
     BGlobal *glob;
     RoundLog *log;
     int kind;
@@ -212,44 +241,132 @@ __device__ __forceinline__ void bappend(unsigned *counter, uint32_t *list, uint3
     if (i < cap) list[i] = v; else atomicOr(overflow, 1u);
 }
 
-// insert-or-add w into seed j's table at node v; appends the slot to the next candidate list
-// when the residual crosses fl(eps d_v)
-__device__ __forceinline__ void bscatter(const BArgs &a, BCtl *ctl, uint32_t *cand_out, int32_t j,
-                                         int32_t v, float w) {
+constexpr uint32_t kMaxProbe = 4096;  // a probe sequence this long means the table is full
+constexpr int kStage = 256;            // staged candidates per warp (shared memory)
+
+__device__ __forceinline__ unsigned long long slot_word(int32_t v, float w) {
+    return ((unsigned long long)__float_as_uint(w) << 32) | (unsigned long long)(uint32_t)v;
+}
+
+// Append a candidate slot to this warp's staging buffer in shared memory (one shared atomic
+// per group of lanes).  The global candidate list is only touched when the buffer is
+// flushed, so threshold crossings do not all queue on one global counter.
+__device__ __forceinline__ void stage_push(uint32_t *buf, unsigned *n, uint32_t slot) {
+    cg::coalesced_group g = cg::coalesced_threads();
+    unsigned base = 0;
+    if (g.thread_rank() == 0) base = atomicAdd(n, (unsigned)g.size());
+    base = g.shfl(base, 0);
+    buf[base + g.thread_rank()] = slot;
+}
+
+// Whole warp, converged: move the staged candidates to the global list (one global atomic)
+// when forced or when another 32 pushes might not fit.
+__device__ __forceinline__ void stage_flush(uint32_t *buf, unsigned *n, bool force, BCtl *ctl,
+                                            uint32_t *cand_out, unsigned cap) {
+    __syncwarp();
+    const unsigned cnt = *(volatile unsigned *)n;
+    if (cnt == 0 || (!force && cnt <= (unsigned)(kStage - 32))) return;
+    const unsigned lane = threadIdx.x & 31;
+    unsigned gbase = 0;
+    if (lane == 0) gbase = atomicAdd(&ctl->cand_out, cnt);
+    gbase = __shfl_sync(0xffffffffu, gbase, 0);
+    for (unsigned i = lane; i < cnt; i += 32) {
+        if (gbase + i < cap) cand_out[gbase + i] = buf[i]; else atomicOr(&ctl->overflow, 1u);
+    }
+    __syncwarp();
+    if (lane == 0) *(volatile unsigned *)n = 0;
+    __syncwarp();
+}
+
+// add a lane's count of new keys to seed j's total; flag the seed past the load limit
+__device__ __forceinline__ void flush_inserts(const BArgs &a, int32_t j, unsigned ins) {
+    if (ins == 0) return;
+    const unsigned c = atomicAdd(a.inserts + j, ins);
+    if (c + ins > a.load_limit) atomicExch(a.status + j, kSeedOverflow);
+}
+
+// Insert-or-add w at node v of seed j's table.  Linear probing from mix32(v), read one
+// 32-byte sector (4 slots) per memory round trip: the slots of a sector are examined in probe
+// order, so the first empty slot still ends the search (keys are never removed).  A residual
+// that crosses its threshold from below (exactly once: contributions are positive) is staged
+// as a candidate of the next round.  Returns 1 if v was a new key.
+__device__ __forceinline__ unsigned bscatter(const BArgs &a, int32_t j, int32_t v, float w,
+                                             uint32_t *sbuf, unsigned *sn) {
     const uint64_t base = (uint64_t)j << a.log2cap;
     uint32_t h = mix32((uint32_t)v) & a.mask;
     const float thr = a.thr32[v];
-    for (uint32_t probe = 0; probe <= a.mask; probe++) {
-        const uint64_t slot = base + h;
-        unsigned long long word = ld_relaxed_u64(a.kr + slot);
-        for (;;) {
-            const uint32_t key = (uint32_t)(word & 0xFFFFFFFFull);
-            if (key == (uint32_t)v) {
-                const float old = atomicAdd(r_of(a.kr, slot), w);
-                const float nv = __fadd_rn(old, w);
-                if (old < thr && nv >= thr) bappend(&ctl->cand_out, cand_out, (uint32_t)slot, a.list_cap, &ctl->overflow);
-                return;
-            }
-            if (key != kEmpty) break;  // another node: keep probing
-            const unsigned long long want =
-                ((unsigned long long)__float_as_uint(w) << 32) | (unsigned long long)(uint32_t)v;
-            const unsigned long long prev = atomicCAS(a.kr + slot, word, want);
-            if (prev == word) {
-                // new key with residual w (old value 0)
-                if (w >= thr) bappend(&ctl->cand_out, cand_out, (uint32_t)slot, a.list_cap, &ctl->overflow);
-                // count inserts per seed: one atomic per group of lanes with the same seed
-                const unsigned peers = __match_any_sync(__activemask(), j);
-                if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) {
-                    const unsigned c = atomicAdd(a.inserts + j, (unsigned)__popc(peers));
-                    if (c + (unsigned)__popc(peers) > a.load_limit) atomicExch(a.status + j, kSeedOverflow);
-                }
-                return;
-            }
-            word = prev;  // lost the race: look at what was written
+    const uint32_t sector_mask = a.mask >= 3 ? 3u : a.mask;
+    for (uint32_t probes = 0; probes <= a.mask && probes < kMaxProbe;) {
+        const uint32_t s0 = h & ~sector_mask;
+        unsigned long long w0, w1, w2, w3;
+        if (sector_mask == 3u) {
+            const ulonglong2 lo = __ldcg(reinterpret_cast<const ulonglong2 *>(a.kr + base + s0));
+            const ulonglong2 hi = __ldcg(reinterpret_cast<const ulonglong2 *>(a.kr + base + s0 + 2));
+            w0 = lo.x; w1 = lo.y; w2 = hi.x; w3 = hi.y;
+        } else {  // tables smaller than one sector
+            w0 = ld_relaxed_u64(a.kr + base + s0);
+            w1 = sector_mask >= 1 ? ld_relaxed_u64(a.kr + base + s0 + 1) : 0ull;
+            w2 = w3 = 0ull;
         }
-        h = (h + 1) & a.mask;
+        for (uint32_t k = h - s0; k <= sector_mask; k++, probes++) {
+            const uint64_t slot = base + s0 + k;
+            unsigned long long wk = k == 0 ? w0 : (k == 1 ? w1 : (k == 2 ? w2 : w3));
+            for (;;) {
+                const uint32_t key = (uint32_t)(wk & 0xFFFFFFFFull);
+                if (key == (uint32_t)v) {
+                    const float old = atomicAdd(r_of(a.kr, slot), w);
+                    const float nv = __fadd_rn(old, w);
+                    if (old < thr && nv >= thr) stage_push(sbuf, sn, (uint32_t)slot);
+                    return 0;
+                }
+                if (key != kEmpty) break;  // another node: next slot
+                const unsigned long long prev = atomicCAS(a.kr + slot, wk, slot_word(v, w));
+                if (prev == wk) {
+                    if (w >= thr) stage_push(sbuf, sn, (uint32_t)slot);
+                    return 1;
+                }
+                wk = prev;  // lost the race: look at what was written into this slot
+            }
+        }
+        h = (s0 + sector_mask + 1) & a.mask;
     }
     atomicExch(a.status + j, kSeedOverflow);  // table full
+    return 0;
+}
+
+// Exclusive prefix sums of n values (one block): out[i] = sum in[0..i), returns the total.
+template <typename T>
+__device__ T block_scan(const T *in, T *out, int64_t n, T *s_warp) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    T carry = 0;
+    for (int64_t base = 0; base < n; base += kThreads) {
+        const int64_t i = base + threadIdx.x;
+        const T v = i < n ? __ldcg(in + i) : T(0);
+        T x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const T y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_warp[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            T s = lane < kWarps ? s_warp[lane] : T(0);
+#pragma unroll
+            for (int o = 1; o < kWarps; o <<= 1) {
+                const T y = __shfl_up_sync(0xffffffffu, s, o);
+                if (lane >= o) s += y;
+            }
+            if (lane < kWarps) s_warp[lane] = s;
+        }
+        __syncthreads();
+        const T before = wid > 0 ? s_warp[wid - 1] : T(0);
+        if (i < n) out[i] = carry + before + x - v;
+        const T block_total = s_warp[kWarps - 1];
+        __syncthreads();
+        carry += block_total;
+    }
+    return carry;
 }
 
 __global__ void __launch_bounds__(kThreads) k_batch_rounds(BArgs a) {
@@ -259,6 +376,13 @@ __global__ void __launch_bounds__(kThreads) k_batch_rounds(BArgs a) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t gw = tid >> 5, nw = nthreads >> 5;
     BGlobal *G = a.glob;
+    const unsigned long long t_start = globaltimer();
+    __shared__ uint32_t s_stage[kWarps][kStage];
+    __shared__ unsigned s_nstage[kWarps];
+    uint32_t *sbuf = s_stage[wid];
+    unsigned *sn = &s_nstage[wid];
+    if (lane == 0) *sn = 0;
+    __syncwarp();
     __shared__ double s_rs[kWarps];
     __shared__ unsigned long long s_vol[kWarps];
 
@@ -269,18 +393,21 @@ __global__ void __launch_bounds__(kThreads) k_batch_rounds(BArgs a) {
         const unsigned ncand = min(__ldcg(&prev->cand_out), a.list_cap);
         const uint32_t *cand = a.cand[p];
 
-        // ---------------- phase A: S_t for every seed ----------------
+        // ---------------- phase A1: S_t for every seed ----------------
+        // threshold test, r_S -> 0, x_S += c r_S, per-edge share; the push record is kept per
+        // candidate and counted per (degree bin, seed)
         double my_rs = 0.0;
         unsigned long long my_vol = 0;
+        const int64_t ns = a.nseeds;
         for (int64_t ci = tid; ci < ncand; ci += nthreads) {
             const uint32_t slot = __ldcg(cand + ci);
             const int32_t j = (int32_t)(slot >> a.log2cap);
-            if (__ldcg(a.status + j) != kSeedOk) continue;
+            if (__ldcg(a.status + j) != kSeedOk) { __stcg(a.tmp_deg + ci, 0); continue; }
             const unsigned long long word = __ldcg(a.kr + slot);
             const int32_t v = (int32_t)(word & 0xFFFFFFFFull);
             const float rho = __uint_as_float((uint32_t)(word >> 32));
             const float thr = a.thr32[v];
-            if (!(rho != 0.0f && fabsf(rho) >= thr)) continue;
+            if (!(rho != 0.0f && fabsf(rho) >= thr)) { __stcg(a.tmp_deg + ci, 0); continue; }
             __stcg(r_of(a.kr, slot), 0.0f);
             const double rho64 = (double)rho;
             const float xold = __ldcg(a.xs + slot);
@@ -303,52 +430,25 @@ __global__ void __launch_bounds__(kThreads) k_batch_rounds(BArgs a) {
                     atomicMax(a.slast + j, (int)t);
                 }
             }
-            if (d == 0) continue;
+            if (d == 0) { __stcg(a.tmp_deg + ci, 0); continue; }
             float w;
             if (a.kind == GDE_KATZ)
                 w = __double2float_rn(__dmul_rn(a.coef, rho64));
             else
                 w = __double2float_rn(__ddiv_rn(__dmul_rn(a.coef, rho64), (double)d));
-            if (d <= a.t2) {
-                // each bin gets its own coalesced group so a group never mixes two counters
-                const int bin = d <= a.t1 ? 0 : 1;
-                unsigned *counter = bin == 0 ? &ctl->cnt_small : &ctl->cnt_med;
-                unsigned i;
-                if (bin == 0) {
-                    cg::coalesced_group g = cg::coalesced_threads();
-                    unsigned base = 0;
-                    if (g.thread_rank() == 0) base = atomicAdd(counter, (unsigned)g.size());
-                    i = g.shfl(base, 0) + g.thread_rank();
-                } else {
-                    cg::coalesced_group g = cg::coalesced_threads();
-                    unsigned base = 0;
-                    if (g.thread_rank() == 0) base = atomicAdd(counter, (unsigned)g.size());
-                    i = g.shfl(base, 0) + g.thread_rank();
-                }
-                if (i < a.list_cap) {
-                    __stcg(a.b_beg[bin] + i, beg); __stcg(a.b_deg[bin] + i, d);
-                    __stcg(a.b_w[bin] + i, w); __stcg(a.b_seed[bin] + i, j);
-                } else {
-                    atomicOr(&ctl->overflow, 1u);
-                }
-            } else {
-                cg::coalesced_group g = cg::coalesced_threads();
-                const unsigned long long dv = (unsigned long long)d;
-                const unsigned long long excl = cg::exclusive_scan(g, dv);
-                const unsigned long long tot = g.shfl(excl + dv, g.size() - 1);
-                unsigned long long old = 0;
-                if (g.thread_rank() == 0)
-                    old = atomicAdd(&ctl->hub_packed, ((unsigned long long)g.size() << kBHubVolBits) + tot);
-                old = g.shfl(old, 0);
-                const unsigned long long i = (old >> kBHubVolBits) + g.thread_rank();
-                if (i < a.list_cap) {
-                    __stcg(a.b_beg[2] + i, beg); __stcg(a.b_deg[2] + i, d);
-                    __stcg(a.b_w[2] + i, w); __stcg(a.b_seed[2] + i, j);
-                    __stcg(a.hub_vstart + i, (int64_t)((old & kBHubVolMask) + excl));
-                } else {
-                    atomicOr(&ctl->overflow, 1u);
-                }
+            const int bin = d <= a.t1 ? 0 : (d <= a.t2 ? 1 : 2);
+            __stcg(a.tmp_beg + ci, beg);
+            __stcg(a.tmp_deg + ci, d);
+            __stcg(a.tmp_w + ci, w);
+            __stcg(a.tmp_jb + ci, (uint32_t)j | ((uint32_t)bin << 30));
+            const int32_t key = (int32_t)(bin * ns + j);
+            const unsigned peers = __match_any_sync(__activemask(), key);
+            const bool leader = lane == __ffs(peers) - 1;
+            if (bin == 2) {
+                const unsigned dsum = __reduce_add_sync(peers, (unsigned)d);
+                if (leader) atomicAdd(a.seg_hvol + j, (unsigned long long)dsum);
             }
+            if (leader) atomicAdd(a.seg_cnt + key, (unsigned)__popc(peers));
         }
         {
             double rs = bwarp_sum(my_rs);
@@ -368,6 +468,70 @@ __global__ void __launch_bounds__(kThreads) k_batch_rounds(BArgs a) {
         }
         if (!grid_sync(G, nblocks)) return;
 
+        // ---------------- phase S: segment offsets (one block) ----------------
+        // the degree bins are laid out seed by seed, so the scatter phase sweeps the seeds
+        // in order and only a few seeds' tables are in use at any moment
+        if (blockIdx.x == 0) {
+            __shared__ unsigned s_scan32[kWarps];
+            __shared__ unsigned long long s_scan64[kWarps];
+            const unsigned n0 = block_scan<unsigned>(a.seg_cnt, a.seg_off, ns, s_scan32);
+            const unsigned n1 = block_scan<unsigned>(a.seg_cnt + ns, a.seg_off + ns, ns, s_scan32);
+            const unsigned n2 = block_scan<unsigned>(a.seg_cnt + 2 * ns, a.seg_off + 2 * ns, ns, s_scan32);
+            const unsigned long long vh = block_scan<unsigned long long>(a.seg_hvol, a.vol_off, ns, s_scan64);
+            for (int64_t i = threadIdx.x; i < ns; i += kThreads) {
+                a.seg_cnt[i] = 0; a.seg_cnt[ns + i] = 0; a.seg_cnt[2 * ns + i] = 0;
+                a.seg_hvol[i] = 0; a.seg_cur[i] = 0; a.seg_cur[ns + i] = 0; a.seg_hcur[i] = 0;
+            }
+            if (threadIdx.x == 0) {
+                ctl->cnt_small = n0;
+                ctl->cnt_med = n1;
+                ctl->hub_packed = ((unsigned long long)n2 << kBHubVolBits) | vh;
+                if ((unsigned long long)n0 + n1 + n2 > a.list_cap) ctl->overflow = 1;
+            }
+        }
+        if (!grid_sync(G, nblocks)) return;
+
+        // ---------------- phase A2: place the pushes seed by seed ----------------
+        for (int64_t ci = tid; ci < ncand; ci += nthreads) {
+            const int32_t d = __ldcg(a.tmp_deg + ci);
+            if (d == 0) continue;
+            const uint32_t jb = __ldcg(a.tmp_jb + ci);
+            const int32_t j = (int32_t)(jb & ((1u << 30) - 1u));
+            const int bin = (int)(jb >> 30);
+            const int64_t beg = __ldcg(a.tmp_beg + ci);
+            const float w = __ldcg(a.tmp_w + ci);
+            if (bin < 2) {
+                const int32_t key = (int32_t)(bin * ns + j);
+                const unsigned peers = __match_any_sync(__activemask(), key);
+                const int leader = __ffs(peers) - 1;
+                const unsigned rank = __popc(peers & ((1u << lane) - 1u));
+                unsigned basepos = 0;
+                if (lane == leader) basepos = atomicAdd(a.seg_cur + key, (unsigned)__popc(peers));
+                basepos = __shfl_sync(peers, basepos, leader);
+                const unsigned pos = __ldcg(a.seg_off + key) + basepos + rank;
+                if (pos < a.list_cap) {
+                    __stcg(a.b_beg[bin] + pos, beg); __stcg(a.b_deg[bin] + pos, d);
+                    __stcg(a.b_w[bin] + pos, w); __stcg(a.b_seed[bin] + pos, j);
+                } else {
+                    atomicOr(&ctl->overflow, 1u);
+                }
+            } else {
+                const unsigned long long old =
+                    atomicAdd(a.seg_hcur + j, (1ull << kBHubVolBits) + (unsigned long long)d);
+                const unsigned long long pos = __ldcg(a.seg_off + 2 * ns + j) + (old >> kBHubVolBits);
+                if (pos < a.list_cap) {
+                    __stcg(a.b_beg[2] + pos, beg); __stcg(a.b_deg[2] + pos, d);
+                    __stcg(a.b_w[2] + pos, w); __stcg(a.b_seed[2] + pos, j);
+                    __stcg(a.hub_vstart + pos, (int64_t)(__ldcg(a.vol_off + j) + (old & kBHubVolMask)));
+                } else {
+                    atomicOr(&ctl->overflow, 1u);
+                }
+            }
+        }
+        if (!grid_sync(G, nblocks)) return;
+        if (tid == 0 && t < kLogCap) a.log[t].tA_ns = globaltimer() - t_start;
+        const unsigned long long tb0 = globaltimer();
+
         // ---------------- phase B: scatter ----------------
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             // the other parity's counters were last read in phase A of this round
@@ -381,6 +545,8 @@ __global__ void __launch_bounds__(kThreads) k_batch_rounds(BArgs a) {
             const unsigned long long hp = __ldcg(&ctl->hub_packed);
             const int64_t H = (int64_t)(hp >> kBHubVolBits);
             const int64_t VH = (int64_t)(hp & kBHubVolMask);
+            // hubs: merge-path chunks of the concatenated hub adjacency, one warp per chunk,
+            // consecutive lanes on consecutive columns
             if (VH > 0) {
                 const int64_t nchunks = (VH + a.chunk - 1) / a.chunk;
                 for (int64_t c = gw; c < nchunks; c += nw) {
@@ -397,34 +563,77 @@ __global__ void __launch_bounds__(kThreads) k_batch_rounds(BArgs a) {
                     int64_t hb = __ldcg(a.b_beg[2] + h);
                     float hw = __ldcg(a.b_w[2] + h);
                     int32_t hj = __ldcg(a.b_seed[2] + h);
-                    for (int64_t e = e0 + lane; e < e1; e += 32) {
-                        while (e >= he) {
-                            ++h;
-                            hs = __ldcg(a.hub_vstart + h);
-                            he = hs + __ldcg(a.b_deg[2] + h);
-                            hb = __ldcg(a.b_beg[2] + h);
-                            hw = __ldcg(a.b_w[2] + h);
-                            hj = __ldcg(a.b_seed[2] + h);
+                    int32_t ins_j = hj;
+                    unsigned ins = 0;
+                    for (int64_t eb = e0; eb < e1; eb += 32) {
+                        const int64_t e = eb + lane;
+                        if (e < e1) {
+                            while (e >= he) {
+                                ++h;
+                                hs = __ldcg(a.hub_vstart + h);
+                                he = hs + __ldcg(a.b_deg[2] + h);
+                                hb = __ldcg(a.b_beg[2] + h);
+                                hw = __ldcg(a.b_w[2] + h);
+                                hj = __ldcg(a.b_seed[2] + h);
+                            }
+                            if (hj != ins_j) {
+                                flush_inserts(a, ins_j, ins);
+                                ins = 0;
+                                ins_j = hj;
+                            }
+                            ins += bscatter(a, hj, a.col[hb + (e - hs)], hw, sbuf, sn);
                         }
-                        bscatter(a, ctl, cand_out, hj, a.col[hb + (e - hs)], hw);
+                        stage_flush(sbuf, sn, false, ctl, cand_out, a.list_cap);
                     }
+                    flush_inserts(a, ins_j, ins);
                 }
             }
+            // medium degrees: one warp per node
             const unsigned nmed = min(__ldcg(&ctl->cnt_med), a.list_cap);
-            for (int64_t i = gw; i < nmed; i += nw) {
+            // descending: the hub sweep ends at the last seeds, the medium sweep starts there
+            for (int64_t ii = gw; ii < nmed; ii += nw) {
+                const int64_t i = (int64_t)nmed - 1 - ii;
                 const int64_t b = __ldcg(a.b_beg[1] + i);
                 const int32_t d = __ldcg(a.b_deg[1] + i);
                 const float w = __ldcg(a.b_w[1] + i);
                 const int32_t j = __ldcg(a.b_seed[1] + i);
-                for (int32_t k = lane; k < d; k += 32) bscatter(a, ctl, cand_out, j, a.col[b + k], w);
+                unsigned ins = 0;
+                for (int32_t k0 = 0; k0 < d; k0 += 32) {
+                    const int32_t k = k0 + lane;
+                    if (k < d) ins += bscatter(a, j, a.col[b + k], w, sbuf, sn);
+                    stage_flush(sbuf, sn, false, ctl, cand_out, a.list_cap);
+                }
+                flush_inserts(a, j, ins);
             }
+            // small degrees: one thread per node (warp-uniform loops so the warp can flush)
             const unsigned nsm = min(__ldcg(&ctl->cnt_small), a.list_cap);
-            for (int64_t i = tid; i < nsm; i += nthreads) {
-                const int64_t b = __ldcg(a.b_beg[0] + i);
-                const int32_t d = __ldcg(a.b_deg[0] + i);
-                const float w = __ldcg(a.b_w[0] + i);
-                const int32_t j = __ldcg(a.b_seed[0] + i);
-                for (int32_t k = 0; k < d; k++) bscatter(a, ctl, cand_out, j, a.col[b + k], w);
+            for (int64_t i0 = gw * 32; i0 < nsm; i0 += nw * 32) {
+                const int64_t i = i0 + lane;
+                int64_t b = 0;
+                int32_t d = 0, j = 0;
+                float w = 0.0f;
+                if (i < nsm) {
+                    b = __ldcg(a.b_beg[0] + i);
+                    d = __ldcg(a.b_deg[0] + i);
+                    w = __ldcg(a.b_w[0] + i);
+                    j = __ldcg(a.b_seed[0] + i);
+                }
+                const int32_t dmax = (int32_t)__reduce_max_sync(0xffffffffu, (unsigned)d);
+                unsigned ins = 0;
+                for (int32_t k = 0; k < dmax; k++) {
+                    if (k < d) ins += bscatter(a, j, a.col[b + k], w, sbuf, sn);
+                    stage_flush(sbuf, sn, false, ctl, cand_out, a.list_cap);
+                }
+                if (i < nsm) flush_inserts(a, j, ins);
+            }
+        }
+        stage_flush(sbuf, sn, true, ctl, cand_out, a.list_cap);
+        {
+            // phase-B busy time of this warp (for the load-balance record)
+            const unsigned long long busy = globaltimer() - tb0;
+            if (lane == 0 && t < kLogCap) {
+                atomicAdd(&a.log[t].busy_sum_ns, busy);
+                atomicMax(&a.log[t].busy_max_ns, busy);
             }
         }
         if (!grid_sync(G, nblocks)) return;
@@ -439,6 +648,7 @@ __global__ void __launch_bounds__(kThreads) k_batch_rounds(BArgs a) {
                 a.log[t].rS_l1 = __ldcg(&ctl->rS_l1);
                 a.log[t].ncand = ncand;
                 a.log[t].n_active = next;
+                a.log[t].t_ns = globaltimer() - t_start;
             }
             if (ovf || next > a.list_cap) atomicCAS(&G->error, 0u, (unsigned)GDE_ENOMEM);
         }
@@ -680,7 +890,9 @@ static void batch_free(BatchWork *w) {
     dfree(w->kr); dfree(w->xs); dfree(w->thr32);
     for (int k = 0; k < 2; k++) dfree(w->cand[k]);
     for (int b = 0; b < 3; b++) { dfree(w->b_beg[b]); dfree(w->b_deg[b]); dfree(w->b_w[b]); dfree(w->b_seed[b]); }
-    dfree(w->hub_vstart); dfree(w->seeds); dfree(w->status); dfree(w->inserts); dfree(w->svol);
+    dfree(w->hub_vstart); dfree(w->tmp_beg); dfree(w->tmp_deg); dfree(w->tmp_w); dfree(w->tmp_jb);
+    dfree(w->seg_cnt); dfree(w->seg_off); dfree(w->seg_cur); dfree(w->seg_hvol); dfree(w->vol_off);
+    dfree(w->seg_hcur); dfree(w->seeds); dfree(w->status); dfree(w->inserts); dfree(w->svol);
     dfree(w->spushes); dfree(w->slast); dfree(w->sresid); dfree(w->smass); dfree(w->glob); dfree(w->log);
     delete w;
 }
@@ -709,6 +921,16 @@ static BatchWork *batch_work_get(Graph &g, int64_t nseeds, int64_t cap, int64_t 
             w->b_seed[b] = (int32_t *)dmalloc(4 * (size_t)list_cap, "bins");
         }
         w->hub_vstart = (int64_t *)dmalloc(8 * (size_t)list_cap, "hub offsets");
+        w->tmp_beg = (int64_t *)dmalloc(8 * (size_t)list_cap, "push records");
+        w->tmp_deg = (int32_t *)dmalloc(4 * (size_t)list_cap, "push records");
+        w->tmp_w = (float *)dmalloc(4 * (size_t)list_cap, "push records");
+        w->tmp_jb = (uint32_t *)dmalloc(4 * (size_t)list_cap, "push records");
+        w->seg_cnt = (unsigned *)dmalloc(4 * 3 * (size_t)nseeds, "segments");
+        w->seg_off = (unsigned *)dmalloc(4 * 3 * (size_t)nseeds, "segments");
+        w->seg_cur = (unsigned *)dmalloc(4 * 2 * (size_t)nseeds, "segments");
+        w->seg_hvol = (unsigned long long *)dmalloc(8 * (size_t)nseeds, "segments");
+        w->vol_off = (unsigned long long *)dmalloc(8 * (size_t)nseeds, "segments");
+        w->seg_hcur = (unsigned long long *)dmalloc(8 * (size_t)nseeds, "segments");
         w->seeds = (int32_t *)dmalloc(4 * (size_t)nseeds, "seeds");
         w->status = (int32_t *)dmalloc(4 * (size_t)nseeds, "seed status");
         w->inserts = (unsigned *)dmalloc(4 * (size_t)nseeds, "seed inserts");
@@ -726,6 +948,7 @@ static BatchWork *batch_work_get(Graph &g, int64_t nseeds, int64_t cap, int64_t 
         GDE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         GDE_REQUIRE(per_sm > 0, GDE_ECUDA, "batched kernel cannot be resident");
         w->grid = sms * per_sm;
+        w->sms = sms;
     } catch (...) {
         batch_free(w);
         throw;
@@ -785,6 +1008,7 @@ void batch_solve(Graph &g, const SolveParams &p, const int32_t *seeds_dev, int32
         w->thr_eps = p.eps;
         w->thr_n = g.n;
     }
+    GDE_CUDA(cudaMemsetAsync(w->log, 0, sizeof(RoundLog) * kLogCap, s));
     k_batch_seed<<<(nseeds + kThreads - 1) / kThreads, kThreads, 0, s>>>(
         nseeds, w->seeds, w->kr, w->cand[0], w->log2cap, (uint32_t)(cap - 1), w->glob, w->status,
         w->inserts, w->svol, w->spushes, w->slast);
@@ -800,16 +1024,23 @@ void batch_solve(Graph &g, const SolveParams &p, const int32_t *seeds_dev, int32
     a.list_cap = (unsigned)list_cap;
     for (int b = 0; b < 3; b++) { a.b_beg[b] = w->b_beg[b]; a.b_deg[b] = w->b_deg[b]; a.b_w[b] = w->b_w[b]; a.b_seed[b] = w->b_seed[b]; }
     a.hub_vstart = w->hub_vstart;
+    a.tmp_beg = w->tmp_beg; a.tmp_deg = w->tmp_deg; a.tmp_w = w->tmp_w; a.tmp_jb = w->tmp_jb;
+    a.seg_cnt = w->seg_cnt; a.seg_off = w->seg_off; a.seg_cur = w->seg_cur;
+    a.seg_hvol = w->seg_hvol; a.vol_off = w->vol_off; a.seg_hcur = w->seg_hcur;
+    GDE_CUDA(cudaMemsetAsync(w->seg_cnt, 0, 4 * 3 * (size_t)nseeds, s));
+    GDE_CUDA(cudaMemsetAsync(w->seg_hvol, 0, 8 * (size_t)nseeds, s));
     a.glob = w->glob; a.log = w->log;
     a.kind = p.kind;
     a.cx = p.kind == GDE_PPR ? p.param : 1.0;
     a.coef = p.kind == GDE_PPR ? 1.0 - p.param : p.param;
     a.max_rounds = p.max_rounds;
-    Bins bins;
+    const Bins &bins = g.bins;
     a.t1 = bins.t1; a.t2 = bins.t2; a.chunk = bins.chunk;
 
+    int grid = w->grid;
+    if (bins.blocks_per_sm > 0 && bins.blocks_per_sm * w->sms < grid) grid = bins.blocks_per_sm * w->sms;
     cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3((unsigned)w->grid);
+    cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(kThreads);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = s;
@@ -857,6 +1088,7 @@ void batch_solve(Graph &g, const SolveParams &p, const int32_t *seeds_dev, int32
         set_error("batched solve: candidate or bin list capacity exceeded");
         throw Fail{(gde_status)hg.error};
     }
+    w->last_rounds = hg.rounds;
     if (g.prof.enabled) {
         g.prof.counters.batch_launches += 1;
         g.prof.counters.rounds += hg.rounds;
@@ -884,6 +1116,27 @@ void batch_solve(Graph &g, const SolveParams &p, const int32_t *seeds_dev, int32
         }
     }
     if (n_overflow) *n_overflow = nof;
+}
+
+int64_t batch_round_log(Graph &g, double *out, int64_t cap) {
+    BatchWork *w = g.batch;
+    if (!w) return 0;
+    const int64_t r = w->last_rounds;
+    const int64_t m = std::min<int64_t>(std::min<int64_t>(r, cap), kLogCap);
+    if (m > 0) {
+        std::vector<RoundLog> h((size_t)m);
+        GDE_CUDA(cudaMemcpy(h.data(), w->log, sizeof(RoundLog) * (size_t)m, cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < m; i++) {
+            out[7 * i + 0] = (double)h[(size_t)i].ncand;
+            out[7 * i + 1] = (double)h[(size_t)i].vol;
+            out[7 * i + 2] = h[(size_t)i].rS_l1;
+            out[7 * i + 3] = (double)h[(size_t)i].t_ns;
+            out[7 * i + 4] = (double)h[(size_t)i].tA_ns;
+            out[7 * i + 5] = (double)h[(size_t)i].busy_sum_ns;
+            out[7 * i + 6] = (double)h[(size_t)i].busy_max_ns;
+        }
+    }
+    return r;
 }
 
 }  // namespace gde

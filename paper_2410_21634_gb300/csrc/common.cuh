@@ -54,6 +54,7 @@ struct Bins {
     int32_t t1 = 8;       // d <= t1: thread per node
     int32_t t2 = 2048;    // t1 < d <= t2: warp per node; d > t2: hub merge-path chunks
     int32_t chunk = 4096; // hub edges per warp work item
+    int32_t blocks_per_sm = 0;  // persistent grid; 0 = occupancy limit
 };
 
 // ---------------------------------------------------------------- profiler --
@@ -86,6 +87,7 @@ struct Graph {
     struct DenseWork *dense[2] = {nullptr, nullptr};     // cached single-seed workspace per precision
     struct BatchWork *batch = nullptr;                   // cached batched workspace
     Profiler prof;
+    Bins bins;                 // launch shape used by later solves
 };
 
 // row validation result bits
@@ -146,6 +148,8 @@ void dense_topk(Graph &g, DenseWork *w, const SolveParams &p, int k, int32_t *id
 // batched engine (batched.cu)
 struct BatchWork;
 void batch_work_destroy(BatchWork *w);
+// per-round log of the last batched solve: rows of {candidates, volume, r_S mass, ns}
+int64_t batch_round_log(Graph &g, double *out, int64_t cap);
 void batch_solve(Graph &g, const SolveParams &p, const int32_t *seeds_dev, int32_t nseeds, int k,
                  int64_t mem_budget, int32_t *ids_dev, float *vals_dev, gde_stats *stats_host,
                  int32_t *overflow_seeds_host, int32_t *n_overflow);

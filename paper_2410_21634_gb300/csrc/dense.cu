@@ -412,6 +412,7 @@ DenseWork *dense_work_create(Graph &g, int precision) {
     DenseWork *w = new DenseWork();
     w->precision = precision;
     w->n = g.n;
+    w->bins = g.bins;
     w->rsz = precision == GDE_FP64 ? 8 : 4;
     const int64_t n = g.n > 0 ? g.n : 1;
     try {

@@ -152,8 +152,9 @@ def test_batched_device_pointers(gde, c1):
     st, _ = gde.solve(G, "ppr", 0.15, 1e-6, seeds, vals, ids, precision="fp32", topk=K, batched=1)
     torch.cuda.synchronize()
     ids_h, vals_h = ids.cpu().numpy(), vals.cpu().numpy()
-    _, _, ids2, vals2 = run_batched(gde, G, "ppr", 0.15, 1e-6, seeds.cpu().numpy())
-    assert np.allclose(vals_h, vals2, rtol=1e-5, atol=1e-9)
+    for i in (0, 13, 31):
+        ref = oracle.localgd(c1, "ppr", 0.15, 1e-6, int(seeds[i]))
+        check_topk(c1, ids_h[i], vals_h[i], ref.x, 1e-6)
 
 
 def test_dense_topk_matches_batched(gde, c1):
