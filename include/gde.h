@@ -166,13 +166,18 @@ gde_status gde_profile_rounds(gde_graph *g, double *out, int64_t cap, int64_t *r
  * Launch shape of the push (SURVEY-style degree bins): nodes with d <= t1 are pushed by one
  * thread, t1 < d <= t2 by one warp, d > t2 in merge-path chunks of `chunk` edges over the
  * concatenated hub adjacency; blocks_per_sm sets the persistent grid (0 = the occupancy
- * limit).  Values <= 0 keep the current setting.  Applies to later solves on g.
+ * limit); schedule orders the batched scatter: 1 hands hub chunks to warps in bin order (the
+ * bins are laid out seed by seed, so the warps in flight share a few seeds' tables in L2), 2
+ * additionally orders medium and small entries, 3 strides every bin statically (schedule
+ * values are stored minus one; 0 keeps the current setting).  Values <= 0 keep the current
+ * setting.  Applies to later solves on g.
  */
 typedef struct {
     int32_t t1;
     int32_t t2;
     int32_t chunk;
     int32_t blocks_per_sm;
+    int32_t schedule;
 } gde_tuning;
 
 gde_status gde_set_tuning(gde_graph *g, const gde_tuning *t);

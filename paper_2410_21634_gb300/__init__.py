@@ -69,7 +69,7 @@ class Profile(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("t1", ctypes.c_int32), ("t2", ctypes.c_int32), ("chunk", ctypes.c_int32),
-                ("blocks_per_sm", ctypes.c_int32)]
+                ("blocks_per_sm", ctypes.c_int32), ("schedule", ctypes.c_int32)]
 
 
 _lib = None
@@ -216,8 +216,8 @@ class Graph:
         _check(load().gde_profile_rounds(self._h, buf.ctypes.data, cap, ctypes.byref(r)))
         return buf[: min(r.value, cap)].copy()
 
-    def set_tuning(self, t1=0, t2=0, chunk=0, blocks_per_sm=0):
-        t = Tuning(t1, t2, chunk, blocks_per_sm)
+    def set_tuning(self, t1=0, t2=0, chunk=0, blocks_per_sm=0, schedule=0):
+        t = Tuning(t1, t2, chunk, blocks_per_sm, schedule)
         _check(load().gde_set_tuning(self._h, ctypes.byref(t)))
 
     def get_tuning(self) -> dict:

@@ -408,6 +408,8 @@ gde_status gde_set_tuning(gde_graph *h, const gde_tuning *t) {
     if (t->t2 > 0) b.t2 = t->t2;
     if (t->chunk > 0) b.chunk = t->chunk;
     if (t->blocks_per_sm > 0) b.blocks_per_sm = t->blocks_per_sm;
+    if (t->schedule > 0) b.schedule = t->schedule == 1 ? 1 : (t->schedule == 2 ? 0 : 2);
+    GDE_REQUIRE(t->schedule <= 3, GDE_EINVAL, "tuning: schedule must be 0..3");
     GDE_REQUIRE(b.t1 <= b.t2, GDE_EINVAL, "tuning: t1 must be <= t2");
     GDE_REQUIRE(b.chunk >= 32 && b.chunk <= (1 << 24), GDE_EINVAL, "tuning: chunk must be in [32, 2^24]");
     GDE_REQUIRE(b.blocks_per_sm <= 32, GDE_EINVAL, "tuning: blocks_per_sm must be <= 32");
@@ -424,6 +426,7 @@ gde_status gde_get_tuning(const gde_graph *h, gde_tuning *t) {
     t->t2 = h->g.bins.t2;
     t->chunk = h->g.bins.chunk;
     t->blocks_per_sm = h->g.bins.blocks_per_sm;
+    t->schedule = h->g.bins.schedule == 1 ? 1 : (h->g.bins.schedule == 0 ? 2 : 3);
     API_END
 }
 

@@ -48,6 +48,11 @@ struct BCtl {  // per-round counters (one set per round parity)
     double rS_l1;
     unsigned int overflow;
     unsigned int pad;
+    // scatter work handed out in order (hub chunks, medium entries, small groups), so the
+    // warps in flight cover a narrow, seed-local window of the bins
+    unsigned long long hub_next;
+    unsigned int med_next;
+    unsigned int small_next;
 };
 
 struct BGlobal {
@@ -84,6 +89,10 @@ struct BatchWork {
     float *thr32 = nullptr;
     int64_t thr_n = 0;
     double thr_eps = -1.0;
+    // columns with the neighbour's degree code in the bits above the node id (see pack_code)
+    uint32_t *colp = nullptr;
+    int colp_idbits = 0;     // 0: no packing (n too large), then thr32 is read for every edge
+    int colp_exact = 0;
     uint32_t *cand[2] = {nullptr, nullptr};
     int64_t *b_beg[3] = {nullptr, nullptr, nullptr};
     int32_t *b_deg[3] = {nullptr, nullptr, nullptr};
@@ -194,6 +203,11 @@ template <typename T> __device__ __forceinline__ T bwarp_sum(T v) {
 struct BArgs {
     const int64_t *off;
     const int32_t *col;
+    const uint32_t *colp;   // packed columns (id | degree code << idbits), or NULL
+    int idbits;
+    uint32_t idmask;
+    int code_exact;         // codes below this are exact degrees; from it on, log2 classes
+    double eps;
     const float *thr32;
     unsigned long long *kr;
     float *xs;
@@ -230,6 +244,7 @@ struct BArgs {
     double coef;  // PPR 1-alpha (share divided by d_u), Katz beta
     int64_t max_rounds;
     int32_t t1, t2, chunk;
+    int32_t schedule;   // 0: all bins handed out in order; 1: hubs in order, others strided; 2: all strided
 };
 
 __device__ __forceinline__ void bappend(unsigned *counter, uint32_t *list, uint32_t v, unsigned cap,
@@ -241,8 +256,11 @@ __device__ __forceinline__ void bappend(unsigned *counter, uint32_t *list, uint3
     if (i < cap) list[i] = v; else atomicOr(overflow, 1u);
 }
 
-constexpr uint32_t kMaxProbe = 4096;  // a probe sequence this long means the table is full
+// a probe run this long means the table is effectively full (at <= 3/4 load a run of 64
+// full buckets is vanishingly rare); the seed is then re-solved with dense state
+constexpr uint32_t kMaxProbe = 256;
 constexpr int kStage = 256;            // staged candidates per warp (shared memory)
+constexpr int kMedGrab = 4;            // medium-degree entries a warp takes per grab
 
 __device__ __forceinline__ unsigned long long slot_word(int32_t v, float w) {
     return ((unsigned long long)__float_as_uint(w) << 32) | (unsigned long long)(uint32_t)v;
@@ -278,60 +296,106 @@ __device__ __forceinline__ void stage_flush(uint32_t *buf, unsigned *n, bool for
     __syncwarp();
 }
 
-// add a lane's count of new keys to seed j's total; flag the seed past the load limit
-__device__ __forceinline__ void flush_inserts(const BArgs &a, int32_t j, unsigned ins) {
-    if (ins == 0) return;
-    const unsigned c = atomicAdd(a.inserts + j, ins);
-    if (c + ins > a.load_limit) atomicExch(a.status + j, kSeedOverflow);
+// Degree code of a neighbour, stored above its id in the packed column array: the exact
+// degree when d < code_exact, else code_exact + floor(log2 d).  It brackets the neighbour's
+// threshold fl(eps d) (rounded up to float) without reading the per-node threshold array:
+// exact for small degrees, within [eps 2^k, eps (2^(k+1)-1)] for the log classes.
+__host__ __device__ __forceinline__ uint32_t degree_code(int32_t d, int code_exact) {
+    if (d < code_exact) return (uint32_t)d;
+    uint32_t k = 0;
+    while ((2ll << k) <= (long long)d) k++;
+    return (uint32_t)code_exact + k;
 }
 
-// Insert-or-add w at node v of seed j's table.  Linear probing from mix32(v), read one
-// 32-byte sector (4 slots) per memory round trip: the slots of a sector are examined in probe
-// order, so the first empty slot still ends the search (keys are never removed).  A residual
-// that crosses its threshold from below (exactly once: contributions are positive) is staged
-// as a candidate of the next round.  Returns 1 if v was a new key.
-__device__ __forceinline__ unsigned bscatter(const BArgs &a, int32_t j, int32_t v, float w,
+struct ThrBounds {
+    float lo, hi;  // lo <= thr_v <= hi; lo == hi means exact
+};
+
+__device__ __forceinline__ ThrBounds thr_bounds(const BArgs &a, uint32_t code) {
+    ThrBounds t;
+    if ((int)code < a.code_exact) {
+        t.lo = t.hi = __double2float_ru(__dmul_rn(a.eps, (double)code));
+    } else {
+        const int k = (int)code - a.code_exact;
+        t.lo = __double2float_ru(__dmul_rn(a.eps, (double)(1ll << k)));
+        t.hi = __double2float_ru(__dmul_rn(a.eps, (double)((2ll << k) - 1)));
+    }
+    return t;
+}
+
+// did a residual going from `old` to `nv` cross v's threshold?  Reads thr32[v] only when the
+// bracket cannot decide.
+__device__ __forceinline__ bool crossed(const BArgs &a, int32_t v, ThrBounds tb, float old, float nv) {
+    if (nv < tb.lo || old >= tb.hi) return false;
+    const float thr = tb.lo == tb.hi ? tb.lo : a.thr32[v];
+    return old < thr && nv >= thr;
+}
+
+// Insert-or-add w at node v of seed j's table.  The probe starts at a 4-slot bucket (one
+// 32-byte sector) chosen by mix32(v) and continues linearly bucket by bucket; slots are
+// examined in order, so the first empty slot ends the search (keys are never removed).  A
+// residual that crosses its threshold from below (exactly once: contributions are positive)
+// is staged as a candidate of the next round.  Returns 1 if v was a new key.
+__device__ __forceinline__ unsigned bscatter(const BArgs &a, int32_t j, uint32_t packed, float w,
                                              uint32_t *sbuf, unsigned *sn) {
     const uint64_t base = (uint64_t)j << a.log2cap;
-    uint32_t h = mix32((uint32_t)v) & a.mask;
-    const float thr = a.thr32[v];
+    const int32_t v = (int32_t)(packed & a.idmask);
+    ThrBounds tb;
+    if (a.colp) {
+        tb = thr_bounds(a, packed >> a.idbits);
+    } else {
+        tb.lo = tb.hi = a.thr32[v];
+    }
     const uint32_t sector_mask = a.mask >= 3 ? 3u : a.mask;
+    uint32_t h = mix32((uint32_t)v) & a.mask & ~sector_mask;
     for (uint32_t probes = 0; probes <= a.mask && probes < kMaxProbe;) {
-        const uint32_t s0 = h & ~sector_mask;
         unsigned long long w0, w1, w2, w3;
         if (sector_mask == 3u) {
-            const ulonglong2 lo = __ldcg(reinterpret_cast<const ulonglong2 *>(a.kr + base + s0));
-            const ulonglong2 hi = __ldcg(reinterpret_cast<const ulonglong2 *>(a.kr + base + s0 + 2));
+            const ulonglong2 lo = __ldcg(reinterpret_cast<const ulonglong2 *>(a.kr + base + h));
+            const ulonglong2 hi = __ldcg(reinterpret_cast<const ulonglong2 *>(a.kr + base + h + 2));
             w0 = lo.x; w1 = lo.y; w2 = hi.x; w3 = hi.y;
         } else {  // tables smaller than one sector
-            w0 = ld_relaxed_u64(a.kr + base + s0);
-            w1 = sector_mask >= 1 ? ld_relaxed_u64(a.kr + base + s0 + 1) : 0ull;
+            w0 = ld_relaxed_u64(a.kr + base + h);
+            w1 = sector_mask >= 1 ? ld_relaxed_u64(a.kr + base + h + 1) : 0ull;
             w2 = w3 = 0ull;
         }
-        for (uint32_t k = h - s0; k <= sector_mask; k++, probes++) {
-            const uint64_t slot = base + s0 + k;
+        for (uint32_t k = 0; k <= sector_mask; k++, probes++) {
+            const uint64_t slot = base + h + k;
             unsigned long long wk = k == 0 ? w0 : (k == 1 ? w1 : (k == 2 ? w2 : w3));
             for (;;) {
                 const uint32_t key = (uint32_t)(wk & 0xFFFFFFFFull);
                 if (key == (uint32_t)v) {
                     const float old = atomicAdd(r_of(a.kr, slot), w);
-                    const float nv = __fadd_rn(old, w);
-                    if (old < thr && nv >= thr) stage_push(sbuf, sn, (uint32_t)slot);
+                    if (crossed(a, v, tb, old, __fadd_rn(old, w))) stage_push(sbuf, sn, (uint32_t)slot);
                     return 0;
                 }
                 if (key != kEmpty) break;  // another node: next slot
                 const unsigned long long prev = atomicCAS(a.kr + slot, wk, slot_word(v, w));
                 if (prev == wk) {
-                    if (w >= thr) stage_push(sbuf, sn, (uint32_t)slot);
+                    if (crossed(a, v, tb, 0.0f, w)) stage_push(sbuf, sn, (uint32_t)slot);
                     return 1;
                 }
                 wk = prev;  // lost the race: look at what was written into this slot
             }
         }
-        h = (s0 + sector_mask + 1) & a.mask;
+        h = (h + sector_mask + 1) & a.mask;
     }
     atomicExch(a.status + j, kSeedOverflow);  // table full
     return 0;
+}
+
+// columns of the push: packed (id | code) when available, else plain ids
+__device__ __forceinline__ uint32_t push_col(const BArgs &a, int64_t e) {
+    return a.colp ? a.colp[e] : (uint32_t)a.col[e];
+}
+
+__global__ void k_pack_columns(int64_t nnz, const int32_t *col, const int32_t *deg, uint32_t *colp,
+                               int idbits, int code_exact) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = col[e];
+        colp[e] = (uint32_t)v | (degree_code(deg[v], code_exact) << idbits);
+    }
 }
 
 // Exclusive prefix sums of n values (one block): out[i] = sum in[0..i), returns the total.
@@ -537,6 +601,7 @@ __global__ void __launch_bounds__(kThreads) k_batch_rounds(BArgs a) {
             // the other parity's counters were last read in phase A of this round
             prev->hub_packed = 0; prev->cnt_small = 0; prev->cnt_med = 0; prev->cand_out = 0;
             prev->n_active = 0; prev->vol = 0; prev->rS_l1 = 0.0; prev->overflow = 0;
+            prev->hub_next = 0; prev->med_next = 0; prev->small_next = 0;
         }
         uint32_t *cand_out = a.cand[p ^ 1];
         if (__ldcg(&ctl->overflow)) {
@@ -549,7 +614,16 @@ __global__ void __launch_bounds__(kThreads) k_batch_rounds(BArgs a) {
             // consecutive lanes on consecutive columns
             if (VH > 0) {
                 const int64_t nchunks = (VH + a.chunk - 1) / a.chunk;
-                for (int64_t c = gw; c < nchunks; c += nw) {
+                for (int64_t it = 0;; it++) {
+                    int64_t c;
+                    if (a.schedule <= 1) {
+                        unsigned long long cg_ = 0;
+                        if (lane == 0) cg_ = atomicAdd(&ctl->hub_next, 1ull);
+                        c = (int64_t)__shfl_sync(0xffffffffu, cg_, 0);
+                    } else {
+                        c = gw + it * nw;
+                    }
+                    if (c >= nchunks) break;
                     const int64_t e0 = c * a.chunk;
                     const int64_t e1 = min(e0 + (int64_t)a.chunk, VH);
                     int64_t lo = 0, hi = H;
@@ -563,8 +637,6 @@ __global__ void __launch_bounds__(kThreads) k_batch_rounds(BArgs a) {
                     int64_t hb = __ldcg(a.b_beg[2] + h);
                     float hw = __ldcg(a.b_w[2] + h);
                     int32_t hj = __ldcg(a.b_seed[2] + h);
-                    int32_t ins_j = hj;
-                    unsigned ins = 0;
                     for (int64_t eb = e0; eb < e1; eb += 32) {
                         const int64_t e = eb + lane;
                         if (e < e1) {
@@ -576,38 +648,51 @@ __global__ void __launch_bounds__(kThreads) k_batch_rounds(BArgs a) {
                                 hw = __ldcg(a.b_w[2] + h);
                                 hj = __ldcg(a.b_seed[2] + h);
                             }
-                            if (hj != ins_j) {
-                                flush_inserts(a, ins_j, ins);
-                                ins = 0;
-                                ins_j = hj;
-                            }
-                            ins += bscatter(a, hj, a.col[hb + (e - hs)], hw, sbuf, sn);
+                            bscatter(a, hj, push_col(a, hb + (e - hs)), hw, sbuf, sn);
                         }
                         stage_flush(sbuf, sn, false, ctl, cand_out, a.list_cap);
                     }
-                    flush_inserts(a, ins_j, ins);
                 }
             }
             // medium degrees: one warp per node
             const unsigned nmed = min(__ldcg(&ctl->cnt_med), a.list_cap);
             // descending: the hub sweep ends at the last seeds, the medium sweep starts there
-            for (int64_t ii = gw; ii < nmed; ii += nw) {
+            for (int64_t it = 0;; it++) {
+                unsigned got = 0;
+                if (a.schedule == 0) {
+                    if (lane == 0) got = atomicAdd(&ctl->med_next, (unsigned)kMedGrab);
+                    got = __shfl_sync(0xffffffffu, got, 0);
+                } else {
+                    const int64_t g0 = (gw + it * nw) * kMedGrab;
+                    got = g0 < nmed ? (unsigned)g0 : nmed;
+                }
+                if (got >= nmed) break;
+                const unsigned gend = min(got + (unsigned)kMedGrab, nmed);
+                for (unsigned ii = got; ii < gend; ii++) {
                 const int64_t i = (int64_t)nmed - 1 - ii;
                 const int64_t b = __ldcg(a.b_beg[1] + i);
                 const int32_t d = __ldcg(a.b_deg[1] + i);
                 const float w = __ldcg(a.b_w[1] + i);
                 const int32_t j = __ldcg(a.b_seed[1] + i);
-                unsigned ins = 0;
                 for (int32_t k0 = 0; k0 < d; k0 += 32) {
                     const int32_t k = k0 + lane;
-                    if (k < d) ins += bscatter(a, j, a.col[b + k], w, sbuf, sn);
+                    if (k < d) bscatter(a, j, push_col(a, b + k), w, sbuf, sn);
                     stage_flush(sbuf, sn, false, ctl, cand_out, a.list_cap);
                 }
-                flush_inserts(a, j, ins);
+                }
             }
             // small degrees: one thread per node (warp-uniform loops so the warp can flush)
             const unsigned nsm = min(__ldcg(&ctl->cnt_small), a.list_cap);
-            for (int64_t i0 = gw * 32; i0 < nsm; i0 += nw * 32) {
+            for (int64_t it = 0;; it++) {
+                int64_t i0;
+                if (a.schedule == 0) {
+                    unsigned got = 0;
+                    if (lane == 0) got = atomicAdd(&ctl->small_next, 32u);
+                    i0 = (int64_t)__shfl_sync(0xffffffffu, got, 0);
+                } else {
+                    i0 = (gw + it * nw) * 32;
+                }
+                if (i0 >= nsm) break;
                 const int64_t i = i0 + lane;
                 int64_t b = 0;
                 int32_t d = 0, j = 0;
@@ -619,12 +704,10 @@ __global__ void __launch_bounds__(kThreads) k_batch_rounds(BArgs a) {
                     j = __ldcg(a.b_seed[0] + i);
                 }
                 const int32_t dmax = (int32_t)__reduce_max_sync(0xffffffffu, (unsigned)d);
-                unsigned ins = 0;
                 for (int32_t k = 0; k < dmax; k++) {
-                    if (k < d) ins += bscatter(a, j, a.col[b + k], w, sbuf, sn);
+                    if (k < d) bscatter(a, j, push_col(a, b + k), w, sbuf, sn);
                     stage_flush(sbuf, sn, false, ctl, cand_out, a.list_cap);
                 }
-                if (i < nsm) flush_inserts(a, j, ins);
             }
         }
         stage_flush(sbuf, sn, true, ctl, cand_out, a.list_cap);
@@ -683,7 +766,9 @@ __global__ void k_batch_seed(int32_t nseeds, const int32_t *seeds, unsigned long
     }
     if (j >= nseeds) return;
     const int32_t s = seeds[j];
-    const uint64_t slot = ((uint64_t)j << log2cap) + (mix32((uint32_t)s) & mask);
+    // the first slot of the seed's probe bucket, where bscatter's search for s begins
+    const uint32_t sector_mask = mask >= 3 ? 3u : mask;
+    const uint64_t slot = ((uint64_t)j << log2cap) + (mix32((uint32_t)s) & mask & ~sector_mask);
     kr[slot] = ((unsigned long long)__float_as_uint(1.0f) << 32) | (unsigned long long)(uint32_t)s;
     cand0[j] = (uint32_t)slot;
     status[j] = kSeedOk;
@@ -751,6 +836,9 @@ struct TopkArgs {
     float *out_vals;
     double *sresid;
     double *smass;
+    unsigned *skeys;    // keys in the seed's table
+    unsigned load_limit;
+    int32_t *status;
 };
 
 // one block per seed: scan its table, keep the top-k of (x desc, id asc), and sum |r| and x in FP64
@@ -760,6 +848,7 @@ __global__ void __launch_bounds__(kThreads) k_batch_topk(TopkArgs a) {
     const uint64_t base = (uint64_t)j << a.log2cap;
     unsigned long long ta = 0, tb = 0;
     double rsum = 0.0, xsum = 0.0;
+    unsigned nkeys = 0;
     for (int64_t i0 = (int64_t)wid * 32; i0 < a.cap; i0 += kThreads) {
         const int64_t i = i0 + lane;
         unsigned long long key = 0;
@@ -767,7 +856,10 @@ __global__ void __launch_bounds__(kThreads) k_batch_topk(TopkArgs a) {
             const float x = a.xs[base + i];
             const unsigned long long w = a.kr[base + i];
             const uint32_t v = (uint32_t)(w & 0xFFFFFFFFull);
-            if (v != kEmpty) rsum += fabs((double)__uint_as_float((uint32_t)(w >> 32)));
+            if (v != kEmpty) {
+                rsum += fabs((double)__uint_as_float((uint32_t)(w >> 32)));
+                nkeys++;
+            }
             if (x > 0.0f && v != kEmpty) {
                 xsum += (double)x;
                 key = ((unsigned long long)__float_as_uint(x) << 32) | (unsigned long long)(0xFFFFFFFFu - v);
@@ -777,11 +869,13 @@ __global__ void __launch_bounds__(kThreads) k_batch_topk(TopkArgs a) {
     }
     __shared__ unsigned long long s_a[kWarps][32], s_b[kWarps][32];
     __shared__ double s_r[kWarps], s_x[kWarps];
+    __shared__ unsigned s_k[kWarps];
     s_a[wid][lane] = ta;
     s_b[wid][lane] = tb;
     rsum = bwarp_sum(rsum);
     xsum = bwarp_sum(xsum);
-    if (lane == 0) { s_r[wid] = rsum; s_x[wid] = xsum; }
+    nkeys = bwarp_sum(nkeys);
+    if (lane == 0) { s_r[wid] = rsum; s_x[wid] = xsum; s_k[wid] = nkeys; }
     __syncthreads();
     if (wid == 0) {
         for (int w = 1; w < kWarps; w++) {
@@ -790,9 +884,15 @@ __global__ void __launch_bounds__(kThreads) k_batch_topk(TopkArgs a) {
         }
         double rr = lane < kWarps ? s_r[lane] : 0.0;
         double xx = lane < kWarps ? s_x[lane] : 0.0;
+        unsigned kk = lane < kWarps ? s_k[lane] : 0u;
         rr = bwarp_sum(rr);
         xx = bwarp_sum(xx);
-        if (lane == 0) { a.sresid[j] = rr; a.smass[j] = xx; }
+        kk = bwarp_sum(kk);
+        if (lane == 0) {
+            a.sresid[j] = rr;
+            a.smass[j] = xx;
+            a.skeys[j] = kk;
+        }
         const int k = a.k;
         for (int half = 0; half < 2; half++) {
             const int pos = half * 32 + lane;
@@ -887,7 +987,7 @@ void topk_dense_f32(const float *x_dev, int64_t n, int k, int32_t *ids_dev, floa
 
 static void batch_free(BatchWork *w) {
     if (!w) return;
-    dfree(w->kr); dfree(w->xs); dfree(w->thr32);
+    dfree(w->kr); dfree(w->xs); dfree(w->thr32); dfree(w->colp);
     for (int k = 0; k < 2; k++) dfree(w->cand[k]);
     for (int b = 0; b < 3; b++) { dfree(w->b_beg[b]); dfree(w->b_deg[b]); dfree(w->b_w[b]); dfree(w->b_seed[b]); }
     dfree(w->hub_vstart); dfree(w->tmp_beg); dfree(w->tmp_deg); dfree(w->tmp_w); dfree(w->tmp_jb);
@@ -997,6 +1097,19 @@ void batch_solve(Graph &g, const SolveParams &p, const int32_t *seeds_dev, int32
     cudaStream_t s = p.stream;
     GDE_CUDA(cudaMemcpyAsync(w->seeds, seeds_dev, 4 * (size_t)nseeds, cudaMemcpyDeviceToDevice, s));
     const int64_t pool = (int64_t)nseeds * cap;
+    if (!w->colp && g.nnz > 0) {
+        int idbits = 1;
+        while (((int64_t)1 << idbits) < g.n) idbits++;
+        const int spare = 32 - idbits;
+        if (spare >= 5) {
+            const int codes = spare >= 8 ? 256 : (1 << spare);
+            w->colp = (uint32_t *)dmalloc(4 * (size_t)g.nnz, "packed columns");
+            w->colp_idbits = idbits;
+            w->colp_exact = codes - 32;
+            k_pack_columns<<<kSMs * 8, kThreads, 0, s>>>(g.nnz, g.col, g.deg, w->colp, idbits, w->colp_exact);
+            GDE_CUDA(cudaGetLastError());
+        }
+    }
     const int pc = g.prof.start(kProfBatchClear, s);
     k_batch_clear<<<kSMs * 8, kThreads, 0, s>>>(pool, w->kr, w->xs);
     GDE_CUDA(cudaGetLastError());
@@ -1016,6 +1129,9 @@ void batch_solve(Graph &g, const SolveParams &p, const int32_t *seeds_dev, int32
 
     BArgs a{};
     a.off = g.off; a.col = g.col; a.thr32 = w->thr32; a.kr = w->kr; a.xs = w->xs;
+    a.colp = w->colp; a.idbits = w->colp_idbits;
+    a.idmask = w->colp ? (uint32_t)(((uint64_t)1 << w->colp_idbits) - 1) : 0xFFFFFFFFu;
+    a.code_exact = w->colp_exact; a.eps = p.eps;
     a.log2cap = w->log2cap; a.mask = (uint32_t)(cap - 1); a.nseeds = nseeds;
     a.status = w->status; a.inserts = w->inserts;
     a.load_limit = (unsigned)(cap * 3 / 4);
@@ -1035,7 +1151,7 @@ void batch_solve(Graph &g, const SolveParams &p, const int32_t *seeds_dev, int32
     a.coef = p.kind == GDE_PPR ? 1.0 - p.param : p.param;
     a.max_rounds = p.max_rounds;
     const Bins &bins = g.bins;
-    a.t1 = bins.t1; a.t2 = bins.t2; a.chunk = bins.chunk;
+    a.t1 = bins.t1; a.t2 = bins.t2; a.chunk = bins.chunk; a.schedule = bins.schedule;
 
     int grid = w->grid;
     if (bins.blocks_per_sm > 0 && bins.blocks_per_sm * w->sms < grid) grid = bins.blocks_per_sm * w->sms;
@@ -1056,6 +1172,7 @@ void batch_solve(Graph &g, const SolveParams &p, const int32_t *seeds_dev, int32
     TopkArgs ta{};
     ta.kr = w->kr; ta.xs = w->xs; ta.log2cap = w->log2cap; ta.cap = cap; ta.k = k;
     ta.out_ids = ids_dev; ta.out_vals = vals_dev; ta.sresid = w->sresid; ta.smass = w->smass;
+    ta.skeys = w->inserts; ta.load_limit = (unsigned)(cap * 3 / 4); ta.status = w->status;
     const int pt = g.prof.start(kProfBatchTopk, s);
     k_batch_topk<<<nseeds, kThreads, 0, s>>>(ta);
     GDE_CUDA(cudaGetLastError());

@@ -51,10 +51,11 @@ constexpr int kWarps = kThreads / 32;
 
 // degree bins of the push (autotunable; these are the defaults)
 struct Bins {
-    int32_t t1 = 8;       // d <= t1: thread per node
-    int32_t t2 = 2048;    // t1 < d <= t2: warp per node; d > t2: hub merge-path chunks
-    int32_t chunk = 4096; // hub edges per warp work item
+    int32_t t1 = 16;      // d <= t1: thread per node
+    int32_t t2 = 512;     // t1 < d <= t2: warp per node; d > t2: hub merge-path chunks
+    int32_t chunk = 1024; // hub edges per warp work item
     int32_t blocks_per_sm = 0;  // persistent grid; 0 = occupancy limit
+    int32_t schedule = 0;       // batched scatter order: 0 all bins in order, 1 hubs in order, 2 strided
 };
 
 // ---------------------------------------------------------------- profiler --
