@@ -145,8 +145,9 @@ typedef struct {
     int64_t dense_rounds;        /* single-seed rounds timed */
     int64_t edges;               /* sum of vol(S_t) over the timed work */
     int64_t pushes;              /* sum of |S_t| over the timed work */
-    int64_t inserts;             /* batched: new hash keys */
+    int64_t support;             /* batched: sum over seeds of |supp(x)| */
     int64_t rounds;              /* batched: rounds of the persistent loop */
+    int64_t launches;            /* kernels this library launched */
 } gde_profile;
 
 gde_status gde_profile_enable(gde_graph *g, int enable);

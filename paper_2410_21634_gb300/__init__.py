@@ -61,7 +61,8 @@ class Profile(ctypes.Structure):
                 ("batch_topk_ms", ctypes.c_double), ("dense_frontier_ms", ctypes.c_double),
                 ("dense_push_ms", ctypes.c_double), ("batch_launches", ctypes.c_int64),
                 ("dense_rounds", ctypes.c_int64), ("edges", ctypes.c_int64),
-                ("pushes", ctypes.c_int64), ("inserts", ctypes.c_int64), ("rounds", ctypes.c_int64)]
+                ("pushes", ctypes.c_int64), ("support", ctypes.c_int64), ("rounds", ctypes.c_int64),
+                ("launches", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

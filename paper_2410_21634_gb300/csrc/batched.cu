@@ -3,10 +3,13 @@
 // tables in HBM, top-k output per seed.
 //
 // Layout (pool of P = nseeds * cap slots, cap a power of two):
-//   kr[slot]  64-bit word {low: node id (0xFFFFFFFF = empty), high: r as float bits}; key and
-//             residual share one 8-byte word, so a probe and the atomic add on r touch the
-//             same 32-byte sector (4 slots per sector)
-//   xs[slot]  float x of that node
+//   kr[slot]  64-bit word {low: key, high: r as float bits}; key and residual share one
+//             8-byte word, so a probe and the atomic add on r touch the same 32-byte sector.
+//             key = node id | epoch tag << idbits; a slot whose tag is not the current
+//             solve's (or 0xFFFFFFFF) is empty, so tables need no reset between solves
+//   xs[slot]  float x of that node (zero outside the current solve's x-lists)
+//   xlist     per seed, the slots whose x became nonzero (appended on first activation);
+//             the top-k reads only these and zeroes their x
 // seed j owns slots [j*cap, (j+1)*cap); a slot index therefore names its seed (slot >> log2cap).
 // thr32[v] = fl(eps d_v) rounded up to float (one array shared by all seeds).
 //
@@ -117,13 +120,18 @@ struct BatchWork {
     unsigned long long *svol = nullptr;  // per seed
     unsigned *spushes = nullptr;     // per seed
     int32_t *slast = nullptr;        // per seed: last round with a push
-    double *sresid = nullptr;        // per seed
-    double *smass = nullptr;         // per seed
+    double *spush = nullptr;         // per seed: sum of pushed residual mass (FP64)
+    double *sscat = nullptr;         // per seed: sum of scattered mass d_u w_u (FP64)
+    uint32_t *xlist = nullptr;       // per seed: xcap slots whose x is nonzero
+    unsigned *xcnt = nullptr;        // per seed: x-list length (may exceed xcap: overflow)
+    int64_t xcap = 0;
     BGlobal *glob = nullptr;
     RoundLog *log = nullptr;
     int grid = 0;    // co-resident blocks of the persistent kernel
     int sms = 0;
     int64_t last_rounds = 0;
+    bool need_clear = true;   // reset every table before the next solve
+    uint32_t epoch = 0;       // tag of the current solve's keys
 };
 
 // ------------------------------------------------------------- device bits --
@@ -209,6 +217,13 @@ struct BArgs {
     int code_exact;         // codes below this are exact degrees; from it on, log2 classes
     double eps;
     const float *thr32;
+    uint32_t key_idmask;    // node-id bits of a table key
+    uint32_t key_tag;       // this solve's epoch tag, already shifted above the id bits
+    uint32_t *xlist;
+    unsigned *xcnt;
+    unsigned xcap;
+    double *spush;
+    double *sscat;
     unsigned long long *kr;
     float *xs;
     int log2cap;
@@ -262,8 +277,8 @@ constexpr uint32_t kMaxProbe = 256;
 constexpr int kStage = 256;            // staged candidates per warp (shared memory)
 constexpr int kMedGrab = 4;            // medium-degree entries a warp takes per grab
 
-__device__ __forceinline__ unsigned long long slot_word(int32_t v, float w) {
-    return ((unsigned long long)__float_as_uint(w) << 32) | (unsigned long long)(uint32_t)v;
+__device__ __forceinline__ unsigned long long slot_word(uint32_t key, float w) {
+    return ((unsigned long long)__float_as_uint(w) << 32) | (unsigned long long)key;
 }
 
 // Append a candidate slot to this warp's staging buffer in shared memory (one shared atomic
@@ -340,6 +355,7 @@ __device__ __forceinline__ unsigned bscatter(const BArgs &a, int32_t j, uint32_t
                                              uint32_t *sbuf, unsigned *sn) {
     const uint64_t base = (uint64_t)j << a.log2cap;
     const int32_t v = (int32_t)(packed & a.idmask);
+    const uint32_t kcur = (uint32_t)v | a.key_tag;
     ThrBounds tb;
     if (a.colp) {
         tb = thr_bounds(a, packed >> a.idbits);
@@ -364,13 +380,14 @@ __device__ __forceinline__ unsigned bscatter(const BArgs &a, int32_t j, uint32_t
             unsigned long long wk = k == 0 ? w0 : (k == 1 ? w1 : (k == 2 ? w2 : w3));
             for (;;) {
                 const uint32_t key = (uint32_t)(wk & 0xFFFFFFFFull);
-                if (key == (uint32_t)v) {
+                if (key == kcur) {
                     const float old = atomicAdd(r_of(a.kr, slot), w);
                     if (crossed(a, v, tb, old, __fadd_rn(old, w))) stage_push(sbuf, sn, (uint32_t)slot);
                     return 0;
                 }
-                if (key != kEmpty) break;  // another node: next slot
-                const unsigned long long prev = atomicCAS(a.kr + slot, wk, slot_word(v, w));
+                // another node of this solve: next slot (empty and stale-tag slots are free)
+                if (key != kEmpty && (key & ~a.key_idmask) == a.key_tag) break;
+                const unsigned long long prev = atomicCAS(a.kr + slot, wk, slot_word(kcur, w));
                 if (prev == wk) {
                     if (crossed(a, v, tb, 0.0f, w)) stage_push(sbuf, sn, (uint32_t)slot);
                     return 1;
@@ -468,7 +485,7 @@ __global__ void __launch_bounds__(kThreads) k_batch_rounds(BArgs a) {
             const int32_t j = (int32_t)(slot >> a.log2cap);
             if (__ldcg(a.status + j) != kSeedOk) { __stcg(a.tmp_deg + ci, 0); continue; }
             const unsigned long long word = __ldcg(a.kr + slot);
-            const int32_t v = (int32_t)(word & 0xFFFFFFFFull);
+            const int32_t v = (int32_t)((uint32_t)(word & 0xFFFFFFFFull) & a.key_idmask);
             const float rho = __uint_as_float((uint32_t)(word >> 32));
             const float thr = a.thr32[v];
             if (!(rho != 0.0f && fabsf(rho) >= thr)) { __stcg(a.tmp_deg + ci, 0); continue; }
@@ -481,25 +498,45 @@ __global__ void __launch_bounds__(kThreads) k_batch_rounds(BArgs a) {
                 __stcg(a.xs + slot, __fadd_rn(xold, rho));
             const int64_t beg = a.off[v];
             const int32_t d = (int32_t)(a.off[v + 1] - beg);
+            float w = 0.0f;
+            if (d > 0) {
+                if (a.kind == GDE_KATZ)
+                    w = __double2float_rn(__dmul_rn(a.coef, rho64));
+                else
+                    w = __double2float_rn(__ddiv_rn(__dmul_rn(a.coef, rho64), (double)d));
+            }
             my_rs += fabs(rho64);
             my_vol += (unsigned long long)d;
             {
-                // per-seed counters: one atomic per group of lanes with the same seed
+                // per-seed counters and FP64 mass: one atomic per group of lanes with the same seed
                 const unsigned am = __activemask();
                 const unsigned peers = __match_any_sync(am, j);
                 const unsigned dsum = __reduce_add_sync(peers, (unsigned)d);
+                double psum = 0.0, ssum = 0.0;
+                const double scat = d > 0 ? __dmul_rn((double)w, (double)d) : 0.0;
+                for (unsigned m = peers; m; m &= m - 1) {
+                    const int src = __ffs(m) - 1;
+                    psum += __shfl_sync(peers, rho64, src);
+                    ssum += __shfl_sync(peers, scat, src);
+                }
                 if (lane == __ffs(peers) - 1) {
                     atomicAdd(a.svol + j, (unsigned long long)dsum);
                     atomicAdd(a.spushes + j, (unsigned)__popc(peers));
                     atomicMax(a.slast + j, (int)t);
+                    atomicAdd(a.spush + j, psum);
+                    atomicAdd(a.sscat + j, ssum);
                 }
             }
+            if (xold == 0.0f) {
+                // first activation of this node in this solve: remember the slot for the top-k
+                const unsigned xpeers = __match_any_sync(__activemask(), j);
+                const int xl = __ffs(xpeers) - 1;
+                unsigned xb = 0;
+                if (lane == xl) xb = atomicAdd(a.xcnt + j, (unsigned)__popc(xpeers));
+                xb = __shfl_sync(xpeers, xb, xl) + __popc(xpeers & ((1u << lane) - 1u));
+                if (xb < a.xcap) __stcg(a.xlist + (uint64_t)j * a.xcap + xb, slot);
+            }
             if (d == 0) { __stcg(a.tmp_deg + ci, 0); continue; }
-            float w;
-            if (a.kind == GDE_KATZ)
-                w = __double2float_rn(__dmul_rn(a.coef, rho64));
-            else
-                w = __double2float_rn(__ddiv_rn(__dmul_rn(a.coef, rho64), (double)d));
             const int bin = d <= a.t1 ? 0 : (d <= a.t2 ? 1 : 2);
             __stcg(a.tmp_beg + ci, beg);
             __stcg(a.tmp_deg + ci, d);
@@ -758,7 +795,8 @@ __global__ void k_batch_thr(int64_t n, const int32_t *deg, float *thr32, double 
 __global__ void k_batch_seed(int32_t nseeds, const int32_t *seeds, unsigned long long *kr,
                              uint32_t *cand0, int log2cap, uint32_t mask, BGlobal *G,
                              int32_t *status, unsigned *inserts, unsigned long long *svol,
-                             unsigned *spushes, int32_t *slast) {
+                             unsigned *spushes, int32_t *slast, uint32_t key_tag, unsigned *xcnt,
+                             double *spush, double *sscat) {
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j == 0) {
         memset(G, 0, sizeof(BGlobal));
@@ -769,10 +807,13 @@ __global__ void k_batch_seed(int32_t nseeds, const int32_t *seeds, unsigned long
     // the first slot of the seed's probe bucket, where bscatter's search for s begins
     const uint32_t sector_mask = mask >= 3 ? 3u : mask;
     const uint64_t slot = ((uint64_t)j << log2cap) + (mix32((uint32_t)s) & mask & ~sector_mask);
-    kr[slot] = ((unsigned long long)__float_as_uint(1.0f) << 32) | (unsigned long long)(uint32_t)s;
+    kr[slot] = ((unsigned long long)__float_as_uint(1.0f) << 32) | (unsigned long long)((uint32_t)s | key_tag);
     cand0[j] = (uint32_t)slot;
     status[j] = kSeedOk;
     inserts[j] = 1;
+    xcnt[j] = 0;
+    spush[j] = 0.0;
+    sscat[j] = 0.0;
     svol[j] = 0;
     spushes[j] = 0;
     slast[j] = -1;
@@ -828,71 +869,61 @@ __device__ __forceinline__ void top64_insert(unsigned long long &a, unsigned lon
 
 struct TopkArgs {
     const unsigned long long *kr;
-    const float *xs;
+    float *xs;                  // read, then zeroed for the next solve
     int log2cap;
     int64_t cap;
+    uint32_t key_idmask;
+    const uint32_t *xlist;
+    const unsigned *xcnt;
+    unsigned xcap;
     int k;
     int32_t *out_ids;
     float *out_vals;
-    double *sresid;
-    double *smass;
-    unsigned *skeys;    // keys in the seed's table
-    unsigned load_limit;
-    int32_t *status;
+    unsigned *ssupport;         // |supp(x)| per seed
 };
 
-// one block per seed: scan its table, keep the top-k of (x desc, id asc), and sum |r| and x in FP64
+// One block per seed: the top-k of (x desc, id asc) over the slots of the seed's x-list (every
+// node with nonzero x), which are zeroed for the next solve.  If the list overflowed, the whole
+// table is scanned instead.
 __global__ void __launch_bounds__(kThreads) k_batch_topk(TopkArgs a) {
     const int j = blockIdx.x;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint64_t base = (uint64_t)j << a.log2cap;
     unsigned long long ta = 0, tb = 0;
-    double rsum = 0.0, xsum = 0.0;
-    unsigned nkeys = 0;
-    for (int64_t i0 = (int64_t)wid * 32; i0 < a.cap; i0 += kThreads) {
+    const unsigned nx = a.xcnt[j];
+    const bool use_list = nx <= a.xcap;
+    const int64_t n = use_list ? (int64_t)nx : a.cap;
+    unsigned support = 0;
+    for (int64_t i0 = (int64_t)wid * 32; i0 < n; i0 += kThreads) {
         const int64_t i = i0 + lane;
         unsigned long long key = 0;
-        if (i < a.cap) {
-            const float x = a.xs[base + i];
-            const unsigned long long w = a.kr[base + i];
-            const uint32_t v = (uint32_t)(w & 0xFFFFFFFFull);
-            if (v != kEmpty) {
-                rsum += fabs((double)__uint_as_float((uint32_t)(w >> 32)));
-                nkeys++;
-            }
-            if (x > 0.0f && v != kEmpty) {
-                xsum += (double)x;
+        if (i < n) {
+            const uint64_t slot = use_list ? (uint64_t)a.xlist[(uint64_t)j * a.xcap + i] : base + (uint64_t)i;
+            const float x = a.xs[slot];
+            if (x > 0.0f) {
+                const uint32_t v = (uint32_t)(a.kr[slot] & 0xFFFFFFFFull) & a.key_idmask;
                 key = ((unsigned long long)__float_as_uint(x) << 32) | (unsigned long long)(0xFFFFFFFFu - v);
+                a.xs[slot] = 0.0f;
+                support++;
             }
         }
         top64_insert(ta, tb, key, lane);
     }
     __shared__ unsigned long long s_a[kWarps][32], s_b[kWarps][32];
-    __shared__ double s_r[kWarps], s_x[kWarps];
     __shared__ unsigned s_k[kWarps];
     s_a[wid][lane] = ta;
     s_b[wid][lane] = tb;
-    rsum = bwarp_sum(rsum);
-    xsum = bwarp_sum(xsum);
-    nkeys = bwarp_sum(nkeys);
-    if (lane == 0) { s_r[wid] = rsum; s_x[wid] = xsum; s_k[wid] = nkeys; }
+    support = bwarp_sum(support);
+    if (lane == 0) s_k[wid] = support;
     __syncthreads();
     if (wid == 0) {
-        for (int w = 1; w < kWarps; w++) {
-            top64_insert(ta, tb, s_a[w][lane], lane);
-            top64_insert(ta, tb, s_b[w][lane], lane);
+        for (int ww = 1; ww < kWarps; ww++) {
+            top64_insert(ta, tb, s_a[ww][lane], lane);
+            top64_insert(ta, tb, s_b[ww][lane], lane);
         }
-        double rr = lane < kWarps ? s_r[lane] : 0.0;
-        double xx = lane < kWarps ? s_x[lane] : 0.0;
         unsigned kk = lane < kWarps ? s_k[lane] : 0u;
-        rr = bwarp_sum(rr);
-        xx = bwarp_sum(xx);
         kk = bwarp_sum(kk);
-        if (lane == 0) {
-            a.sresid[j] = rr;
-            a.smass[j] = xx;
-            a.skeys[j] = kk;
-        }
+        if (lane == 0) a.ssupport[j] = kk;
         const int k = a.k;
         for (int half = 0; half < 2; half++) {
             const int pos = half * 32 + lane;
@@ -993,7 +1024,7 @@ static void batch_free(BatchWork *w) {
     dfree(w->hub_vstart); dfree(w->tmp_beg); dfree(w->tmp_deg); dfree(w->tmp_w); dfree(w->tmp_jb);
     dfree(w->seg_cnt); dfree(w->seg_off); dfree(w->seg_cur); dfree(w->seg_hvol); dfree(w->vol_off);
     dfree(w->seg_hcur); dfree(w->seeds); dfree(w->status); dfree(w->inserts); dfree(w->svol);
-    dfree(w->spushes); dfree(w->slast); dfree(w->sresid); dfree(w->smass); dfree(w->glob); dfree(w->log);
+    dfree(w->spushes); dfree(w->slast); dfree(w->spush); dfree(w->sscat); dfree(w->xlist); dfree(w->xcnt); dfree(w->glob); dfree(w->log);
     delete w;
 }
 
@@ -1037,8 +1068,11 @@ static BatchWork *batch_work_get(Graph &g, int64_t nseeds, int64_t cap, int64_t 
         w->svol = (unsigned long long *)dmalloc(8 * (size_t)nseeds, "seed volume");
         w->spushes = (unsigned *)dmalloc(4 * (size_t)nseeds, "seed pushes");
         w->slast = (int32_t *)dmalloc(4 * (size_t)nseeds, "seed rounds");
-        w->sresid = (double *)dmalloc(8 * (size_t)nseeds, "seed residual");
-        w->smass = (double *)dmalloc(8 * (size_t)nseeds, "seed mass");
+        w->spush = (double *)dmalloc(8 * (size_t)nseeds, "seed pushed mass");
+        w->sscat = (double *)dmalloc(8 * (size_t)nseeds, "seed scattered mass");
+        w->xcap = cap < ((int64_t)1 << 16) ? cap : ((int64_t)1 << 16);
+        w->xlist = (uint32_t *)dmalloc(4 * (size_t)nseeds * (size_t)w->xcap, "x lists");
+        w->xcnt = (unsigned *)dmalloc(4 * (size_t)nseeds, "x list lengths");
         w->glob = (BGlobal *)dmalloc(sizeof(BGlobal), "batch control");
         w->log = (RoundLog *)dmalloc(sizeof(RoundLog) * kLogCap, "round log");
         int per_sm = 0;
@@ -1108,30 +1142,52 @@ void batch_solve(Graph &g, const SolveParams &p, const int32_t *seeds_dev, int32
             w->colp_exact = codes - 32;
             k_pack_columns<<<kSMs * 8, kThreads, 0, s>>>(g.nnz, g.col, g.deg, w->colp, idbits, w->colp_exact);
             GDE_CUDA(cudaGetLastError());
+            g.prof.launched();
         }
     }
-    const int pc = g.prof.start(kProfBatchClear, s);
-    k_batch_clear<<<kSMs * 8, kThreads, 0, s>>>(pool, w->kr, w->xs);
-    GDE_CUDA(cudaGetLastError());
-    g.prof.stop(pc, s);
+    // epoch tags: keys carry the solve's tag above their id bits, so the previous solve's keys
+    // read as empty; the tables are only reset on first use, after a failure, or when the tag
+    // wraps (x is zeroed by the previous top-k through the x-lists)
+    int key_idbits = 1;
+    while (((int64_t)1 << key_idbits) < g.n) key_idbits++;
+    const int tag_bits = 32 - key_idbits < 8 ? 32 - key_idbits : 8;
+    const uint32_t max_tag = tag_bits >= 2 ? (1u << tag_bits) - 2u : 0u;  // never all ones
+    w->epoch = w->epoch + 1;
+    if (w->need_clear || w->epoch > max_tag) {
+        const int pc = g.prof.start(kProfBatchClear, s);
+        k_batch_clear<<<kSMs * 8, kThreads, 0, s>>>(w->pool, w->kr, w->xs);
+        GDE_CUDA(cudaGetLastError());
+        g.prof.launched();
+        g.prof.stop(pc, s);
+        w->epoch = max_tag >= 1 ? 1u : 0u;
+    }
+    w->need_clear = true;  // until this solve completes
+    const uint32_t key_tag = w->epoch << key_idbits;
+    const uint32_t key_idmask = (uint32_t)(((uint64_t)1 << key_idbits) - 1);
+    (void)pool;
     if (w->thr_eps != p.eps || w->thr_n != g.n || !w->thr32) {
         if (!w->thr32) w->thr32 = (float *)dmalloc(4 * (size_t)(g.n > 0 ? g.n : 1), "thresholds");
         k_batch_thr<<<kSMs * 8, kThreads, 0, s>>>(g.n, g.deg, w->thr32, p.eps);
         GDE_CUDA(cudaGetLastError());
+        g.prof.launched();
         w->thr_eps = p.eps;
         w->thr_n = g.n;
     }
     GDE_CUDA(cudaMemsetAsync(w->log, 0, sizeof(RoundLog) * kLogCap, s));
     k_batch_seed<<<(nseeds + kThreads - 1) / kThreads, kThreads, 0, s>>>(
         nseeds, w->seeds, w->kr, w->cand[0], w->log2cap, (uint32_t)(cap - 1), w->glob, w->status,
-        w->inserts, w->svol, w->spushes, w->slast);
+        w->inserts, w->svol, w->spushes, w->slast, key_tag, w->xcnt, w->spush, w->sscat);
     GDE_CUDA(cudaGetLastError());
+    g.prof.launched();
 
     BArgs a{};
     a.off = g.off; a.col = g.col; a.thr32 = w->thr32; a.kr = w->kr; a.xs = w->xs;
     a.colp = w->colp; a.idbits = w->colp_idbits;
     a.idmask = w->colp ? (uint32_t)(((uint64_t)1 << w->colp_idbits) - 1) : 0xFFFFFFFFu;
     a.code_exact = w->colp_exact; a.eps = p.eps;
+    a.key_idmask = key_idmask; a.key_tag = key_tag;
+    a.xlist = w->xlist; a.xcnt = w->xcnt; a.xcap = (unsigned)w->xcap;
+    a.spush = w->spush; a.sscat = w->sscat;
     a.log2cap = w->log2cap; a.mask = (uint32_t)(cap - 1); a.nseeds = nseeds;
     a.status = w->status; a.inserts = w->inserts;
     a.load_limit = (unsigned)(cap * 3 / 4);
@@ -1167,15 +1223,17 @@ void batch_solve(Graph &g, const SolveParams &p, const int32_t *seeds_dev, int32
     cfg.numAttrs = 1;
     const int pr = g.prof.start(kProfBatchRounds, s);
     GDE_CUDA(cudaLaunchKernelEx(&cfg, k_batch_rounds, a));
+    g.prof.launched();
     g.prof.stop(pr, s);
 
     TopkArgs ta{};
     ta.kr = w->kr; ta.xs = w->xs; ta.log2cap = w->log2cap; ta.cap = cap; ta.k = k;
-    ta.out_ids = ids_dev; ta.out_vals = vals_dev; ta.sresid = w->sresid; ta.smass = w->smass;
-    ta.skeys = w->inserts; ta.load_limit = (unsigned)(cap * 3 / 4); ta.status = w->status;
+    ta.key_idmask = key_idmask; ta.xlist = w->xlist; ta.xcnt = w->xcnt; ta.xcap = (unsigned)w->xcap;
+    ta.out_ids = ids_dev; ta.out_vals = vals_dev; ta.ssupport = w->inserts;
     const int pt = g.prof.start(kProfBatchTopk, s);
     k_batch_topk<<<nseeds, kThreads, 0, s>>>(ta);
     GDE_CUDA(cudaGetLastError());
+    g.prof.launched();
     g.prof.stop(pt, s);
 
     // per-seed results
@@ -1184,7 +1242,7 @@ void batch_solve(Graph &g, const SolveParams &p, const int32_t *seeds_dev, int32
     std::vector<int32_t> st(nseeds), last(nseeds);
     std::vector<unsigned long long> vol(nseeds);
     std::vector<unsigned> pushes(nseeds);
-    std::vector<double> resid(nseeds), mass(nseeds);
+    std::vector<double> pushed(nseeds), scat(nseeds);
     std::vector<unsigned> ins(nseeds);
     GDE_CUDA(cudaMemcpyAsync(st.data(), w->status, 4 * (size_t)nseeds, cudaMemcpyDeviceToHost, s));
     if (g.prof.enabled)
@@ -1193,10 +1251,11 @@ void batch_solve(Graph &g, const SolveParams &p, const int32_t *seeds_dev, int32
         GDE_CUDA(cudaMemcpyAsync(last.data(), w->slast, 4 * (size_t)nseeds, cudaMemcpyDeviceToHost, s));
         GDE_CUDA(cudaMemcpyAsync(vol.data(), w->svol, 8 * (size_t)nseeds, cudaMemcpyDeviceToHost, s));
         GDE_CUDA(cudaMemcpyAsync(pushes.data(), w->spushes, 4 * (size_t)nseeds, cudaMemcpyDeviceToHost, s));
-        GDE_CUDA(cudaMemcpyAsync(resid.data(), w->sresid, 8 * (size_t)nseeds, cudaMemcpyDeviceToHost, s));
-        GDE_CUDA(cudaMemcpyAsync(mass.data(), w->smass, 8 * (size_t)nseeds, cudaMemcpyDeviceToHost, s));
+        GDE_CUDA(cudaMemcpyAsync(pushed.data(), w->spush, 8 * (size_t)nseeds, cudaMemcpyDeviceToHost, s));
+        GDE_CUDA(cudaMemcpyAsync(scat.data(), w->sscat, 8 * (size_t)nseeds, cudaMemcpyDeviceToHost, s));
     }
     GDE_CUDA(cudaStreamSynchronize(s));
+    w->need_clear = false;  // the top-k zeroed x on every x-list (or table) it read
     if (hg.error == GDE_ETIMEOUT) {
         set_error("batched solve: a grid barrier wait timed out");
         throw Fail{GDE_ETIMEOUT};
@@ -1212,7 +1271,7 @@ void batch_solve(Graph &g, const SolveParams &p, const int32_t *seeds_dev, int32
         for (int32_t j = 0; j < nseeds; j++) {
             g.prof.counters.edges += (int64_t)vol[j];
             g.prof.counters.pushes += pushes[j];
-            g.prof.counters.inserts += ins[j];
+            g.prof.counters.support += ins[j];
         }
     }
     const bool capped = (int64_t)hg.rounds >= p.max_rounds;
@@ -1226,8 +1285,9 @@ void batch_solve(Graph &g, const SolveParams &p, const int32_t *seeds_dev, int32
             o.rounds = last[j] + 1;
             o.active_volume = (int64_t)vol[j];
             o.pushes = pushes[j];
-            o.resid_l1 = resid[j];
-            o.mass_l1 = mass[j];
+            // unit source: ||r||_1 = 1 - pushed + scattered; ||x||_1 = c_x * pushed
+            o.resid_l1 = 1.0 - pushed[j] + scat[j];
+            o.mass_l1 = (p.kind == GDE_PPR ? p.param : 1.0) * pushed[j];
             o.status = of ? GDE_ENOMEM : ((capped && last[j] + 1 >= (int64_t)hg.rounds) ? GDE_ENOTCONV : GDE_OK);
             o.reserved = 0;
         }

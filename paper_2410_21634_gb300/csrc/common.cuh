@@ -71,6 +71,7 @@ struct Profiler {
     void stop(int idx, cudaStream_t s);
     void reset();
     void read(gde_profile *out);
+    void launched(int n = 1) { if (enabled) counters.launches += n; }
 };
 
 // ------------------------------------------------------------------- graph --

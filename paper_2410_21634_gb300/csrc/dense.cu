@@ -473,12 +473,16 @@ static void begin_impl(Graph &g, DenseWork *w, const SolveParams &p, int32_t see
         k_init_layers<real><<<grid, kThreads, 0, p.stream>>>(g.n, (real *)w->x, (real *)w->rl[0],
                                                              (real *)w->rl[1], seed);
         GDE_CUDA(cudaGetLastError());
+    g.prof.launched();
         k_prep<<<1, 32, 0, p.stream>>>(w->ctl, w->cand[0], w->touched[0], seed);
+        g.prof.launched();
     } else {
         k_init_pairs<real><<<grid, kThreads, 0, p.stream>>>(g.n, g.deg, (real *)w->x,
                                                             (RPair<real> *)w->rp, p.eps, seed);
         GDE_CUDA(cudaGetLastError());
+    g.prof.launched();
         k_prep<<<1, 32, 0, p.stream>>>(w->ctl, w->cand[0], nullptr, seed);
+        g.prof.launched();
     }
     GDE_CUDA(cudaGetLastError());
     w->kind = p.kind;
@@ -502,6 +506,7 @@ static int64_t round_impl(Graph &g, DenseWork *w, const SolveParams &p, RoundInf
     const bool last_layer = KIND == GDE_HK && t >= p.hk_N;
     k_prep<<<1, 32, 0, p.stream>>>(w->ctl, nullptr, nullptr, 0);
     GDE_CUDA(cudaGetLastError());
+    g.prof.launched();
 
     FrontierArgs<real> fa{};
     fa.off = g.off;
@@ -532,6 +537,7 @@ static int64_t round_impl(Graph &g, DenseWork *w, const SolveParams &p, RoundInf
     const int pf = g.prof.start(kProfDenseFrontier, p.stream);
     k_frontier<real, KIND><<<grid_for(fitems), kThreads, 0, p.stream>>>(fa);
     GDE_CUDA(cudaGetLastError());
+    g.prof.launched();
     g.prof.stop(pf, p.stream);
 
     if (!last_layer) {
@@ -555,6 +561,7 @@ static int64_t round_impl(Graph &g, DenseWork *w, const SolveParams &p, RoundInf
         const int pp = g.prof.start(kProfDensePush, p.stream);
         k_push<real, KIND><<<kSMs * 4, kThreads, 0, p.stream>>>(pa);
         GDE_CUDA(cudaGetLastError());
+    g.prof.launched();
         g.prof.stop(pp, p.stream);
     }
     GDE_CUDA(cudaMemcpyAsync(w->hctl, w->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, p.stream));
@@ -649,6 +656,7 @@ void dense_output(Graph &g, DenseWork *w, const SolveParams &p, void *dst_dev) {
         k_scale_copy<float><<<grid_for(g.n), kThreads, 0, p.stream>>>(g.n, (const float *)w->x,
                                                                       (float *)dst_dev, scale, apply);
     GDE_CUDA(cudaGetLastError());
+    g.prof.launched();
 }
 
 }  // namespace gde

@@ -183,3 +183,18 @@ def test_full_size_rmat24_sampled(gde):
     for n, i in enumerate(sample):
         check_topk(g, ids[i], vals[i], xs[n], 1e-7)
         assert stats[i]["active_volume"] == pytest.approx(info[n][1], rel=0.02)
+
+
+def test_consecutive_solves_reuse_the_pool(gde, rmat16):
+    """The top-k scan resets the tables it read, so back-to-back solves on one graph with
+    different seeds and batch sizes must not see each other's accumulators."""
+    g = rmat16
+    G = gde.Graph.from_synth(g)
+    all_seeds = synth.seeds_mixed(g, 64, 64, seed=12)
+    for sel in (all_seeds[:64], all_seeds[64:80], all_seeds[40:104], all_seeds[:64]):
+        st, stats, ids, vals = run_batched(gde, G, "ppr", 0.1, 1e-6, sel)
+        assert st == gde.OK
+        for i in (0, len(sel) - 1):
+            ref = oracle.localgd(g, "ppr", 0.1, 1e-6, int(sel[i]))
+            check_topk(g, ids[i], vals[i], ref.x, 1e-6)
+            assert stats[i]["mass_l1"] + stats[i]["resid_l1"] == pytest.approx(1.0, abs=1e-4)
