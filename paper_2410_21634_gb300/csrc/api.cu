@@ -131,6 +131,8 @@ static SolveParams make_params(Graph &g, gde_kind kind, double param, double eps
     p.hk_tol = o.hk_tol > 0.0 ? o.hk_tol : 1e-12;
     p.max_rounds = o.max_rounds > 0 ? o.max_rounds : 1000000;
     p.hk_N = kind == GDE_HK ? hk_terms(param, p.hk_tol) : 0;
+    GDE_REQUIRE(o.deterministic == 0 || o.deterministic == 1, GDE_EINVAL, "bad deterministic flag");
+    p.deterministic = o.deterministic;
     p.stream = o.cuda_stream ? (cudaStream_t)o.cuda_stream : g.stream;
     return p;
 }
@@ -262,7 +264,8 @@ gde_status gde_solve(gde_graph *h, gde_kind kind, double param, double eps, cons
     GDE_REQUIRE(o.topk <= 64, GDE_EINVAL, "topk must be <= 64");
     GDE_REQUIRE(o.topk == 0 || o.precision == GDE_FP32, GDE_EINVAL, "topk output is FP32");
     GDE_REQUIRE(o.batched == 0 || o.batched == 1, GDE_EINVAL, "bad batched flag");
-    GDE_REQUIRE(o.deterministic == 0, GDE_EINVAL, "deterministic mode is not available in this build");
+    GDE_REQUIRE(!(o.deterministic && o.batched), GDE_EINVAL,
+                "deterministic mode solves one seed at a time (batched must be 0)");
     const bool dev = (o.flags & GDE_DEVICE_PTRS) != 0;
     std::vector<int32_t> hs((size_t)nseeds);
     if (dev) {

@@ -110,6 +110,7 @@ struct SolveParams {
     double hk_tol;
     int64_t max_rounds;
     int64_t hk_N;      // Taylor layers - 1 (HK)
+    int deterministic; // sort-based scatter (dense engine)
     cudaStream_t stream;
 };
 

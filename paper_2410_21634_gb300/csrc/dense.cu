@@ -24,6 +24,7 @@
 #include <cstring>
 
 #include "common.cuh"
+#include "detsort.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -70,6 +71,17 @@ struct DenseWork {
     Ctl *ctl = nullptr;
     Ctl *hctl = nullptr;  // pinned
     Bins bins;
+    // deterministic scatter (sort + segmented reduce), allocated on first use
+    void *wbuf = nullptr;            // real[n]
+    uint32_t *sact[2] = {nullptr, nullptr};   // sorted active ids + temporary
+    int64_t *vdeg = nullptr;         // degrees of the sorted active nodes, then their edge starts
+    int64_t *vstart = nullptr;
+    uint32_t *pkey[2] = {nullptr, nullptr};   // pair targets v
+    void *pval[2] = {nullptr, nullptr};       // pair shares w
+    void *dscratch = nullptr;
+    int64_t *dtotal = nullptr;       // device scalar
+    int64_t *htotal = nullptr;       // pinned
+    int64_t pair_cap = 0;
     // host-side round state
     gde_kind kind = GDE_PPR;
     int64_t t = 0;
@@ -176,6 +188,7 @@ template <typename real> struct FrontierArgs {
     const int32_t *clear_list;
     unsigned nclear;
     real *rclear;
+    real *wbuf;           // deterministic mode: per-node share of the pushed nodes (no bins)
 };
 
 template <typename real, int KIND>
@@ -220,7 +233,9 @@ __global__ void __launch_bounds__(kThreads) k_frontier(FrontierArgs<real> a) {
                     w64 = __ddiv_rn(__dmul_rn(a.coef, rho64), (double)d);
                 const real w = from_f64<real>(w64);
                 my_scat += __dmul_rn((double)w, (double)d);
-                if (d <= a.t1) {
+                if (a.wbuf) {
+                    a.wbuf[u] = w;
+                } else if (d <= a.t1) {
                     cg::coalesced_group g = cg::coalesced_threads();
                     unsigned base = 0;
                     if (g.thread_rank() == 0) base = atomicAdd(&a.ctl->cnt_small, (unsigned)g.size());
@@ -399,6 +414,74 @@ __global__ void k_read_r_pairs(int64_t n, const RPair<real> *__restrict__ rp, re
         dst[i] = rp[i].r;
 }
 
+// ---------------------------------------------------- deterministic scatter --
+//
+// Each round: the active ids are sorted, their edges are written out as (v, w_u) pairs in
+// ascending u and CSR order, the pairs are sorted by v with a stable sort (so equal targets
+// keep ascending u), and each target adds its run sequentially to the residual it had after
+// the frontier phase.  That is the order of a sequential FP64 evaluation of Eq. (local-gd)
+// that pushes S_t in ascending id, and the result does not depend on thread timing.
+
+__global__ void k_det_degrees(int64_t na, const uint32_t *__restrict__ act, const int64_t *__restrict__ off,
+                              int64_t *__restrict__ deg) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < na; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t u = act[i];
+        deg[i] = off[u + 1] - off[u];
+    }
+}
+
+template <typename real>
+__global__ void k_det_expand(int64_t na, const uint32_t *__restrict__ act, const int64_t *__restrict__ off,
+                             const int32_t *__restrict__ col, const int64_t *__restrict__ vstart,
+                             const real *__restrict__ wbuf, uint32_t *__restrict__ pkey, real *__restrict__ pval) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = gw; i < na; i += nw) {
+        const uint32_t u = act[i];
+        const int64_t b = off[u], d = off[u + 1] - b, s = vstart[i];
+        const real w = wbuf[u];
+        for (int64_t k = lane; k < d; k += 32) {
+            pkey[s + k] = (uint32_t)col[b + k];
+            pval[s + k] = w;
+        }
+    }
+}
+
+// one thread per run of equal targets: sequential sum in pair order, then the threshold test
+// on the run's start and end values (contributions are positive)
+template <typename real, int KIND>
+__global__ void k_det_apply(int64_t np, const uint32_t *__restrict__ pkey, const real *__restrict__ pval,
+                            RPair<real> *rp, real *rnext, const int32_t *__restrict__ deg, double eps_theta_next,
+                            int32_t *cand_out, int32_t *touched_out, Ctl *ctl, unsigned cap) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < np; p += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t v = pkey[p];
+        if (p > 0 && pkey[p - 1] == v) continue;
+        real r0, thr;
+        double thr64 = 0.0;
+        if (KIND == GDE_HK) {
+            r0 = rnext[v];
+            thr64 = __dmul_rn(eps_theta_next, (double)deg[v]);
+        } else {
+            r0 = rp[v].r;
+            thr = rp[v].thr;
+        }
+        real r = r0;
+        for (int64_t q = p; q < np && pkey[q] == v; q++) r = radd<real>(r, pval[q]);
+        bool cross;
+        if (KIND == GDE_HK) {
+            rnext[v] = r;
+            if (r0 == real(0) && r != real(0))
+                append_u32(&ctl->touched_out, touched_out, (int32_t)v, cap, &ctl->overflow);
+            cross = (double)r0 < thr64 && (double)r >= thr64;
+        } else {
+            rp[v].r = r;
+            cross = r0 < thr && r >= thr;
+        }
+        if (cross) append_u32(&ctl->cand_out, cand_out, (int32_t)v, cap, &ctl->overflow);
+    }
+}
+
 // ============================================================ host side =====
 
 static unsigned grid_for(int64_t items, int64_t per_block = kThreads) {
@@ -435,6 +518,25 @@ DenseWork *dense_work_create(Graph &g, int precision) {
     return w;
 }
 
+static void ensure_det(DenseWork *w, Graph &g) {
+    if (w->wbuf) return;
+    const int64_t n = w->n > 0 ? w->n : 1;
+    w->pair_cap = g.nnz > 0 ? g.nnz : 1;
+    w->wbuf = dmalloc(w->rsz * n, "deterministic shares");
+    w->sact[0] = (uint32_t *)dmalloc(4 * n, "sorted active");
+    w->vdeg = (int64_t *)dmalloc(8 * n, "active degrees");
+    w->vstart = (int64_t *)dmalloc(8 * n, "active edge starts");
+    for (int k = 0; k < 2; k++) {
+        w->pkey[k] = (uint32_t *)dmalloc(4 * (size_t)w->pair_cap, "pair targets");
+        w->pval[k] = dmalloc(w->rsz * (size_t)w->pair_cap, "pair shares");
+    }
+    const int64_t big = w->pair_cap > n ? w->pair_cap : n;
+    size_t sb = sort_scratch_bytes(big), cb = scan_scratch_bytes(n);
+    w->dscratch = dmalloc(sb > cb ? sb : cb, "sort scratch");
+    w->dtotal = (int64_t *)dmalloc(sizeof(int64_t), "pair count");
+    GDE_CUDA(cudaMallocHost((void **)&w->htotal, sizeof(int64_t)));
+}
+
 static void ensure_layers(DenseWork *w) {
     if (w->rl[0]) return;
     const int64_t n = w->n > 0 ? w->n : 1;
@@ -461,6 +563,10 @@ void dense_work_destroy(DenseWork *w) {
     }
     dfree(w->hub_vstart);
     dfree(w->ctl);
+    dfree(w->wbuf);
+    for (int k = 0; k < 2; k++) { dfree(w->sact[k]); dfree(w->pkey[k]); dfree(w->pval[k]); }
+    dfree(w->vdeg); dfree(w->vstart); dfree(w->dscratch); dfree(w->dtotal);
+    if (w->htotal) cudaFreeHost(w->htotal);
     if (w->hctl) cudaFreeHost(w->hctl);
     delete w;
 }
@@ -532,6 +638,10 @@ static int64_t round_impl(Graph &g, DenseWork *w, const SolveParams &p, RoundInf
     fa.hub_vstart = w->hub_vstart;
     fa.active = w->active;
     fa.ctl = w->ctl;
+    if (p.deterministic) {
+        ensure_det(w, g);
+        fa.wbuf = (real *)w->wbuf;
+    }
     fa.cap = (unsigned)(g.n > 0 ? g.n : 1);
     const int64_t fitems = w->ncand > fa.nclear ? (int64_t)w->ncand : (int64_t)fa.nclear;
     const int pf = g.prof.start(kProfDenseFrontier, p.stream);
@@ -540,7 +650,43 @@ static int64_t round_impl(Graph &g, DenseWork *w, const SolveParams &p, RoundInf
     g.prof.launched();
     g.prof.stop(pf, p.stream);
 
-    if (!last_layer) {
+    if (!last_layer && p.deterministic) {
+        // S_t is known only on the device: read its size, then sort, expand, sort, apply
+        GDE_CUDA(cudaMemcpyAsync(w->hctl, w->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, p.stream));
+        GDE_CUDA(cudaStreamSynchronize(p.stream));
+        GDE_REQUIRE(w->hctl->overflow == 0, GDE_ECUDA, "internal list overflow in a LocalGD round");
+        const int64_t na = w->hctl->n_active;
+        int key_bits = 1;
+        while (((int64_t)1 << key_bits) < g.n) key_bits++;
+        if (na > 0) {
+            uint32_t *act = (uint32_t *)w->active;
+            const int r1 = radix_sort<uint32_t>(act, nullptr, w->sact[0], nullptr, na, key_bits, w->dscratch, p.stream);
+            const uint32_t *sorted = r1 ? w->sact[0] : act;
+            k_det_degrees<<<grid_for(na), kThreads, 0, p.stream>>>(na, sorted, g.off, w->vdeg);
+            GDE_CUDA(cudaGetLastError());
+            exclusive_scan_i64(w->vdeg, w->vstart, na, w->dtotal, (int64_t *)w->dscratch, p.stream);
+            GDE_CUDA(cudaMemcpyAsync(w->htotal, w->dtotal, sizeof(int64_t), cudaMemcpyDeviceToHost, p.stream));
+            GDE_CUDA(cudaStreamSynchronize(p.stream));
+            const int64_t np = *w->htotal;
+            GDE_REQUIRE(np >= 0 && np <= w->pair_cap, GDE_ECUDA, "deterministic scatter: pair count out of range");
+            if (np > 0) {
+                k_det_expand<real><<<grid_for(na * 32), kThreads, 0, p.stream>>>(
+                    na, sorted, g.off, g.col, w->vstart, (const real *)w->wbuf, w->pkey[0], (real *)w->pval[0]);
+                GDE_CUDA(cudaGetLastError());
+                const int r2 = radix_sort<real>(w->pkey[0], (real *)w->pval[0], w->pkey[1], (real *)w->pval[1],
+                                                np, key_bits, w->dscratch, p.stream);
+                const uint32_t *pk = w->pkey[r2];
+                const real *pv = (const real *)w->pval[r2];
+                double etn = 0.0;
+                if (KIND == GDE_HK) etn = hk_theta(p.param, p.hk_N, t + 1, p.hk_mode) * p.eps;
+                k_det_apply<real, KIND><<<grid_for(np), kThreads, 0, p.stream>>>(
+                    np, pk, pv, (RPair<real> *)w->rp, KIND == GDE_HK ? (real *)w->rl[nxt] : nullptr, g.deg, etn,
+                    w->cand[nxt], KIND == GDE_HK ? w->touched[nxt] : nullptr, w->ctl, (unsigned)(g.n > 0 ? g.n : 1));
+                GDE_CUDA(cudaGetLastError());
+                g.prof.launched(2 * ((key_bits + 3) / 4) * 5 + 4);
+            }
+        }
+    } else if (!last_layer) {
         PushArgs<real> pa{};
         pa.col = g.col;
         pa.deg = g.deg;
