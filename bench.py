@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--seeds", type=int, default=1024)
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the library's default tuning")
     ap.add_argument("--budget-gb", type=float, default=0.0,
                     help="hash accumulator budget (0: the library default)")
     return ap.parse_args()
@@ -249,6 +250,13 @@ def main():
         return gde.solve(G, "ppr", ALPHA, EPS, seeds, vals, ids, precision="fp32", topk=TOPK, batched=1,
                          mem_budget_bytes=budget)
 
+    # the project's autotuner picks the push's bin thresholds, hub chunk, order and grid on
+    # this batch before anything is timed
+    tuning, tune_ms = None, None
+    if not args.no_autotune:
+        t0 = time.time()
+        tuning, tune_ms = G.autotune("ppr", ALPHA, EPS, seeds, topk=TOPK, mem_budget_bytes=budget)
+        log(f"[bench] autotune: {tuning} ({tune_ms:.1f} ms) in {time.time() - t0:.1f}s")
     for _ in range(max(args.warmup, 3)):
         st, stats = step()
     overflow = sum(1 for s in stats if s["status"] == gde.ENOMEM)
@@ -367,6 +375,8 @@ def main():
         "hash_overflow_seeds": overflow,
         "edges_per_step": edges_step,
         "rounds_per_step": prof["rounds"] / launches,
+        "tuning": G.get_tuning(),
+        "autotuned": tuning is not None,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -185,6 +185,18 @@ gde_status gde_set_tuning(gde_graph *g, const gde_tuning *t);
 gde_status gde_get_tuning(const gde_graph *g, gde_tuning *t);
 
 /*
+ * Autotuner of the batched push: one pass of coordinate descent over t1, t2, chunk,
+ * schedule and blocks_per_sm (in that order; each tried over a fixed candidate list with the
+ * others held), timing batched solves of `seeds` (kind/param/eps/opts as for gde_solve;
+ * opts->topk in [1,64], batched forced on, FP32) with CUDA events on the solve stream, the
+ * fastest of two timed runs per candidate.  The best tuning is applied to g as by
+ * gde_set_tuning and, if best is not NULL, returned; *best_ms (may be NULL) receives its time.
+ * Allocates its own device buffers; results of the timed solves are discarded.
+ */
+gde_status gde_autotune(gde_graph *g, gde_kind kind, double param, double eps, const int32_t *seeds,
+                        int32_t nseeds, const gde_solve_opts *opts, gde_tuning *best, double *best_ms);
+
+/*
  * Top-k of a dense float vector that allocates no device memory (no counterpart in the
  * paper: an interface for callers that cannot allocate).  Some callers cannot call
  * cudaMalloc: an application that has already handed all device memory to its own pool

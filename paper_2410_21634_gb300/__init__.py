@@ -29,7 +29,8 @@ STATUS_NAMES = {0: "GDE_OK", 1: "GDE_EINVAL", 2: "GDE_ENOMEM", 3: "GDE_ECUDA",
 EXPORTED = ["gde_solve_opts_init", "gde_graph_create", "gde_graph_destroy", "gde_graph_info",
             "gde_solve", "gde_last_error", "gde_session_begin", "gde_session_step",
             "gde_session_read", "gde_session_end", "gde_profile_enable", "gde_profile_read",
-            "gde_topk_f32_noalloc", "gde_profile_rounds", "gde_set_tuning", "gde_get_tuning"]
+            "gde_topk_f32_noalloc", "gde_profile_rounds", "gde_set_tuning", "gde_get_tuning",
+            "gde_autotune"]
 
 
 class GdeError(RuntimeError):
@@ -108,7 +109,9 @@ def load(path: str | None = None):
     lib.gde_profile_rounds.argtypes = [vp, vp, I64, ctypes.POINTER(I64)]
     lib.gde_set_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
     lib.gde_get_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
-    for name in ("gde_profile_rounds", "gde_set_tuning", "gde_get_tuning"):
+    lib.gde_autotune.argtypes = [vp, ctypes.c_int, D, D, vp, I32, ctypes.POINTER(SolveOpts),
+                                 ctypes.POINTER(Tuning), ctypes.POINTER(D)]
+    for name in ("gde_profile_rounds", "gde_set_tuning", "gde_get_tuning", "gde_autotune"):
         getattr(lib, name).restype = ctypes.c_int
     lib.gde_profile_enable.argtypes = [vp, ctypes.c_int]
     lib.gde_profile_read.argtypes = [vp, ctypes.POINTER(Profile)]
@@ -225,6 +228,20 @@ class Graph:
         t = Tuning()
         _check(load().gde_get_tuning(self._h, ctypes.byref(t)))
         return {f: getattr(t, f) for f, _ in t._fields_}
+
+    def autotune(self, kind, param: float, eps: float, seeds, **opt_kw):
+        """gde_autotune on this graph; returns (tuning dict, best ms)."""
+        ps, ds = _ptr(seeds)
+        flags = opt_kw.pop("flags", 0) | (DEVICE_PTRS if ds else 0)
+        if ds and "stream" not in opt_kw:
+            opt_kw["stream"] = _current_stream()
+        opt_kw.setdefault("topk", 64)
+        o = make_opts(flags=flags, precision=FP32, batched=1, **opt_kw)
+        t = Tuning()
+        ms = ctypes.c_double()
+        _check(load().gde_autotune(self._h, _kind(kind), float(param), float(eps), ps, int(seeds.shape[0]),
+                                   ctypes.byref(o), ctypes.byref(t), ctypes.byref(ms)))
+        return {f: getattr(t, f) for f, _ in t._fields_}, ms.value
 
     def close(self):
         if getattr(self, "_h", None):

@@ -143,6 +143,14 @@ static DenseWork *dense_for(Graph &g, int precision) {
     return g.dense[k];
 }
 
+static void tuning_from_bins(const Bins &b, gde_tuning *t) {
+    t->t1 = b.t1;
+    t->t2 = b.t2;
+    t->chunk = b.chunk;
+    t->blocks_per_sm = b.blocks_per_sm;
+    t->schedule = b.schedule == 1 ? 1 : (b.schedule == 0 ? 2 : 3);
+}
+
 }  // namespace gde
 
 using namespace gde;
@@ -425,11 +433,97 @@ gde_status gde_set_tuning(gde_graph *h, const gde_tuning *t) {
 gde_status gde_get_tuning(const gde_graph *h, gde_tuning *t) {
     API_BEGIN
     GDE_REQUIRE(h != nullptr && t != nullptr, GDE_EINVAL, "graph or tuning is NULL");
-    t->t1 = h->g.bins.t1;
-    t->t2 = h->g.bins.t2;
-    t->chunk = h->g.bins.chunk;
-    t->blocks_per_sm = h->g.bins.blocks_per_sm;
-    t->schedule = h->g.bins.schedule == 1 ? 1 : (h->g.bins.schedule == 0 ? 2 : 3);
+    tuning_from_bins(h->g.bins, t);
+    API_END
+}
+
+gde_status gde_autotune(gde_graph *h, gde_kind kind, double param, double eps, const int32_t *seeds,
+                        int32_t nseeds, const gde_solve_opts *opts, gde_tuning *best, double *best_ms) {
+    API_BEGIN
+    GDE_REQUIRE(h != nullptr && seeds != nullptr && nseeds > 0, GDE_EINVAL, "graph, seeds or nseeds invalid");
+    gde_solve_opts o;
+    gde_solve_opts_init(&o);
+    if (opts) o = *opts;
+    o.batched = 1;
+    o.precision = GDE_FP32;
+    o.deterministic = 0;
+    if (o.topk <= 0) o.topk = 64;
+    GDE_REQUIRE(o.topk <= 64, GDE_EINVAL, "topk must be <= 64");
+    Graph &g = h->g;
+    std::lock_guard<std::mutex> lock(g.mu);
+    SolveParams p = make_params(g, kind, param, eps, o);
+    GDE_REQUIRE(kind == GDE_PPR || kind == GDE_KATZ, GDE_EINVAL, "the batched push serves PPR and Katz");
+    const bool dev = (o.flags & GDE_DEVICE_PTRS) != 0;
+    std::vector<void *> owned;
+    auto alloc = [&](size_t bytes, const char *what) {
+        void *q = dmalloc(bytes, what);
+        owned.push_back(q);
+        return q;
+    };
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    const Bins saved = g.bins;
+    try {
+        int32_t *sd = (int32_t *)alloc(4 * (size_t)nseeds, "autotune seeds");
+        GDE_CUDA(cudaMemcpyAsync(sd, seeds, 4 * (size_t)nseeds,
+                                 dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, p.stream));
+        int32_t *ids = (int32_t *)alloc(4 * (size_t)nseeds * o.topk, "autotune ids");
+        float *vals = (float *)alloc(4 * (size_t)nseeds * o.topk, "autotune values");
+        std::vector<int32_t> of((size_t)nseeds);
+        GDE_CUDA(cudaEventCreate(&e0));
+        GDE_CUDA(cudaEventCreate(&e1));
+        auto time_bins = [&](const Bins &b) {
+            g.bins = b;
+            int32_t nof = 0;
+            batch_solve(g, p, sd, nseeds, o.topk, o.mem_budget_bytes, ids, vals, nullptr, of.data(), &nof);
+            float bestt = 1e30f;
+            for (int rep = 0; rep < 2; rep++) {
+                GDE_CUDA(cudaEventRecord(e0, p.stream));
+                batch_solve(g, p, sd, nseeds, o.topk, o.mem_budget_bytes, ids, vals, nullptr, of.data(), &nof);
+                GDE_CUDA(cudaEventRecord(e1, p.stream));
+                GDE_CUDA(cudaEventSynchronize(e1));
+                float ms = 0.0f;
+                GDE_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < bestt) bestt = ms;
+            }
+            return (double)bestt;
+        };
+        Bins cur = saved;
+        double cur_ms = time_bins(cur);
+        const int t1s[] = {4, 8, 16, 32};
+        const int t2s[] = {128, 256, 512, 1024, 2048};
+        const int chunks[] = {256, 512, 1024, 2048, 4096};
+        const int scheds[] = {0, 1, 2};
+        const int bpss[] = {0, 3, 2};
+        auto sweep = [&](const int *vals_, int nv, int Bins::*field, bool need_order) {
+            for (int i = 0; i < nv; i++) {
+                Bins b = cur;
+                b.*field = vals_[i];
+                if (need_order && b.t1 > b.t2) continue;
+                if (b.*field == cur.*field) continue;
+                const double ms = time_bins(b);
+                if (ms < cur_ms) { cur_ms = ms; cur = b; }
+            }
+        };
+        sweep(t1s, 4, &Bins::t1, true);
+        sweep(t2s, 5, &Bins::t2, true);
+        sweep(chunks, 5, &Bins::chunk, false);
+        sweep(scheds, 3, &Bins::schedule, false);
+        sweep(bpss, 3, &Bins::blocks_per_sm, false);
+        g.bins = cur;
+        for (int k = 0; k < 2; k++)
+            if (g.dense[k]) { dense_work_destroy(g.dense[k]); g.dense[k] = nullptr; }
+        if (best) tuning_from_bins(cur, best);
+        if (best_ms) *best_ms = cur_ms;
+    } catch (...) {
+        g.bins = saved;
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        for (void *q : owned) dfree(q);
+        throw;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (void *q : owned) dfree(q);
     API_END
 }
 

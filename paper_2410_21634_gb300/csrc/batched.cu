@@ -1124,7 +1124,9 @@ void batch_solve(Graph &g, const SolveParams &p, const int32_t *seeds_dev, int32
     // per-round frontier of all seeds together is far smaller than the pool; past this
     // capacity the solve reports GDE_ENOMEM
     int64_t list_cap = (int64_t)nseeds * cap;
-    const int64_t list_max = (int64_t)1 << 24;
+    int64_t list_max = (int64_t)nseeds << 14;
+    if (list_max < ((int64_t)1 << 22)) list_max = (int64_t)1 << 22;
+    if (list_max > ((int64_t)1 << 24)) list_max = (int64_t)1 << 24;
     if (list_cap > list_max) list_cap = list_max;
     GDE_REQUIRE(nseeds <= list_cap, GDE_EINVAL, "too many seeds for one batch");
     BatchWork *w = batch_work_get(g, nseeds, cap, list_cap);

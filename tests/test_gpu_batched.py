@@ -198,3 +198,22 @@ def test_consecutive_solves_reuse_the_pool(gde, rmat16):
             ref = oracle.localgd(g, "ppr", 0.1, 1e-6, int(sel[i]))
             check_topk(g, ids[i], vals[i], ref.x, 1e-6)
             assert stats[i]["mass_l1"] + stats[i]["resid_l1"] == pytest.approx(1.0, abs=1e-4)
+
+
+def test_autotune_picks_a_valid_tuning(gde, rmat16):
+    """gde_autotune sweeps the push's bins, chunk, order and grid on a sample batch, applies
+    the fastest, and solves stay correct with it."""
+    g = rmat16
+    G = gde.Graph.from_synth(g)
+    seeds = synth.seeds_mixed(g, 16, 16, seed=13)
+    before = G.get_tuning()
+    best, ms = G.autotune("ppr", 0.1, 1e-6, seeds, topk=K)
+    assert ms > 0
+    assert best["t1"] in (4, 8, 16, 32) and best["t2"] in (128, 256, 512, 1024, 2048)
+    assert best["t1"] <= best["t2"] and best["chunk"] in (256, 512, 1024, 2048, 4096)
+    assert best["schedule"] in (1, 2, 3) and best["blocks_per_sm"] in (0, 2, 3)
+    assert G.get_tuning() == best and set(before) == set(best)
+    st, stats, ids, vals = run_batched(gde, G, "ppr", 0.1, 1e-6, seeds)
+    for i in (0, 31):
+        ref = oracle.localgd(g, "ppr", 0.1, 1e-6, int(seeds[i]))
+        check_topk(g, ids[i], vals[i], ref.x, 1e-6)
