@@ -450,7 +450,10 @@ __device__ T block_scan(const T *in, T *out, int64_t n, T *s_warp) {
     return carry;
 }
 
-__global__ void __launch_bounds__(kThreads) k_batch_rounds(BArgs a) {
+#ifndef GDE_ROUNDS_MIN_BLOCKS
+#define GDE_ROUNDS_MIN_BLOCKS 8  // 32 registers: full occupancy (the kernel is latency-bound)
+#endif
+__global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_rounds(BArgs a) {
     const unsigned nblocks = gridDim.x;
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
@@ -650,7 +653,13 @@ __global__ void __launch_bounds__(kThreads) k_batch_rounds(BArgs a) {
             // hubs: merge-path chunks of the concatenated hub adjacency, one warp per chunk,
             // consecutive lanes on consecutive columns
             if (VH > 0) {
-                const int64_t nchunks = (VH + a.chunk - 1) / a.chunk;
+                // small rounds get shorter chunks so every warp has a share (a lone warp walking
+                // a long chunk would set the round's latency)
+                int64_t chunk = (VH + 2 * nw - 1) / (2 * nw);
+                chunk = (chunk + 31) & ~(int64_t)31;
+                if (chunk < 64) chunk = 64;
+                if (chunk > a.chunk) chunk = a.chunk;
+                const int64_t nchunks = (VH + chunk - 1) / chunk;
                 for (int64_t it = 0;; it++) {
                     int64_t c;
                     if (a.schedule <= 1) {
@@ -661,8 +670,8 @@ __global__ void __launch_bounds__(kThreads) k_batch_rounds(BArgs a) {
                         c = gw + it * nw;
                     }
                     if (c >= nchunks) break;
-                    const int64_t e0 = c * a.chunk;
-                    const int64_t e1 = min(e0 + (int64_t)a.chunk, VH);
+                    const int64_t e0 = c * chunk;
+                    const int64_t e1 = min(e0 + chunk, VH);
                     int64_t lo = 0, hi = H;
                     while (hi - lo > 1) {
                         const int64_t mid = (lo + hi) >> 1;
