@@ -164,7 +164,7 @@ gde_status gde_profile_read(gde_graph *g, gde_profile *out);
 gde_status gde_profile_rounds(gde_graph *g, double *out, int64_t cap, int64_t *rounds);
 
 /*
- * Launch shape of the push (SURVEY-style degree bins): nodes with d <= t1 are pushed by one
+ * Launch shape of the push (degree bins): nodes with d <= t1 are pushed by one
  * thread, t1 < d <= t2 by one warp, d > t2 in merge-path chunks of `chunk` edges over the
  * concatenated hub adjacency; blocks_per_sm sets the persistent grid (0 = the occupancy
  * limit); schedule orders the batched scatter: 1 hands hub chunks to warps in bin order (the
