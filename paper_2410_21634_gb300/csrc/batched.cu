@@ -326,6 +326,10 @@ struct ThrBounds {
     float lo, hi;  // lo <= thr_v <= hi; lo == hi means exact
 };
 
+// the brackets of every degree code, built once per block of the round kernel (the FP64
+// products that define them are then not on the per-edge path)
+__shared__ float2 s_thr_br[256];
+
 __device__ __forceinline__ ThrBounds thr_bounds(const BArgs &a, uint32_t code) {
     ThrBounds t;
     if ((int)code < a.code_exact) {
@@ -358,7 +362,9 @@ __device__ __forceinline__ unsigned bscatter(const BArgs &a, int32_t j, uint32_t
     const uint32_t kcur = (uint32_t)v | a.key_tag;
     ThrBounds tb;
     if (a.colp) {
-        tb = thr_bounds(a, packed >> a.idbits);
+        const float2 br = s_thr_br[packed >> a.idbits];
+        tb.lo = br.x;
+        tb.hi = br.y;
     } else {
         tb.lo = tb.hi = a.thr32[v];
     }
@@ -451,14 +457,17 @@ __device__ T block_scan(const T *in, T *out, int64_t n, T *s_warp) {
 }
 
 #ifndef GDE_ROUNDS_MIN_BLOCKS
-#define GDE_ROUNDS_MIN_BLOCKS 8  // 32 registers: full occupancy (the kernel is latency-bound)
+#define GDE_ROUNDS_MIN_BLOCKS 6  // 40 registers, 48 warps per SM (the kernel is latency-bound)
 #endif
 __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_rounds(BArgs a) {
     const unsigned nblocks = gridDim.x;
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t gw = tid >> 5, nw = nthreads >> 5;
+    const int64_t nw = nthreads >> 5;
+    // warp rank, warp-major across blocks: the first k warps sit on k different SMs, so a
+    // phase that only needs a few warps still spreads them over the GPU
+    const int64_t gw = (int64_t)wid * gridDim.x + blockIdx.x;
     BGlobal *G = a.glob;
     const unsigned long long t_start = globaltimer();
     __shared__ uint32_t s_stage[kWarps][kStage];
@@ -469,6 +478,19 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
     __syncwarp();
     __shared__ double s_rs[kWarps];
     __shared__ unsigned long long s_vol[kWarps];
+    __shared__ unsigned long long s_busy[kWarps];
+    if (a.colp) {
+        for (int c = threadIdx.x; c < 256; c += kThreads) {
+            // codes past the last log2 class never occur in the columns
+            if (c >= a.code_exact && c - a.code_exact > 32) {
+                s_thr_br[c] = make_float2(__int_as_float(0x7f800000), __int_as_float(0x7f800000));
+                continue;
+            }
+            const ThrBounds tb = thr_bounds(a, (uint32_t)c);
+            s_thr_br[c] = make_float2(tb.lo, tb.hi);
+        }
+    }
+    __syncthreads();
 
     for (int64_t t = 0; t < a.max_rounds; t++) {
         const int p = (int)(t & 1);
@@ -660,7 +682,9 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
                 if (chunk < 64) chunk = 64;
                 if (chunk > a.chunk) chunk = a.chunk;
                 const int64_t nchunks = (VH + chunk - 1) / chunk;
-                for (int64_t it = 0;; it++) {
+                // warps beyond the chunk count would only find the work gone: they stay out,
+                // so small rounds do not queue every warp on the hand-out counter
+                for (int64_t it = 0; gw < nchunks; it++) {
                     int64_t c;
                     if (a.schedule <= 1) {
                         unsigned long long cg_ = 0;
@@ -703,7 +727,7 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
             // medium degrees: one warp per node
             const unsigned nmed = min(__ldcg(&ctl->cnt_med), a.list_cap);
             // descending: the hub sweep ends at the last seeds, the medium sweep starts there
-            for (int64_t it = 0;; it++) {
+            for (int64_t it = 0; gw * kMedGrab < (int64_t)nmed; it++) {
                 unsigned got = 0;
                 if (a.schedule == 0) {
                     if (lane == 0) got = atomicAdd(&ctl->med_next, (unsigned)kMedGrab);
@@ -729,7 +753,7 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
             }
             // small degrees: one thread per node (warp-uniform loops so the warp can flush)
             const unsigned nsm = min(__ldcg(&ctl->cnt_small), a.list_cap);
-            for (int64_t it = 0;; it++) {
+            for (int64_t it = 0; gw * 32 < (int64_t)nsm; it++) {
                 int64_t i0;
                 if (a.schedule == 0) {
                     unsigned got = 0;
@@ -757,12 +781,17 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
             }
         }
         stage_flush(sbuf, sn, true, ctl, cand_out, a.list_cap);
-        {
-            // phase-B busy time of this warp (for the load-balance record)
+        if (t < kLogCap) {
+            // phase-B busy time of the warps (for the load-balance record), summed per block
+            // first so the record costs two global atomics per block
             const unsigned long long busy = globaltimer() - tb0;
-            if (lane == 0 && t < kLogCap) {
-                atomicAdd(&a.log[t].busy_sum_ns, busy);
-                atomicMax(&a.log[t].busy_max_ns, busy);
+            if (lane == 0) s_busy[wid] = busy;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                unsigned long long bs = 0, bm = 0;
+                for (int w2 = 0; w2 < kWarps; w2++) { bs += s_busy[w2]; bm = bm > s_busy[w2] ? bm : s_busy[w2]; }
+                atomicAdd(&a.log[t].busy_sum_ns, bs);
+                atomicMax(&a.log[t].busy_max_ns, bm);
             }
         }
         if (!grid_sync(G, nblocks)) return;
