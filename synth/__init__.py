@@ -255,3 +255,27 @@ def workload_graph(name: str, **override) -> Graph:
         g = rmat(spec["scale"], spec["edge_factor"], seed=spec["seed"])
     g.name = name
     return g
+
+
+# ------------------------------------------------------------ dynamic graphs ----
+
+def random_edges(n: int, m: int, seed: int) -> tuple[np.ndarray, np.ndarray]:
+    """m endpoint pairs drawn uniformly over the n nodes (an edge-insertion batch of the
+    serving workload; self-loops and repeats are left in, the consumer skips them)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return (rng.integers(0, n, size=m).astype(np.int32), rng.integers(0, n, size=m).astype(np.int32))
+
+
+def with_edges(g: Graph, src, dst) -> Graph:
+    """g plus the undirected edges (src[i], dst[i]) (self-loops and duplicates dropped)."""
+    rows = np.repeat(np.arange(g.n, dtype=np.int32), np.diff(g.offsets))
+    return from_pairs(g.n, np.concatenate([rows, np.asarray(src, dtype=np.int32)]),
+                      np.concatenate([g.cols, np.asarray(dst, dtype=np.int32)]), name=g.name, info=dict(g.info))
+
+
+def poisson_arrivals(rate_per_s: float, duration_s: float, seed: int) -> np.ndarray:
+    """Arrival times (seconds, ascending) of a Poisson stream of the given rate."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    gaps = rng.exponential(1.0 / rate_per_s, size=int(rate_per_s * duration_s * 1.5) + 16)
+    t = np.cumsum(gaps)
+    return t[t < duration_s]
