@@ -112,6 +112,29 @@ gde_status gde_graph_destroy(gde_graph *g);
 gde_status gde_graph_info(const gde_graph *g, int64_t *n, int64_t *nnz, int32_t *max_degree);
 
 /*
+ * Copies the current CSR out: offsets (n + 1 int64) and cols (nnz int32), host arrays or,
+ * with GDE_DEVICE_PTRS in flags, device arrays, allocated by the caller (sizes from
+ * gde_graph_info).  Either pointer may be NULL to skip it.  Synchronous.
+ */
+gde_status gde_graph_csr(const gde_graph *g, int64_t *offsets, int32_t *cols, uint32_t flags);
+
+/*
+ * Edge insertion (the dynamic graphs of Section 4: G_t becomes G_{t+1} through a batch of
+ * insertion events).  Inserts the m undirected edges (src[i], dst[i]): both adjacencies
+ * src -> dst and dst -> src are added to the CSR, self-loops and adjacencies already present
+ * are skipped (the graph stays simple; rows stay sorted), degrees follow.  src and dst are
+ * host arrays, or device arrays if flags has GDE_DEVICE_PTRS; the library copies them.
+ * *added (may be NULL) receives the number of directed adjacencies added.  Solves issued
+ * afterwards see the new graph; solved states of earlier calls are not corrected here (a
+ * server, below, corrects its resident queries).  Errors: GDE_EINVAL for m < 0, NULL arrays
+ * with m > 0 or an endpoint outside [0, n) (the graph is then unchanged); GDE_ENOMEM if the
+ * new arrays cannot be allocated (the graph is then unchanged).  Synchronous: returns after
+ * the device CSR has been rebuilt.
+ */
+gde_status gde_update_edges(gde_graph *g, const int32_t *src, const int32_t *dst, int64_t m, uint32_t flags,
+                            int64_t *added);
+
+/*
  * Approximate diffusion vectors for nseeds independent unit sources.
  *   kind, param  GDE_PPR with alpha in (0,1); GDE_KATZ with beta > 0 (LocalGD terminates
  *                when beta lambda_max(A) < 1); GDE_HK with tau > 0

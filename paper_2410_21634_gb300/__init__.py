@@ -30,7 +30,7 @@ EXPORTED = ["gde_solve_opts_init", "gde_graph_create", "gde_graph_destroy", "gde
             "gde_solve", "gde_last_error", "gde_session_begin", "gde_session_step",
             "gde_session_read", "gde_session_end", "gde_profile_enable", "gde_profile_read",
             "gde_topk_f32_noalloc", "gde_profile_rounds", "gde_set_tuning", "gde_get_tuning",
-            "gde_autotune"]
+            "gde_autotune", "gde_update_edges", "gde_graph_csr"]
 
 
 class GdeError(RuntimeError):
@@ -111,7 +111,10 @@ def load(path: str | None = None):
     lib.gde_get_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
     lib.gde_autotune.argtypes = [vp, ctypes.c_int, D, D, vp, I32, ctypes.POINTER(SolveOpts),
                                  ctypes.POINTER(Tuning), ctypes.POINTER(D)]
-    for name in ("gde_profile_rounds", "gde_set_tuning", "gde_get_tuning", "gde_autotune"):
+    lib.gde_update_edges.argtypes = [vp, vp, vp, I64, ctypes.c_uint32, ctypes.POINTER(I64)]
+    lib.gde_graph_csr.argtypes = [vp, vp, vp, ctypes.c_uint32]
+    for name in ("gde_profile_rounds", "gde_set_tuning", "gde_get_tuning", "gde_autotune",
+                 "gde_update_edges", "gde_graph_csr"):
         getattr(lib, name).restype = ctypes.c_int
     lib.gde_profile_enable.argtypes = [vp, ctypes.c_int]
     lib.gde_profile_read.argtypes = [vp, ctypes.POINTER(Profile)]
@@ -203,6 +206,26 @@ class Graph:
         n, nnz, md = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
         _check(load().gde_graph_info(self._h, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(md)))
         return {"n": n.value, "nnz": nnz.value, "max_degree": md.value}
+
+    def update_edges(self, src, dst) -> int:
+        """gde_update_edges: insert the undirected edges (src[i], dst[i]); returns the number
+        of directed adjacencies added."""
+        ps, ds = _ptr(src)
+        pd, dd = _ptr(dst)
+        if ds != dd or src.shape != dst.shape:
+            raise ValueError("src and dst must be alike (both host or both device, same length)")
+        added = ctypes.c_int64()
+        _check(load().gde_update_edges(self._h, ps, pd, int(src.shape[0]), DEVICE_PTRS if ds else 0,
+                                       ctypes.byref(added)))
+        return added.value
+
+    def csr(self):
+        """gde_graph_csr: (offsets int64 [n+1], cols int32 [nnz]) of the current graph."""
+        inf = self.info()
+        off = np.zeros(inf["n"] + 1, dtype=np.int64)
+        cols = np.zeros(max(inf["nnz"], 1), dtype=np.int32)
+        _check(load().gde_graph_csr(self._h, off.ctypes.data, cols.ctypes.data, 0))
+        return off, cols[: inf["nnz"]]
 
     def profile_enable(self, enable: bool = True):
         _check(load().gde_profile_enable(self._h, int(enable)))

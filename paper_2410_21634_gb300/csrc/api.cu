@@ -254,6 +254,30 @@ gde_status gde_graph_info(const gde_graph *h, int64_t *n, int64_t *nnz, int32_t 
     API_END
 }
 
+gde_status gde_graph_csr(const gde_graph *hc, int64_t *offsets, int32_t *cols, uint32_t flags) {
+    API_BEGIN
+    GDE_REQUIRE(hc != nullptr, GDE_EINVAL, "graph is NULL");
+    gde_graph *h = const_cast<gde_graph *>(hc);
+    Graph &g = h->g;
+    std::lock_guard<std::mutex> lock(g.mu);
+    const cudaMemcpyKind k = (flags & GDE_DEVICE_PTRS) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (offsets) GDE_CUDA(cudaMemcpyAsync(offsets, g.off, 8 * (size_t)(g.n + 1), k, g.stream));
+    if (cols && g.nnz > 0) GDE_CUDA(cudaMemcpyAsync(cols, g.col, 4 * (size_t)g.nnz, k, g.stream));
+    GDE_CUDA(cudaStreamSynchronize(g.stream));
+    API_END
+}
+
+gde_status gde_update_edges(gde_graph *h, const int32_t *src, const int32_t *dst, int64_t m, uint32_t flags,
+                            int64_t *added) {
+    API_BEGIN
+    GDE_REQUIRE(h != nullptr, GDE_EINVAL, "graph is NULL");
+    Graph &g = h->g;
+    std::lock_guard<std::mutex> lock(g.mu);
+    const int64_t a = graph_insert_edges(g, src, dst, m, (flags & GDE_DEVICE_PTRS) != 0, nullptr);
+    if (added) *added = a;
+    API_END
+}
+
 gde_status gde_solve(gde_graph *h, gde_kind kind, double param, double eps, const int32_t *seeds,
                      int32_t nseeds, const gde_solve_opts *opts, void *out_x, int32_t *out_ids,
                      gde_stats *stats) {

@@ -1068,6 +1068,21 @@ static void batch_free(BatchWork *w) {
 
 void batch_work_destroy(BatchWork *w) { batch_free(w); }
 
+// the CSR changed (edge insertions): columns, degrees and offsets moved, so the packed
+// columns and thresholds are rebuilt on the next solve and the dense workspaces dropped
+void graph_changed(Graph &g) {
+    for (int k = 0; k < 2; k++) {
+        dense_work_destroy(g.dense[k]);
+        g.dense[k] = nullptr;
+    }
+    if (BatchWork *w = g.batch) {
+        dfree(w->colp);
+        w->colp = nullptr;
+        w->thr_eps = -1.0;
+        w->thr_n = -1;
+    }
+}
+
 static BatchWork *batch_work_get(Graph &g, int64_t nseeds, int64_t cap, int64_t list_cap) {
     BatchWork *w = g.batch;
     if (w && w->nseeds_cap >= nseeds && w->cap == cap && w->list_cap >= list_cap) return w;

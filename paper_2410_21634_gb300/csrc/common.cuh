@@ -99,6 +99,27 @@ enum : unsigned {
 
 void graph_validate(Graph &g, bool check_symmetric, unsigned *bits_out);
 
+// Directed adjacencies added by one insertion batch (device arrays; sorted by (u, v)), with
+// the rows that gained them and those rows' degrees before the batch.
+struct EdgeBatch {
+    int64_t m = 0;               // adjacencies added
+    int32_t *u = nullptr, *v = nullptr;
+    int64_t rows = 0;            // rows that gained adjacencies (ascending)
+    int32_t *row = nullptr;
+    int32_t *row_cnt = nullptr;  // adjacencies gained by each
+    int64_t *row_start = nullptr;  // first of them in u / v
+    int32_t *old_deg = nullptr;  // degree before the batch
+};
+
+// Inserts the undirected edges (src[i], dst[i]) into g (both directions; self-loops and
+// present adjacencies skipped) and returns the number of directed adjacencies added.  If out
+// is not NULL it receives the batch (free with edge_batch_free).  Derived per-graph state
+// (packed columns, thresholds, cached workspaces) is dropped through graph_changed.
+int64_t graph_insert_edges(Graph &g, const int32_t *src, const int32_t *dst, int64_t m, bool dev_ptrs,
+                           EdgeBatch *out);
+void edge_batch_free(EdgeBatch &b);
+void graph_changed(Graph &g);
+
 // ------------------------------------------------------------------- solve --
 
 struct SolveParams {
