@@ -265,6 +265,79 @@ gde_status gde_session_step(gde_session *s, int64_t *n_active);
 gde_status gde_session_read(gde_session *s, void *x, void *r, int32_t *active, int64_t *n_active);
 gde_status gde_session_end(gde_session *s);
 
+/*
+ * Serving (continuous batching of PPR and Katz queries on a graph that receives edge
+ * insertions; the dynamic setting of Section 4).  A server owns a pool of `slots` resident
+ * queries, each a per-query hash table of FP32 x and r in device memory (12 bytes per
+ * table slot; the pool holds mem_budget_bytes, default 16 GB, so slots * cap * 12 <= budget
+ * with cap a power of two <= 2 n).
+ *   gde_server_submit        queues a query (qid chosen by the caller; kind GDE_PPR with
+ *                            param = alpha in (0,1), or GDE_KATZ with param = beta > 0;
+ *                            eps_class picks one of the server's tolerances; t_submit is the
+ *                            arrival time on gde_server_clock, < 0 for now).  Returns at once.
+ *   gde_server_insert_edges  queues an edge-insertion batch (copied); applied at the next step.
+ *   gde_server_step          one device step: applies the queued edge batches to the graph
+ *                            (as gde_update_edges) and corrects every resident query's state
+ *                            for them (the Insert of Algorithm 3: x_u rescaled, r moved along
+ *                            the new adjacencies; Katz: r_v += beta x_u), so it resumes from
+ *                            there instead of from its seed; admits queued queries into free
+ *                            slots (then into the slots answered longest ago) in arrival
+ *                            order; runs at most rounds_per_step LocalGD rounds of all resident
+ *                            queries in one persistent launch; and emits the top-k of every
+ *                            query that has no active node left (first answer, or an update
+ *                            after an edge batch).  *running and *queued (may be NULL) receive
+ *                            the queries still running and still waiting.
+ *   gde_server_poll          moves up to cap emitted results into out (oldest first).
+ * Results: ids/vals hold the k largest x entries (x desc, id asc; -1 pads), x approximates
+ * f_PPR, or (I - beta A)^-1 e_s for Katz, within the eps bound of Corollary 3.6 on the graph
+ * as of the step that emitted it; t_done - t_submit is the latency (for an update: from the
+ * step that applied the edge batch).  status GDE_ENOMEM: the query's table filled up (its
+ * slot is released).  submit / insert_edges / poll may be called from other threads while a
+ * step runs; steps are serialised.  Errors as elsewhere (GDE_EINVAL for bad arguments; a step
+ * that fails leaves the server unusable and reports the failure).
+ */
+typedef struct gde_server gde_server;
+
+typedef struct {
+    int32_t slots;            /* resident queries (default 256) */
+    int32_t rounds_per_step;  /* LocalGD rounds per device step (default 4) */
+    int32_t topk;             /* entries per result, 1..64 (default 64) */
+    int32_t n_eps;            /* tolerance classes, 1..4 (default 1) */
+    double eps[4];            /* their tolerances (default eps[0] = 1e-6) */
+    int64_t mem_budget_bytes; /* hash pool bytes, 0 = 16 GB */
+} gde_server_opts;
+
+typedef struct {
+    uint64_t qid;
+    int32_t status;           /* GDE_OK or GDE_ENOMEM */
+    int32_t update;           /* 0: first answer, 1: refreshed after an edge batch */
+    int32_t k;
+    int32_t slot;
+    int64_t volume;           /* edges pushed for this query so far */
+    double t_submit, t_done;  /* gde_server_clock seconds */
+    int32_t ids[64];
+    float vals[64];
+} gde_server_result;
+
+typedef struct {
+    int32_t slots, running, answered, queued;
+    int64_t steps;            /* device steps so far */
+    int64_t rounds;           /* LocalGD rounds run by the pool so far */
+    int64_t edge_batches;     /* insertion batches applied */
+    int64_t cap;              /* hash slots per query table */
+} gde_server_info_t;
+
+void gde_server_opts_init(gde_server_opts *o);
+double gde_server_clock(void);  /* steady clock, seconds */
+gde_status gde_server_create(gde_graph *g, const gde_server_opts *opts, gde_server **out);
+gde_status gde_server_destroy(gde_server *s);
+gde_status gde_server_submit(gde_server *s, uint64_t qid, gde_kind kind, double param, int32_t eps_class,
+                             int32_t seed, double t_submit);
+gde_status gde_server_insert_edges(gde_server *s, const int32_t *src, const int32_t *dst, int64_t m);
+gde_status gde_server_step(gde_server *s, int32_t *running, int32_t *queued);
+gde_status gde_server_poll(gde_server *s, gde_server_result *out, int32_t cap, int32_t *n);
+gde_status gde_server_info(gde_server *s, gde_server_info_t *info);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,7 +30,9 @@ EXPORTED = ["gde_solve_opts_init", "gde_graph_create", "gde_graph_destroy", "gde
             "gde_solve", "gde_last_error", "gde_session_begin", "gde_session_step",
             "gde_session_read", "gde_session_end", "gde_profile_enable", "gde_profile_read",
             "gde_topk_f32_noalloc", "gde_profile_rounds", "gde_set_tuning", "gde_get_tuning",
-            "gde_autotune", "gde_update_edges", "gde_graph_csr"]
+            "gde_autotune", "gde_update_edges", "gde_graph_csr", "gde_server_opts_init",
+            "gde_server_clock", "gde_server_create", "gde_server_destroy", "gde_server_submit",
+            "gde_server_insert_edges", "gde_server_step", "gde_server_poll", "gde_server_info"]
 
 
 class GdeError(RuntimeError):
@@ -74,6 +76,24 @@ class Tuning(ctypes.Structure):
                 ("blocks_per_sm", ctypes.c_int32), ("schedule", ctypes.c_int32)]
 
 
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("rounds_per_step", ctypes.c_int32), ("topk", ctypes.c_int32),
+                ("n_eps", ctypes.c_int32), ("eps", ctypes.c_double * 4), ("mem_budget_bytes", ctypes.c_int64)]
+
+
+class ServerResult(ctypes.Structure):
+    _fields_ = [("qid", ctypes.c_uint64), ("status", ctypes.c_int32), ("update", ctypes.c_int32),
+                ("k", ctypes.c_int32), ("slot", ctypes.c_int32), ("volume", ctypes.c_int64),
+                ("t_submit", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("ids", ctypes.c_int32 * 64), ("vals", ctypes.c_float * 64)]
+
+
+class ServerInfo(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("running", ctypes.c_int32), ("answered", ctypes.c_int32),
+                ("queued", ctypes.c_int32), ("steps", ctypes.c_int64), ("rounds", ctypes.c_int64),
+                ("edge_batches", ctypes.c_int64), ("cap", ctypes.c_int64)]
+
+
 _lib = None
 
 
@@ -113,6 +133,20 @@ def load(path: str | None = None):
                                  ctypes.POINTER(Tuning), ctypes.POINTER(D)]
     lib.gde_update_edges.argtypes = [vp, vp, vp, I64, ctypes.c_uint32, ctypes.POINTER(I64)]
     lib.gde_graph_csr.argtypes = [vp, vp, vp, ctypes.c_uint32]
+    lib.gde_server_opts_init.argtypes = [ctypes.POINTER(ServerOpts)]
+    lib.gde_server_opts_init.restype = None
+    lib.gde_server_clock.argtypes = []
+    lib.gde_server_clock.restype = D
+    lib.gde_server_create.argtypes = [vp, ctypes.POINTER(ServerOpts), ctypes.POINTER(vp)]
+    lib.gde_server_destroy.argtypes = [vp]
+    lib.gde_server_submit.argtypes = [vp, ctypes.c_uint64, ctypes.c_int, D, I32, I32, D]
+    lib.gde_server_insert_edges.argtypes = [vp, vp, vp, I64]
+    lib.gde_server_step.argtypes = [vp, ctypes.POINTER(I32), ctypes.POINTER(I32)]
+    lib.gde_server_poll.argtypes = [vp, ctypes.POINTER(ServerResult), I32, ctypes.POINTER(I32)]
+    lib.gde_server_info.argtypes = [vp, ctypes.POINTER(ServerInfo)]
+    for name in ("gde_server_create", "gde_server_destroy", "gde_server_submit", "gde_server_insert_edges",
+                 "gde_server_step", "gde_server_poll", "gde_server_info"):
+        getattr(lib, name).restype = ctypes.c_int
     for name in ("gde_profile_rounds", "gde_set_tuning", "gde_get_tuning", "gde_autotune",
                  "gde_update_edges", "gde_graph_csr"):
         getattr(lib, name).restype = ctypes.c_int
@@ -353,6 +387,93 @@ class Session:
     def close(self):
         if getattr(self, "_h", None):
             load().gde_session_end(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def server_clock() -> float:
+    """The steady clock (seconds) that server timestamps use."""
+    return float(load().gde_server_clock())
+
+
+class Server:
+    """Continuous-batching server of PPR/Katz queries on a graph with edge insertions
+    (gde_server_*).  submit() and insert_edges() queue work; step() runs one device step;
+    poll() returns the results emitted so far as dicts."""
+
+    def __init__(self, graph: Graph, slots: int = 256, rounds_per_step: int = 4, topk: int = 64,
+                 eps=(1e-6,), mem_budget_bytes: int = 0):
+        lib = load()
+        o = ServerOpts()
+        lib.gde_server_opts_init(ctypes.byref(o))
+        o.slots, o.rounds_per_step, o.topk = int(slots), int(rounds_per_step), int(topk)
+        eps = list(eps)
+        if not 1 <= len(eps) <= 4:
+            raise ValueError("1 to 4 tolerance classes")
+        o.n_eps = len(eps)
+        for i, e in enumerate(eps):
+            o.eps[i] = float(e)
+        o.mem_budget_bytes = int(mem_budget_bytes)
+        h = ctypes.c_void_p()
+        _check(lib.gde_server_create(graph.handle, ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        self.graph = graph
+        self.topk = int(topk)
+
+    def submit(self, qid: int, kind, param: float, eps_class: int, seed: int, t_submit: float = -1.0):
+        _check(load().gde_server_submit(self._h, int(qid), _kind(kind), float(param), int(eps_class),
+                                        int(seed), float(t_submit)))
+
+    def insert_edges(self, src, dst):
+        src = np.ascontiguousarray(src, dtype=np.int32)
+        dst = np.ascontiguousarray(dst, dtype=np.int32)
+        if src.shape != dst.shape:
+            raise ValueError("src and dst differ in length")
+        _check(load().gde_server_insert_edges(self._h, src.ctypes.data, dst.ctypes.data, int(src.shape[0])))
+
+    def step(self):
+        """One device step; returns (queries still running, queries still queued)."""
+        r, q = ctypes.c_int32(), ctypes.c_int32()
+        _check(load().gde_server_step(self._h, ctypes.byref(r), ctypes.byref(q)))
+        return r.value, q.value
+
+    def poll(self, cap: int = 4096):
+        buf = (ServerResult * cap)()
+        n = ctypes.c_int32()
+        _check(load().gde_server_poll(self._h, buf, cap, ctypes.byref(n)))
+        out = []
+        for i in range(n.value):
+            r = buf[i]
+            k = r.k
+            out.append({"qid": r.qid, "status": r.status, "update": bool(r.update), "slot": r.slot,
+                        "volume": r.volume, "t_submit": r.t_submit, "t_done": r.t_done,
+                        "ids": np.frombuffer(r.ids, dtype=np.int32, count=k).copy(),
+                        "vals": np.frombuffer(r.vals, dtype=np.float32, count=k).copy()})
+        return out
+
+    def info(self) -> dict:
+        i = ServerInfo()
+        _check(load().gde_server_info(self._h, ctypes.byref(i)))
+        return {f: getattr(i, f) for f, _ in i._fields_}
+
+    def run_until_idle(self, max_steps: int = 100000):
+        """step() until nothing runs or waits; returns the results emitted meanwhile."""
+        out = []
+        for _ in range(max_steps):
+            running, queued = self.step()
+            out += self.poll()
+            if running == 0 and queued == 0:
+                break
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().gde_server_destroy(self._h)
             self._h = None
 
     def __del__(self):

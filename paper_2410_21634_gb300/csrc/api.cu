@@ -162,13 +162,6 @@ struct gde_session {
     uint32_t flags = 0;
 };
 
-#define API_BEGIN try { clear_error();
-#define API_END                                                                 \
-    }                                                                           \
-    catch (const Fail &f) { return f.st; }                                      \
-    catch (const std::bad_alloc &) { set_error("host allocation failed"); return GDE_ENOMEM; } \
-    catch (...) { set_error("unexpected C++ exception"); return GDE_ECUDA; }    \
-    return GDE_OK;
 
 extern "C" {
 

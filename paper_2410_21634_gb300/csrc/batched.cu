@@ -41,6 +41,17 @@ constexpr unsigned long long kBarrierLimitNs = 20ull * 1000 * 1000 * 1000;  // 2
 
 enum : int { kSeedOk = 0, kSeedOverflow = 1 };
 
+constexpr int kMaxCls = 4;  // tolerance classes one launch can mix (per-slot eps)
+
+// Per-slot solve parameters, for launches that mix queries (a server's slots): x += cx rho,
+// share = coef rho (divided by d_u when divide != 0), tolerance class cls.
+struct SlotParam {
+    double cx;
+    double coef;
+    int32_t divide;
+    int32_t cls;
+};
+
 struct BCtl {  // per-round counters (one set per round parity)
     unsigned long long hub_packed;
     unsigned int cnt_small;
@@ -215,8 +226,13 @@ struct BArgs {
     int idbits;
     uint32_t idmask;
     int code_exact;         // codes below this are exact degrees; from it on, log2 classes
-    double eps;
-    const float *thr32;
+    double eps;              // tolerance of class 0
+    double eps_cls[kMaxCls]; // tolerance of each class
+    int ncls;
+    const float *thr32;      // ncls arrays of n thresholds, thr_stride apart
+    int64_t thr_stride;
+    const SlotParam *sparam; // per-slot parameters, or NULL: kind/cx/coef below, class 0
+    int64_t t0;              // first round of this launch (a resumed launch continues t)
     uint32_t key_idmask;    // node-id bits of a table key
     uint32_t key_tag;       // this solve's epoch tag, already shifted above the id bits
     uint32_t *xlist;
@@ -328,45 +344,51 @@ struct ThrBounds {
 
 // the brackets of every degree code, built once per block of the round kernel (the FP64
 // products that define them are then not on the per-edge path)
-__shared__ float2 s_thr_br[256];
+__shared__ float2 s_thr_br[kMaxCls][256];
 
-__device__ __forceinline__ ThrBounds thr_bounds(const BArgs &a, uint32_t code) {
+__device__ __forceinline__ ThrBounds thr_bounds(const BArgs &a, double eps, uint32_t code) {
     ThrBounds t;
     if ((int)code < a.code_exact) {
-        t.lo = t.hi = __double2float_ru(__dmul_rn(a.eps, (double)code));
+        t.lo = t.hi = __double2float_ru(__dmul_rn(eps, (double)code));
     } else {
         const int k = (int)code - a.code_exact;
-        t.lo = __double2float_ru(__dmul_rn(a.eps, (double)(1ll << k)));
-        t.hi = __double2float_ru(__dmul_rn(a.eps, (double)((2ll << k) - 1)));
+        t.lo = __double2float_ru(__dmul_rn(eps, (double)(1ll << k)));
+        t.hi = __double2float_ru(__dmul_rn(eps, (double)((2ll << k) - 1)));
     }
     return t;
 }
 
-// did a residual going from `old` to `nv` cross v's threshold?  Reads thr32[v] only when the
-// bracket cannot decide.
-__device__ __forceinline__ bool crossed(const BArgs &a, int32_t v, ThrBounds tb, float old, float nv) {
-    if (nv < tb.lo || old >= tb.hi) return false;
-    const float thr = tb.lo == tb.hi ? tb.lo : a.thr32[v];
-    return old < thr && nv >= thr;
+// did a residual going from `old` to `nv` cross v's threshold, |old| < thr <= |nv|?  Reads the
+// class's threshold array only when the bracket cannot decide.  (With nonnegative residuals
+// this happens once per node and round; when corrections made some residuals negative a node
+// can cross more than once, and the frontier phase drops the repeats.)
+__device__ __forceinline__ bool crossed(const float *thr32c, int32_t v, ThrBounds tb, float old, float nv) {
+    const float ao = fabsf(old), an = fabsf(nv);
+    if (an < tb.lo || ao >= tb.hi) return false;
+    const float thr = tb.lo == tb.hi ? tb.lo : thr32c[v];
+    return ao < thr && an >= thr;
 }
+
+__device__ __forceinline__ int slot_cls(const BArgs &a, int32_t j) { return a.sparam ? a.sparam[j].cls : 0; }
 
 // Insert-or-add w at node v of seed j's table.  The probe starts at a 4-slot bucket (one
 // 32-byte sector) chosen by mix32(v) and continues linearly bucket by bucket; slots are
 // examined in order, so the first empty slot ends the search (keys are never removed).  A
 // residual that crosses its threshold from below (exactly once: contributions are positive)
 // is staged as a candidate of the next round.  Returns 1 if v was a new key.
-__device__ __forceinline__ unsigned bscatter(const BArgs &a, int32_t j, uint32_t packed, float w,
+__device__ __forceinline__ unsigned bscatter(const BArgs &a, int32_t j, int cls, uint32_t packed, float w,
                                              uint32_t *sbuf, unsigned *sn) {
     const uint64_t base = (uint64_t)j << a.log2cap;
     const int32_t v = (int32_t)(packed & a.idmask);
     const uint32_t kcur = (uint32_t)v | a.key_tag;
+    const float *thr32c = a.thr32 + (int64_t)cls * a.thr_stride;
     ThrBounds tb;
     if (a.colp) {
-        const float2 br = s_thr_br[packed >> a.idbits];
+        const float2 br = s_thr_br[cls][packed >> a.idbits];
         tb.lo = br.x;
         tb.hi = br.y;
     } else {
-        tb.lo = tb.hi = a.thr32[v];
+        tb.lo = tb.hi = thr32c[v];
     }
     const uint32_t sector_mask = a.mask >= 3 ? 3u : a.mask;
     uint32_t h = mix32((uint32_t)v) & a.mask & ~sector_mask;
@@ -388,14 +410,14 @@ __device__ __forceinline__ unsigned bscatter(const BArgs &a, int32_t j, uint32_t
                 const uint32_t key = (uint32_t)(wk & 0xFFFFFFFFull);
                 if (key == kcur) {
                     const float old = atomicAdd(r_of(a.kr, slot), w);
-                    if (crossed(a, v, tb, old, __fadd_rn(old, w))) stage_push(sbuf, sn, (uint32_t)slot);
+                    if (crossed(thr32c, v, tb, old, __fadd_rn(old, w))) stage_push(sbuf, sn, (uint32_t)slot);
                     return 0;
                 }
                 // another node of this solve: next slot (empty and stale-tag slots are free)
                 if (key != kEmpty && (key & ~a.key_idmask) == a.key_tag) break;
                 const unsigned long long prev = atomicCAS(a.kr + slot, wk, slot_word(kcur, w));
                 if (prev == wk) {
-                    if (crossed(a, v, tb, 0.0f, w)) stage_push(sbuf, sn, (uint32_t)slot);
+                    if (crossed(thr32c, v, tb, 0.0f, w)) stage_push(sbuf, sn, (uint32_t)slot);
                     return 1;
                 }
                 wk = prev;  // lost the race: look at what was written into this slot
@@ -480,19 +502,21 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
     __shared__ unsigned long long s_vol[kWarps];
     __shared__ unsigned long long s_busy[kWarps];
     if (a.colp) {
-        for (int c = threadIdx.x; c < 256; c += kThreads) {
+        for (int i = threadIdx.x; i < a.ncls * 256; i += kThreads) {
+            const int cls = i >> 8, c = i & 255;
             // codes past the last log2 class never occur in the columns
             if (c >= a.code_exact && c - a.code_exact > 32) {
-                s_thr_br[c] = make_float2(__int_as_float(0x7f800000), __int_as_float(0x7f800000));
+                s_thr_br[cls][c] = make_float2(__int_as_float(0x7f800000), __int_as_float(0x7f800000));
                 continue;
             }
-            const ThrBounds tb = thr_bounds(a, (uint32_t)c);
-            s_thr_br[c] = make_float2(tb.lo, tb.hi);
+            const ThrBounds tb = thr_bounds(a, a.eps_cls[cls], (uint32_t)c);
+            s_thr_br[cls][c] = make_float2(tb.lo, tb.hi);
         }
     }
     __syncthreads();
 
-    for (int64_t t = 0; t < a.max_rounds; t++) {
+    for (int64_t t = a.t0; t < a.t0 + a.max_rounds; t++) {
+        const int64_t lt = t - a.t0;  // round of this launch (log row)
         const int p = (int)(t & 1);
         BCtl *ctl = &G->ctl[p];
         BCtl *prev = &G->ctl[p ^ 1];
@@ -511,24 +535,31 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
             if (__ldcg(a.status + j) != kSeedOk) { __stcg(a.tmp_deg + ci, 0); continue; }
             const unsigned long long word = __ldcg(a.kr + slot);
             const int32_t v = (int32_t)((uint32_t)(word & 0xFFFFFFFFull) & a.key_idmask);
-            const float rho = __uint_as_float((uint32_t)(word >> 32));
-            const float thr = a.thr32[v];
+            float rho = __uint_as_float((uint32_t)(word >> 32));
+            double cx = a.cx, coef = a.coef;
+            bool divide = a.kind != GDE_KATZ;
+            int cls = 0;
+            if (a.sparam) {
+                const SlotParam sp = a.sparam[j];
+                cx = sp.cx; coef = sp.coef; divide = sp.divide != 0; cls = sp.cls;
+            }
+            const float thr = a.thr32[(int64_t)cls * a.thr_stride + v];
             if (!(rho != 0.0f && fabsf(rho) >= thr)) { __stcg(a.tmp_deg + ci, 0); continue; }
-            __stcg(r_of(a.kr, slot), 0.0f);
+            // take the residual: a slot listed twice (possible once residuals can be negative)
+            // is pushed by one taker only
+            rho = atomicExch(r_of(a.kr, slot), 0.0f);
+            if (!(rho != 0.0f && fabsf(rho) >= thr)) { __stcg(a.tmp_deg + ci, 0); continue; }
             const double rho64 = (double)rho;
             const float xold = __ldcg(a.xs + slot);
-            if (a.kind == GDE_PPR)
-                __stcg(a.xs + slot, __fadd_rn(xold, __double2float_rn(__dmul_rn(a.cx, rho64))));
-            else
-                __stcg(a.xs + slot, __fadd_rn(xold, rho));
+            __stcg(a.xs + slot, __fadd_rn(xold, __double2float_rn(__dmul_rn(cx, rho64))));
             const int64_t beg = a.off[v];
             const int32_t d = (int32_t)(a.off[v + 1] - beg);
             float w = 0.0f;
             if (d > 0) {
-                if (a.kind == GDE_KATZ)
-                    w = __double2float_rn(__dmul_rn(a.coef, rho64));
+                if (divide)
+                    w = __double2float_rn(__ddiv_rn(__dmul_rn(coef, rho64), (double)d));
                 else
-                    w = __double2float_rn(__ddiv_rn(__dmul_rn(a.coef, rho64), (double)d));
+                    w = __double2float_rn(__dmul_rn(coef, rho64));
             }
             my_rs += fabs(rho64);
             my_vol += (unsigned long long)d;
@@ -655,7 +686,7 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
             }
         }
         if (!grid_sync(G, nblocks)) return;
-        if (tid == 0 && t < kLogCap) a.log[t].tA_ns = globaltimer() - t_start;
+        if (tid == 0 && lt < kLogCap) a.log[lt].tA_ns = globaltimer() - t_start;
         const unsigned long long tb0 = globaltimer();
 
         // ---------------- phase B: scatter ----------------
@@ -707,6 +738,7 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
                     int64_t hb = __ldcg(a.b_beg[2] + h);
                     float hw = __ldcg(a.b_w[2] + h);
                     int32_t hj = __ldcg(a.b_seed[2] + h);
+                    int hcls = slot_cls(a, hj);
                     for (int64_t eb = e0; eb < e1; eb += 32) {
                         const int64_t e = eb + lane;
                         if (e < e1) {
@@ -717,8 +749,9 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
                                 hb = __ldcg(a.b_beg[2] + h);
                                 hw = __ldcg(a.b_w[2] + h);
                                 hj = __ldcg(a.b_seed[2] + h);
+                                hcls = slot_cls(a, hj);
                             }
-                            bscatter(a, hj, push_col(a, hb + (e - hs)), hw, sbuf, sn);
+                            bscatter(a, hj, hcls, push_col(a, hb + (e - hs)), hw, sbuf, sn);
                         }
                         stage_flush(sbuf, sn, false, ctl, cand_out, a.list_cap);
                     }
@@ -744,9 +777,10 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
                 const int32_t d = __ldcg(a.b_deg[1] + i);
                 const float w = __ldcg(a.b_w[1] + i);
                 const int32_t j = __ldcg(a.b_seed[1] + i);
+                const int cls = slot_cls(a, j);
                 for (int32_t k0 = 0; k0 < d; k0 += 32) {
                     const int32_t k = k0 + lane;
-                    if (k < d) bscatter(a, j, push_col(a, b + k), w, sbuf, sn);
+                    if (k < d) bscatter(a, j, cls, push_col(a, b + k), w, sbuf, sn);
                     stage_flush(sbuf, sn, false, ctl, cand_out, a.list_cap);
                 }
                 }
@@ -774,14 +808,15 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
                     j = __ldcg(a.b_seed[0] + i);
                 }
                 const int32_t dmax = (int32_t)__reduce_max_sync(0xffffffffu, (unsigned)d);
+                const int cls = d > 0 ? slot_cls(a, j) : 0;
                 for (int32_t k = 0; k < dmax; k++) {
-                    if (k < d) bscatter(a, j, push_col(a, b + k), w, sbuf, sn);
+                    if (k < d) bscatter(a, j, cls, push_col(a, b + k), w, sbuf, sn);
                     stage_flush(sbuf, sn, false, ctl, cand_out, a.list_cap);
                 }
             }
         }
         stage_flush(sbuf, sn, true, ctl, cand_out, a.list_cap);
-        if (t < kLogCap) {
+        if (lt < kLogCap) {
             // phase-B busy time of the warps (for the load-balance record), summed per block
             // first so the record costs two global atomics per block
             const unsigned long long busy = globaltimer() - tb0;
@@ -790,8 +825,8 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
             if (threadIdx.x == 0) {
                 unsigned long long bs = 0, bm = 0;
                 for (int w2 = 0; w2 < kWarps; w2++) { bs += s_busy[w2]; bm = bm > s_busy[w2] ? bm : s_busy[w2]; }
-                atomicAdd(&a.log[t].busy_sum_ns, bs);
-                atomicMax(&a.log[t].busy_max_ns, bm);
+                atomicAdd(&a.log[lt].busy_sum_ns, bs);
+                atomicMax(&a.log[lt].busy_max_ns, bm);
             }
         }
         if (!grid_sync(G, nblocks)) return;
@@ -801,12 +836,12 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
             G->rounds = (unsigned)(t + 1);
             const unsigned long long rv = __ldcg(&ctl->vol);
             G->total_vol += rv;
-            if (t < kLogCap) {
-                a.log[t].vol = rv;
-                a.log[t].rS_l1 = __ldcg(&ctl->rS_l1);
-                a.log[t].ncand = ncand;
-                a.log[t].n_active = next;
-                a.log[t].t_ns = globaltimer() - t_start;
+            if (lt < kLogCap) {
+                a.log[lt].vol = rv;
+                a.log[lt].rS_l1 = __ldcg(&ctl->rS_l1);
+                a.log[lt].ncand = ncand;
+                a.log[lt].n_active = next;
+                a.log[lt].t_ns = globaltimer() - t_start;
             }
             if (ovf || next > a.list_cap) atomicCAS(&G->error, 0u, (unsigned)GDE_ENOMEM);
         }
@@ -918,13 +953,16 @@ struct TopkArgs {
     int32_t *out_ids;
     float *out_vals;
     unsigned *ssupport;         // |supp(x)| per seed
+    const int32_t *slots;       // block b reads seed slots[b] (NULL: seed b); output row b
+    int keep;                   // nonzero: leave x in place (a server's resident queries)
 };
 
 // One block per seed: the top-k of (x desc, id asc) over the slots of the seed's x-list (every
 // node with nonzero x), which are zeroed for the next solve.  If the list overflowed, the whole
 // table is scanned instead.
 __global__ void __launch_bounds__(kThreads) k_batch_topk(TopkArgs a) {
-    const int j = blockIdx.x;
+    const int j = a.slots ? a.slots[blockIdx.x] : (int)blockIdx.x;
+    const int64_t orow = blockIdx.x;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint64_t base = (uint64_t)j << a.log2cap;
     unsigned long long ta = 0, tb = 0;
@@ -941,7 +979,7 @@ __global__ void __launch_bounds__(kThreads) k_batch_topk(TopkArgs a) {
             if (x > 0.0f) {
                 const uint32_t v = (uint32_t)(a.kr[slot] & 0xFFFFFFFFull) & a.key_idmask;
                 key = ((unsigned long long)__float_as_uint(x) << 32) | (unsigned long long)(0xFFFFFFFFu - v);
-                a.xs[slot] = 0.0f;
+                if (!a.keep) a.xs[slot] = 0.0f;
                 support++;
             }
         }
@@ -968,8 +1006,8 @@ __global__ void __launch_bounds__(kThreads) k_batch_topk(TopkArgs a) {
             const unsigned long long key = half ? tb : ta;
             if (pos < k) {
                 const bool valid = key != 0;
-                a.out_ids[(int64_t)j * k + pos] = valid ? (int32_t)(0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFull)) : -1;
-                a.out_vals[(int64_t)j * k + pos] = valid ? __uint_as_float((uint32_t)(key >> 32)) : 0.0f;
+                a.out_ids[orow * k + pos] = valid ? (int32_t)(0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFull)) : -1;
+                a.out_vals[orow * k + pos] = valid ? __uint_as_float((uint32_t)(key >> 32)) : 0.0f;
             }
         }
     }
@@ -1083,11 +1121,8 @@ void graph_changed(Graph &g) {
     }
 }
 
-static BatchWork *batch_work_get(Graph &g, int64_t nseeds, int64_t cap, int64_t list_cap) {
-    BatchWork *w = g.batch;
-    if (w && w->nseeds_cap >= nseeds && w->cap == cap && w->list_cap >= list_cap) return w;
-    if (w) { batch_free(w); g.batch = nullptr; }
-    w = new BatchWork();
+static BatchWork *batch_work_alloc(int64_t nseeds, int64_t cap, int64_t list_cap) {
+    BatchWork *w = new BatchWork();
     try {
         w->nseeds_cap = nseeds;
         w->cap = cap;
@@ -1140,8 +1175,80 @@ static BatchWork *batch_work_get(Graph &g, int64_t nseeds, int64_t cap, int64_t 
         batch_free(w);
         throw;
     }
-    g.batch = w;
     return w;
+}
+
+static BatchWork *batch_work_get(Graph &g, int64_t nseeds, int64_t cap, int64_t list_cap) {
+    BatchWork *w = g.batch;
+    if (w && w->nseeds_cap >= nseeds && w->cap == cap && w->list_cap >= list_cap) return w;
+    if (w) { batch_free(w); g.batch = nullptr; }
+    g.batch = batch_work_alloc(nseeds, cap, list_cap);
+    return g.batch;
+}
+
+// packed columns (id | degree code) of the current CSR, built on first use
+static void ensure_colp(Graph &g, BatchWork *w, cudaStream_t s) {
+    if (w->colp || g.nnz <= 0) return;
+    int idbits = 1;
+    while (((int64_t)1 << idbits) < g.n) idbits++;
+    const int spare = 32 - idbits;
+    if (spare < 5) return;
+    const int codes = spare >= 8 ? 256 : (1 << spare);
+    w->colp = (uint32_t *)dmalloc(4 * (size_t)g.nnz, "packed columns");
+    w->colp_idbits = idbits;
+    w->colp_exact = codes - 32;
+    k_pack_columns<<<kSMs * 8, kThreads, 0, s>>>(g.nnz, g.col, g.deg, w->colp, idbits, w->colp_exact);
+    GDE_CUDA(cudaGetLastError());
+    g.prof.launched();
+}
+
+// the fields of the round kernel's arguments that come from the graph and the workspace
+static BArgs bargs_base(Graph &g, BatchWork *w, int64_t cap, int64_t list_cap, int32_t nseeds,
+                        uint32_t key_tag, uint32_t key_idmask) {
+    BArgs a{};
+    a.off = g.off; a.col = g.col; a.thr32 = w->thr32; a.kr = w->kr; a.xs = w->xs;
+    a.colp = w->colp; a.idbits = w->colp_idbits;
+    a.idmask = w->colp ? (uint32_t)(((uint64_t)1 << w->colp_idbits) - 1) : 0xFFFFFFFFu;
+    a.code_exact = w->colp_exact;
+    a.thr_stride = g.n;
+    a.key_idmask = key_idmask; a.key_tag = key_tag;
+    a.xlist = w->xlist; a.xcnt = w->xcnt; a.xcap = (unsigned)w->xcap;
+    a.spush = w->spush; a.sscat = w->sscat;
+    a.log2cap = w->log2cap; a.mask = (uint32_t)(cap - 1); a.nseeds = nseeds;
+    a.status = w->status; a.inserts = w->inserts;
+    a.load_limit = (unsigned)(cap * 3 / 4);
+    a.svol = w->svol; a.spushes = w->spushes; a.slast = w->slast;
+    a.cand[0] = w->cand[0]; a.cand[1] = w->cand[1];
+    a.list_cap = (unsigned)list_cap;
+    for (int b = 0; b < 3; b++) { a.b_beg[b] = w->b_beg[b]; a.b_deg[b] = w->b_deg[b]; a.b_w[b] = w->b_w[b]; a.b_seed[b] = w->b_seed[b]; }
+    a.hub_vstart = w->hub_vstart;
+    a.tmp_beg = w->tmp_beg; a.tmp_deg = w->tmp_deg; a.tmp_w = w->tmp_w; a.tmp_jb = w->tmp_jb;
+    a.seg_cnt = w->seg_cnt; a.seg_off = w->seg_off; a.seg_cur = w->seg_cur;
+    a.seg_hvol = w->seg_hvol; a.vol_off = w->vol_off; a.seg_hcur = w->seg_hcur;
+    a.glob = w->glob; a.log = w->log;
+    const Bins &bins = g.bins;
+    a.t1 = bins.t1; a.t2 = bins.t2; a.chunk = bins.chunk; a.schedule = bins.schedule;
+    return a;
+}
+
+// cooperative launch of the round kernel on the persistent grid (tuning's blocks_per_sm)
+static void launch_rounds(Graph &g, BatchWork *w, const BArgs &a, cudaStream_t s) {
+    int grid = w->grid;
+    if (g.bins.blocks_per_sm > 0 && g.bins.blocks_per_sm * w->sms < grid) grid = g.bins.blocks_per_sm * w->sms;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const int pr = g.prof.start(kProfBatchRounds, s);
+    GDE_CUDA(cudaLaunchKernelEx(&cfg, k_batch_rounds, a));
+    g.prof.launched();
+    g.prof.stop(pr, s);
 }
 
 static inline int64_t floor_pow2(int64_t v) {
@@ -1186,20 +1293,7 @@ void batch_solve(Graph &g, const SolveParams &p, const int32_t *seeds_dev, int32
     cudaStream_t s = p.stream;
     GDE_CUDA(cudaMemcpyAsync(w->seeds, seeds_dev, 4 * (size_t)nseeds, cudaMemcpyDeviceToDevice, s));
     const int64_t pool = (int64_t)nseeds * cap;
-    if (!w->colp && g.nnz > 0) {
-        int idbits = 1;
-        while (((int64_t)1 << idbits) < g.n) idbits++;
-        const int spare = 32 - idbits;
-        if (spare >= 5) {
-            const int codes = spare >= 8 ? 256 : (1 << spare);
-            w->colp = (uint32_t *)dmalloc(4 * (size_t)g.nnz, "packed columns");
-            w->colp_idbits = idbits;
-            w->colp_exact = codes - 32;
-            k_pack_columns<<<kSMs * 8, kThreads, 0, s>>>(g.nnz, g.col, g.deg, w->colp, idbits, w->colp_exact);
-            GDE_CUDA(cudaGetLastError());
-            g.prof.launched();
-        }
-    }
+    ensure_colp(g, w, s);
     // epoch tags: keys carry the solve's tag above their id bits, so the previous solve's keys
     // read as empty; the tables are only reset on first use, after a failure, or when the tag
     // wraps (x is zeroed by the previous top-k through the x-lists)
@@ -1235,51 +1329,16 @@ void batch_solve(Graph &g, const SolveParams &p, const int32_t *seeds_dev, int32
     GDE_CUDA(cudaGetLastError());
     g.prof.launched();
 
-    BArgs a{};
-    a.off = g.off; a.col = g.col; a.thr32 = w->thr32; a.kr = w->kr; a.xs = w->xs;
-    a.colp = w->colp; a.idbits = w->colp_idbits;
-    a.idmask = w->colp ? (uint32_t)(((uint64_t)1 << w->colp_idbits) - 1) : 0xFFFFFFFFu;
-    a.code_exact = w->colp_exact; a.eps = p.eps;
-    a.key_idmask = key_idmask; a.key_tag = key_tag;
-    a.xlist = w->xlist; a.xcnt = w->xcnt; a.xcap = (unsigned)w->xcap;
-    a.spush = w->spush; a.sscat = w->sscat;
-    a.log2cap = w->log2cap; a.mask = (uint32_t)(cap - 1); a.nseeds = nseeds;
-    a.status = w->status; a.inserts = w->inserts;
-    a.load_limit = (unsigned)(cap * 3 / 4);
-    a.svol = w->svol; a.spushes = w->spushes; a.slast = w->slast;
-    a.cand[0] = w->cand[0]; a.cand[1] = w->cand[1];
-    a.list_cap = (unsigned)list_cap;
-    for (int b = 0; b < 3; b++) { a.b_beg[b] = w->b_beg[b]; a.b_deg[b] = w->b_deg[b]; a.b_w[b] = w->b_w[b]; a.b_seed[b] = w->b_seed[b]; }
-    a.hub_vstart = w->hub_vstart;
-    a.tmp_beg = w->tmp_beg; a.tmp_deg = w->tmp_deg; a.tmp_w = w->tmp_w; a.tmp_jb = w->tmp_jb;
-    a.seg_cnt = w->seg_cnt; a.seg_off = w->seg_off; a.seg_cur = w->seg_cur;
-    a.seg_hvol = w->seg_hvol; a.vol_off = w->vol_off; a.seg_hcur = w->seg_hcur;
+    BArgs a = bargs_base(g, w, cap, list_cap, nseeds, key_tag, key_idmask);
+    a.eps = p.eps;
+    a.eps_cls[0] = p.eps; a.ncls = 1; a.sparam = nullptr; a.t0 = 0;
     GDE_CUDA(cudaMemsetAsync(w->seg_cnt, 0, 4 * 3 * (size_t)nseeds, s));
     GDE_CUDA(cudaMemsetAsync(w->seg_hvol, 0, 8 * (size_t)nseeds, s));
-    a.glob = w->glob; a.log = w->log;
     a.kind = p.kind;
     a.cx = p.kind == GDE_PPR ? p.param : 1.0;
     a.coef = p.kind == GDE_PPR ? 1.0 - p.param : p.param;
     a.max_rounds = p.max_rounds;
-    const Bins &bins = g.bins;
-    a.t1 = bins.t1; a.t2 = bins.t2; a.chunk = bins.chunk; a.schedule = bins.schedule;
-
-    int grid = w->grid;
-    if (bins.blocks_per_sm > 0 && bins.blocks_per_sm * w->sms < grid) grid = bins.blocks_per_sm * w->sms;
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3(kThreads);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    const int pr = g.prof.start(kProfBatchRounds, s);
-    GDE_CUDA(cudaLaunchKernelEx(&cfg, k_batch_rounds, a));
-    g.prof.launched();
-    g.prof.stop(pr, s);
+    launch_rounds(g, w, a, s);
 
     TopkArgs ta{};
     ta.kr = w->kr; ta.xs = w->xs; ta.log2cap = w->log2cap; ta.cap = cap; ta.k = k;
@@ -1349,6 +1408,454 @@ void batch_solve(Graph &g, const SolveParams &p, const int32_t *seeds_dev, int32
     }
     if (n_overflow) *n_overflow = nof;
 }
+
+// ============================================================ serving pool ====
+// A long-lived batch whose solves continue across launches (continuous batching): a query is
+// admitted into a free slot (table cleared, unit residual at its seed, the slot listed as a
+// candidate of the next round), resident queries are corrected after edge insertions (the
+// Insert of Algorithm 3, Section 4, applied to every slot whose x touches a changed row), and
+// each launch runs at most R rounds of all slots together, resuming the round counter, the
+// candidate list and every table where the previous launch stopped.  Slots carry their own
+// kind, coefficient and tolerance class.
+
+struct ServePool {
+    BatchWork *w = nullptr;
+    int32_t slots = 0;
+    int64_t cap = 0, list_cap = 0;
+    int ncls = 0;
+    double eps[kMaxCls] = {};
+    float *thr = nullptr;        // ncls arrays of n thresholds
+    int64_t thr_n = -1;          // rebuilt when the graph changed
+    SlotParam *d_param = nullptr;
+    std::vector<SlotParam> h_param;
+    uint32_t key_tag = 0, key_idmask = 0;
+    int64_t T = 0;               // the next round to run
+    unsigned *pend = nullptr;    // per-slot candidates of the next round
+    int32_t *d_list = nullptr;   // slot-list scratch
+    int32_t *d_seeds = nullptr;
+    int32_t *d_ids = nullptr;
+    float *d_vals = nullptr;
+    cudaStream_t s = nullptr;
+};
+
+// device view of one slot table's probing, shared by the admission and correction kernels
+struct SlotTable {
+    unsigned long long *kr;
+    float *xs;
+    int log2cap;
+    uint32_t mask;
+    uint32_t key_tag, key_idmask;
+};
+
+// slot of node v in table j, or -1 (the probe stops at the first free slot)
+__device__ int64_t slot_find(const SlotTable &t, int32_t j, uint32_t v) {
+    const uint64_t base = (uint64_t)j << t.log2cap;
+    const uint32_t kcur = v | t.key_tag;
+    const uint32_t sector_mask = t.mask >= 3 ? 3u : t.mask;
+    uint32_t h = mix32(v) & t.mask & ~sector_mask;
+    for (uint32_t probes = 0; probes <= t.mask && probes < kMaxProbe; probes++) {
+        const uint32_t key = (uint32_t)(ld_relaxed_u64(t.kr + base + h) & 0xFFFFFFFFull);
+        if (key == kcur) return (int64_t)(base + h);
+        if (key == kEmpty || (key & ~t.key_idmask) != t.key_tag) return -1;
+        h = (h + 1) & t.mask;
+    }
+    return -1;
+}
+
+// insert-or-add w at node v of table j; returns the slot (and the residual after the add in
+// *nv), or -1 if the table is full
+__device__ int64_t slot_add(const SlotTable &t, int32_t j, uint32_t v, float w, float *nv) {
+    const uint64_t base = (uint64_t)j << t.log2cap;
+    const uint32_t kcur = v | t.key_tag;
+    const uint32_t sector_mask = t.mask >= 3 ? 3u : t.mask;
+    uint32_t h = mix32(v) & t.mask & ~sector_mask;
+    for (uint32_t probes = 0; probes <= t.mask && probes < kMaxProbe; probes++) {
+        const uint64_t slot = base + h;
+        unsigned long long wk = ld_relaxed_u64(t.kr + slot);
+        for (;;) {
+            const uint32_t key = (uint32_t)(wk & 0xFFFFFFFFull);
+            if (key == kcur) {
+                *nv = __fadd_rn(atomicAdd(r_of(t.kr, slot), w), w);
+                return (int64_t)slot;
+            }
+            if (key != kEmpty && (key & ~t.key_idmask) == t.key_tag) break;
+            const unsigned long long prev = atomicCAS(t.kr + slot, wk, slot_word(kcur, w));
+            if (prev == wk) {
+                *nv = w;
+                return (int64_t)slot;
+            }
+            wk = prev;
+        }
+        h = (h + 1) & t.mask;
+    }
+    return -1;
+}
+
+__device__ __forceinline__ void list_append(uint32_t *cand, unsigned *count, unsigned cap, unsigned *error,
+                                            uint32_t slot) {
+    const unsigned pos = atomicAdd(count, 1u);
+    if (pos < cap) cand[pos] = slot; else atomicCAS(error, 0u, (unsigned)GDE_ENOMEM);
+}
+
+__global__ void k_serve_clear(int64_t n_entries, const int32_t *slots, int log2cap, int64_t cap,
+                              unsigned long long *kr, float *xs) {
+    const unsigned long long empty = (unsigned long long)kEmpty;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_entries;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t slot = ((uint64_t)slots[i / cap] << log2cap) + (uint64_t)(i % cap);
+        kr[slot] = empty;
+        xs[slot] = 0.0f;
+    }
+}
+
+struct AdmitArgs {
+    SlotTable t;
+    int32_t n;
+    const int32_t *slots;
+    const int32_t *seeds;
+    uint32_t *cand;
+    unsigned *count;
+    unsigned list_cap;
+    unsigned *error;
+    int32_t *status;
+    unsigned *inserts;
+    unsigned long long *svol;
+    unsigned *spushes;
+    int32_t *slast;
+    unsigned *xcnt;
+    double *spush;
+    double *sscat;
+};
+
+// unit residual at the seed of each admitted slot (its table was just cleared), per-slot
+// counters reset, the seed's slot listed for the next round
+__global__ void k_serve_seed(AdmitArgs a) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const int32_t j = a.slots[i];
+    const uint32_t s = (uint32_t)a.seeds[i];
+    const uint32_t sector_mask = a.t.mask >= 3 ? 3u : a.t.mask;
+    const uint64_t slot = ((uint64_t)j << a.t.log2cap) + (mix32(s) & a.t.mask & ~sector_mask);
+    a.t.kr[slot] = ((unsigned long long)__float_as_uint(1.0f) << 32) | (unsigned long long)(s | a.t.key_tag);
+    a.status[j] = kSeedOk;
+    a.inserts[j] = 1;
+    a.xcnt[j] = 0;
+    a.spush[j] = 0.0;
+    a.sscat[j] = 0.0;
+    a.svol[j] = 0;
+    a.spushes[j] = 0;
+    a.slast[j] = -1;
+    list_append(a.cand, a.count, a.list_cap, a.error, (uint32_t)slot);
+}
+
+struct CorrectArgs {
+    SlotTable t;
+    const SlotParam *sparam;
+    const float *thr;
+    int64_t thr_stride;
+    const int32_t *res;       // resident slots
+    int32_t nres;
+    const int32_t *row;       // rows that gained adjacencies (EdgeBatch)
+    const int32_t *row_cnt;
+    const int64_t *row_start;
+    const int32_t *old_deg;
+    const int32_t *added;     // the gained columns, row by row
+    int64_t rows;
+    uint32_t *cand;
+    unsigned *count;
+    unsigned list_cap;
+    unsigned *error;
+    int32_t *status;
+};
+
+// One thread per (resident slot, changed row u).  PPR (unit mass, d the degree before the
+// batch, k the adjacencies u gained, x_u / d unchanged by each single insertion):
+//   x_u <- x_u (d + k) / d,  r_u -= k x_u / (alpha d),  r_v += (1 - alpha) x_u / (alpha d) for
+//   each gained v; a row of degree 0 scatters nothing before its first adjacency, so there
+//   x_u <- k x_u, r_u -= (k - 1) x_u / alpha, r_v += (1 - alpha) x_u / alpha.
+// Katz: r_v += beta x_u for each gained v.  (x and d before the batch: the per-insertion
+// updates of a batch commute, so the batch is applied at once.)  Every residual that ends at
+// or above its threshold is listed for the next round.
+__global__ void k_serve_correct(CorrectArgs a) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= (int64_t)a.nres * a.rows) return;
+    const int32_t j = a.res[i / a.rows];
+    const int64_t ri = i % a.rows;
+    const int32_t u = a.row[ri];
+    const int64_t su = slot_find(a.t, j, (uint32_t)u);
+    if (su < 0) return;
+    const float x = a.t.xs[su];
+    if (x == 0.0f) return;
+    const SlotParam sp = a.sparam[j];
+    const float *thr = a.thr + (int64_t)sp.cls * a.thr_stride;
+    const int32_t k = a.row_cnt[ri];
+    const int32_t d0 = a.old_deg[ri];
+    const int64_t st = a.row_start[ri];
+    float give;
+    if (sp.divide) {
+        const double alpha = sp.cx;
+        const double denom = d0 > 0 ? (double)d0 : 1.0;
+        const double share = (double)x / (alpha * denom);
+        a.t.xs[su] = (float)(((double)x * (double)(d0 + k)) / denom);
+        const double take = (double)(d0 > 0 ? k : k - 1) * share;
+        if (take != 0.0) {
+            const float tf = (float)take;
+            const float old = atomicAdd(r_of(a.t.kr, (uint64_t)su), -tf);
+            if (fabsf(__fadd_rn(old, -tf)) >= thr[u])
+                list_append(a.cand, a.count, a.list_cap, a.error, (uint32_t)su);
+        }
+        give = (float)((1.0 - alpha) * share);
+    } else {
+        give = (float)(sp.coef * (double)x);
+    }
+    for (int32_t e = 0; e < k; e++) {
+        const int32_t v = a.added[st + e];
+        float nv = 0.0f;
+        const int64_t sv = slot_add(a.t, j, (uint32_t)v, give, &nv);
+        if (sv < 0) {
+            atomicExch(a.status + j, kSeedOverflow);
+            continue;
+        }
+        if (fabsf(nv) >= thr[v]) list_append(a.cand, a.count, a.list_cap, a.error, (uint32_t)sv);
+    }
+}
+
+__global__ void k_serve_pending(const unsigned *count, unsigned list_cap, const uint32_t *cand, int log2cap,
+                                unsigned *pend) {
+    const unsigned n = min(*count, list_cap);
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        atomicAdd(pend + (cand[i] >> log2cap), 1u);
+}
+
+static unsigned *next_count(ServePool *P) {
+    // candidates of round T sit in cand[T & 1], counted by the other parity's cand_out
+    BCtl *ctl = &P->w->glob->ctl[(P->T & 1) ^ 1];
+    return &ctl->cand_out;
+}
+
+static SlotTable slot_table(ServePool *P) {
+    SlotTable t;
+    t.kr = P->w->kr; t.xs = P->w->xs; t.log2cap = P->w->log2cap; t.mask = (uint32_t)(P->cap - 1);
+    t.key_tag = P->key_tag; t.key_idmask = P->key_idmask;
+    return t;
+}
+
+static void serve_check_error(ServePool *P) {
+    unsigned err = 0;
+    GDE_CUDA(cudaMemcpyAsync(&err, &P->w->glob->error, sizeof(unsigned), cudaMemcpyDeviceToHost, P->s));
+    GDE_CUDA(cudaStreamSynchronize(P->s));
+    if (err == GDE_ETIMEOUT) {
+        set_error("serving pool: a grid barrier wait timed out");
+        throw Fail{GDE_ETIMEOUT};
+    }
+    if (err != 0) {
+        set_error("serving pool: candidate or bin list capacity exceeded");
+        throw Fail{(gde_status)err};
+    }
+}
+
+ServePool *serve_pool_create(Graph &g, int32_t slots, int64_t budget, const double *eps, int ncls) {
+    GDE_REQUIRE(slots >= 1, GDE_EINVAL, "a server needs at least one slot");
+    GDE_REQUIRE(ncls >= 1 && ncls <= kMaxCls, GDE_EINVAL, "1 to 4 tolerance classes");
+    for (int c = 0; c < ncls; c++) GDE_REQUIRE(eps[c] > 0.0, GDE_EINVAL, "tolerances must be > 0");
+    GDE_REQUIRE(g.n < ((int64_t)1 << 31) - 1, GDE_EINVAL, "graph too large for 32-bit keys");
+    if (budget <= 0) budget = (int64_t)16 << 30;
+    int64_t cap = floor_pow2(budget / (12 * (int64_t)slots));
+    const int64_t cap_max = ceil_pow2(2 * (g.n > 0 ? g.n : 1));
+    if (cap > cap_max) cap = cap_max;
+    GDE_REQUIRE(cap >= 64 || cap == cap_max, GDE_ENOMEM, "memory budget too small for the slots");
+    GDE_REQUIRE((int64_t)slots * cap < ((int64_t)1 << 32), GDE_EINVAL, "pool exceeds 2^32 slots");
+    int64_t list_cap = (int64_t)slots << 14;
+    if (list_cap < ((int64_t)1 << 22)) list_cap = (int64_t)1 << 22;
+    if (list_cap > ((int64_t)1 << 24)) list_cap = (int64_t)1 << 24;
+    if (list_cap > (int64_t)slots * cap) list_cap = (int64_t)slots * cap;
+    ServePool *P = new ServePool();
+    try {
+        P->slots = slots;
+        P->cap = cap;
+        P->list_cap = list_cap;
+        P->ncls = ncls;
+        for (int c = 0; c < ncls; c++) P->eps[c] = eps[c];
+        P->s = g.stream;
+        P->w = batch_work_alloc(slots, cap, list_cap);
+        P->thr = (float *)dmalloc(4 * (size_t)ncls * (size_t)(g.n > 0 ? g.n : 1), "class thresholds");
+        P->d_param = (SlotParam *)dmalloc(sizeof(SlotParam) * (size_t)slots, "slot parameters");
+        P->h_param.assign((size_t)slots, SlotParam{0.15, 0.85, 1, 0});
+        P->pend = (unsigned *)dmalloc(4 * (size_t)slots, "pending counts");
+        P->d_list = (int32_t *)dmalloc(4 * (size_t)slots, "slot list");
+        P->d_seeds = (int32_t *)dmalloc(4 * (size_t)slots, "slot seeds");
+        P->d_ids = (int32_t *)dmalloc(4 * 64 * (size_t)slots, "slot top-k");
+        P->d_vals = (float *)dmalloc(4 * 64 * (size_t)slots, "slot top-k");
+        int key_idbits = 1;
+        while (((int64_t)1 << key_idbits) < g.n) key_idbits++;
+        const int tag_bits = 32 - key_idbits < 8 ? 32 - key_idbits : 8;
+        const uint32_t max_tag = tag_bits >= 2 ? (1u << tag_bits) - 2u : 0u;
+        P->key_tag = (max_tag >= 1 ? 1u : 0u) << key_idbits;
+        P->key_idmask = (uint32_t)(((uint64_t)1 << key_idbits) - 1);
+        cudaStream_t s = P->s;
+        k_batch_clear<<<kSMs * 8, kThreads, 0, s>>>(P->w->pool, P->w->kr, P->w->xs);
+        GDE_CUDA(cudaGetLastError());
+        GDE_CUDA(cudaMemsetAsync(P->w->glob, 0, sizeof(BGlobal), s));
+        GDE_CUDA(cudaMemsetAsync(P->w->seg_cnt, 0, 4 * 3 * (size_t)slots, s));
+        GDE_CUDA(cudaMemsetAsync(P->w->seg_hvol, 0, 8 * (size_t)slots, s));
+        GDE_CUDA(cudaMemsetAsync(P->w->status, 0, 4 * (size_t)slots, s));
+        GDE_CUDA(cudaMemsetAsync(P->w->xcnt, 0, 4 * (size_t)slots, s));
+        GDE_CUDA(cudaStreamSynchronize(s));
+    } catch (...) {
+        serve_pool_destroy(P);
+        throw;
+    }
+    return P;
+}
+
+void serve_pool_destroy(ServePool *P) {
+    if (!P) return;
+    if (P->s) cudaStreamSynchronize(P->s);
+    batch_free(P->w);
+    dfree(P->thr); dfree(P->d_param); dfree(P->pend); dfree(P->d_list); dfree(P->d_seeds);
+    dfree(P->d_ids); dfree(P->d_vals);
+    delete P;
+}
+
+int64_t serve_pool_cap(const ServePool *P) { return P->cap; }
+
+void serve_pool_graph_changed(ServePool *P) {
+    dfree(P->w->colp);
+    P->w->colp = nullptr;
+    P->thr_n = -1;
+}
+
+static void serve_ensure_graph_state(Graph &g, ServePool *P) {
+    ensure_colp(g, P->w, P->s);
+    if (P->thr_n != g.n) {
+        for (int c = 0; c < P->ncls; c++) {
+            k_batch_thr<<<kSMs * 8, kThreads, 0, P->s>>>(g.n, g.deg, P->thr + (int64_t)c * g.n, P->eps[c]);
+            GDE_CUDA(cudaGetLastError());
+        }
+        P->thr_n = g.n;
+    }
+}
+
+void serve_pool_admit(Graph &g, ServePool *P, int32_t n, const int32_t *slots, const int32_t *seeds,
+                      const gde_kind *kinds, const double *params, const int32_t *cls) {
+    if (n <= 0) return;
+    cudaStream_t s = P->s;
+    for (int32_t i = 0; i < n; i++) {
+        GDE_REQUIRE(slots[i] >= 0 && slots[i] < P->slots, GDE_EINVAL, "slot out of range");
+        GDE_REQUIRE(seeds[i] >= 0 && seeds[i] < g.n, GDE_EINVAL, "seed out of range");
+        GDE_REQUIRE(cls[i] >= 0 && cls[i] < P->ncls, GDE_EINVAL, "tolerance class out of range");
+        SlotParam &sp = P->h_param[(size_t)slots[i]];
+        if (kinds[i] == GDE_PPR) {
+            GDE_REQUIRE(params[i] > 0.0 && params[i] < 1.0, GDE_EINVAL, "PPR alpha must be in (0,1)");
+            sp = SlotParam{params[i], 1.0 - params[i], 1, cls[i]};
+        } else {
+            GDE_REQUIRE(kinds[i] == GDE_KATZ && params[i] > 0.0, GDE_EINVAL, "a server serves PPR and Katz");
+            sp = SlotParam{1.0, params[i], 0, cls[i]};
+        }
+    }
+    GDE_CUDA(cudaMemcpyAsync(P->d_param, P->h_param.data(), sizeof(SlotParam) * (size_t)P->slots,
+                             cudaMemcpyHostToDevice, s));
+    GDE_CUDA(cudaMemcpyAsync(P->d_list, slots, 4 * (size_t)n, cudaMemcpyHostToDevice, s));
+    GDE_CUDA(cudaMemcpyAsync(P->d_seeds, seeds, 4 * (size_t)n, cudaMemcpyHostToDevice, s));
+    k_serve_clear<<<kSMs * 8, kThreads, 0, s>>>((int64_t)n * P->cap, P->d_list, P->w->log2cap, P->cap, P->w->kr,
+                                               P->w->xs);
+    GDE_CUDA(cudaGetLastError());
+    AdmitArgs a{};
+    a.t = slot_table(P);
+    a.n = n; a.slots = P->d_list; a.seeds = P->d_seeds;
+    a.cand = P->w->cand[P->T & 1]; a.count = next_count(P); a.list_cap = (unsigned)P->list_cap;
+    a.error = &P->w->glob->error;
+    a.status = P->w->status; a.inserts = P->w->inserts; a.svol = P->w->svol; a.spushes = P->w->spushes;
+    a.slast = P->w->slast; a.xcnt = P->w->xcnt; a.spush = P->w->spush; a.sscat = P->w->sscat;
+    k_serve_seed<<<(n + kThreads - 1) / kThreads, kThreads, 0, s>>>(a);
+    GDE_CUDA(cudaGetLastError());
+    g.prof.launched(2);
+}
+
+void serve_pool_correct(Graph &g, ServePool *P, const EdgeBatch &eb, int32_t nres, const int32_t *res) {
+    if (nres <= 0 || eb.rows <= 0) return;
+    serve_ensure_graph_state(g, P);
+    GDE_CUDA(cudaMemcpyAsync(P->d_list, res, 4 * (size_t)nres, cudaMemcpyHostToDevice, P->s));
+    CorrectArgs a{};
+    a.t = slot_table(P);
+    a.sparam = P->d_param; a.thr = P->thr; a.thr_stride = g.n;
+    a.res = P->d_list; a.nres = nres;
+    a.row = eb.row; a.row_cnt = eb.row_cnt; a.row_start = eb.row_start; a.old_deg = eb.old_deg;
+    a.added = eb.v; a.rows = eb.rows;
+    a.cand = P->w->cand[P->T & 1]; a.count = next_count(P); a.list_cap = (unsigned)P->list_cap;
+    a.error = &P->w->glob->error; a.status = P->w->status;
+    const int64_t total = (int64_t)nres * eb.rows;
+    k_serve_correct<<<(unsigned)((total + kThreads - 1) / kThreads), kThreads, 0, P->s>>>(a);
+    GDE_CUDA(cudaGetLastError());
+    g.prof.launched();
+}
+
+int64_t serve_pool_run(Graph &g, ServePool *P, int64_t rounds) {
+    serve_ensure_graph_state(g, P);
+    BatchWork *w = P->w;
+    BArgs a = bargs_base(g, w, P->cap, P->list_cap, P->slots, P->key_tag, P->key_idmask);
+    a.thr32 = P->thr;
+    a.thr_stride = g.n;
+    a.eps = P->eps[0];
+    for (int c = 0; c < kMaxCls; c++) a.eps_cls[c] = c < P->ncls ? P->eps[c] : P->eps[0];
+    a.ncls = P->ncls;
+    a.sparam = P->d_param;
+    a.t0 = P->T;
+    a.max_rounds = rounds;
+    a.kind = GDE_PPR;
+    a.cx = 0.0;
+    a.coef = 0.0;
+    launch_rounds(g, w, a, P->s);
+    BGlobal hg;
+    GDE_CUDA(cudaMemcpyAsync(&hg, w->glob, sizeof(BGlobal), cudaMemcpyDeviceToHost, P->s));
+    GDE_CUDA(cudaStreamSynchronize(P->s));
+    if (hg.error != 0) serve_check_error(P);
+    const int64_t ran = (int64_t)hg.rounds - P->T;
+    P->T = hg.rounds;
+    return ran;
+}
+
+void serve_pool_pending(Graph &g, ServePool *P, unsigned *pend_host) {
+    GDE_CUDA(cudaMemsetAsync(P->pend, 0, 4 * (size_t)P->slots, P->s));
+    k_serve_pending<<<kSMs * 2, kThreads, 0, P->s>>>(next_count(P), (unsigned)P->list_cap, P->w->cand[P->T & 1],
+                                                      P->w->log2cap, P->pend);
+    GDE_CUDA(cudaGetLastError());
+    g.prof.launched();
+    GDE_CUDA(cudaMemcpyAsync(pend_host, P->pend, 4 * (size_t)P->slots, cudaMemcpyDeviceToHost, P->s));
+    GDE_CUDA(cudaStreamSynchronize(P->s));
+}
+
+void serve_pool_results(Graph &g, ServePool *P, int32_t n, const int32_t *slots, int k, int32_t *ids,
+                        float *vals, int32_t *status, int64_t *volume, int32_t *last_round) {
+    if (n <= 0) return;
+    GDE_REQUIRE(k >= 1 && k <= kTopMax, GDE_EINVAL, "topk must be in [1, 64]");
+    cudaStream_t s = P->s;
+    GDE_CUDA(cudaMemcpyAsync(P->d_list, slots, 4 * (size_t)n, cudaMemcpyHostToDevice, s));
+    TopkArgs ta{};
+    ta.kr = P->w->kr; ta.xs = P->w->xs; ta.log2cap = P->w->log2cap; ta.cap = P->cap; ta.k = k;
+    ta.key_idmask = P->key_idmask; ta.xlist = P->w->xlist; ta.xcnt = P->w->xcnt; ta.xcap = (unsigned)P->w->xcap;
+    ta.out_ids = P->d_ids; ta.out_vals = P->d_vals; ta.ssupport = P->w->inserts;
+    ta.slots = P->d_list; ta.keep = 1;
+    k_batch_topk<<<n, kThreads, 0, s>>>(ta);
+    GDE_CUDA(cudaGetLastError());
+    g.prof.launched();
+    GDE_CUDA(cudaMemcpyAsync(ids, P->d_ids, 4 * (size_t)n * k, cudaMemcpyDeviceToHost, s));
+    GDE_CUDA(cudaMemcpyAsync(vals, P->d_vals, 4 * (size_t)n * k, cudaMemcpyDeviceToHost, s));
+    std::vector<int32_t> st((size_t)P->slots), last((size_t)P->slots);
+    std::vector<unsigned long long> vol((size_t)P->slots);
+    GDE_CUDA(cudaMemcpyAsync(st.data(), P->w->status, 4 * (size_t)P->slots, cudaMemcpyDeviceToHost, s));
+    GDE_CUDA(cudaMemcpyAsync(last.data(), P->w->slast, 4 * (size_t)P->slots, cudaMemcpyDeviceToHost, s));
+    GDE_CUDA(cudaMemcpyAsync(vol.data(), P->w->svol, 8 * (size_t)P->slots, cudaMemcpyDeviceToHost, s));
+    GDE_CUDA(cudaStreamSynchronize(s));
+    for (int32_t i = 0; i < n; i++) {
+        const size_t j = (size_t)slots[i];
+        status[i] = st[j] == kSeedOk ? GDE_OK : GDE_ENOMEM;
+        volume[i] = (int64_t)vol[j];
+        last_round[i] = last[j];
+    }
+}
+
+int64_t serve_pool_round(const ServePool *P) { return P->T; }
 
 int64_t batch_round_log(Graph &g, double *out, int64_t cap) {
     BatchWork *w = g.batch;

@@ -174,6 +174,32 @@ struct BatchWork;
 void batch_work_destroy(BatchWork *w);
 // per-round log of the last batched solve: rows of {candidates, volume, r_S mass, ns}
 int64_t batch_round_log(Graph &g, double *out, int64_t cap);
+
+// C entry points: exceptions become status codes (the message is kept for gde_last_error)
+#define API_BEGIN try { ::gde::clear_error();
+#define API_END                                                                 \
+    }                                                                           \
+    catch (const ::gde::Fail &f) { return f.st; }                               \
+    catch (const std::bad_alloc &) { ::gde::set_error("host allocation failed"); return GDE_ENOMEM; } \
+    catch (...) { ::gde::set_error("unexpected C++ exception"); return GDE_ECUDA; } \
+    return GDE_OK;
+
+double server_clock();
+
+// serving pool (batched.cu): slots whose solves continue across launches
+struct ServePool;
+ServePool *serve_pool_create(Graph &g, int32_t slots, int64_t budget, const double *eps, int ncls);
+void serve_pool_destroy(ServePool *P);
+int64_t serve_pool_cap(const ServePool *P);
+int64_t serve_pool_round(const ServePool *P);
+void serve_pool_graph_changed(ServePool *P);
+void serve_pool_admit(Graph &g, ServePool *P, int32_t n, const int32_t *slots, const int32_t *seeds,
+                      const gde_kind *kinds, const double *params, const int32_t *cls);
+void serve_pool_correct(Graph &g, ServePool *P, const EdgeBatch &eb, int32_t nres, const int32_t *res);
+int64_t serve_pool_run(Graph &g, ServePool *P, int64_t rounds);
+void serve_pool_pending(Graph &g, ServePool *P, unsigned *pend_host);
+void serve_pool_results(Graph &g, ServePool *P, int32_t n, const int32_t *slots, int k, int32_t *ids,
+                        float *vals, int32_t *status, int64_t *volume, int32_t *last_round);
 void batch_solve(Graph &g, const SolveParams &p, const int32_t *seeds_dev, int32_t nseeds, int k,
                  int64_t mem_budget, int32_t *ids_dev, float *vals_dev, gde_stats *stats_host,
                  int32_t *overflow_seeds_host, int32_t *n_overflow);

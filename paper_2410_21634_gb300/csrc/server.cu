@@ -1,0 +1,327 @@
+// Serving loop over a serving pool (continuous batching of PPR/Katz queries on a changing
+// graph, Section 4): queries wait in a FIFO and are admitted into free slots between device
+// steps; a step runs a bounded number of LocalGD rounds for every resident query at once, so a
+// query that arrives while others are on the GPU joins them at the next step; a query whose
+// slot has no candidate left has converged and its top-k is emitted; edge-insertion batches
+// are applied between steps, after which every resident query is corrected (warm start) and
+// runs again until it re-converges, its refreshed result emitted as an update.  Answered
+// queries stay resident, tracking the graph, until their slot is needed (oldest answer first).
+#include <algorithm>
+#include <chrono>
+#include <deque>
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+
+namespace gde {
+
+double server_clock() {
+    using namespace std::chrono;
+    return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace gde
+
+using namespace gde;
+
+namespace {
+
+enum SlotState { kFree = 0, kRunning = 1, kAnswered = 2 };
+
+struct Query {
+    uint64_t qid;
+    gde_kind kind;
+    double param;
+    int32_t cls;
+    int32_t seed;
+    double t_submit;
+};
+
+struct Slot {
+    SlotState state = kFree;
+    Query q{};
+    bool answered_once = false;
+    double t_answer = 0.0;
+    double t_start = 0.0;  // when the current run (first solve or re-convergence) began
+};
+
+struct EdgeChunk {
+    std::vector<int32_t> src, dst;
+};
+
+}  // namespace
+
+struct gde_server {
+    gde_graph *graph = nullptr;
+    gde_server_opts opts{};
+    ServePool *pool = nullptr;
+    std::mutex mu;  // queue, pending edges, results (submit / insert / poll may run on other threads)
+    std::deque<Query> queue;
+    std::vector<EdgeChunk> edges;
+    std::vector<gde_server_result> done;
+    std::vector<Slot> slots;
+    std::mutex step_mu;  // one step at a time
+    int64_t steps = 0;
+    int64_t edge_batches = 0;
+};
+
+extern "C" {
+
+void gde_server_opts_init(gde_server_opts *o) {
+    if (!o) return;
+    *o = gde_server_opts{};
+    o->slots = 256;
+    o->rounds_per_step = 4;
+    o->topk = 64;
+    o->n_eps = 1;
+    o->eps[0] = 1e-6;
+    o->mem_budget_bytes = 0;
+}
+
+double gde_server_clock(void) { return server_clock(); }
+
+gde_status gde_server_create(gde_graph *g, const gde_server_opts *o, gde_server **out) {
+    API_BEGIN
+    GDE_REQUIRE(g != nullptr && out != nullptr, GDE_EINVAL, "graph or out is NULL");
+    *out = nullptr;
+    gde_server_opts op;
+    gde_server_opts_init(&op);
+    if (o) op = *o;
+    GDE_REQUIRE(op.slots >= 1 && op.slots <= (1 << 20), GDE_EINVAL, "slots must be in [1, 2^20]");
+    GDE_REQUIRE(op.rounds_per_step >= 1, GDE_EINVAL, "rounds_per_step must be >= 1");
+    GDE_REQUIRE(op.topk >= 1 && op.topk <= 64, GDE_EINVAL, "topk must be in [1, 64]");
+    GDE_REQUIRE(op.n_eps >= 1 && op.n_eps <= 4, GDE_EINVAL, "n_eps must be in [1, 4]");
+    gde_server *S = new gde_server();
+    try {
+        Graph &G = g->g;
+        std::lock_guard<std::mutex> lock(G.mu);
+        S->graph = g;
+        S->opts = op;
+        S->pool = serve_pool_create(G, op.slots, op.mem_budget_bytes, op.eps, op.n_eps);
+        S->slots.resize((size_t)op.slots);
+    } catch (...) {
+        if (S->pool) serve_pool_destroy(S->pool);
+        delete S;
+        throw;
+    }
+    *out = S;
+    API_END
+}
+
+gde_status gde_server_destroy(gde_server *S) {
+    if (!S) return GDE_OK;
+    API_BEGIN
+    {
+        std::lock_guard<std::mutex> lock(S->graph->g.mu);
+        serve_pool_destroy(S->pool);
+    }
+    delete S;
+    API_END
+}
+
+gde_status gde_server_submit(gde_server *S, uint64_t qid, gde_kind kind, double param, int32_t eps_class,
+                             int32_t seed, double t_submit) {
+    API_BEGIN
+    GDE_REQUIRE(S != nullptr, GDE_EINVAL, "server is NULL");
+    GDE_REQUIRE(kind == GDE_PPR || kind == GDE_KATZ, GDE_EINVAL, "a server serves PPR and Katz");
+    GDE_REQUIRE(kind != GDE_PPR || (param > 0.0 && param < 1.0), GDE_EINVAL, "PPR alpha must be in (0,1)");
+    GDE_REQUIRE(kind != GDE_KATZ || param > 0.0, GDE_EINVAL, "Katz beta must be > 0");
+    GDE_REQUIRE(eps_class >= 0 && eps_class < S->opts.n_eps, GDE_EINVAL, "tolerance class out of range");
+    GDE_REQUIRE(seed >= 0 && seed < S->graph->g.n, GDE_EINVAL, "seed out of range");
+    std::lock_guard<std::mutex> lock(S->mu);
+    S->queue.push_back(Query{qid, kind, param, eps_class, seed, t_submit >= 0.0 ? t_submit : server_clock()});
+    API_END
+}
+
+gde_status gde_server_insert_edges(gde_server *S, const int32_t *src, const int32_t *dst, int64_t m) {
+    API_BEGIN
+    GDE_REQUIRE(S != nullptr, GDE_EINVAL, "server is NULL");
+    GDE_REQUIRE(m >= 0 && (m == 0 || (src && dst)), GDE_EINVAL, "bad edge arrays");
+    const int64_t n = S->graph->g.n;
+    for (int64_t i = 0; i < m; i++)
+        GDE_REQUIRE(src[i] >= 0 && src[i] < n && dst[i] >= 0 && dst[i] < n, GDE_EINVAL, "edge endpoint out of range");
+    EdgeChunk c;
+    c.src.assign(src, src + m);
+    c.dst.assign(dst, dst + m);
+    std::lock_guard<std::mutex> lock(S->mu);
+    S->edges.push_back(std::move(c));
+    API_END
+}
+
+gde_status gde_server_step(gde_server *S, int32_t *running, int32_t *queued) {
+    API_BEGIN
+    GDE_REQUIRE(S != nullptr, GDE_EINVAL, "server is NULL");
+    std::lock_guard<std::mutex> step_lock(S->step_mu);
+    Graph &G = S->graph->g;
+    std::vector<EdgeChunk> edges;
+    {
+        std::lock_guard<std::mutex> lock(S->mu);
+        edges.swap(S->edges);
+    }
+    std::lock_guard<std::mutex> glock(G.mu);
+    ServePool *P = S->pool;
+    const int32_t nslots = S->opts.slots;
+
+    // 1. edge batches: update the graph, then correct every resident query (warm start)
+    if (!edges.empty()) {
+        EdgeChunk all;
+        for (auto &c : edges) {
+            all.src.insert(all.src.end(), c.src.begin(), c.src.end());
+            all.dst.insert(all.dst.end(), c.dst.begin(), c.dst.end());
+        }
+        EdgeBatch eb{};
+        const int64_t added = graph_insert_edges(G, all.src.data(), all.dst.data(), (int64_t)all.src.size(),
+                                                 false, &eb);
+        S->edge_batches += (int64_t)edges.size();
+        if (added > 0) {
+            serve_pool_graph_changed(P);
+            std::vector<int32_t> res;
+            for (int32_t j = 0; j < nslots; j++)
+                if (S->slots[(size_t)j].state != kFree) res.push_back(j);
+            try {
+                serve_pool_correct(G, P, eb, (int32_t)res.size(), res.data());
+            } catch (...) {
+                edge_batch_free(eb);
+                throw;
+            }
+            const double now = server_clock();
+            for (int32_t j : res) {
+                Slot &sl = S->slots[(size_t)j];
+                if (sl.state == kAnswered) {
+                    sl.state = kRunning;
+                    sl.t_start = now;
+                }
+            }
+        }
+        edge_batch_free(eb);
+    }
+
+    // 2. admission: free slots first, then the slots answered longest ago
+    std::vector<Query> admit;
+    {
+        std::lock_guard<std::mutex> lock(S->mu);
+        if (!S->queue.empty()) {
+            std::vector<int32_t> free_slots, answered;
+            for (int32_t j = 0; j < nslots; j++) {
+                const Slot &sl = S->slots[(size_t)j];
+                if (sl.state == kFree) free_slots.push_back(j);
+                else if (sl.state == kAnswered) answered.push_back(j);
+            }
+            std::sort(answered.begin(), answered.end(), [&](int32_t a, int32_t b) {
+                return S->slots[(size_t)a].t_answer < S->slots[(size_t)b].t_answer;
+            });
+            free_slots.insert(free_slots.end(), answered.begin(), answered.end());
+            size_t take = std::min(free_slots.size(), S->queue.size());
+            std::vector<int32_t> sl_ids, seeds, cls;
+            std::vector<gde_kind> kinds;
+            std::vector<double> params;
+            const double now = server_clock();
+            for (size_t i = 0; i < take; i++) {
+                const Query q = S->queue.front();
+                S->queue.pop_front();
+                const int32_t j = free_slots[i];
+                Slot &sl = S->slots[(size_t)j];
+                sl.state = kRunning;
+                sl.q = q;
+                sl.answered_once = false;
+                sl.t_start = now;
+                sl_ids.push_back(j);
+                seeds.push_back(q.seed);
+                kinds.push_back(q.kind);
+                params.push_back(q.param);
+                cls.push_back(q.cls);
+            }
+            if (take) serve_pool_admit(G, P, (int32_t)take, sl_ids.data(), seeds.data(), kinds.data(), params.data(),
+                                       cls.data());
+        }
+    }
+
+    // 3. a bounded number of rounds for every resident query
+    int32_t nrun = 0;
+    for (const Slot &sl : S->slots) nrun += sl.state == kRunning;
+    if (nrun > 0) {
+        serve_pool_run(G, P, S->opts.rounds_per_step);
+        // 4. converged: no candidate left in the slot
+        std::vector<unsigned> pend((size_t)nslots);
+        serve_pool_pending(G, P, pend.data());
+        std::vector<int32_t> fin;
+        for (int32_t j = 0; j < nslots; j++)
+            if (S->slots[(size_t)j].state == kRunning && pend[(size_t)j] == 0) fin.push_back(j);
+        if (!fin.empty()) {
+            const int k = S->opts.topk;
+            const int32_t nf = (int32_t)fin.size();
+            std::vector<int32_t> ids((size_t)nf * k), st((size_t)nf), last((size_t)nf);
+            std::vector<float> vals((size_t)nf * k);
+            std::vector<int64_t> vol((size_t)nf);
+            serve_pool_results(G, P, nf, fin.data(), k, ids.data(), vals.data(), st.data(), vol.data(), last.data());
+            const double now = server_clock();
+            std::lock_guard<std::mutex> lock(S->mu);
+            for (int32_t i = 0; i < nf; i++) {
+                Slot &sl = S->slots[(size_t)fin[(size_t)i]];
+                gde_server_result r{};
+                r.qid = sl.q.qid;
+                r.status = st[(size_t)i];
+                r.update = sl.answered_once ? 1 : 0;
+                r.k = k;
+                r.slot = fin[(size_t)i];
+                r.volume = vol[(size_t)i];
+                r.t_submit = sl.answered_once ? sl.t_start : sl.q.t_submit;
+                r.t_done = now;
+                for (int e = 0; e < k; e++) {
+                    r.ids[e] = ids[(size_t)i * k + e];
+                    r.vals[e] = vals[(size_t)i * k + e];
+                }
+                S->done.push_back(r);
+                if (r.status != GDE_OK) {
+                    sl.state = kFree;  // a failed query leaves its slot
+                } else {
+                    sl.state = kAnswered;
+                    sl.answered_once = true;
+                    sl.t_answer = now;
+                }
+            }
+        }
+    }
+    S->steps++;
+    int32_t nr = 0;
+    for (const Slot &sl : S->slots) nr += sl.state == kRunning;
+    if (running) *running = nr;
+    if (queued) {
+        std::lock_guard<std::mutex> lock(S->mu);
+        *queued = (int32_t)S->queue.size();
+    }
+    API_END
+}
+
+gde_status gde_server_poll(gde_server *S, gde_server_result *out, int32_t cap, int32_t *n) {
+    API_BEGIN
+    GDE_REQUIRE(S != nullptr && n != nullptr, GDE_EINVAL, "server or n is NULL");
+    GDE_REQUIRE(cap >= 0 && (cap == 0 || out != nullptr), GDE_EINVAL, "bad output buffer");
+    std::lock_guard<std::mutex> lock(S->mu);
+    const int32_t m = (int32_t)std::min<size_t>((size_t)cap, S->done.size());
+    for (int32_t i = 0; i < m; i++) out[i] = S->done[(size_t)i];
+    S->done.erase(S->done.begin(), S->done.begin() + m);
+    *n = m;
+    API_END
+}
+
+gde_status gde_server_info(gde_server *S, gde_server_info_t *info) {
+    API_BEGIN
+    GDE_REQUIRE(S != nullptr && info != nullptr, GDE_EINVAL, "server or info is NULL");
+    std::lock_guard<std::mutex> lock(S->mu);
+    info->slots = S->opts.slots;
+    info->running = info->answered = 0;
+    for (const Slot &sl : S->slots) {
+        info->running += sl.state == kRunning;
+        info->answered += sl.state == kAnswered;
+    }
+    info->queued = (int32_t)S->queue.size();
+    info->steps = S->steps;
+    info->rounds = serve_pool_round(S->pool);
+    info->edge_batches = S->edge_batches;
+    info->cap = serve_pool_cap(S->pool);
+    API_END
+}
+
+}  // extern "C"

@@ -44,24 +44,27 @@ def test_exported_symbols_are_c_linkage(lib):
 
 
 def test_struct_layout_matches_header(tmp_path):
+    """sizeof and every field offset of each C struct the binding mirrors"""
     import paper_2410_21634_gb300 as gde
+    pairs = [("gde_solve_opts", gde.SolveOpts), ("gde_stats", gde.Stats), ("gde_profile", gde.Profile),
+             ("gde_tuning", gde.Tuning), ("gde_server_opts", gde.ServerOpts),
+             ("gde_server_result", gde.ServerResult), ("gde_server_info_t", gde.ServerInfo)]
+    lines = []
+    for cname, cls in pairs:
+        lines.append(f'  printf("%zu\\n", sizeof({cname}));')
+        for f in cls._fields_:
+            lines.append(f'  printf("%zu\\n", offsetof({cname}, {f[0]}));')
     prog = tmp_path / "layout.c"
-    prog.write_text("""
-#include <stdio.h>
-#include <stddef.h>
-#include "gde.h"
-int main(void) {
-  printf("%zu %zu %zu %zu %zu\\n", sizeof(gde_solve_opts), offsetof(gde_solve_opts, max_rounds),
-         offsetof(gde_solve_opts, hk_tol), offsetof(gde_solve_opts, cuda_stream), sizeof(gde_stats));
-  return 0;
-}
-""")
+    prog.write_text("#include <stdio.h>\n#include <stddef.h>\n#include \"gde.h\"\nint main(void) {\n"
+                    + "\n".join(lines) + "\n  return 0;\n}\n")
     exe = tmp_path / "layout"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
     vals = [int(v) for v in subprocess.check_output([str(exe)]).split()]
-    O = gde.SolveOpts
-    assert vals == [ctypes.sizeof(O), O.max_rounds.offset, O.hk_tol.offset, O.cuda_stream.offset,
-                    ctypes.sizeof(gde.Stats)]
+    want = []
+    for _, cls in pairs:
+        want.append(ctypes.sizeof(cls))
+        want += [getattr(cls, f[0]).offset for f in cls._fields_]
+    assert vals == want
 
 
 def test_opts_init_and_last_error_without_gpu(lib):
