@@ -273,16 +273,20 @@ gde_status gde_session_end(gde_session *s);
  * with cap a power of two <= 2 n).
  *   gde_server_submit        queues a query (qid chosen by the caller; kind GDE_PPR with
  *                            param = alpha in (0,1), or GDE_KATZ with param = beta > 0;
- *                            eps_class picks one of the server's tolerances; t_submit is the
- *                            arrival time on gde_server_clock, < 0 for now).  Returns at once.
+ *                            eps_class picks one of the server's tolerances; flags
+ *                            GDE_SERVE_TRACK keeps the answered query resident as a standing
+ *                            query that is corrected and re-answered after every edge batch
+ *                            (until its slot is needed), without it the slot is released at
+ *                            the first answer; t_submit is the arrival time on
+ *                            gde_server_clock, < 0 for now).  Returns at once.
  *   gde_server_insert_edges  queues an edge-insertion batch (copied); applied at the next step.
  *   gde_server_step          one device step: applies the queued edge batches to the graph
  *                            (as gde_update_edges) and corrects every resident query's state
  *                            for them (the Insert of Algorithm 3: x_u rescaled, r moved along
  *                            the new adjacencies; Katz: r_v += beta x_u), so it resumes from
  *                            there instead of from its seed; admits queued queries into free
- *                            slots (then into the slots answered longest ago) in arrival
- *                            order; runs at most rounds_per_step LocalGD rounds of all resident
+ *                            slots (then into the slots of standing queries answered longest
+ *                            ago) in arrival order; runs at most rounds_per_step LocalGD rounds of all resident
  *                            queries in one persistent launch; and emits the top-k of every
  *                            query that has no active node left (first answer, or an update
  *                            after an edge batch).  *running and *queued (may be NULL) receive
@@ -297,6 +301,8 @@ gde_status gde_session_end(gde_session *s);
  * that fails leaves the server unusable and reports the failure).
  */
 typedef struct gde_server gde_server;
+
+#define GDE_SERVE_TRACK 1u  /* gde_server_submit: keep the query as a standing query */
 
 typedef struct {
     int32_t slots;            /* resident queries (default 256) */
@@ -325,6 +331,12 @@ typedef struct {
     int64_t rounds;           /* LocalGD rounds run by the pool so far */
     int64_t edge_batches;     /* insertion batches applied */
     int64_t cap;              /* hash slots per query table */
+    int64_t volume;           /* edges pushed by the pool so far (all queries, all rounds) */
+    double t_graph;           /* seconds spent in steps on: graph updates (CSR rebuild), */
+    double t_correct;         /*   warm-start corrections of resident queries, */
+    double t_admit;           /*   admissions, */
+    double t_rounds;          /*   LocalGD rounds (the persistent launches), */
+    double t_results;         /*   convergence checks and top-k of answered queries */
 } gde_server_info_t;
 
 void gde_server_opts_init(gde_server_opts *o);
@@ -332,7 +344,7 @@ double gde_server_clock(void);  /* steady clock, seconds */
 gde_status gde_server_create(gde_graph *g, const gde_server_opts *opts, gde_server **out);
 gde_status gde_server_destroy(gde_server *s);
 gde_status gde_server_submit(gde_server *s, uint64_t qid, gde_kind kind, double param, int32_t eps_class,
-                             int32_t seed, double t_submit);
+                             int32_t seed, uint32_t flags, double t_submit);
 gde_status gde_server_insert_edges(gde_server *s, const int32_t *src, const int32_t *dst, int64_t m);
 gde_status gde_server_step(gde_server *s, int32_t *running, int32_t *queued);
 gde_status gde_server_poll(gde_server *s, gde_server_result *out, int32_t cap, int32_t *n);

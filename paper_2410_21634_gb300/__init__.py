@@ -23,6 +23,7 @@ FP64, FP32 = 0, 1
 DEVICE_PTRS = 0x1
 CHECK_SYMMETRIC = 0x2
 OK, EINVAL, ENOMEM, ECUDA, ENOTCONV, ETIMEOUT = range(6)
+SERVE_TRACK = 1
 STATUS_NAMES = {0: "GDE_OK", 1: "GDE_EINVAL", 2: "GDE_ENOMEM", 3: "GDE_ECUDA",
                 4: "GDE_ENOTCONV", 5: "GDE_ETIMEOUT"}
 
@@ -91,7 +92,9 @@ class ServerResult(ctypes.Structure):
 class ServerInfo(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int32), ("running", ctypes.c_int32), ("answered", ctypes.c_int32),
                 ("queued", ctypes.c_int32), ("steps", ctypes.c_int64), ("rounds", ctypes.c_int64),
-                ("edge_batches", ctypes.c_int64), ("cap", ctypes.c_int64)]
+                ("edge_batches", ctypes.c_int64), ("cap", ctypes.c_int64), ("volume", ctypes.c_int64),
+                ("t_graph", ctypes.c_double), ("t_correct", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_rounds", ctypes.c_double), ("t_results", ctypes.c_double)]
 
 
 _lib = None
@@ -139,7 +142,7 @@ def load(path: str | None = None):
     lib.gde_server_clock.restype = D
     lib.gde_server_create.argtypes = [vp, ctypes.POINTER(ServerOpts), ctypes.POINTER(vp)]
     lib.gde_server_destroy.argtypes = [vp]
-    lib.gde_server_submit.argtypes = [vp, ctypes.c_uint64, ctypes.c_int, D, I32, I32, D]
+    lib.gde_server_submit.argtypes = [vp, ctypes.c_uint64, ctypes.c_int, D, I32, I32, ctypes.c_uint32, D]
     lib.gde_server_insert_edges.argtypes = [vp, vp, vp, I64]
     lib.gde_server_step.argtypes = [vp, ctypes.POINTER(I32), ctypes.POINTER(I32)]
     lib.gde_server_poll.argtypes = [vp, ctypes.POINTER(ServerResult), I32, ctypes.POINTER(I32)]
@@ -425,9 +428,11 @@ class Server:
         self.graph = graph
         self.topk = int(topk)
 
-    def submit(self, qid: int, kind, param: float, eps_class: int, seed: int, t_submit: float = -1.0):
+    def submit(self, qid: int, kind, param: float, eps_class: int, seed: int, track: bool = False,
+               t_submit: float = -1.0):
+        """Queue a query; track=True keeps it as a standing query (updated after edge batches)."""
         _check(load().gde_server_submit(self._h, int(qid), _kind(kind), float(param), int(eps_class),
-                                        int(seed), float(t_submit)))
+                                        int(seed), SERVE_TRACK if track else 0, float(t_submit)))
 
     def insert_edges(self, src, dst):
         src = np.ascontiguousarray(src, dtype=np.int32)

@@ -229,6 +229,7 @@ gde_status gde_graph_destroy(gde_graph *h) {
     if (g.stream) cudaStreamSynchronize(g.stream);
     for (int k = 0; k < 2; k++) dense_work_destroy(g.dense[k]);
     batch_work_destroy(g.batch);
+    update_scratch_free(g);
     g.prof.reset();
     dfree(g.off);
     dfree(g.col);

@@ -50,6 +50,8 @@ struct SlotParam {
     double coef;
     int32_t divide;
     int32_t cls;
+    uint32_t tag;    // the slot's key tag (shifted above the id bits): a server retags a slot
+    uint32_t pad;    // for every query, so the previous query's keys read as free
 };
 
 struct BCtl {  // per-round counters (one set per round parity)
@@ -107,6 +109,8 @@ struct BatchWork {
     uint32_t *colp = nullptr;
     int colp_idbits = 0;     // 0: no packing (n too large), then thr32 is read for every edge
     int colp_exact = 0;
+    int64_t colp_cap = 0;    // entries the packed array can hold
+    bool colp_valid = false; // packed from the current CSR
     uint32_t *cand[2] = {nullptr, nullptr};
     int64_t *b_beg[3] = {nullptr, nullptr, nullptr};
     int32_t *b_deg[3] = {nullptr, nullptr, nullptr};
@@ -369,18 +373,29 @@ __device__ __forceinline__ bool crossed(const float *thr32c, int32_t v, ThrBound
     return ao < thr && an >= thr;
 }
 
-__device__ __forceinline__ int slot_cls(const BArgs &a, int32_t j) { return a.sparam ? a.sparam[j].cls : 0; }
+// tolerance class and key tag of seed j's table
+struct SlotMeta {
+    int cls;
+    uint32_t tag;
+};
+
+__device__ __forceinline__ SlotMeta slot_meta(const BArgs &a, int32_t j) {
+    if (!a.sparam) return SlotMeta{0, a.key_tag};
+    const SlotParam &sp = a.sparam[j];
+    return SlotMeta{sp.cls, sp.tag};
+}
 
 // Insert-or-add w at node v of seed j's table.  The probe starts at a 4-slot bucket (one
 // 32-byte sector) chosen by mix32(v) and continues linearly bucket by bucket; slots are
 // examined in order, so the first empty slot ends the search (keys are never removed).  A
 // residual that crosses its threshold from below (exactly once: contributions are positive)
 // is staged as a candidate of the next round.  Returns 1 if v was a new key.
-__device__ __forceinline__ unsigned bscatter(const BArgs &a, int32_t j, int cls, uint32_t packed, float w,
+__device__ __forceinline__ unsigned bscatter(const BArgs &a, int32_t j, SlotMeta m, uint32_t packed, float w,
                                              uint32_t *sbuf, unsigned *sn) {
     const uint64_t base = (uint64_t)j << a.log2cap;
     const int32_t v = (int32_t)(packed & a.idmask);
-    const uint32_t kcur = (uint32_t)v | a.key_tag;
+    const uint32_t kcur = (uint32_t)v | m.tag;
+    const int cls = m.cls;
     const float *thr32c = a.thr32 + (int64_t)cls * a.thr_stride;
     ThrBounds tb;
     if (a.colp) {
@@ -414,7 +429,7 @@ __device__ __forceinline__ unsigned bscatter(const BArgs &a, int32_t j, int cls,
                     return 0;
                 }
                 // another node of this solve: next slot (empty and stale-tag slots are free)
-                if (key != kEmpty && (key & ~a.key_idmask) == a.key_tag) break;
+                if (key != kEmpty && (key & ~a.key_idmask) == m.tag) break;
                 const unsigned long long prev = atomicCAS(a.kr + slot, wk, slot_word(kcur, w));
                 if (prev == wk) {
                     if (crossed(thr32c, v, tb, 0.0f, w)) stage_push(sbuf, sn, (uint32_t)slot);
@@ -738,7 +753,7 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
                     int64_t hb = __ldcg(a.b_beg[2] + h);
                     float hw = __ldcg(a.b_w[2] + h);
                     int32_t hj = __ldcg(a.b_seed[2] + h);
-                    int hcls = slot_cls(a, hj);
+                    SlotMeta hm = slot_meta(a, hj);
                     for (int64_t eb = e0; eb < e1; eb += 32) {
                         const int64_t e = eb + lane;
                         if (e < e1) {
@@ -749,9 +764,9 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
                                 hb = __ldcg(a.b_beg[2] + h);
                                 hw = __ldcg(a.b_w[2] + h);
                                 hj = __ldcg(a.b_seed[2] + h);
-                                hcls = slot_cls(a, hj);
+                                hm = slot_meta(a, hj);
                             }
-                            bscatter(a, hj, hcls, push_col(a, hb + (e - hs)), hw, sbuf, sn);
+                            bscatter(a, hj, hm, push_col(a, hb + (e - hs)), hw, sbuf, sn);
                         }
                         stage_flush(sbuf, sn, false, ctl, cand_out, a.list_cap);
                     }
@@ -777,10 +792,10 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
                 const int32_t d = __ldcg(a.b_deg[1] + i);
                 const float w = __ldcg(a.b_w[1] + i);
                 const int32_t j = __ldcg(a.b_seed[1] + i);
-                const int cls = slot_cls(a, j);
+                const SlotMeta m = slot_meta(a, j);
                 for (int32_t k0 = 0; k0 < d; k0 += 32) {
                     const int32_t k = k0 + lane;
-                    if (k < d) bscatter(a, j, cls, push_col(a, b + k), w, sbuf, sn);
+                    if (k < d) bscatter(a, j, m, push_col(a, b + k), w, sbuf, sn);
                     stage_flush(sbuf, sn, false, ctl, cand_out, a.list_cap);
                 }
                 }
@@ -808,9 +823,9 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
                     j = __ldcg(a.b_seed[0] + i);
                 }
                 const int32_t dmax = (int32_t)__reduce_max_sync(0xffffffffu, (unsigned)d);
-                const int cls = d > 0 ? slot_cls(a, j) : 0;
+                const SlotMeta m = d > 0 ? slot_meta(a, j) : SlotMeta{0, a.key_tag};
                 for (int32_t k = 0; k < dmax; k++) {
-                    if (k < d) bscatter(a, j, cls, push_col(a, b + k), w, sbuf, sn);
+                    if (k < d) bscatter(a, j, m, push_col(a, b + k), w, sbuf, sn);
                     stage_flush(sbuf, sn, false, ctl, cand_out, a.list_cap);
                 }
             }
@@ -1114,14 +1129,13 @@ void graph_changed(Graph &g) {
         g.dense[k] = nullptr;
     }
     if (BatchWork *w = g.batch) {
-        dfree(w->colp);
-        w->colp = nullptr;
+        w->colp_valid = false;  // repacked (into the same buffer if it fits) on next use
         w->thr_eps = -1.0;
         w->thr_n = -1;
     }
 }
 
-static BatchWork *batch_work_alloc(int64_t nseeds, int64_t cap, int64_t list_cap) {
+static BatchWork *batch_work_alloc(int64_t nseeds, int64_t cap, int64_t list_cap, int64_t xcap_max = (int64_t)1 << 16) {
     BatchWork *w = new BatchWork();
     try {
         w->nseeds_cap = nseeds;
@@ -1158,7 +1172,7 @@ static BatchWork *batch_work_alloc(int64_t nseeds, int64_t cap, int64_t list_cap
         w->slast = (int32_t *)dmalloc(4 * (size_t)nseeds, "seed rounds");
         w->spush = (double *)dmalloc(8 * (size_t)nseeds, "seed pushed mass");
         w->sscat = (double *)dmalloc(8 * (size_t)nseeds, "seed scattered mass");
-        w->xcap = cap < ((int64_t)1 << 16) ? cap : ((int64_t)1 << 16);
+        w->xcap = cap < xcap_max ? cap : xcap_max;
         w->xlist = (uint32_t *)dmalloc(4 * (size_t)nseeds * (size_t)w->xcap, "x lists");
         w->xcnt = (unsigned *)dmalloc(4 * (size_t)nseeds, "x list lengths");
         w->glob = (BGlobal *)dmalloc(sizeof(BGlobal), "batch control");
@@ -1188,13 +1202,21 @@ static BatchWork *batch_work_get(Graph &g, int64_t nseeds, int64_t cap, int64_t 
 
 // packed columns (id | degree code) of the current CSR, built on first use
 static void ensure_colp(Graph &g, BatchWork *w, cudaStream_t s) {
-    if (w->colp || g.nnz <= 0) return;
+    if ((w->colp && w->colp_valid) || g.nnz <= 0) return;
     int idbits = 1;
     while (((int64_t)1 << idbits) < g.n) idbits++;
     const int spare = 32 - idbits;
     if (spare < 5) return;
     const int codes = spare >= 8 ? 256 : (1 << spare);
-    w->colp = (uint32_t *)dmalloc(4 * (size_t)g.nnz, "packed columns");
+    if (w->colp_cap < g.nnz) {
+        dfree(w->colp);
+        w->colp = nullptr;
+        // after edge insertions the graph has grown: leave room for more
+        const int64_t cap = w->colp_cap ? g.nnz + g.nnz / 4 + 1024 : g.nnz;
+        w->colp = (uint32_t *)dmalloc(4 * (size_t)cap, "packed columns");
+        w->colp_cap = cap;
+    }
+    w->colp_valid = true;
     w->colp_idbits = idbits;
     w->colp_exact = codes - 32;
     k_pack_columns<<<kSMs * 8, kThreads, 0, s>>>(g.nnz, g.col, g.deg, w->colp, idbits, w->colp_exact);
@@ -1207,8 +1229,8 @@ static BArgs bargs_base(Graph &g, BatchWork *w, int64_t cap, int64_t list_cap, i
                         uint32_t key_tag, uint32_t key_idmask) {
     BArgs a{};
     a.off = g.off; a.col = g.col; a.thr32 = w->thr32; a.kr = w->kr; a.xs = w->xs;
-    a.colp = w->colp; a.idbits = w->colp_idbits;
-    a.idmask = w->colp ? (uint32_t)(((uint64_t)1 << w->colp_idbits) - 1) : 0xFFFFFFFFu;
+    a.colp = w->colp_valid ? w->colp : nullptr; a.idbits = w->colp_idbits;
+    a.idmask = a.colp ? (uint32_t)(((uint64_t)1 << w->colp_idbits) - 1) : 0xFFFFFFFFu;
     a.code_exact = w->colp_exact;
     a.thr_stride = g.n;
     a.key_idmask = key_idmask; a.key_tag = key_tag;
@@ -1276,10 +1298,11 @@ void batch_solve(Graph &g, const SolveParams &p, const int32_t *seeds_dev, int32
     const int64_t budget = mem_budget > 0 ? mem_budget : ((int64_t)16 << 30);
     int64_t cap = floor_pow2(budget / (12 * (int64_t)nseeds));
     // a table of 2n slots never exceeds half load (at most n keys)
-    const int64_t cap_max = ceil_pow2(2 * (g.n > 0 ? g.n : 1));
+    // (at most 2^31 slots per table: slot indices are 32-bit and carry the seed above log2(cap))
+    const int64_t cap_max = std::min<int64_t>(ceil_pow2(2 * (g.n > 0 ? g.n : 1)), (int64_t)1 << 31);
     if (cap > cap_max) cap = cap_max;
     GDE_REQUIRE(cap >= 64 || cap == cap_max, GDE_ENOMEM, "memory budget too small for the batch");
-    GDE_REQUIRE((int64_t)nseeds * cap < ((int64_t)1 << 32), GDE_EINVAL, "batch pool exceeds 2^32 slots");
+    GDE_REQUIRE((int64_t)nseeds * cap <= ((int64_t)1 << 32), GDE_EINVAL, "batch pool exceeds 2^32 slots");
     // candidate and bin lists: every slot can enter a list at most once per round, but the
     // per-round frontier of all seeds together is far smaller than the pool; past this
     // capacity the solve reports GDE_ENOMEM
@@ -1428,13 +1451,19 @@ struct ServePool {
     int64_t thr_n = -1;          // rebuilt when the graph changed
     SlotParam *d_param = nullptr;
     std::vector<SlotParam> h_param;
-    uint32_t key_tag = 0, key_idmask = 0;
+    uint32_t key_idmask = 0;
+    int key_idbits = 0;
+    uint32_t max_tag = 0;
+    std::vector<uint32_t> epoch;  // per slot: the tag of its current query (0: never used)
+    uint32_t *d_tags = nullptr;
     int64_t T = 0;               // the next round to run
+    int64_t volume = 0;          // edges pushed so far
     unsigned *pend = nullptr;    // per-slot candidates of the next round
     int32_t *d_list = nullptr;   // slot-list scratch
     int32_t *d_seeds = nullptr;
     int32_t *d_ids = nullptr;
     float *d_vals = nullptr;
+    unsigned long long *d_partial = nullptr;  // top-k parts
     cudaStream_t s = nullptr;
 };
 
@@ -1444,19 +1473,19 @@ struct SlotTable {
     float *xs;
     int log2cap;
     uint32_t mask;
-    uint32_t key_tag, key_idmask;
+    uint32_t key_idmask;
 };
 
 // slot of node v in table j, or -1 (the probe stops at the first free slot)
-__device__ int64_t slot_find(const SlotTable &t, int32_t j, uint32_t v) {
+__device__ int64_t slot_find(const SlotTable &t, int32_t j, uint32_t tag, uint32_t v) {
     const uint64_t base = (uint64_t)j << t.log2cap;
-    const uint32_t kcur = v | t.key_tag;
+    const uint32_t kcur = v | tag;
     const uint32_t sector_mask = t.mask >= 3 ? 3u : t.mask;
     uint32_t h = mix32(v) & t.mask & ~sector_mask;
     for (uint32_t probes = 0; probes <= t.mask && probes < kMaxProbe; probes++) {
         const uint32_t key = (uint32_t)(ld_relaxed_u64(t.kr + base + h) & 0xFFFFFFFFull);
         if (key == kcur) return (int64_t)(base + h);
-        if (key == kEmpty || (key & ~t.key_idmask) != t.key_tag) return -1;
+        if (key == kEmpty || (key & ~t.key_idmask) != tag) return -1;
         h = (h + 1) & t.mask;
     }
     return -1;
@@ -1464,9 +1493,9 @@ __device__ int64_t slot_find(const SlotTable &t, int32_t j, uint32_t v) {
 
 // insert-or-add w at node v of table j; returns the slot (and the residual after the add in
 // *nv), or -1 if the table is full
-__device__ int64_t slot_add(const SlotTable &t, int32_t j, uint32_t v, float w, float *nv) {
+__device__ int64_t slot_add(const SlotTable &t, int32_t j, uint32_t tag, uint32_t v, float w, float *nv) {
     const uint64_t base = (uint64_t)j << t.log2cap;
-    const uint32_t kcur = v | t.key_tag;
+    const uint32_t kcur = v | tag;
     const uint32_t sector_mask = t.mask >= 3 ? 3u : t.mask;
     uint32_t h = mix32(v) & t.mask & ~sector_mask;
     for (uint32_t probes = 0; probes <= t.mask && probes < kMaxProbe; probes++) {
@@ -1478,7 +1507,7 @@ __device__ int64_t slot_add(const SlotTable &t, int32_t j, uint32_t v, float w, 
                 *nv = __fadd_rn(atomicAdd(r_of(t.kr, slot), w), w);
                 return (int64_t)slot;
             }
-            if (key != kEmpty && (key & ~t.key_idmask) == t.key_tag) break;
+            if (key != kEmpty && (key & ~t.key_idmask) == tag) break;
             const unsigned long long prev = atomicCAS(t.kr + slot, wk, slot_word(kcur, w));
             if (prev == wk) {
                 *nv = w;
@@ -1508,11 +1537,26 @@ __global__ void k_serve_clear(int64_t n_entries, const int32_t *slots, int log2c
     }
 }
 
+// one block per reused slot: zero the x entries its previous query set (its x-list; the whole
+// x range if the list overflowed)
+__global__ void k_serve_xzero(const int32_t *slots, const uint32_t *xlist, const unsigned *xcnt, int64_t xcap,
+                              float *xs, int log2cap, int64_t cap) {
+    const int32_t j = slots[blockIdx.x];
+    const unsigned nx = xcnt[j];
+    const uint64_t base = (uint64_t)j << log2cap;
+    if ((int64_t)nx <= xcap) {
+        for (unsigned i = threadIdx.x; i < nx; i += blockDim.x) xs[xlist[(uint64_t)j * xcap + i]] = 0.0f;
+    } else {
+        for (int64_t i = threadIdx.x; i < cap; i += blockDim.x) xs[base + i] = 0.0f;
+    }
+}
+
 struct AdmitArgs {
     SlotTable t;
     int32_t n;
     const int32_t *slots;
     const int32_t *seeds;
+    const uint32_t *tags;     // the admitted queries' key tags
     uint32_t *cand;
     unsigned *count;
     unsigned list_cap;
@@ -1527,8 +1571,9 @@ struct AdmitArgs {
     double *sscat;
 };
 
-// unit residual at the seed of each admitted slot (its table was just cleared), per-slot
-// counters reset, the seed's slot listed for the next round
+// unit residual at the seed of each admitted slot (under the slot's new tag every older key
+// reads as free, so the seed takes the first slot of its probe), per-slot counters reset, the
+// seed's slot listed for the next round
 __global__ void k_serve_seed(AdmitArgs a) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= a.n) return;
@@ -1536,7 +1581,7 @@ __global__ void k_serve_seed(AdmitArgs a) {
     const uint32_t s = (uint32_t)a.seeds[i];
     const uint32_t sector_mask = a.t.mask >= 3 ? 3u : a.t.mask;
     const uint64_t slot = ((uint64_t)j << a.t.log2cap) + (mix32(s) & a.t.mask & ~sector_mask);
-    a.t.kr[slot] = ((unsigned long long)__float_as_uint(1.0f) << 32) | (unsigned long long)(s | a.t.key_tag);
+    a.t.kr[slot] = ((unsigned long long)__float_as_uint(1.0f) << 32) | (unsigned long long)(s | a.tags[i]);
     a.status[j] = kSeedOk;
     a.inserts[j] = 1;
     a.xcnt[j] = 0;
@@ -1582,11 +1627,11 @@ __global__ void k_serve_correct(CorrectArgs a) {
     const int32_t j = a.res[i / a.rows];
     const int64_t ri = i % a.rows;
     const int32_t u = a.row[ri];
-    const int64_t su = slot_find(a.t, j, (uint32_t)u);
+    const SlotParam sp = a.sparam[j];
+    const int64_t su = slot_find(a.t, j, sp.tag, (uint32_t)u);
     if (su < 0) return;
     const float x = a.t.xs[su];
     if (x == 0.0f) return;
-    const SlotParam sp = a.sparam[j];
     const float *thr = a.thr + (int64_t)sp.cls * a.thr_stride;
     const int32_t k = a.row_cnt[ri];
     const int32_t d0 = a.old_deg[ri];
@@ -1611,7 +1656,7 @@ __global__ void k_serve_correct(CorrectArgs a) {
     for (int32_t e = 0; e < k; e++) {
         const int32_t v = a.added[st + e];
         float nv = 0.0f;
-        const int64_t sv = slot_add(a.t, j, (uint32_t)v, give, &nv);
+        const int64_t sv = slot_add(a.t, j, sp.tag, (uint32_t)v, give, &nv);
         if (sv < 0) {
             atomicExch(a.status + j, kSeedOverflow);
             continue;
@@ -1636,7 +1681,7 @@ static unsigned *next_count(ServePool *P) {
 static SlotTable slot_table(ServePool *P) {
     SlotTable t;
     t.kr = P->w->kr; t.xs = P->w->xs; t.log2cap = P->w->log2cap; t.mask = (uint32_t)(P->cap - 1);
-    t.key_tag = P->key_tag; t.key_idmask = P->key_idmask;
+    t.key_idmask = P->key_idmask;
     return t;
 }
 
@@ -1654,6 +1699,76 @@ static void serve_check_error(ServePool *P) {
     }
 }
 
+// Top-k of served queries in two passes, so a query with a large support is ranked by many
+// blocks: block (i, c) ranks part c of query i's x-list (or of its whole table if the list
+// overflowed) into a partial top-64, then one block per query merges its parts.
+constexpr int kServeTopkParts = 16;
+
+__global__ void __launch_bounds__(kThreads) k_serve_topk_partial(TopkArgs a, unsigned long long *partial) {
+    const int qi = blockIdx.x / kServeTopkParts, part = blockIdx.x % kServeTopkParts;
+    const int j = a.slots[qi];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint64_t base = (uint64_t)j << a.log2cap;
+    const unsigned nx = a.xcnt[j];
+    const bool use_list = nx <= a.xcap;
+    const int64_t n = use_list ? (int64_t)nx : a.cap;
+    const int64_t per = (n + kServeTopkParts - 1) / kServeTopkParts;
+    const int64_t lo = (int64_t)part * per, hi = min(lo + per, n);
+    unsigned long long ta = 0, tb = 0;
+    for (int64_t i0 = lo + (int64_t)wid * 32; i0 < hi; i0 += kThreads) {
+        const int64_t i = i0 + lane;
+        unsigned long long key = 0;
+        if (i < hi) {
+            const uint64_t slot = use_list ? (uint64_t)a.xlist[(uint64_t)j * a.xcap + i] : base + (uint64_t)i;
+            const float x = a.xs[slot];
+            if (x > 0.0f) {
+                const uint32_t v = (uint32_t)(a.kr[slot] & 0xFFFFFFFFull) & a.key_idmask;
+                key = ((unsigned long long)__float_as_uint(x) << 32) | (unsigned long long)(0xFFFFFFFFu - v);
+            }
+        }
+        top64_insert(ta, tb, key, lane);
+    }
+    __shared__ unsigned long long s_a[kWarps][32], s_b[kWarps][32];
+    s_a[wid][lane] = ta;
+    s_b[wid][lane] = tb;
+    __syncthreads();
+    if (wid == 0) {
+        for (int w = 1; w < kWarps; w++) {
+            top64_insert(ta, tb, s_a[w][lane], lane);
+            top64_insert(ta, tb, s_b[w][lane], lane);
+        }
+        partial[(int64_t)blockIdx.x * 64 + lane] = ta;
+        partial[(int64_t)blockIdx.x * 64 + 32 + lane] = tb;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_serve_topk_final(int k, const unsigned long long *partial,
+                                                               int32_t *out_ids, float *out_vals) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned long long *pp = partial + (int64_t)blockIdx.x * kServeTopkParts * 64;
+    unsigned long long ta = 0, tb = 0;
+    for (int i0 = wid * 32; i0 < kServeTopkParts * 64; i0 += kThreads) top64_insert(ta, tb, pp[i0 + lane], lane);
+    __shared__ unsigned long long s_a[kWarps][32], s_b[kWarps][32];
+    s_a[wid][lane] = ta;
+    s_b[wid][lane] = tb;
+    __syncthreads();
+    if (wid == 0) {
+        for (int w = 1; w < kWarps; w++) {
+            top64_insert(ta, tb, s_a[w][lane], lane);
+            top64_insert(ta, tb, s_b[w][lane], lane);
+        }
+        for (int half = 0; half < 2; half++) {
+            const int pos = half * 32 + lane;
+            const unsigned long long key = half ? tb : ta;
+            if (pos < k) {
+                const bool valid = key != 0;
+                out_ids[(int64_t)blockIdx.x * k + pos] = valid ? (int32_t)(0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFull)) : -1;
+                out_vals[(int64_t)blockIdx.x * k + pos] = valid ? __uint_as_float((uint32_t)(key >> 32)) : 0.0f;
+            }
+        }
+    }
+}
+
 ServePool *serve_pool_create(Graph &g, int32_t slots, int64_t budget, const double *eps, int ncls) {
     GDE_REQUIRE(slots >= 1, GDE_EINVAL, "a server needs at least one slot");
     GDE_REQUIRE(ncls >= 1 && ncls <= kMaxCls, GDE_EINVAL, "1 to 4 tolerance classes");
@@ -1661,10 +1776,11 @@ ServePool *serve_pool_create(Graph &g, int32_t slots, int64_t budget, const doub
     GDE_REQUIRE(g.n < ((int64_t)1 << 31) - 1, GDE_EINVAL, "graph too large for 32-bit keys");
     if (budget <= 0) budget = (int64_t)16 << 30;
     int64_t cap = floor_pow2(budget / (12 * (int64_t)slots));
-    const int64_t cap_max = ceil_pow2(2 * (g.n > 0 ? g.n : 1));
+    // (at most 2^31 slots per table: slot indices are 32-bit and carry the seed above log2(cap))
+    const int64_t cap_max = std::min<int64_t>(ceil_pow2(2 * (g.n > 0 ? g.n : 1)), (int64_t)1 << 31);
     if (cap > cap_max) cap = cap_max;
     GDE_REQUIRE(cap >= 64 || cap == cap_max, GDE_ENOMEM, "memory budget too small for the slots");
-    GDE_REQUIRE((int64_t)slots * cap < ((int64_t)1 << 32), GDE_EINVAL, "pool exceeds 2^32 slots");
+    GDE_REQUIRE((int64_t)slots * cap <= ((int64_t)1 << 32), GDE_EINVAL, "pool exceeds 2^32 slots (32-bit slot indices)");
     int64_t list_cap = (int64_t)slots << 14;
     if (list_cap < ((int64_t)1 << 22)) list_cap = (int64_t)1 << 22;
     if (list_cap > ((int64_t)1 << 24)) list_cap = (int64_t)1 << 24;
@@ -1677,20 +1793,26 @@ ServePool *serve_pool_create(Graph &g, int32_t slots, int64_t budget, const doub
         P->ncls = ncls;
         for (int c = 0; c < ncls; c++) P->eps[c] = eps[c];
         P->s = g.stream;
-        P->w = batch_work_alloc(slots, cap, list_cap);
+        // x-lists of up to 2^22 entries: a served query's support stays listed, so its top-k
+        // and the zeroing at the slot's next admission touch only that support
+        P->w = batch_work_alloc(slots, cap, list_cap, (int64_t)1 << 22);
         P->thr = (float *)dmalloc(4 * (size_t)ncls * (size_t)(g.n > 0 ? g.n : 1), "class thresholds");
         P->d_param = (SlotParam *)dmalloc(sizeof(SlotParam) * (size_t)slots, "slot parameters");
         P->h_param.assign((size_t)slots, SlotParam{0.15, 0.85, 1, 0});
         P->pend = (unsigned *)dmalloc(4 * (size_t)slots, "pending counts");
         P->d_list = (int32_t *)dmalloc(4 * (size_t)slots, "slot list");
         P->d_seeds = (int32_t *)dmalloc(4 * (size_t)slots, "slot seeds");
+        P->d_tags = (uint32_t *)dmalloc(4 * (size_t)slots, "slot tags");
+        P->epoch.assign((size_t)slots, 0u);
         P->d_ids = (int32_t *)dmalloc(4 * 64 * (size_t)slots, "slot top-k");
         P->d_vals = (float *)dmalloc(4 * 64 * (size_t)slots, "slot top-k");
+        P->d_partial = (unsigned long long *)dmalloc(8 * 64 * (size_t)kServeTopkParts * (size_t)slots, "top-k parts");
         int key_idbits = 1;
         while (((int64_t)1 << key_idbits) < g.n) key_idbits++;
         const int tag_bits = 32 - key_idbits < 8 ? 32 - key_idbits : 8;
         const uint32_t max_tag = tag_bits >= 2 ? (1u << tag_bits) - 2u : 0u;
-        P->key_tag = (max_tag >= 1 ? 1u : 0u) << key_idbits;
+        P->key_idbits = key_idbits;
+        P->max_tag = max_tag;
         P->key_idmask = (uint32_t)(((uint64_t)1 << key_idbits) - 1);
         cudaStream_t s = P->s;
         k_batch_clear<<<kSMs * 8, kThreads, 0, s>>>(P->w->pool, P->w->kr, P->w->xs);
@@ -1712,16 +1834,15 @@ void serve_pool_destroy(ServePool *P) {
     if (!P) return;
     if (P->s) cudaStreamSynchronize(P->s);
     batch_free(P->w);
-    dfree(P->thr); dfree(P->d_param); dfree(P->pend); dfree(P->d_list); dfree(P->d_seeds);
-    dfree(P->d_ids); dfree(P->d_vals);
+    dfree(P->thr); dfree(P->d_param); dfree(P->pend); dfree(P->d_list); dfree(P->d_seeds); dfree(P->d_tags);
+    dfree(P->d_ids); dfree(P->d_vals); dfree(P->d_partial);
     delete P;
 }
 
 int64_t serve_pool_cap(const ServePool *P) { return P->cap; }
 
 void serve_pool_graph_changed(ServePool *P) {
-    dfree(P->w->colp);
-    P->w->colp = nullptr;
+    P->w->colp_valid = false;
     P->thr_n = -1;
 }
 
@@ -1753,16 +1874,44 @@ void serve_pool_admit(Graph &g, ServePool *P, int32_t n, const int32_t *slots, c
             sp = SlotParam{1.0, params[i], 0, cls[i]};
         }
     }
+    // new key tag per admitted slot; a slot whose tag would wrap is cleared and starts over,
+    // a reused slot only has its previous query's x zeroed
+    std::vector<int32_t> wrap, reuse;
+    std::vector<uint32_t> tags((size_t)n);
+    for (int32_t i = 0; i < n; i++) {
+        uint32_t &e = P->epoch[(size_t)slots[i]];
+        const bool used = e != 0;
+        e++;
+        if (e > P->max_tag || P->max_tag == 0) {
+            wrap.push_back(slots[i]);
+            e = P->max_tag >= 1 ? 1u : 0u;
+        } else if (used) {
+            reuse.push_back(slots[i]);
+        }
+        tags[(size_t)i] = e << P->key_idbits;
+        P->h_param[(size_t)slots[i]].tag = tags[(size_t)i];
+        P->h_param[(size_t)slots[i]].pad = 0;
+    }
     GDE_CUDA(cudaMemcpyAsync(P->d_param, P->h_param.data(), sizeof(SlotParam) * (size_t)P->slots,
                              cudaMemcpyHostToDevice, s));
+    if (!reuse.empty()) {
+        GDE_CUDA(cudaMemcpyAsync(P->d_list, reuse.data(), 4 * reuse.size(), cudaMemcpyHostToDevice, s));
+        k_serve_xzero<<<(unsigned)reuse.size(), kThreads, 0, s>>>(P->d_list, P->w->xlist, P->w->xcnt, P->w->xcap,
+                                                                  P->w->xs, P->w->log2cap, P->cap);
+        GDE_CUDA(cudaGetLastError());
+    }
+    if (!wrap.empty()) {
+        GDE_CUDA(cudaMemcpyAsync(P->d_seeds, wrap.data(), 4 * wrap.size(), cudaMemcpyHostToDevice, s));
+        k_serve_clear<<<kSMs * 8, kThreads, 0, s>>>((int64_t)wrap.size() * P->cap, P->d_seeds, P->w->log2cap,
+                                                   P->cap, P->w->kr, P->w->xs);
+        GDE_CUDA(cudaGetLastError());
+    }
     GDE_CUDA(cudaMemcpyAsync(P->d_list, slots, 4 * (size_t)n, cudaMemcpyHostToDevice, s));
     GDE_CUDA(cudaMemcpyAsync(P->d_seeds, seeds, 4 * (size_t)n, cudaMemcpyHostToDevice, s));
-    k_serve_clear<<<kSMs * 8, kThreads, 0, s>>>((int64_t)n * P->cap, P->d_list, P->w->log2cap, P->cap, P->w->kr,
-                                               P->w->xs);
-    GDE_CUDA(cudaGetLastError());
+    GDE_CUDA(cudaMemcpyAsync(P->d_tags, tags.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, s));
     AdmitArgs a{};
     a.t = slot_table(P);
-    a.n = n; a.slots = P->d_list; a.seeds = P->d_seeds;
+    a.n = n; a.slots = P->d_list; a.seeds = P->d_seeds; a.tags = P->d_tags;
     a.cand = P->w->cand[P->T & 1]; a.count = next_count(P); a.list_cap = (unsigned)P->list_cap;
     a.error = &P->w->glob->error;
     a.status = P->w->status; a.inserts = P->w->inserts; a.svol = P->w->svol; a.spushes = P->w->spushes;
@@ -1793,7 +1942,7 @@ void serve_pool_correct(Graph &g, ServePool *P, const EdgeBatch &eb, int32_t nre
 int64_t serve_pool_run(Graph &g, ServePool *P, int64_t rounds) {
     serve_ensure_graph_state(g, P);
     BatchWork *w = P->w;
-    BArgs a = bargs_base(g, w, P->cap, P->list_cap, P->slots, P->key_tag, P->key_idmask);
+    BArgs a = bargs_base(g, w, P->cap, P->list_cap, P->slots, 1u << P->key_idbits, P->key_idmask);
     a.thr32 = P->thr;
     a.thr_stride = g.n;
     a.eps = P->eps[0];
@@ -1812,8 +1961,11 @@ int64_t serve_pool_run(Graph &g, ServePool *P, int64_t rounds) {
     if (hg.error != 0) serve_check_error(P);
     const int64_t ran = (int64_t)hg.rounds - P->T;
     P->T = hg.rounds;
+    P->volume = (int64_t)hg.total_vol;
     return ran;
 }
+
+int64_t serve_pool_volume(const ServePool *P) { return P->volume; }
 
 void serve_pool_pending(Graph &g, ServePool *P, unsigned *pend_host) {
     GDE_CUDA(cudaMemsetAsync(P->pend, 0, 4 * (size_t)P->slots, P->s));
@@ -1836,9 +1988,11 @@ void serve_pool_results(Graph &g, ServePool *P, int32_t n, const int32_t *slots,
     ta.key_idmask = P->key_idmask; ta.xlist = P->w->xlist; ta.xcnt = P->w->xcnt; ta.xcap = (unsigned)P->w->xcap;
     ta.out_ids = P->d_ids; ta.out_vals = P->d_vals; ta.ssupport = P->w->inserts;
     ta.slots = P->d_list; ta.keep = 1;
-    k_batch_topk<<<n, kThreads, 0, s>>>(ta);
+    k_serve_topk_partial<<<(unsigned)(n * kServeTopkParts), kThreads, 0, s>>>(ta, P->d_partial);
     GDE_CUDA(cudaGetLastError());
-    g.prof.launched();
+    k_serve_topk_final<<<(unsigned)n, kThreads, 0, s>>>(k, P->d_partial, P->d_ids, P->d_vals);
+    GDE_CUDA(cudaGetLastError());
+    g.prof.launched(2);
     GDE_CUDA(cudaMemcpyAsync(ids, P->d_ids, 4 * (size_t)n * k, cudaMemcpyDeviceToHost, s));
     GDE_CUDA(cudaMemcpyAsync(vals, P->d_vals, 4 * (size_t)n * k, cudaMemcpyDeviceToHost, s));
     std::vector<int32_t> st((size_t)P->slots), last((size_t)P->slots);
@@ -1856,6 +2010,7 @@ void serve_pool_results(Graph &g, ServePool *P, int32_t n, const int32_t *slots,
 }
 
 int64_t serve_pool_round(const ServePool *P) { return P->T; }
+
 
 int64_t batch_round_log(Graph &g, double *out, int64_t cap) {
     BatchWork *w = g.batch;

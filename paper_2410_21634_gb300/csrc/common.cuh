@@ -88,6 +88,7 @@ struct Graph {
     std::mutex mu;
     struct DenseWork *dense[2] = {nullptr, nullptr};     // cached single-seed workspace per precision
     struct BatchWork *batch = nullptr;                   // cached batched workspace
+    struct UpdateScratch *upd = nullptr;                 // edge-insertion buffers, kept between batches
     Profiler prof;
     Bins bins;                 // launch shape used by later solves
 };
@@ -118,6 +119,7 @@ struct EdgeBatch {
 int64_t graph_insert_edges(Graph &g, const int32_t *src, const int32_t *dst, int64_t m, bool dev_ptrs,
                            EdgeBatch *out);
 void edge_batch_free(EdgeBatch &b);
+void update_scratch_free(Graph &g);
 void graph_changed(Graph &g);
 
 // ------------------------------------------------------------------- solve --
@@ -192,6 +194,7 @@ ServePool *serve_pool_create(Graph &g, int32_t slots, int64_t budget, const doub
 void serve_pool_destroy(ServePool *P);
 int64_t serve_pool_cap(const ServePool *P);
 int64_t serve_pool_round(const ServePool *P);
+int64_t serve_pool_volume(const ServePool *P);
 void serve_pool_graph_changed(ServePool *P);
 void serve_pool_admit(Graph &g, ServePool *P, int32_t n, const int32_t *slots, const int32_t *seeds,
                       const gde_kind *kinds, const double *params, const int32_t *cls);

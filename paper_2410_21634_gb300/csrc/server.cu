@@ -4,8 +4,9 @@
 // query that arrives while others are on the GPU joins them at the next step; a query whose
 // slot has no candidate left has converged and its top-k is emitted; edge-insertion batches
 // are applied between steps, after which every resident query is corrected (warm start) and
-// runs again until it re-converges, its refreshed result emitted as an update.  Answered
-// queries stay resident, tracking the graph, until their slot is needed (oldest answer first).
+// runs on from its corrected state.  A one-shot query leaves its slot at its answer; a standing
+// query stays resident, tracking the graph (re-answered as an update after every batch), until
+// its slot is needed (oldest answer first).
 #include <algorithm>
 #include <chrono>
 #include <deque>
@@ -35,6 +36,7 @@ struct Query {
     double param;
     int32_t cls;
     int32_t seed;
+    bool track;
     double t_submit;
 };
 
@@ -64,6 +66,7 @@ struct gde_server {
     std::mutex step_mu;  // one step at a time
     int64_t steps = 0;
     int64_t edge_batches = 0;
+    double t_phase[5] = {0, 0, 0, 0, 0};  // graph, correct, admit, rounds, results (seconds)
 };
 
 extern "C" {
@@ -121,7 +124,7 @@ gde_status gde_server_destroy(gde_server *S) {
 }
 
 gde_status gde_server_submit(gde_server *S, uint64_t qid, gde_kind kind, double param, int32_t eps_class,
-                             int32_t seed, double t_submit) {
+                             int32_t seed, uint32_t flags, double t_submit) {
     API_BEGIN
     GDE_REQUIRE(S != nullptr, GDE_EINVAL, "server is NULL");
     GDE_REQUIRE(kind == GDE_PPR || kind == GDE_KATZ, GDE_EINVAL, "a server serves PPR and Katz");
@@ -130,7 +133,8 @@ gde_status gde_server_submit(gde_server *S, uint64_t qid, gde_kind kind, double 
     GDE_REQUIRE(eps_class >= 0 && eps_class < S->opts.n_eps, GDE_EINVAL, "tolerance class out of range");
     GDE_REQUIRE(seed >= 0 && seed < S->graph->g.n, GDE_EINVAL, "seed out of range");
     std::lock_guard<std::mutex> lock(S->mu);
-    S->queue.push_back(Query{qid, kind, param, eps_class, seed, t_submit >= 0.0 ? t_submit : server_clock()});
+    S->queue.push_back(Query{qid, kind, param, eps_class, seed, (flags & GDE_SERVE_TRACK) != 0,
+                             t_submit >= 0.0 ? t_submit : server_clock()});
     API_END
 }
 
@@ -171,8 +175,10 @@ gde_status gde_server_step(gde_server *S, int32_t *running, int32_t *queued) {
             all.dst.insert(all.dst.end(), c.dst.begin(), c.dst.end());
         }
         EdgeBatch eb{};
+        const double tg = server_clock();
         const int64_t added = graph_insert_edges(G, all.src.data(), all.dst.data(), (int64_t)all.src.size(),
                                                  false, &eb);
+        S->t_phase[0] += server_clock() - tg;
         S->edge_batches += (int64_t)edges.size();
         if (added > 0) {
             serve_pool_graph_changed(P);
@@ -180,7 +186,10 @@ gde_status gde_server_step(gde_server *S, int32_t *running, int32_t *queued) {
             for (int32_t j = 0; j < nslots; j++)
                 if (S->slots[(size_t)j].state != kFree) res.push_back(j);
             try {
+                const double tc = server_clock();
                 serve_pool_correct(G, P, eb, (int32_t)res.size(), res.data());
+                GDE_CUDA(cudaStreamSynchronize(G.stream));
+                S->t_phase[1] += server_clock() - tc;
             } catch (...) {
                 edge_batch_free(eb);
                 throw;
@@ -232,8 +241,13 @@ gde_status gde_server_step(gde_server *S, int32_t *running, int32_t *queued) {
                 params.push_back(q.param);
                 cls.push_back(q.cls);
             }
-            if (take) serve_pool_admit(G, P, (int32_t)take, sl_ids.data(), seeds.data(), kinds.data(), params.data(),
-                                       cls.data());
+            if (take) {
+                const double ta = server_clock();
+                serve_pool_admit(G, P, (int32_t)take, sl_ids.data(), seeds.data(), kinds.data(), params.data(),
+                                 cls.data());
+                GDE_CUDA(cudaStreamSynchronize(G.stream));
+                S->t_phase[2] += server_clock() - ta;
+            }
         }
     }
 
@@ -241,7 +255,10 @@ gde_status gde_server_step(gde_server *S, int32_t *running, int32_t *queued) {
     int32_t nrun = 0;
     for (const Slot &sl : S->slots) nrun += sl.state == kRunning;
     if (nrun > 0) {
+        const double tr = server_clock();
         serve_pool_run(G, P, S->opts.rounds_per_step);
+        const double tq = server_clock();
+        S->t_phase[3] += tq - tr;
         // 4. converged: no candidate left in the slot
         std::vector<unsigned> pend((size_t)nslots);
         serve_pool_pending(G, P, pend.data());
@@ -273,8 +290,8 @@ gde_status gde_server_step(gde_server *S, int32_t *running, int32_t *queued) {
                     r.vals[e] = vals[(size_t)i * k + e];
                 }
                 S->done.push_back(r);
-                if (r.status != GDE_OK) {
-                    sl.state = kFree;  // a failed query leaves its slot
+                if (r.status != GDE_OK || !sl.q.track) {
+                    sl.state = kFree;  // answered one-shot (or failed) queries leave their slot
                 } else {
                     sl.state = kAnswered;
                     sl.answered_once = true;
@@ -282,6 +299,7 @@ gde_status gde_server_step(gde_server *S, int32_t *running, int32_t *queued) {
                 }
             }
         }
+        S->t_phase[4] += server_clock() - tq;
     }
     S->steps++;
     int32_t nr = 0;
@@ -321,6 +339,12 @@ gde_status gde_server_info(gde_server *S, gde_server_info_t *info) {
     info->rounds = serve_pool_round(S->pool);
     info->edge_batches = S->edge_batches;
     info->cap = serve_pool_cap(S->pool);
+    info->volume = serve_pool_volume(S->pool);
+    info->t_graph = S->t_phase[0];
+    info->t_correct = S->t_phase[1];
+    info->t_admit = S->t_phase[2];
+    info->t_rounds = S->t_phase[3];
+    info->t_results = S->t_phase[4];
     API_END
 }
 

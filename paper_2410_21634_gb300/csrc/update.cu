@@ -4,16 +4,15 @@
 // so rows stay sorted and duplicate-free (the store's invariant).
 //
 // The batch is normalised on the host (it is small next to the graph), then the device
-// drops adjacencies already in their row (binary search), computes the new degrees and
-// offsets (scan), and rebuilds the column array in one pass: a warp per row moves the old
-// columns to their new places (shifted past the added columns that sort before them), and
-// a thread per added adjacency drops it into its gap.
+// drops adjacencies already in their row (binary search) and rebuilds the CSR into spare
+// buffers that are kept between batches: new offsets and the old columns' new places come
+// from binary searches over the few changed rows (the rest of the CSR only shifts), and a
+// thread per added adjacency drops it into its gap.
 #include <algorithm>
 #include <utility>
 #include <vector>
 
 #include "common.cuh"
-#include "detsort.cuh"
 
 namespace gde {
 
@@ -32,76 +31,146 @@ __global__ void k_mark_new(int64_t m, const int32_t *__restrict__ u, const int32
     keep[i] = (lo < off[a + 1] && col[lo] == b) ? 0 : 1;
 }
 
-// per-row added counts and first-added index, from the sorted list of rows that gained
-__global__ void k_scatter_rows(int64_t rows, const int32_t *__restrict__ row, const int32_t *__restrict__ cnt,
-                               const int64_t *__restrict__ start, int32_t *__restrict__ add_cnt,
-                               int64_t *__restrict__ add_start) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= rows) return;
-    add_cnt[row[i]] = cnt[i];
-    add_start[row[i]] = start[i];
-}
-
 __global__ void k_gather_deg(int64_t rows, const int32_t *__restrict__ row, const int32_t *__restrict__ deg,
                              int32_t *__restrict__ out) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < rows) out[i] = deg[row[i]];
 }
 
-__global__ void k_new_degrees(int64_t n, int32_t *__restrict__ deg, const int32_t *__restrict__ add_cnt,
-                              int64_t *__restrict__ deg64, int *max_deg) {
-    const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (u >= n) return;
-    const int32_t d = deg[u] + add_cnt[u];
-    deg[u] = d;
-    deg64[u] = d;
-    if (add_cnt[u]) atomicMax(max_deg, d);
+// old row bounds of the changed rows
+__global__ void k_row_bounds(int64_t rows, const int32_t *__restrict__ row, const int64_t *__restrict__ off,
+                             int64_t *__restrict__ rb, int64_t *__restrict__ re) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= rows) return;
+    rb[i] = off[row[i]];
+    re[i] = off[row[i] + 1];
 }
 
-// one warp per row: old column k of row u goes to noff[u] + k + (added columns of u below it)
-__global__ void k_merge_rows(int64_t n, const int64_t *__restrict__ off, const int32_t *__restrict__ col,
-                             const int64_t *__restrict__ noff, int32_t *__restrict__ ncol,
-                             const int32_t *__restrict__ add_cnt, const int64_t *__restrict__ add_start,
-                             const int32_t *__restrict__ added) {
-    const int lane = threadIdx.x & 31;
-    const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t u = w0; u < n; u += nw) {
-        const int64_t b = off[u], e = off[u + 1], nb = noff[u];
-        const int32_t k = add_cnt[u];
-        const int32_t *a = added + (k ? add_start[u] : 0);
-        for (int64_t i = b + lane; i < e; i += 32) {
-            const int32_t c = col[i];
-            int32_t lo = 0, hi = k;  // added columns below c
-            while (lo < hi) {
-                const int32_t mid = (lo + hi) >> 1;
-                if (a[mid] < c) lo = mid + 1; else hi = mid;
-            }
-            ncol[nb + (i - b) + lo] = c;
+// noff[u] = off[u] + (adjacencies added to rows before u): a binary search over the changed
+// rows (ascending) gives their count, and row_start is the running total of their additions
+__global__ void k_new_offsets(int64_t n, const int64_t *__restrict__ off, const int32_t *__restrict__ row,
+                              const int64_t *__restrict__ row_start, int64_t rows, int64_t added,
+                              int64_t *__restrict__ noff) {
+    const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (u > n) return;
+    int64_t lo = 0, hi = rows;  // first changed row >= u
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (row[mid] < u) lo = mid + 1; else hi = mid;
+    }
+    noff[u] = off[u] + (lo < rows ? row_start[lo] : added);
+}
+
+// One thread per old CSR entry e: it moves by the additions to earlier rows, plus, inside a
+// changed row, by that row's added columns that sort before it.  Rows are sorted, so the
+// copy is a shift that changes only at the changed rows: a coalesced streaming pass.
+__global__ void k_shift_columns(int64_t nnz, const int32_t *__restrict__ col, const int64_t *__restrict__ rb,
+                                const int64_t *__restrict__ re, const int64_t *__restrict__ row_start,
+                                const int32_t *__restrict__ row_cnt, int64_t rows,
+                                const int32_t *__restrict__ added, int32_t *__restrict__ ncol) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = col[e];
+        int64_t lo = 0, hi = rows;  // first changed row starting after e
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (rb[mid] <= e) lo = mid + 1; else hi = mid;
         }
+        const int64_t i = lo - 1;  // last changed row starting at or before e
+        int64_t shift = 0;
+        if (i >= 0) {
+            if (e < re[i]) {
+                const int32_t *a = added + row_start[i];
+                int32_t l = 0, h = row_cnt[i];  // added columns of that row below c
+                while (l < h) {
+                    const int32_t m = (l + h) >> 1;
+                    if (a[m] < c) l = m + 1; else h = m;
+                }
+                shift = row_start[i] + l;
+            } else {
+                shift = row_start[i] + row_cnt[i];
+            }
+        }
+        ncol[e + shift] = c;
     }
 }
 
-// one thread per added adjacency (u, v): its place is noff[u] + (its index among u's added)
-// + (old columns of u below v)
+__global__ void k_deg_add(int64_t rows, const int32_t *__restrict__ row, const int32_t *__restrict__ cnt,
+                          int32_t *__restrict__ deg, int *max_deg) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= rows) return;
+    const int32_t d = deg[row[i]] + cnt[i];
+    deg[row[i]] = d;
+    atomicMax(max_deg, d);
+}
+
+// one thread per added adjacency i (row u, column v; the list is sorted by (u, v)): its place
+// is noff[u] + (its index among u's added) + (old columns of u below v)
 __global__ void k_place_added(int64_t m, const int32_t *__restrict__ u, const int32_t *__restrict__ v,
                               const int64_t *__restrict__ off, const int32_t *__restrict__ col,
-                              const int64_t *__restrict__ noff, const int64_t *__restrict__ add_start,
-                              int32_t *__restrict__ ncol) {
+                              const int64_t *__restrict__ noff, const int32_t *__restrict__ row,
+                              const int64_t *__restrict__ row_start, int64_t rows, int32_t *__restrict__ ncol) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= m) return;
     const int32_t a = u[i], c = v[i];
+    int64_t rl = 0, rh = rows;  // a's position among the changed rows
+    while (rl < rh) {
+        const int64_t mid = (rl + rh) >> 1;
+        if (row[mid] < a) rl = mid + 1; else rh = mid;
+    }
     int64_t lo = off[a], hi = off[a + 1];
     while (lo < hi) {
         const int64_t mid = (lo + hi) >> 1;
         if (col[mid] < c) lo = mid + 1; else hi = mid;
     }
-    ncol[noff[a] + (i - add_start[a]) + (lo - off[a])] = c;
+    ncol[noff[a] + (i - row_start[rl]) + (lo - off[a])] = c;
 }
 
 static unsigned blocks_for(int64_t m) {
     const int64_t b = (m + kThreads - 1) / kThreads;
     return (unsigned)(b > 0 ? b : 1);
+}
+
+// Buffers of the CSR rebuild, kept between batches so a batch allocates nothing large: the
+// spare column array (the merge writes there, then it swaps with the graph's), the spare
+// offsets, the per-row counts and starts, and the scan's scratch.
+struct UpdateScratch {
+    int32_t *col = nullptr;
+    int64_t col_cap = 0;         // entries of the spare column array
+    int64_t graph_col_cap = 0;   // entries of the array the graph's columns sit in
+    int64_t *off = nullptr;      // n + 1
+    int *dmax = nullptr;
+    int64_t n = -1;
+};
+
+void update_scratch_free(Graph &g) {
+    UpdateScratch *u = g.upd;
+    if (!u) return;
+    dfree(u->col); dfree(u->off); dfree(u->dmax);
+    delete u;
+    g.upd = nullptr;
+}
+
+static UpdateScratch *update_scratch(Graph &g, int64_t nnz_new) {
+    if (g.upd && g.upd->n != g.n) update_scratch_free(g);
+    if (!g.upd) {
+        UpdateScratch *u = new UpdateScratch();
+        g.upd = u;
+        const int64_t n = g.n;
+        u->n = n;
+        u->off = (int64_t *)dmalloc(8 * (size_t)(n + 1), "CSR offsets");
+        u->dmax = (int *)dmalloc(sizeof(int), "max degree");
+        u->graph_col_cap = g.nnz;  // the graph's columns were allocated to size
+    }
+    UpdateScratch *u = g.upd;
+    if (u->col_cap < nnz_new) {
+        // room for growth: later batches reuse the buffer
+        const int64_t cap = nnz_new + nnz_new / 4 + 1024;
+        dfree(u->col);
+        u->col = nullptr;
+        u->col = (int32_t *)dmalloc(4 * (size_t)cap, "CSR columns");
+        u->col_cap = cap;
+    }
+    return u;
 }
 
 void edge_batch_free(EdgeBatch &b) {
@@ -195,48 +264,41 @@ int64_t graph_insert_edges(Graph &g, const int32_t *src, const int32_t *dst, int
             GDE_CUDA(cudaMemcpyAsync(eb.row, rows.data(), 4 * (size_t)nrows, cudaMemcpyHostToDevice, s));
             GDE_CUDA(cudaMemcpyAsync(eb.row_cnt, rcnt.data(), 4 * (size_t)nrows, cudaMemcpyHostToDevice, s));
             GDE_CUDA(cudaMemcpyAsync(eb.row_start, rstart.data(), 8 * (size_t)nrows, cudaMemcpyHostToDevice, s));
-            // per-row counts and starts over all n rows; new degrees, offsets, columns
+            // new offsets, shifted columns, placed additions, then the degrees of the changed rows
             const int64_t n = g.n;
-            int32_t *add_cnt = (int32_t *)alloc(4 * (size_t)n, "row adds");
-            int64_t *add_start = (int64_t *)alloc(8 * (size_t)n, "row adds");
-            int64_t *deg64 = (int64_t *)alloc(8 * (size_t)n, "new degrees");
-            int64_t *noff = (int64_t *)alloc(8 * (size_t)(n + 1), "CSR offsets");
-            int64_t *scr = (int64_t *)alloc(scan_scratch_bytes(n), "scan scratch");
-            int *dmax = (int *)alloc(sizeof(int), "max degree");
-            GDE_CUDA(cudaMemsetAsync(add_cnt, 0, 4 * (size_t)n, s));
+            UpdateScratch *u = update_scratch(g, g.nnz + added);
+            int64_t *noff = u->off;
+            int *dmax = u->dmax;
+            int64_t *rb = (int64_t *)alloc(8 * (size_t)nrows, "row bounds");
+            int64_t *re = (int64_t *)alloc(8 * (size_t)nrows, "row bounds");
             GDE_CUDA(cudaMemcpyAsync(dmax, &g.max_degree, sizeof(int), cudaMemcpyHostToDevice, s));
-            k_scatter_rows<<<blocks_for(nrows), kThreads, 0, s>>>(nrows, eb.row, eb.row_cnt, eb.row_start,
-                                                                   add_cnt, add_start);
-            GDE_CUDA(cudaGetLastError());
-            // degrees before the update, for the caller's state corrections
             k_gather_deg<<<blocks_for(nrows), kThreads, 0, s>>>(nrows, eb.row, g.deg, eb.old_deg);
             GDE_CUDA(cudaGetLastError());
-            k_new_degrees<<<blocks_for(n), kThreads, 0, s>>>(n, g.deg, add_cnt, deg64, dmax);
+            k_row_bounds<<<blocks_for(nrows), kThreads, 0, s>>>(nrows, eb.row, g.off, rb, re);
             GDE_CUDA(cudaGetLastError());
-            exclusive_scan_i64(deg64, noff, n, noff + n, scr, s);
-            int32_t *ncol = (int32_t *)dmalloc(4 * (size_t)(g.nnz + added), "CSR columns");
-            try {
-                k_merge_rows<<<kSMs * 8, kThreads, 0, s>>>(n, g.off, g.col, noff, ncol, add_cnt, add_start, eb.v);
+            k_new_offsets<<<blocks_for(n + 1), kThreads, 0, s>>>(n, g.off, eb.row, eb.row_start, nrows, added, noff);
+            GDE_CUDA(cudaGetLastError());
+            int32_t *ncol = u->col;
+            if (g.nnz > 0) {
+                k_shift_columns<<<kSMs * 16, kThreads, 0, s>>>(g.nnz, g.col, rb, re, eb.row_start, eb.row_cnt, nrows,
+                                                               eb.v, ncol);
                 GDE_CUDA(cudaGetLastError());
-                k_place_added<<<blocks_for(added), kThreads, 0, s>>>(added, eb.u, eb.v, g.off, g.col, noff,
-                                                                     add_start, ncol);
-                GDE_CUDA(cudaGetLastError());
-                int hmax = 0;
-                GDE_CUDA(cudaMemcpyAsync(&hmax, dmax, sizeof(int), cudaMemcpyDeviceToHost, s));
-                GDE_CUDA(cudaStreamSynchronize(s));
-                g.prof.launched(7);
-                // swap in the new arrays (noff leaves the temporaries)
-                dfree(g.col);
-                g.col = ncol;
-                dfree(g.off);
-                g.off = noff;
-                tmp.erase(std::find(tmp.begin(), tmp.end(), (void *)noff));
-                g.nnz += added;
-                g.max_degree = hmax;
-            } catch (...) {
-                dfree(ncol);
-                throw;
             }
+            k_place_added<<<blocks_for(added), kThreads, 0, s>>>(added, eb.u, eb.v, g.off, g.col, noff, eb.row,
+                                                                 eb.row_start, nrows, ncol);
+            GDE_CUDA(cudaGetLastError());
+            k_deg_add<<<blocks_for(nrows), kThreads, 0, s>>>(nrows, eb.row, eb.row_cnt, g.deg, dmax);
+            GDE_CUDA(cudaGetLastError());
+            int hmax = 0;
+            GDE_CUDA(cudaMemcpyAsync(&hmax, dmax, sizeof(int), cudaMemcpyDeviceToHost, s));
+            GDE_CUDA(cudaStreamSynchronize(s));
+            g.prof.launched(6);
+            // the rebuilt arrays become the graph's, the old ones the next batch's spares
+            std::swap(g.col, u->col);
+            std::swap(g.off, u->off);
+            std::swap(u->col_cap, u->graph_col_cap);
+            g.nnz += added;
+            g.max_degree = hmax;
         } catch (...) {
             edge_batch_free(eb);
             throw;

@@ -84,7 +84,8 @@ def test_answers_match_the_oracle(gde, g0):
         check_answer(g0, r, oracle_x(g0, q), EPS[q[3]])
         assert r["t_done"] >= r["t_submit"]
     inf = S.info()
-    assert inf["running"] == 0 and inf["queued"] == 0 and inf["answered"] == 16
+    # one-shot queries leave their slots at their answers
+    assert inf["running"] == 0 and inf["queued"] == 0 and inf["answered"] == 0
     S.close()
 
 
@@ -132,8 +133,9 @@ def test_warm_start_after_insertions(gde, g0, kind):
     param = 0.15 if kind == "ppr" else beta_of(g0)
     seeds = synth.seeds_quantile(g0, 8)
     for i, s in enumerate(seeds):
-        S.submit(i, kind, param, 1, int(s))
+        S.submit(i, kind, param, 1, int(s), track=True)
     first = [r for r in S.run_until_idle() if not r["update"]]
+    assert S.info()["answered"] == 8  # standing queries stay resident
     assert len(first) == 8
     g = g0
     for b in range(2):  # two batches, applied one after the other
@@ -185,4 +187,26 @@ def test_bad_requests_are_rejected(gde, g0):
         assert e.value.status == gde.EINVAL
     with pytest.raises(gde.GdeError):
         S.insert_edges(np.array([0], np.int32), np.array([g0.n], np.int32))
+    S.close()
+
+
+def test_queries_in_flight_are_corrected(gde, g0):
+    """Edges inserted while queries are mid-solve: their states are corrected (warm start) and
+    their first answers match the oracle on the new graph."""
+    G = gde.Graph.from_synth(g0)
+    S = gde.Server(G, slots=8, rounds_per_step=1, eps=EPS)
+    seeds = synth.seeds_quantile(g0, 8)
+    for i, s in enumerate(seeds):
+        S.submit(i, "ppr", 0.15, 1, int(s))
+    S.step()
+    S.step()  # two rounds in: every query still running
+    assert S.info()["running"] == 8
+    src, dst = synth.random_edges(g0.n, 600, seed=77)
+    S.insert_edges(src, dst)
+    g1 = synth.with_edges(g0, src, dst)
+    first = {r["qid"]: r for r in S.run_until_idle() if not r["update"]}
+    assert sorted(first) == list(range(8))
+    for i, s in enumerate(seeds):
+        fresh = oracle.localgd(g1, "ppr", 0.15, EPS[1], int(s)).x
+        check_answer(g1, first[i], fresh, EPS[1], slack=2.0)
     S.close()
