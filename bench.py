@@ -6,9 +6,12 @@ every seed in one persistent launch, per-seed top-64) for 1024 PPR sources (512 
 + 512 top-1% hubs), alpha=0.1, eps=1e-7, on the synthetic R-MAT 24 graph (edge factor
 16, symmetrised, deduplicated).  Reports seeds/s (value), GTEPS, the plain FP64
 one-seed-per-launch path on the same GPU, the roofline of the persistent round kernel,
-an end-to-end figure through host buffers, and the FP64 oracle on the host's cores.
+an end-to-end figure through host buffers, and the FP64 oracle on the host's cores.  Then,
+as "serving", it measures the serving workload (Chung-Lu 2^23, PPR/Katz queries arriving
+at 2,000/s with eps in {1e-5, 1e-6, 1e-7}, 10,000 random edges inserted every 50 ms):
+p50/p99 latency and throughput of the continuous-batching server.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--serve-seconds S]
 
 Under torchrun (N > 1) every rank solves its own 1024 seeds on a replica of the graph
 (seed sharding, no collective on the data path); rank 0 prints one JSON line.
@@ -55,6 +58,8 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's default tuning")
     ap.add_argument("--budget-gb", type=float, default=0.0,
                     help="hash accumulator budget (0: the library default)")
+    ap.add_argument("--serve-seconds", type=float, default=2.0,
+                    help="seconds of the serving stream measured after the batched bench (0: skip)")
     return ap.parse_args()
 
 
@@ -217,6 +222,7 @@ def run_reference(args):
     return 0
 
 
+SERVE_SLOTS, SERVE_ROUNDS_PER_STEP = 256, 4
 SERVE = {"graph": "chung_lu_2p23", "rate_qps": 2000.0, "batch_edges": 10000, "batch_period_s": 0.05,
          "eps": (1e-5, 1e-6, 1e-7), "alpha": 0.15}
 
@@ -463,6 +469,13 @@ def main():
         cpu = cpu_baseline(g, seeds_np)
 
     gpu_launches = prof["launches"]  # counted by the library for the timed steps
+    tuning_used = G.get_tuning()
+
+    # the serving workload (continuous batching with edge insertions), on its own graph
+    serving = None
+    if args.serve_seconds > 0 and rank == 0 and ws == 1:
+        G.close()  # release the batched pool first
+        serving = run_serving(gde, args.serve_seconds, SERVE_SLOTS, SERVE_ROUNDS_PER_STEP)
     line = {
         "metric": METRIC, "value": value, "unit": "seeds/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
@@ -479,8 +492,9 @@ def main():
         "hash_overflow_seeds": overflow,
         "edges_per_step": edges_step,
         "rounds_per_step": prof["rounds"] / launches,
-        "tuning": G.get_tuning(),
+        "tuning": tuning_used,
         "autotuned": tuning is not None,
+        "serving": serving,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
