@@ -146,6 +146,7 @@ struct BatchWork {
     int sms = 0;
     int64_t last_rounds = 0;
     bool need_clear = true;   // reset every table before the next solve
+    bool list_overflowed = false;  // the last solve ran out of candidate / bin list entries
     uint32_t epoch = 0;       // tag of the current solve's keys
 };
 
@@ -1288,9 +1289,10 @@ static inline int64_t ceil_pow2(int64_t v) {
 // Runs a batched PPR/Katz solve.  seeds_dev: device seed ids.  Outputs (device): ids[nseeds*k],
 // vals[nseeds*k] (float).  stats_host may be NULL.  Seeds whose table overflowed are reported
 // with status GDE_ENOMEM in stats and in *n_overflow; their outputs are not valid.
-void batch_solve(Graph &g, const SolveParams &p, const int32_t *seeds_dev, int32_t nseeds, int k,
-                 int64_t mem_budget, int32_t *ids_dev, float *vals_dev, gde_stats *stats_host,
-                 int32_t *overflow_seeds_host, int32_t *n_overflow) {
+static void batch_solve_once(Graph &g, const SolveParams &p, const int32_t *seeds_dev, int32_t nseeds, int k,
+                             int64_t mem_budget, int32_t *ids_dev, float *vals_dev, gde_stats *stats_host,
+                             int32_t *overflow_seeds_host, int32_t *n_overflow, int list_scale,
+                             bool *list_full) {
     GDE_REQUIRE(k >= 1 && k <= kTopMax, GDE_EINVAL, "batched mode needs 1 <= topk <= 64");
     GDE_REQUIRE(p.kind == GDE_PPR || p.kind == GDE_KATZ, GDE_EINVAL, "batched mode supports PPR and Katz");
     GDE_REQUIRE(p.precision == GDE_FP32, GDE_EINVAL, "batched mode stores x and r in FP32");
@@ -1310,8 +1312,10 @@ void batch_solve(Graph &g, const SolveParams &p, const int32_t *seeds_dev, int32
     int64_t list_max = (int64_t)nseeds << 14;
     if (list_max < ((int64_t)1 << 22)) list_max = (int64_t)1 << 22;
     if (list_max > ((int64_t)1 << 24)) list_max = (int64_t)1 << 24;
+    list_max <<= 2 * list_scale;  // a retry after an overflow: four times larger
     if (list_cap > list_max) list_cap = list_max;
     GDE_REQUIRE(nseeds <= list_cap, GDE_EINVAL, "too many seeds for one batch");
+    *list_full = list_cap == (int64_t)nseeds * cap;
     BatchWork *w = batch_work_get(g, nseeds, cap, list_cap);
     cudaStream_t s = p.stream;
     GDE_CUDA(cudaMemcpyAsync(w->seeds, seeds_dev, 4 * (size_t)nseeds, cudaMemcpyDeviceToDevice, s));
@@ -1399,6 +1403,7 @@ void batch_solve(Graph &g, const SolveParams &p, const int32_t *seeds_dev, int32
     }
     if (hg.error != 0) {
         set_error("batched solve: candidate or bin list capacity exceeded");
+        w->list_overflowed = hg.error == GDE_ENOMEM;
         throw Fail{(gde_status)hg.error};
     }
     w->last_rounds = hg.rounds;
@@ -1781,9 +1786,9 @@ ServePool *serve_pool_create(Graph &g, int32_t slots, int64_t budget, const doub
     if (cap > cap_max) cap = cap_max;
     GDE_REQUIRE(cap >= 64 || cap == cap_max, GDE_ENOMEM, "memory budget too small for the slots");
     GDE_REQUIRE((int64_t)slots * cap <= ((int64_t)1 << 32), GDE_EINVAL, "pool exceeds 2^32 slots (32-bit slot indices)");
-    int64_t list_cap = (int64_t)slots << 14;
-    if (list_cap < ((int64_t)1 << 22)) list_cap = (int64_t)1 << 22;
-    if (list_cap > ((int64_t)1 << 24)) list_cap = (int64_t)1 << 24;
+    // a served stream mixes queries whose rounds touch millions of nodes, and a resumed state
+    // cannot be re-run after an overflow: the lists get room for 2^26 candidates up front
+    int64_t list_cap = (int64_t)1 << 26;
     if (list_cap > (int64_t)slots * cap) list_cap = (int64_t)slots * cap;
     ServePool *P = new ServePool();
     try {
@@ -2011,6 +2016,25 @@ void serve_pool_results(Graph &g, ServePool *P, int32_t n, const int32_t *slots,
 
 int64_t serve_pool_round(const ServePool *P) { return P->T; }
 
+
+// A round's candidates of all seeds must fit the candidate and bin lists, sized from the
+// batch; a solve that overflows them (GDE_ENOMEM from the kernel, the pool marked for a reset)
+// is run again with lists four times larger, up to one entry per pool slot.
+void batch_solve(Graph &g, const SolveParams &p, const int32_t *seeds_dev, int32_t nseeds, int k,
+                 int64_t mem_budget, int32_t *ids_dev, float *vals_dev, gde_stats *stats_host,
+                 int32_t *overflow_seeds_host, int32_t *n_overflow) {
+    for (int scale = 0;; scale++) {
+        bool full = false;
+        try {
+            batch_solve_once(g, p, seeds_dev, nseeds, k, mem_budget, ids_dev, vals_dev, stats_host,
+                             overflow_seeds_host, n_overflow, scale, &full);
+            return;
+        } catch (const Fail &f) {
+            if (f.st != GDE_ENOMEM || full || !g.batch || !g.batch->list_overflowed) throw;
+            g.batch->list_overflowed = false;
+        }
+    }
+}
 
 int64_t batch_round_log(Graph &g, double *out, int64_t cap) {
     BatchWork *w = g.batch;
