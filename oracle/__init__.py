@@ -87,6 +87,11 @@ def _load():
             lib.oracle_push_fifo.argtypes = [I64, i64p, i32p, I, D, D, ctypes.c_int32, I, D,
                                              f64p, ctypes.POINTER(ctypes.c_int64)]
             lib.oracle_push_fifo.restype = I64
+            lib.oracle_gppr_round.argtypes = [I64, i64p, i32p, D, D, D, f64p, f64p, i32p, f64p, rp]
+            lib.oracle_gppr_round.restype = I64
+            lib.oracle_gppr_solve.argtypes = [I64, i64p, i32p, D, D, D, ctypes.c_int32, I64, f64p, rp,
+                                              ctypes.POINTER(ctypes.c_int64)]
+            lib.oracle_gppr_solve.restype = I
             _lib = lib
     return _lib
 
@@ -221,6 +226,30 @@ def push_fifo(g, kind, param: float, eps: float, seed: int, hk_mode: int = 0,
     if p < 0:
         raise MemoryError("oracle_push_fifo: allocation failed")
     return x, int(p), int(vol.value)
+
+
+def gppr_round(g, alpha: float, beta: float, eps: float, x: np.ndarray, r: np.ndarray) -> RoundResult:
+    """One LocalGD round of the generalised propagation M = D^-beta A D^(beta-1), in place."""
+    lib = _load()
+    n = g.n
+    active = np.empty(max(n, 1), dtype=np.int32)
+    rho = np.empty(max(n, 1), dtype=np.float64)
+    st = _Round()
+    cnt = lib.oracle_gppr_round(n, g.offsets, g.cols, alpha, beta, eps, x, r, active, rho, st)
+    return RoundResult(active[:cnt].copy(), rho[:cnt].copy(), st.n_active, st.vol_active, st.rS_l1)
+
+
+def gppr(g, alpha: float, beta: float, eps: float, seed: int, max_rounds: int = 1_000_000):
+    """Generalised-propagation LocalGD from e_seed.  Returns (x, rounds, volume, pushes, ||r||_1)."""
+    lib = _load()
+    x = np.zeros(g.n, dtype=np.float64)
+    tot = _Round()
+    rounds = ctypes.c_int64()
+    st = lib.oracle_gppr_solve(g.n, g.offsets, g.cols, alpha, beta, eps, int(seed), max_rounds, x,
+                               ctypes.byref(tot), ctypes.byref(rounds))
+    if st < 0:
+        raise MemoryError("oracle_gppr_solve: allocation failed")
+    return x, int(rounds.value), int(tot.vol_active), int(tot.n_active), float(tot.rS_l1)
 
 
 def topk(x: np.ndarray, k: int):

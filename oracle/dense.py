@@ -72,3 +72,20 @@ def hk_exact(g, tau: float, s: int) -> np.ndarray:
     from scipy.linalg import expm
     M = walk_matrix(g)
     return expm(-tau * (np.eye(g.n) - M)) @ unit(g.n, s)
+
+
+def gppr_matrix(g, beta: float) -> np.ndarray:
+    """M = D^-beta A D^(beta-1) (the generalised propagation of the InstantGNN push; zero
+    columns and rows at degree-0 nodes)."""
+    A = adjacency(g)
+    d = np.diff(g.offsets).astype(np.float64)
+    nz = d > 0
+    left = np.where(nz, np.power(np.where(nz, d, 1.0), -beta), 0.0)
+    right = np.where(nz, np.power(np.where(nz, d, 1.0), beta - 1.0), 0.0)
+    return left[:, None] * A * right[None, :]
+
+
+def gppr(g, alpha: float, beta: float, s: int) -> np.ndarray:
+    """f = alpha (I - (1-alpha) M)^-1 e_s = sum_k alpha (1-alpha)^k M^k e_s."""
+    M = gppr_matrix(g, beta)
+    return alpha * np.linalg.solve(np.eye(g.n) - (1.0 - alpha) * M, unit(g.n, s))

@@ -113,6 +113,73 @@ int64_t oracle_hk_round(int64_t n, const int64_t *off, const int32_t *col, doubl
     return k;
 }
 
+/*
+ * Generalised propagation (the InstantGNN propagation of Section 4 and its push in the
+ * appendix on InstantGNN(LocalGS); beta = 1/2 gives APPNP's D^-1/2 A D^-1/2 of Table 1,
+ * beta = 0 gives PPR): f = sum_k alpha (1-alpha)^k M^k e_s with M = D^-beta A D^(beta-1).
+ * One LocalGD round: S_t = { u : r_u != 0, |r_u| >= eps d_u^(1-beta) } in ascending id,
+ * snapshot and zero r_S, then for u in S_t: x_u += alpha r_u and, for v in N(u) in CSR
+ * order, r_v += ((1-alpha) r_u) / (d_u^(1-beta) d_v^beta).
+ */
+int64_t oracle_gppr_round(int64_t n, const int64_t *off, const int32_t *col, double alpha,
+                          double beta, double eps, double *x, double *r, int32_t *active,
+                          double *rho, orc_round *st) {
+    int64_t k = 0, vol = 0;
+    double l1 = 0.0;
+    for (int64_t u = 0; u < n; u++) {
+        double thr_u = eps * pow((double)deg_of(off, u), 1.0 - beta);
+        if (r[u] != 0.0 && fabs(r[u]) >= thr_u) active[k++] = (int32_t)u;
+    }
+    for (int64_t i = 0; i < k; i++) {
+        int32_t u = active[i];
+        rho[i] = r[u];
+        vol += deg_of(off, u);
+        l1 += fabs(rho[i]);
+        r[u] = 0.0;
+    }
+    if (st) { st->n_active = k; st->vol_active = vol; st->rS_l1 = l1; }
+    const double keep = 1.0 - alpha;  /* the share 1 - alpha that is propagated */
+    for (int64_t i = 0; i < k; i++) {
+        int32_t u = active[i];
+        int64_t d = deg_of(off, u);
+        x[u] += alpha * rho[i];
+        if (d == 0) continue;
+        double du = pow((double)d, 1.0 - beta);
+        for (int64_t e = off[u]; e < off[u + 1]; e++) {
+            int32_t v = col[e];
+            double dv = pow((double)deg_of(off, v), beta);
+            r[v] = r[v] + (keep * rho[i]) / (du * dv);
+        }
+    }
+    return k;
+}
+
+/* Generalised propagation from e_seed until the active set is empty (or max_rounds). */
+int oracle_gppr_solve(int64_t n, const int64_t *off, const int32_t *col, double alpha, double beta,
+                      double eps, int32_t seed, int64_t max_rounds, double *x, orc_round *total,
+                      int64_t *rounds_out) {
+    double *r = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    int32_t *active = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    double *rho = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    if (!r || !active || !rho) { free(r); free(active); free(rho); return -1; }
+    memset(x, 0, sizeof(double) * (size_t)n);
+    r[seed] = 1.0;
+    int64_t t = 0, vol = 0, pushes = 0;
+    for (; t < max_rounds; t++) {
+        orc_round st;
+        int64_t k = oracle_gppr_round(n, off, col, alpha, beta, eps, x, r, active, rho, &st);
+        if (k == 0) break;
+        vol += st.vol_active;
+        pushes += k;
+    }
+    double rl1 = 0.0;
+    for (int64_t u = 0; u < n; u++) rl1 += fabs(r[u]);
+    if (total) { total->n_active = pushes; total->vol_active = vol; total->rS_l1 = rl1; }
+    if (rounds_out) *rounds_out = t;
+    free(r); free(active); free(rho);
+    return t >= max_rounds ? 1 : 0;
+}
+
 /* ------------------------------------------------------- heat-kernel terms */
 
 /*

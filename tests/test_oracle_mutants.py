@@ -12,6 +12,7 @@ import subprocess
 import pytest
 
 import oracle
+import test_oracle_gppr as gpins
 import test_oracle_pins as pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "localgd.c")
@@ -36,6 +37,13 @@ MUTANTS = {
                            "if (tail <= tol) best = N - 1; else break;"),
     "hk_psi_wrong_factorial": ("term = term * (tau / (double)(k + j));",
                                "term = term * (tau / (double)(j));"),
+    "gppr_target_exponent_sign": ("double dv = pow((double)deg_of(off, v), beta);",
+                                  "double dv = pow((double)deg_of(off, v), -beta);"),
+    "gppr_source_exponent": ("double du = pow((double)d, 1.0 - beta);",
+                             "double du = pow((double)d, beta);"),
+    "gppr_threshold_exponent": ("double thr_u = eps * pow((double)deg_of(off, u), 1.0 - beta);",
+                                "double thr_u = eps * pow((double)deg_of(off, u), beta);"),
+    "gppr_x_drops_alpha": ("x[u] += alpha * rho[i];", "x[u] += rho[i];"),
 }
 
 PIN_CASES = [
@@ -50,6 +58,9 @@ PIN_CASES = [
     (pins.test_hk_terms_against_poisson_tail, {}),
     (pins.test_hk_psi_definition, {}),
     (pins.test_hk_weighted_mass_and_layer_invariant, {}),
+    (gpins.test_star_by_hand, {}),
+    (gpins.test_error_bound_against_dense, dict(gi=0, beta=0.5)),
+    (gpins.test_round_invariant, dict(beta=0.25)),
 ]
 
 
@@ -73,7 +84,7 @@ def test_mutant_is_caught(tmp_path, monkeypatch, name):
     # same signatures as the real library
     for sym in ("oracle_ppr_round", "oracle_katz_round", "oracle_hk_round", "oracle_hk_terms",
                 "oracle_hk_psi", "oracle_hk_theta", "oracle_localgd_solve",
-                "oracle_localgd_solve_many", "oracle_push_fifo"):
+                "oracle_localgd_solve_many", "oracle_push_fifo", "oracle_gppr_round", "oracle_gppr_solve"):
         f, g = getattr(bad, sym), getattr(good, sym)
         f.argtypes, f.restype = g.argtypes, g.restype
     monkeypatch.setattr(oracle, "_lib", bad)
