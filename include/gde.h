@@ -9,6 +9,9 @@
  *   GDE_PPR   personalized PageRank, M = A D^-1, c_k = alpha (1-alpha)^k   (Eq. f-ppr)
  *   GDE_KATZ  Katz, (I - beta A) x = e_s; the Katz vector is x - e_s      (Eq. f-katz)
  *   GDE_HK    heat kernel exp(-tau (I - A D^-1)) e_s via its Taylor layers (Section 2)
+ *   GDE_GPPR  generalised propagation, M = D^-b A D^(b-1), c_k = alpha (1-alpha)^k: the
+ *             InstantGNN push of the appendix (b = opts.prop_beta; b = 1/2 is APPNP's
+ *             D^-1/2 A D^-1/2 of Table 1, b = 0 is PPR)
  *
  * Each round t takes the active set S_t = { u : r_u != 0, |r_u| >= theta_t eps d_u }
  * (Definition 3.1; theta_t = 1 for PPR and Katz), moves r_S into x and scatters
@@ -17,6 +20,11 @@
  *   Katz: x_u += r_u,       r_v += beta r_u
  *   HK  : layer-t node u:  x_u += r_u, r_{t+1,v} += ((tau/(t+1)) r_u)/d_u; the last
  *         Taylor layer N (tail mass <= hk_tol) only moves its residual into x.
+ *   GPPR: x_u += alpha r_u, r_v += ((1-alpha) r_u)/(d_u^(1-b) d_v^b), active iff
+ *         |r_u| >= eps d_u^(1-b).  The library keeps the scaled residual y = S r with
+ *         S = diag(max(d, 1)^b), on which the round is PPR's (the similarity
+ *         M = S^-1 (A D^-1) S): |y_u| >= eps d_u, y_v += ((1-alpha) y_u)/d_u,
+ *         x_u += (alpha y_u)/S_u, seed y_s = S_s.
  * Degree-0 nodes scatter nothing.  All work runs in this library's CUDA kernels
  * (sm_103a); there is no CPU fallback.
  *
@@ -42,7 +50,7 @@ extern "C" {
 typedef struct gde_graph gde_graph;
 typedef struct gde_session gde_session;
 
-typedef enum { GDE_PPR = 0, GDE_KATZ = 1, GDE_HK = 2 } gde_kind;
+typedef enum { GDE_PPR = 0, GDE_KATZ = 1, GDE_HK = 2, GDE_GPPR = 3 } gde_kind;
 
 typedef enum {
     GDE_OK = 0,
@@ -78,6 +86,7 @@ typedef struct {
     int64_t mem_budget_bytes;/* batched: bytes for the hash accumulators; 0 = automatic */
     double hk_tol;           /* HK Taylor tail tolerance; 0 (default) means 1e-12 */
     void *cuda_stream;       /* borrowed cudaStream_t to run on; NULL = the graph's stream */
+    double prop_beta;        /* GDE_GPPR: the exponent b in [0, 1] of M = D^-b A D^(b-1) */
 } gde_solve_opts;
 
 /* Per-seed result statistics (Definition 3.1 and Theorem 3.5). */
@@ -85,7 +94,8 @@ typedef struct {
     int64_t rounds;          /* T: number of rounds with a non-empty S_t */
     int64_t active_volume;   /* sum_t vol(S_t): the operation count of the paper */
     int64_t pushes;          /* sum_t |S_t| */
-    double resid_l1;         /* ||r^(T)||_1 (HK: summed over all Taylor layers) */
+    double resid_l1;         /* ||r^(T)||_1 (HK: summed over all Taylor layers; GPPR: of the
+                                scaled residual y, with mass_l1 the matching ||S x||_1) */
     double mass_l1;          /* ||x^(T)||_1 before any output scaling */
     int32_t status;          /* gde_status of this seed */
     int32_t reserved;
@@ -137,7 +147,8 @@ gde_status gde_update_edges(gde_graph *g, const int32_t *src, const int32_t *dst
 /*
  * Approximate diffusion vectors for nseeds independent unit sources.
  *   kind, param  GDE_PPR with alpha in (0,1); GDE_KATZ with beta > 0 (LocalGD terminates
- *                when beta lambda_max(A) < 1); GDE_HK with tau > 0
+ *                when beta lambda_max(A) < 1); GDE_HK with tau > 0; GDE_GPPR with alpha in
+ *                (0,1) and opts->prop_beta in [0,1] (plain and batched modes)
  *   eps          tolerance > 0 of the active-set test
  *   seeds        nseeds source node ids in [0, n)
  *   out_x        topk == 0: nseeds x n values, row-major (double for GDE_FP64, float for

@@ -111,10 +111,14 @@ double hk_theta(double tau, int64_t N, int64_t t, int mode) {
 
 static SolveParams make_params(Graph &g, gde_kind kind, double param, double eps,
                                const gde_solve_opts &o) {
-    GDE_REQUIRE(kind == GDE_PPR || kind == GDE_KATZ || kind == GDE_HK, GDE_EINVAL, "unknown kind");
+    GDE_REQUIRE(kind == GDE_PPR || kind == GDE_KATZ || kind == GDE_HK || kind == GDE_GPPR, GDE_EINVAL,
+                "unknown kind");
     GDE_REQUIRE(std::isfinite(param) && std::isfinite(eps), GDE_EINVAL, "param and eps must be finite");
     GDE_REQUIRE(eps > 0.0, GDE_EINVAL, "eps must be > 0");
-    if (kind == GDE_PPR) GDE_REQUIRE(param > 0.0 && param < 1.0, GDE_EINVAL, "PPR alpha must be in (0,1)");
+    if (kind == GDE_PPR || kind == GDE_GPPR)
+        GDE_REQUIRE(param > 0.0 && param < 1.0, GDE_EINVAL, "PPR alpha must be in (0,1)");
+    if (kind == GDE_GPPR)
+        GDE_REQUIRE(o.prop_beta >= 0.0 && o.prop_beta <= 1.0, GDE_EINVAL, "prop_beta must be in [0,1]");
     if (kind == GDE_KATZ) GDE_REQUIRE(param > 0.0, GDE_EINVAL, "Katz beta must be > 0");
     if (kind == GDE_HK) GDE_REQUIRE(param > 0.0 && param < 700.0, GDE_EINVAL, "HK tau must be in (0,700)");
     GDE_REQUIRE(o.precision == GDE_FP64 || o.precision == GDE_FP32, GDE_EINVAL, "bad precision");
@@ -134,6 +138,7 @@ static SolveParams make_params(Graph &g, gde_kind kind, double param, double eps
     GDE_REQUIRE(o.deterministic == 0 || o.deterministic == 1, GDE_EINVAL, "bad deterministic flag");
     p.deterministic = o.deterministic;
     p.stream = o.cuda_stream ? (cudaStream_t)o.cuda_stream : g.stream;
+    p.gbeta = kind == GDE_GPPR ? o.prop_beta : 0.0;
     return p;
 }
 
@@ -347,6 +352,12 @@ gde_status gde_solve(gde_graph *h, gde_kind kind, double param, double eps, cons
                 dense_begin(g, w, p, hs[i]);
                 gde_stats one{};
                 double rl1 = 1.0, xl1 = 0.0;
+                if (kind == GDE_GPPR && p.gbeta != 0.0) {
+                    // the scaled system's source mass S_s = max(d_s, 1)^b
+                    int32_t ds = 0;
+                    GDE_CUDA(cudaMemcpy(&ds, g.deg + hs[i], sizeof(int32_t), cudaMemcpyDeviceToHost));
+                    rl1 = std::pow((double)(ds > 0 ? ds : 1), p.gbeta);
+                }
                 int64_t rounds = 0;
                 bool converged = false;
                 while (rounds < p.max_rounds) {
@@ -356,7 +367,7 @@ gde_status gde_solve(gde_graph *h, gde_kind kind, double param, double eps, cons
                     rounds++;
                     one.active_volume += ri.vol;
                     one.pushes += ri.n_active;
-                    xl1 += (kind == GDE_PPR ? param : 1.0) * ri.rS_l1;
+                    xl1 += (kind == GDE_PPR || kind == GDE_GPPR ? param : 1.0) * ri.rS_l1;
                     rl1 = rl1 - ri.rS_l1 + ri.scat;
                 }
                 if (!converged && !dense_pending(w)) converged = true;

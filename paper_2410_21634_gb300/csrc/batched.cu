@@ -137,6 +137,7 @@ struct BatchWork {
     int32_t *slast = nullptr;        // per seed: last round with a push
     double *spush = nullptr;         // per seed: sum of pushed residual mass (FP64)
     double *sscat = nullptr;         // per seed: sum of scattered mass d_u w_u (FP64)
+    double *smass0 = nullptr;        // per seed: the source's residual (1, or S_s when scaled)
     uint32_t *xlist = nullptr;       // per seed: xcap slots whose x is nonzero
     unsigned *xcnt = nullptr;        // per seed: x-list length (may exceed xcap: overflow)
     int64_t xcap = 0;
@@ -278,6 +279,7 @@ struct BArgs {
     int kind;
     double cx;    // x += cx * rho
     double coef;  // PPR 1-alpha (share divided by d_u), Katz beta
+    double gbeta; // generalised propagation: x += (cx * rho) / max(d_u, 1)^gbeta (0: none)
     int64_t max_rounds;
     int32_t t1, t2, chunk;
     int32_t schedule;   // 0: all bins handed out in order; 1: hubs in order, others strided; 2: all strided
@@ -566,10 +568,12 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
             rho = atomicExch(r_of(a.kr, slot), 0.0f);
             if (!(rho != 0.0f && fabsf(rho) >= thr)) { __stcg(a.tmp_deg + ci, 0); continue; }
             const double rho64 = (double)rho;
-            const float xold = __ldcg(a.xs + slot);
-            __stcg(a.xs + slot, __fadd_rn(xold, __double2float_rn(__dmul_rn(cx, rho64))));
             const int64_t beg = a.off[v];
             const int32_t d = (int32_t)(a.off[v + 1] - beg);
+            const float xold = __ldcg(a.xs + slot);
+            double xinc = __dmul_rn(cx, rho64);
+            if (a.gbeta != 0.0) xinc = __ddiv_rn(xinc, pow((double)(d > 0 ? d : 1), a.gbeta));
+            __stcg(a.xs + slot, __fadd_rn(xold, __double2float_rn(xinc)));
             float w = 0.0f;
             if (d > 0) {
                 if (divide)
@@ -885,7 +889,7 @@ __global__ void k_batch_seed(int32_t nseeds, const int32_t *seeds, unsigned long
                              uint32_t *cand0, int log2cap, uint32_t mask, BGlobal *G,
                              int32_t *status, unsigned *inserts, unsigned long long *svol,
                              unsigned *spushes, int32_t *slast, uint32_t key_tag, unsigned *xcnt,
-                             double *spush, double *sscat) {
+                             double *spush, double *sscat, const int32_t *deg, double gbeta, double *smass0) {
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j == 0) {
         memset(G, 0, sizeof(BGlobal));
@@ -896,7 +900,10 @@ __global__ void k_batch_seed(int32_t nseeds, const int32_t *seeds, unsigned long
     // the first slot of the seed's probe bucket, where bscatter's search for s begins
     const uint32_t sector_mask = mask >= 3 ? 3u : mask;
     const uint64_t slot = ((uint64_t)j << log2cap) + (mix32((uint32_t)s) & mask & ~sector_mask);
-    kr[slot] = ((unsigned long long)__float_as_uint(1.0f) << 32) | (unsigned long long)((uint32_t)s | key_tag);
+    // unit source; the generalised propagation keeps it scaled, y_s = max(d_s, 1)^gbeta
+    const double m0 = gbeta != 0.0 ? pow((double)(deg[s] > 0 ? deg[s] : 1), gbeta) : 1.0;
+    kr[slot] = ((unsigned long long)__float_as_uint((float)m0) << 32) | (unsigned long long)((uint32_t)s | key_tag);
+    smass0[j] = (double)(float)m0;
     cand0[j] = (uint32_t)slot;
     status[j] = kSeedOk;
     inserts[j] = 1;
@@ -1116,7 +1123,7 @@ static void batch_free(BatchWork *w) {
     dfree(w->hub_vstart); dfree(w->tmp_beg); dfree(w->tmp_deg); dfree(w->tmp_w); dfree(w->tmp_jb);
     dfree(w->seg_cnt); dfree(w->seg_off); dfree(w->seg_cur); dfree(w->seg_hvol); dfree(w->vol_off);
     dfree(w->seg_hcur); dfree(w->seeds); dfree(w->status); dfree(w->inserts); dfree(w->svol);
-    dfree(w->spushes); dfree(w->slast); dfree(w->spush); dfree(w->sscat); dfree(w->xlist); dfree(w->xcnt); dfree(w->glob); dfree(w->log);
+    dfree(w->spushes); dfree(w->slast); dfree(w->spush); dfree(w->sscat); dfree(w->smass0); dfree(w->xlist); dfree(w->xcnt); dfree(w->glob); dfree(w->log);
     delete w;
 }
 
@@ -1173,6 +1180,7 @@ static BatchWork *batch_work_alloc(int64_t nseeds, int64_t cap, int64_t list_cap
         w->slast = (int32_t *)dmalloc(4 * (size_t)nseeds, "seed rounds");
         w->spush = (double *)dmalloc(8 * (size_t)nseeds, "seed pushed mass");
         w->sscat = (double *)dmalloc(8 * (size_t)nseeds, "seed scattered mass");
+        w->smass0 = (double *)dmalloc(8 * (size_t)nseeds, "seed source mass");
         w->xcap = cap < xcap_max ? cap : xcap_max;
         w->xlist = (uint32_t *)dmalloc(4 * (size_t)nseeds * (size_t)w->xcap, "x lists");
         w->xcnt = (unsigned *)dmalloc(4 * (size_t)nseeds, "x list lengths");
@@ -1294,7 +1302,8 @@ static void batch_solve_once(Graph &g, const SolveParams &p, const int32_t *seed
                              int32_t *overflow_seeds_host, int32_t *n_overflow, int list_scale,
                              bool *list_full) {
     GDE_REQUIRE(k >= 1 && k <= kTopMax, GDE_EINVAL, "batched mode needs 1 <= topk <= 64");
-    GDE_REQUIRE(p.kind == GDE_PPR || p.kind == GDE_KATZ, GDE_EINVAL, "batched mode supports PPR and Katz");
+    GDE_REQUIRE(p.kind == GDE_PPR || p.kind == GDE_KATZ || p.kind == GDE_GPPR, GDE_EINVAL,
+                "batched mode supports PPR, Katz and the generalised propagation");
     GDE_REQUIRE(p.precision == GDE_FP32, GDE_EINVAL, "batched mode stores x and r in FP32");
     GDE_REQUIRE(g.n < ((int64_t)1 << 31) - 1, GDE_EINVAL, "graph too large for 32-bit keys");
     const int64_t budget = mem_budget > 0 ? mem_budget : ((int64_t)16 << 30);
@@ -1352,7 +1361,8 @@ static void batch_solve_once(Graph &g, const SolveParams &p, const int32_t *seed
     GDE_CUDA(cudaMemsetAsync(w->log, 0, sizeof(RoundLog) * kLogCap, s));
     k_batch_seed<<<(nseeds + kThreads - 1) / kThreads, kThreads, 0, s>>>(
         nseeds, w->seeds, w->kr, w->cand[0], w->log2cap, (uint32_t)(cap - 1), w->glob, w->status,
-        w->inserts, w->svol, w->spushes, w->slast, key_tag, w->xcnt, w->spush, w->sscat);
+        w->inserts, w->svol, w->spushes, w->slast, key_tag, w->xcnt, w->spush, w->sscat, g.deg, p.gbeta,
+        w->smass0);
     GDE_CUDA(cudaGetLastError());
     g.prof.launched();
 
@@ -1361,9 +1371,10 @@ static void batch_solve_once(Graph &g, const SolveParams &p, const int32_t *seed
     a.eps_cls[0] = p.eps; a.ncls = 1; a.sparam = nullptr; a.t0 = 0;
     GDE_CUDA(cudaMemsetAsync(w->seg_cnt, 0, 4 * 3 * (size_t)nseeds, s));
     GDE_CUDA(cudaMemsetAsync(w->seg_hvol, 0, 8 * (size_t)nseeds, s));
-    a.kind = p.kind;
-    a.cx = p.kind == GDE_PPR ? p.param : 1.0;
-    a.coef = p.kind == GDE_PPR ? 1.0 - p.param : p.param;
+    a.kind = p.kind == GDE_GPPR ? GDE_PPR : p.kind;
+    a.cx = a.kind == GDE_PPR ? p.param : 1.0;
+    a.coef = a.kind == GDE_PPR ? 1.0 - p.param : p.param;
+    a.gbeta = p.gbeta;
     a.max_rounds = p.max_rounds;
     launch_rounds(g, w, a, s);
 
@@ -1383,7 +1394,7 @@ static void batch_solve_once(Graph &g, const SolveParams &p, const int32_t *seed
     std::vector<int32_t> st(nseeds), last(nseeds);
     std::vector<unsigned long long> vol(nseeds);
     std::vector<unsigned> pushes(nseeds);
-    std::vector<double> pushed(nseeds), scat(nseeds);
+    std::vector<double> pushed(nseeds), scat(nseeds), m0(nseeds);
     std::vector<unsigned> ins(nseeds);
     GDE_CUDA(cudaMemcpyAsync(st.data(), w->status, 4 * (size_t)nseeds, cudaMemcpyDeviceToHost, s));
     if (g.prof.enabled)
@@ -1394,6 +1405,7 @@ static void batch_solve_once(Graph &g, const SolveParams &p, const int32_t *seed
         GDE_CUDA(cudaMemcpyAsync(pushes.data(), w->spushes, 4 * (size_t)nseeds, cudaMemcpyDeviceToHost, s));
         GDE_CUDA(cudaMemcpyAsync(pushed.data(), w->spush, 8 * (size_t)nseeds, cudaMemcpyDeviceToHost, s));
         GDE_CUDA(cudaMemcpyAsync(scat.data(), w->sscat, 8 * (size_t)nseeds, cudaMemcpyDeviceToHost, s));
+        GDE_CUDA(cudaMemcpyAsync(m0.data(), w->smass0, 8 * (size_t)nseeds, cudaMemcpyDeviceToHost, s));
     }
     GDE_CUDA(cudaStreamSynchronize(s));
     w->need_clear = false;  // the top-k zeroed x on every x-list (or table) it read
@@ -1428,8 +1440,8 @@ static void batch_solve_once(Graph &g, const SolveParams &p, const int32_t *seed
             o.active_volume = (int64_t)vol[j];
             o.pushes = pushes[j];
             // unit source: ||r||_1 = 1 - pushed + scattered; ||x||_1 = c_x * pushed
-            o.resid_l1 = 1.0 - pushed[j] + scat[j];
-            o.mass_l1 = (p.kind == GDE_PPR ? p.param : 1.0) * pushed[j];
+            o.resid_l1 = m0[j] - pushed[j] + scat[j];
+            o.mass_l1 = (p.kind == GDE_KATZ ? 1.0 : p.param) * pushed[j];
             o.status = of ? GDE_ENOMEM : ((capped && last[j] + 1 >= (int64_t)hg.rounds) ? GDE_ENOTCONV : GDE_OK);
             o.reserved = 0;
         }

@@ -135,6 +135,7 @@ struct SolveParams {
     int64_t hk_N;      // Taylor layers - 1 (HK)
     int deterministic; // sort-based scatter (dense engine)
     cudaStream_t stream;
+    double gbeta;      // GDE_GPPR: b of M = D^-b A D^(b-1) (the engines run PPR on y = S r, S = max(d,1)^b)
 };
 
 // heat-kernel helpers (host)

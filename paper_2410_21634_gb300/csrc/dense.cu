@@ -133,14 +133,20 @@ template <typename T> __device__ __forceinline__ T warp_sum(T v) {
 
 // --------------------------------------------------------------------- init --
 
+// scale of the generalised propagation's residual at a node: y_u = max(d_u, 1)^b r_u
+__device__ __forceinline__ double gppr_scale(int32_t d, double b) {
+    return pow((double)(d > 0 ? d : 1), b);
+}
+
 template <typename real>
 __global__ void k_init_pairs(int64_t n, const int32_t *__restrict__ deg, real *__restrict__ x,
-                             RPair<real> *__restrict__ rp, double eps, int32_t seed) {
+                             RPair<real> *__restrict__ rp, double eps, int32_t seed, double gbeta) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         x[i] = real(0);
         RPair<real> p;
-        p.r = (i == seed) ? real(1) : real(0);
+        // unit source; the generalised propagation stores it scaled, y_s = S_s
+        p.r = (i == seed) ? (gbeta != 0.0 ? from_f64<real>(gppr_scale(deg[i], gbeta)) : real(1)) : real(0);
         p.thr = thr_store<real>(eps, deg[i]);
         rp[i] = p;
     }
@@ -175,6 +181,7 @@ template <typename real> struct FrontierArgs {
     double eps_theta;     // HK: fl(theta_t eps)
     double cx;            // x_u += cx * rho  (PPR alpha, else 1)
     double coef;          // PPR 1-alpha, Katz beta, HK fl(tau/(t+1))
+    double gbeta;         // generalised propagation: x_u += (cx * rho) / S_u (0: plain PPR)
     int propagate;
     int32_t t1, t2;
     int64_t *b_beg[3];
@@ -217,7 +224,10 @@ __global__ void __launch_bounds__(kThreads) k_frontier(FrontierArgs<real> a) {
         if (act) {
             if (KIND == GDE_HK) a.rcur[u] = real(0); else a.rp[u].r = real(0);
             const double rho64 = (double)rho;
-            if (KIND == GDE_PPR)
+            if (KIND == GDE_PPR && a.gbeta != 0.0)
+                a.x[u] = radd<real>(a.x[u], from_f64<real>(__ddiv_rn(__dmul_rn(a.cx, rho64),
+                                                                     gppr_scale(d, a.gbeta))));
+            else if (KIND == GDE_PPR)
                 a.x[u] = radd<real>(a.x[u], from_f64<real>(__dmul_rn(a.cx, rho64)));
             else
                 a.x[u] = radd<real>(a.x[u], rho);
@@ -408,10 +418,12 @@ __global__ void k_scale_copy(int64_t n, const real *__restrict__ x, real *__rest
 }
 
 template <typename real>
-__global__ void k_read_r_pairs(int64_t n, const RPair<real> *__restrict__ rp, real *__restrict__ dst) {
+__global__ void k_read_r_pairs(int64_t n, const RPair<real> *__restrict__ rp, real *__restrict__ dst,
+                               const int32_t *__restrict__ deg, double gbeta) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
-        dst[i] = rp[i].r;
+        // the generalised propagation's residual is kept scaled: r = y / S
+        dst[i] = gbeta != 0.0 ? from_f64<real>(__ddiv_rn((double)rp[i].r, gppr_scale(deg[i], gbeta))) : rp[i].r;
 }
 
 // ---------------------------------------------------- deterministic scatter --
@@ -584,7 +596,7 @@ static void begin_impl(Graph &g, DenseWork *w, const SolveParams &p, int32_t see
         g.prof.launched();
     } else {
         k_init_pairs<real><<<grid, kThreads, 0, p.stream>>>(g.n, g.deg, (real *)w->x,
-                                                            (RPair<real> *)w->rp, p.eps, seed);
+                                                            (RPair<real> *)w->rp, p.eps, seed, p.gbeta);
         GDE_CUDA(cudaGetLastError());
     g.prof.launched();
         k_prep<<<1, 32, 0, p.stream>>>(w->ctl, w->cand[0], nullptr, seed);
@@ -622,7 +634,7 @@ static int64_t round_impl(Graph &g, DenseWork *w, const SolveParams &p, RoundInf
     fa.rp = (RPair<real> *)w->rp;
     fa.rcur = KIND == GDE_HK ? (real *)w->rl[cur] : nullptr;
     fa.propagate = last_layer ? 0 : 1;
-    if (KIND == GDE_PPR) { fa.cx = p.param; fa.coef = 1.0 - p.param; }
+    if (KIND == GDE_PPR) { fa.cx = p.param; fa.coef = 1.0 - p.param; fa.gbeta = p.gbeta; }
     else if (KIND == GDE_KATZ) { fa.cx = 1.0; fa.coef = p.param; }
     else {
         fa.cx = 1.0;
@@ -742,11 +754,11 @@ int64_t dense_round(Graph &g, DenseWork *w, const SolveParams &p, RoundInfo *inf
         return 0;
     }
     if (p.precision == GDE_FP64) {
-        if (p.kind == GDE_PPR) return round_impl<double, GDE_PPR>(g, w, p, info);
+        if (p.kind == GDE_PPR || p.kind == GDE_GPPR) return round_impl<double, GDE_PPR>(g, w, p, info);
         if (p.kind == GDE_KATZ) return round_impl<double, GDE_KATZ>(g, w, p, info);
         return round_impl<double, GDE_HK>(g, w, p, info);
     }
-    if (p.kind == GDE_PPR) return round_impl<float, GDE_PPR>(g, w, p, info);
+    if (p.kind == GDE_PPR || p.kind == GDE_GPPR) return round_impl<float, GDE_PPR>(g, w, p, info);
     if (p.kind == GDE_KATZ) return round_impl<float, GDE_KATZ>(g, w, p, info);
     return round_impl<float, GDE_HK>(g, w, p, info);
 }
@@ -772,10 +784,10 @@ void dense_read(Graph &g, DenseWork *w, const SolveParams &p, void *x, void *r, 
             try {
                 if (p.precision == GDE_FP64)
                     k_read_r_pairs<double><<<grid_for(g.n), kThreads, 0, p.stream>>>(
-                        g.n, (const RPair<double> *)w->rp, (double *)tmp);
+                        g.n, (const RPair<double> *)w->rp, (double *)tmp, g.deg, p.gbeta);
                 else
                     k_read_r_pairs<float><<<grid_for(g.n), kThreads, 0, p.stream>>>(
-                        g.n, (const RPair<float> *)w->rp, (float *)tmp);
+                        g.n, (const RPair<float> *)w->rp, (float *)tmp, g.deg, p.gbeta);
                 GDE_CUDA(cudaGetLastError());
                 GDE_CUDA(cudaMemcpyAsync(r, tmp, bytes, k, p.stream));
                 GDE_CUDA(cudaStreamSynchronize(p.stream));
