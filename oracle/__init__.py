@@ -92,6 +92,15 @@ def _load():
             lib.oracle_gppr_solve.argtypes = [I64, i64p, i32p, D, D, D, ctypes.c_int32, I64, f64p, rp,
                                               ctypes.POINTER(ctypes.c_int64)]
             lib.oracle_gppr_solve.restype = I
+            lib.oracle_series_round.argtypes = [I64, i64p, i32p, D, I, D, f64p, f64p, f64p, i32p, f64p, rp]
+            lib.oracle_series_round.restype = I64
+            lib.oracle_series_psi.argtypes = [f64p, I64, I64]
+            lib.oracle_series_psi.restype = D
+            lib.oracle_series_theta.argtypes = [f64p, I64, I64, I]
+            lib.oracle_series_theta.restype = D
+            lib.oracle_series_solve.argtypes = [I64, i64p, i32p, f64p, I64, D, ctypes.c_int32, I, I64, f64p,
+                                                ctypes.POINTER(_Solve)]
+            lib.oracle_series_solve.restype = I
             _lib = lib
     return _lib
 
@@ -250,6 +259,25 @@ def gppr(g, alpha: float, beta: float, eps: float, seed: int, max_rounds: int = 
     if st < 0:
         raise MemoryError("oracle_gppr_solve: allocation failed")
     return x, int(rounds.value), int(tot.vol_active), int(tot.n_active), float(tot.rS_l1)
+
+
+def series(g, coef, eps: float, seed: int, mode: int = 0, max_rounds: int = 1_000_000) -> SolveResult:
+    """LocalGD on the layered system of f = sum_k coef[k] (A D^-1)^k e_s (coef > 0, N =
+    len(coef) - 1); x is returned scaled by coef[0], so that it approximates f."""
+    lib = _load()
+    c = np.ascontiguousarray(coef, dtype=np.float64)
+    x = np.zeros(g.n, dtype=np.float64)
+    res = _Solve()
+    st = lib.oracle_series_solve(g.n, g.offsets, g.cols, c, c.shape[0] - 1, eps, int(seed), mode,
+                                 max_rounds, x, ctypes.byref(res))
+    if st < 0:
+        raise MemoryError("oracle_series_solve: allocation failed")
+    return SolveResult(x, res.rounds, res.volume, res.pushes, res.resid_l1, res.x_l1, res.status, [])
+
+
+def series_theta(coef, t: int, mode: int = 0) -> float:
+    c = np.ascontiguousarray(coef, dtype=np.float64)
+    return float(_load().oracle_series_theta(c, c.shape[0] - 1, t, mode))
 
 
 def topk(x: np.ndarray, k: int):

@@ -89,3 +89,14 @@ def gppr(g, alpha: float, beta: float, s: int) -> np.ndarray:
     """f = alpha (I - (1-alpha) M)^-1 e_s = sum_k alpha (1-alpha)^k M^k e_s."""
     M = gppr_matrix(g, beta)
     return alpha * np.linalg.solve(np.eye(g.n) - (1.0 - alpha) * M, unit(g.n, s))
+
+
+def series(g, coef, s: int) -> np.ndarray:
+    """sum_{k<=N} coef[k] (A D^-1)^k e_s"""
+    M = walk_matrix(g)
+    v = unit(g.n, s)
+    f = np.zeros(g.n)
+    for c in coef:
+        f += c * v
+        v = M @ v
+    return f

@@ -34,6 +34,15 @@ typedef struct {
     double rS_l1;
 } orc_round;
 
+typedef struct {
+    int64_t rounds;       /* T: first round with S_T empty (or the layer count for HK) */
+    int64_t volume;       /* sum_t vol(S_t), Definition 3.1 */
+    int64_t pushes;       /* sum_t |S_t| */
+    double resid_l1;      /* ||r^(T)||_1 (HK: sum over the layers left behind) */
+    double x_l1;          /* ||x^(T)||_1 (before the HK e^-tau scaling) */
+    int status;           /* 0 converged, 1 round cap reached, -1 allocation failure */
+} orc_solve;
+
 static inline int64_t deg_of(const int64_t *off, int64_t u) { return off[u + 1] - off[u]; }
 
 /*
@@ -180,6 +189,86 @@ int oracle_gppr_solve(int64_t n, const int64_t *off, const int32_t *col, double 
     return t >= max_rounds ? 1 : 0;
 }
 
+/*
+ * A general power series f = sum_{k=0}^{N} c_k M^k e_s, M = A D^-1, c_k > 0 (Eq. 1 with the
+ * coefficients of Table 1, e.g. IPR's theta^k / (theta^k + theta^10)^2): the heat kernel's
+ * layered system (Section 2) with layer ratio c_{t+1}/c_t.  Round t: the active layer-t
+ * nodes move their residual into x and, unless t = N, scatter ((c_{t+1}/c_t) r_u)/d_u to
+ * each neighbour's layer-(t+1) residual.  The result is f ~ c_0 x.
+ */
+int64_t oracle_series_round(int64_t n, const int64_t *off, const int32_t *col, double ratio,
+                            int propagate, double eps_theta, double *x, double *r, double *r_next,
+                            int32_t *active, double *rho, orc_round *st) {
+    int64_t k = select_and_snapshot(n, off, eps_theta, r, active, rho, st);
+    for (int64_t i = 0; i < k; i++) {
+        int32_t u = active[i];
+        int64_t d = deg_of(off, u);
+        x[u] = x[u] + rho[i];
+        if (!propagate || d == 0) continue;
+        double w = (ratio * rho[i]) / (double)d;
+        for (int64_t e = off[u]; e < off[u + 1]; e++) r_next[col[e]] = r_next[col[e]] + w;
+    }
+    return k;
+}
+
+/* psi_t = sum_{j=0}^{N-t} c_{t+j}/c_t: the weight of one unit of layer-t residual */
+double oracle_series_psi(const double *c, int64_t N, int64_t t) {
+    double psi = 0.0;
+    for (int64_t j = 0; j <= N - t; j++) psi += c[t + j] / c[t];
+    return psi;
+}
+
+/*
+ * Threshold scale of layer t: 1/((N+1) c_0 psi_t) (mode 0), which gives
+ * 0 <= f_N - c_0 x <= eps d_u at exit (each layer's leftover residual r_t adds at most
+ * c_0 psi_t theta_t eps d_u through the reversibility of A D^-1), or 1 (mode 1).
+ */
+double oracle_series_theta(const double *c, int64_t N, int64_t t, int mode) {
+    if (mode == 1) return 1.0;
+    return 1.0 / ((double)(N + 1) * c[0] * oracle_series_psi(c, N, t));
+}
+
+/* The series solve from e_seed: layers 0..N, x returned already scaled by c_0. */
+int oracle_series_solve(int64_t n, const int64_t *off, const int32_t *col, const double *c, int64_t N,
+                        double eps, int32_t seed, int mode, int64_t max_rounds, double *x,
+                        orc_solve *res) {
+    memset(res, 0, sizeof(*res));
+    double *r = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    double *r2 = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    int32_t *active = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    double *rho = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    if (!r || !r2 || !active || !rho) {
+        free(r); free(r2); free(active); free(rho);
+        res->status = -1;
+        return -1;
+    }
+    memset(x, 0, sizeof(double) * (size_t)n);
+    r[seed] = 1.0;
+    double retired = 0.0;
+    int64_t t = 0;
+    for (t = 0; t < max_rounds && t <= N; t++) {
+        orc_round st;
+        double ratio = t < N ? c[t + 1] / c[t] : 0.0;
+        double eps_theta = oracle_series_theta(c, N, t, mode) * eps;
+        int64_t k = oracle_series_round(n, off, col, ratio, t < N, eps_theta, x, r, r2, active, rho, &st);
+        if (k == 0) break;
+        res->volume += st.vol_active;
+        res->pushes += st.n_active;
+        for (int64_t u = 0; u < n; u++) retired += fabs(r[u]);
+        double *tmp = r; r = r2; r2 = tmp;
+        memset(r2, 0, sizeof(double) * (size_t)n);
+    }
+    res->rounds = t;
+    res->status = (t >= max_rounds) ? 1 : 0;
+    double rl1 = retired, xl1 = 0.0;
+    for (int64_t u = 0; u < n; u++) { rl1 += fabs(r[u]); xl1 += fabs(x[u]); }
+    res->resid_l1 = rl1;
+    res->x_l1 = xl1;
+    for (int64_t u = 0; u < n; u++) x[u] = c[0] * x[u];
+    free(r); free(r2); free(active); free(rho);
+    return res->status;
+}
+
 /* ------------------------------------------------------- heat-kernel terms */
 
 /*
@@ -227,14 +316,6 @@ double oracle_hk_theta(double tau, int64_t N, int64_t t, int mode) {
 
 /* ----------------------------------------------------------------- solve */
 
-typedef struct {
-    int64_t rounds;       /* T: first round with S_T empty (or the layer count for HK) */
-    int64_t volume;       /* sum_t vol(S_t), Definition 3.1 */
-    int64_t pushes;       /* sum_t |S_t| */
-    double resid_l1;      /* ||r^(T)||_1 (HK: sum over the layers left behind) */
-    double x_l1;          /* ||x^(T)||_1 (before the HK e^-tau scaling) */
-    int status;           /* 0 converged, 1 round cap reached, -1 allocation failure */
-} orc_solve;
 
 /*
  * LocalGD from the unit source e_s until S_T is empty (or max_rounds rounds).

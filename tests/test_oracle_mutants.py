@@ -13,6 +13,7 @@ import pytest
 
 import oracle
 import test_oracle_gppr as gpins
+import test_oracle_series as spins
 import test_oracle_pins as pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "localgd.c")
@@ -44,6 +45,11 @@ MUTANTS = {
     "gppr_threshold_exponent": ("double thr_u = eps * pow((double)deg_of(off, u), 1.0 - beta);",
                                 "double thr_u = eps * pow((double)deg_of(off, u), beta);"),
     "gppr_x_drops_alpha": ("x[u] += alpha * rho[i];", "x[u] += rho[i];"),
+    "series_ratio_off_by_one": ("double ratio = t < N ? c[t + 1] / c[t] : 0.0;",
+                                "double ratio = t + 1 < N ? c[t + 2] / c[t + 1] : 0.0;"),
+    "series_theta_without_psi": ("return 1.0 / ((double)(N + 1) * c[0] * oracle_series_psi(c, N, t));",
+                                 "return 1.0 / ((double)(N + 1) * c[0]);"),
+    "series_result_unscaled": ("for (int64_t u = 0; u < n; u++) x[u] = c[0] * x[u];", ""),
 }
 
 PIN_CASES = [
@@ -61,6 +67,8 @@ PIN_CASES = [
     (gpins.test_star_by_hand, {}),
     (gpins.test_error_bound_against_dense, dict(gi=0, beta=0.5)),
     (gpins.test_round_invariant, dict(beta=0.25)),
+    (spins.test_ipr_bound_against_dense, dict(gi=0, theta=1.3)),
+    (spins.test_heat_kernel_coefficients_give_the_heat_kernel, {}),
 ]
 
 
@@ -84,7 +92,8 @@ def test_mutant_is_caught(tmp_path, monkeypatch, name):
     # same signatures as the real library
     for sym in ("oracle_ppr_round", "oracle_katz_round", "oracle_hk_round", "oracle_hk_terms",
                 "oracle_hk_psi", "oracle_hk_theta", "oracle_localgd_solve",
-                "oracle_localgd_solve_many", "oracle_push_fifo", "oracle_gppr_round", "oracle_gppr_solve"):
+                "oracle_localgd_solve_many", "oracle_push_fifo", "oracle_gppr_round", "oracle_gppr_solve",
+                "oracle_series_round", "oracle_series_psi", "oracle_series_theta", "oracle_series_solve"):
         f, g = getattr(bad, sym), getattr(good, sym)
         f.argtypes, f.restype = g.argtypes, g.restype
     monkeypatch.setattr(oracle, "_lib", bad)
