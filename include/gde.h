@@ -12,6 +12,11 @@
  *   GDE_GPPR  generalised propagation, M = D^-b A D^(b-1), c_k = alpha (1-alpha)^k: the
  *             InstantGNN push of the appendix (b = opts.prop_beta; b = 1/2 is APPNP's
  *             D^-1/2 A D^-1/2 of Table 1, b = 0 is PPR)
+ *   GDE_SERIES a general series f = sum_{k<=N} c_k (A D^-1)^k e_s with c_k > 0 given in
+ *             opts.series_coef (e.g. IPR's theta^k/(theta^k+theta^10)^2 of Table 1), on the
+ *             heat kernel's layered system with layer ratio c_{t+1}/c_t and threshold scale
+ *             theta_t = 1/((N+1) c_0 psi_t), psi_t = sum_{j<=N-t} c_{t+j}/c_t, which bounds
+ *             0 <= f_N - c_0 x <= eps d_u; the result is c_0 x
  *
  * Each round t takes the active set S_t = { u : r_u != 0, |r_u| >= theta_t eps d_u }
  * (Definition 3.1; theta_t = 1 for PPR and Katz), moves r_S into x and scatters
@@ -50,7 +55,7 @@ extern "C" {
 typedef struct gde_graph gde_graph;
 typedef struct gde_session gde_session;
 
-typedef enum { GDE_PPR = 0, GDE_KATZ = 1, GDE_HK = 2, GDE_GPPR = 3 } gde_kind;
+typedef enum { GDE_PPR = 0, GDE_KATZ = 1, GDE_HK = 2, GDE_GPPR = 3, GDE_SERIES = 4 } gde_kind;
 
 typedef enum {
     GDE_OK = 0,
@@ -87,6 +92,8 @@ typedef struct {
     double hk_tol;           /* HK Taylor tail tolerance; 0 (default) means 1e-12 */
     void *cuda_stream;       /* borrowed cudaStream_t to run on; NULL = the graph's stream */
     double prop_beta;        /* GDE_GPPR: the exponent b in [0, 1] of M = D^-b A D^(b-1) */
+    const double *series_coef; /* GDE_SERIES: c_0..c_N (host array, copied; all > 0) */
+    int64_t series_terms;    /* GDE_SERIES: N + 1, in [1, 10^6] */
 } gde_solve_opts;
 
 /* Per-seed result statistics (Definition 3.1 and Theorem 3.5). */
@@ -148,7 +155,8 @@ gde_status gde_update_edges(gde_graph *g, const int32_t *src, const int32_t *dst
  * Approximate diffusion vectors for nseeds independent unit sources.
  *   kind, param  GDE_PPR with alpha in (0,1); GDE_KATZ with beta > 0 (LocalGD terminates
  *                when beta lambda_max(A) < 1); GDE_HK with tau > 0; GDE_GPPR with alpha in
- *                (0,1) and opts->prop_beta in [0,1] (plain and batched modes)
+ *                (0,1) and opts->prop_beta in [0,1] (plain and batched modes); GDE_SERIES
+ *                with opts->series_coef (param unused; plain mode)
  *   eps          tolerance > 0 of the active-set test
  *   seeds        nseeds source node ids in [0, n)
  *   out_x        topk == 0: nseeds x n values, row-major (double for GDE_FP64, float for

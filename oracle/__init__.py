@@ -275,6 +275,22 @@ def series(g, coef, eps: float, seed: int, mode: int = 0, max_rounds: int = 1_00
     return SolveResult(x, res.rounds, res.volume, res.pushes, res.resid_l1, res.x_l1, res.status, [])
 
 
+def series_round(g, coef, t: int, eps: float, x: np.ndarray, r: np.ndarray, r_next: np.ndarray,
+                 mode: int = 0) -> RoundResult:
+    """Round t of the series' layered system, in place (r is layer t, r_next layer t+1)."""
+    lib = _load()
+    c = np.ascontiguousarray(coef, dtype=np.float64)
+    N = c.shape[0] - 1
+    n = g.n
+    active = np.empty(max(n, 1), dtype=np.int32)
+    rho = np.empty(max(n, 1), dtype=np.float64)
+    st = _Round()
+    ratio = c[t + 1] / c[t] if t < N else 0.0
+    eps_theta = lib.oracle_series_theta(c, N, t, mode) * eps
+    cnt = lib.oracle_series_round(n, g.offsets, g.cols, ratio, int(t < N), eps_theta, x, r, r_next, active, rho, st)
+    return RoundResult(active[:cnt].copy(), rho[:cnt].copy(), st.n_active, st.vol_active, st.rS_l1)
+
+
 def series_theta(coef, t: int, mode: int = 0) -> float:
     c = np.ascontiguousarray(coef, dtype=np.float64)
     return float(_load().oracle_series_theta(c, c.shape[0] - 1, t, mode))

@@ -17,8 +17,8 @@ import numpy as np
 
 from . import _build
 
-PPR, KATZ, HK, GPPR = 0, 1, 2, 3
-KINDS = {"ppr": PPR, "katz": KATZ, "hk": HK, "gppr": GPPR}
+PPR, KATZ, HK, GPPR, SERIES = 0, 1, 2, 3, 4
+KINDS = {"ppr": PPR, "katz": KATZ, "hk": HK, "gppr": GPPR, "series": SERIES}
 FP64, FP32 = 0, 1
 DEVICE_PTRS = 0x1
 CHECK_SYMMETRIC = 0x2
@@ -47,7 +47,8 @@ class SolveOpts(ctypes.Structure):
                 ("topk", ctypes.c_int32), ("hk_threshold", ctypes.c_int32),
                 ("batched", ctypes.c_int32), ("flags", ctypes.c_uint32),
                 ("max_rounds", ctypes.c_int64), ("mem_budget_bytes", ctypes.c_int64),
-                ("hk_tol", ctypes.c_double), ("cuda_stream", ctypes.c_void_p), ("prop_beta", ctypes.c_double)]
+                ("hk_tol", ctypes.c_double), ("cuda_stream", ctypes.c_void_p), ("prop_beta", ctypes.c_double),
+                ("series_coef", ctypes.c_void_p), ("series_terms", ctypes.c_int64)]
 
 
 class Stats(ctypes.Structure):
@@ -205,7 +206,8 @@ def _current_stream():
 
 
 def make_opts(precision=FP64, topk=0, hk_threshold=0, batched=0, deterministic=0, flags=0,
-              max_rounds=0, mem_budget_bytes=0, hk_tol=0.0, stream=None, prop_beta=0.0) -> SolveOpts:
+              max_rounds=0, mem_budget_bytes=0, hk_tol=0.0, stream=None, prop_beta=0.0,
+              series_coef=None) -> SolveOpts:
     o = SolveOpts()
     load().gde_solve_opts_init(ctypes.byref(o))
     o.precision = FP32 if precision in (FP32, "fp32", "float32") else FP64
@@ -213,6 +215,11 @@ def make_opts(precision=FP64, topk=0, hk_threshold=0, batched=0, deterministic=0
     o.flags, o.max_rounds, o.mem_budget_bytes, o.hk_tol = flags, max_rounds, mem_budget_bytes, hk_tol
     o.cuda_stream = stream
     o.prop_beta = float(prop_beta)
+    if series_coef is not None:
+        c = np.ascontiguousarray(series_coef, dtype=np.float64)
+        o._series = c  # kept alive with the options
+        o.series_coef = c.ctypes.data
+        o.series_terms = int(c.shape[0])
     return o
 
 

@@ -109,10 +109,26 @@ double hk_theta(double tau, int64_t N, int64_t t, int mode) {
     return std::exp(tau) / ((double)(N + 1) * psi);
 }
 
+// layered engine: the heat kernel's ratio tau/(t+1) and theta_t, or the series' c_{t+1}/c_t and
+// 1/((N+1) c_0 psi_t) with psi_t = sum_{j<=N-t} c_{t+j}/c_t (mode 1: theta_t = 1)
+double layer_ratio(const SolveParams &p, int64_t t) {
+    if (p.kind != GDE_SERIES) return p.param / (double)(t + 1);
+    return t < p.hk_N ? p.series[(size_t)t + 1] / p.series[(size_t)t] : 0.0;
+}
+
+double layer_theta(const SolveParams &p, int64_t t) {
+    if (p.kind != GDE_SERIES) return hk_theta(p.param, p.hk_N, t, p.hk_mode);
+    if (p.hk_mode == 1) return 1.0;
+    if (t > p.hk_N) return 1.0;
+    double psi = 0.0;
+    for (int64_t j = 0; j <= p.hk_N - t; j++) psi += p.series[(size_t)(t + j)] / p.series[(size_t)t];
+    return 1.0 / ((double)(p.hk_N + 1) * p.series[0] * psi);
+}
+
 static SolveParams make_params(Graph &g, gde_kind kind, double param, double eps,
                                const gde_solve_opts &o) {
-    GDE_REQUIRE(kind == GDE_PPR || kind == GDE_KATZ || kind == GDE_HK || kind == GDE_GPPR, GDE_EINVAL,
-                "unknown kind");
+    GDE_REQUIRE(kind == GDE_PPR || kind == GDE_KATZ || kind == GDE_HK || kind == GDE_GPPR ||
+                    kind == GDE_SERIES, GDE_EINVAL, "unknown kind");
     GDE_REQUIRE(std::isfinite(param) && std::isfinite(eps), GDE_EINVAL, "param and eps must be finite");
     GDE_REQUIRE(eps > 0.0, GDE_EINVAL, "eps must be > 0");
     if (kind == GDE_PPR || kind == GDE_GPPR)
@@ -135,6 +151,14 @@ static SolveParams make_params(Graph &g, gde_kind kind, double param, double eps
     p.hk_tol = o.hk_tol > 0.0 ? o.hk_tol : 1e-12;
     p.max_rounds = o.max_rounds > 0 ? o.max_rounds : 1000000;
     p.hk_N = kind == GDE_HK ? hk_terms(param, p.hk_tol) : 0;
+    if (kind == GDE_SERIES) {
+        GDE_REQUIRE(o.series_coef != nullptr && o.series_terms >= 1 && o.series_terms <= 1000000, GDE_EINVAL,
+                    "a series needs 1 to 10^6 coefficients");
+        p.series.assign(o.series_coef, o.series_coef + o.series_terms);
+        for (double c : p.series)
+            GDE_REQUIRE(std::isfinite(c) && c > 0.0, GDE_EINVAL, "series coefficients must be finite and > 0");
+        p.hk_N = o.series_terms - 1;
+    }
     GDE_REQUIRE(o.deterministic == 0 || o.deterministic == 1, GDE_EINVAL, "bad deterministic flag");
     p.deterministic = o.deterministic;
     p.stream = o.cuda_stream ? (cudaStream_t)o.cuda_stream : g.stream;

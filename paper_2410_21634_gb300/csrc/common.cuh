@@ -136,7 +136,14 @@ struct SolveParams {
     int deterministic; // sort-based scatter (dense engine)
     cudaStream_t stream;
     double gbeta;      // GDE_GPPR: b of M = D^-b A D^(b-1) (the engines run PPR on y = S r, S = max(d,1)^b)
+    std::vector<double> series;  // GDE_SERIES: c_0..c_N (the layered system's coefficients)
 };
+
+// the heat kernel and the general series share the layered engine
+inline bool layered(gde_kind k) { return k == GDE_HK || k == GDE_SERIES; }
+// layer-t ratio c_{t+1}/c_t and threshold scale of the layered engine
+double layer_ratio(const SolveParams &p, int64_t t);
+double layer_theta(const SolveParams &p, int64_t t);
 
 // heat-kernel helpers (host)
 int64_t hk_terms(double tau, double tol);

@@ -586,7 +586,7 @@ void dense_work_destroy(DenseWork *w) {
 template <typename real>
 static void begin_impl(Graph &g, DenseWork *w, const SolveParams &p, int32_t seed) {
     const unsigned grid = grid_for(g.n);
-    if (p.kind == GDE_HK) {
+    if (layered(p.kind)) {
         ensure_layers(w);
         k_init_layers<real><<<grid, kThreads, 0, p.stream>>>(g.n, (real *)w->x, (real *)w->rl[0],
                                                              (real *)w->rl[1], seed);
@@ -606,7 +606,7 @@ static void begin_impl(Graph &g, DenseWork *w, const SolveParams &p, int32_t see
     w->kind = p.kind;
     w->t = 0;
     w->ncand = 1;
-    w->ntouched[0] = p.kind == GDE_HK ? 1 : 0;
+    w->ntouched[0] = layered(p.kind) ? 1 : 0;
     w->ntouched[1] = 0;
     w->last_active = 0;
     w->done = false;
@@ -638,8 +638,8 @@ static int64_t round_impl(Graph &g, DenseWork *w, const SolveParams &p, RoundInf
     else if (KIND == GDE_KATZ) { fa.cx = 1.0; fa.coef = p.param; }
     else {
         fa.cx = 1.0;
-        fa.coef = p.param / (double)(t + 1);
-        fa.eps_theta = hk_theta(p.param, p.hk_N, t, p.hk_mode) * p.eps;
+        fa.coef = layer_ratio(p, t);
+        fa.eps_theta = layer_theta(p, t) * p.eps;
         fa.clear_list = w->touched[nxt];
         fa.nclear = t > 0 ? w->ntouched[nxt] : 0;
         fa.rclear = (real *)w->rl[nxt];
@@ -690,7 +690,7 @@ static int64_t round_impl(Graph &g, DenseWork *w, const SolveParams &p, RoundInf
                 const uint32_t *pk = w->pkey[r2];
                 const real *pv = (const real *)w->pval[r2];
                 double etn = 0.0;
-                if (KIND == GDE_HK) etn = hk_theta(p.param, p.hk_N, t + 1, p.hk_mode) * p.eps;
+                if (KIND == GDE_HK) etn = layer_theta(p, t + 1) * p.eps;
                 k_det_apply<real, KIND><<<grid_for(np), kThreads, 0, p.stream>>>(
                     np, pk, pv, (RPair<real> *)w->rp, KIND == GDE_HK ? (real *)w->rl[nxt] : nullptr, g.deg, etn,
                     w->cand[nxt], KIND == GDE_HK ? w->touched[nxt] : nullptr, w->ctl, (unsigned)(g.n > 0 ? g.n : 1));
@@ -707,7 +707,7 @@ static int64_t round_impl(Graph &g, DenseWork *w, const SolveParams &p, RoundInf
         pa.rp = (RPair<real> *)w->rp;
         if (KIND == GDE_HK) {
             pa.rnext = (real *)w->rl[nxt];
-            pa.eps_theta_next = hk_theta(p.param, p.hk_N, t + 1, p.hk_mode) * p.eps;
+            pa.eps_theta_next = layer_theta(p, t + 1) * p.eps;
             pa.touched_out = w->touched[nxt];
         }
         pa.cand_out = w->cand[nxt];
@@ -748,7 +748,7 @@ static int64_t round_impl(Graph &g, DenseWork *w, const SolveParams &p, RoundInf
 
 int64_t dense_round(Graph &g, DenseWork *w, const SolveParams &p, RoundInfo *info) {
     if (info) *info = RoundInfo{0, 0, 0.0, 0.0, 0.0};
-    if (w->done || w->ncand == 0 || (p.kind == GDE_HK && w->t > p.hk_N)) {
+    if (w->done || w->ncand == 0 || (layered(p.kind) && w->t > p.hk_N)) {
         w->done = true;
         w->last_active = 0;
         return 0;
@@ -775,7 +775,7 @@ void dense_read(Graph &g, DenseWork *w, const SolveParams &p, void *x, void *r, 
     const cudaMemcpyKind k = device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (x && g.n) GDE_CUDA(cudaMemcpyAsync(x, w->x, bytes, k, p.stream));
     if (r && g.n) {
-        if (p.kind == GDE_HK) {
+        if (layered(p.kind)) {
             // after round t-1 the current layer is t
             const int cur = (int)(w->t & 1);
             GDE_CUDA(cudaMemcpyAsync(r, w->rl[cur], bytes, k, p.stream));
@@ -805,8 +805,8 @@ void dense_read(Graph &g, DenseWork *w, const SolveParams &p, void *x, void *r, 
 }
 
 void dense_output(Graph &g, DenseWork *w, const SolveParams &p, void *dst_dev) {
-    const bool apply = p.kind == GDE_HK;
-    const double scale = apply ? std::exp(-p.param) : 1.0;
+    const bool apply = layered(p.kind);
+    const double scale = p.kind == GDE_SERIES ? p.series[0] : (apply ? std::exp(-p.param) : 1.0);
     if (p.precision == GDE_FP64)
         k_scale_copy<double><<<grid_for(g.n), kThreads, 0, p.stream>>>(g.n, (const double *)w->x,
                                                                        (double *)dst_dev, scale, apply);
