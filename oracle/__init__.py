@@ -101,6 +101,8 @@ def _load():
             lib.oracle_series_solve.argtypes = [I64, i64p, i32p, f64p, I64, D, ctypes.c_int32, I, I64, f64p,
                                                 ctypes.POINTER(_Solve)]
             lib.oracle_series_solve.restype = I
+            lib.oracle_gd_solve.argtypes = [I64, i64p, i32p, I, D, D, ctypes.c_int32, I64, f64p]
+            lib.oracle_gd_solve.restype = I64
             _lib = lib
     return _lib
 
@@ -273,6 +275,17 @@ def series(g, coef, eps: float, seed: int, mode: int = 0, max_rounds: int = 1_00
     if st < 0:
         raise MemoryError("oracle_series_solve: allocation failed")
     return SolveResult(x, res.rounds, res.volume, res.pushes, res.resid_l1, res.x_l1, res.status, [])
+
+
+def global_gd(g, kind, param: float, eps: float, seed: int, max_iter: int = 1_000_000):
+    """Standard gradient descent (all nodes every iteration) until ||D^-1 r||_inf < eps.
+    Returns (x, iterations); its operation count is iterations * nnz."""
+    lib = _load()
+    x = np.zeros(g.n, dtype=np.float64)
+    it = lib.oracle_gd_solve(g.n, g.offsets, g.cols, _kind(kind), param, eps, int(seed), max_iter, x)
+    if it < 0:
+        raise MemoryError("oracle_gd_solve: allocation failed")
+    return x, int(it)
 
 
 def series_round(g, coef, t: int, eps: float, x: np.ndarray, r: np.ndarray, r_next: np.ndarray,

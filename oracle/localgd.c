@@ -269,6 +269,39 @@ int oracle_series_solve(int64_t n, const int64_t *off, const int32_t *col, const
     return res->status;
 }
 
+/*
+ * Standard (global) gradient descent, the counterpart of LocalGD in the comparison of
+ * Section 5 (Table 2, Figure 6): every iteration updates every node, x <- x + c r and
+ * r <- M r (PPR: c = alpha, M = (1-alpha) A D^-1; Katz: c = 1, M = beta A), which is the
+ * LocalGD round with the threshold at 0 (nodes with r_u = 0 contribute nothing).  It stops
+ * when max_u |r_u| / d_u < eps (||D^-1 r||_inf, degree-0 nodes read as degree 1), and its
+ * operation count is iterations x nnz (the standard algorithm touches every edge).
+ * Returns the number of iterations, or -1 on allocation failure.
+ */
+int64_t oracle_gd_solve(int64_t n, const int64_t *off, const int32_t *col, int kind, double param,
+                        double eps, int32_t seed, int64_t max_iter, double *x) {
+    double *r = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    int32_t *active = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    double *rho = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    if (!r || !active || !rho) { free(r); free(active); free(rho); return -1; }
+    memset(x, 0, sizeof(double) * (size_t)n);
+    r[seed] = 1.0;
+    int64_t it = 0;
+    for (; it < max_iter; it++) {
+        double worst = 0.0;
+        for (int64_t u = 0; u < n; u++) {
+            int64_t d = deg_of(off, u);
+            double q = fabs(r[u]) / (double)(d > 0 ? d : 1);
+            if (q > worst) worst = q;
+        }
+        if (worst < eps) break;
+        if (kind == ORC_PPR) oracle_ppr_round(n, off, col, param, 0.0, x, r, active, rho, NULL);
+        else oracle_katz_round(n, off, col, param, 0.0, x, r, active, rho, NULL);
+    }
+    free(r); free(active); free(rho);
+    return it;
+}
+
 /* ------------------------------------------------------- heat-kernel terms */
 
 /*

@@ -12,6 +12,7 @@ import subprocess
 import pytest
 
 import oracle
+import test_oracle_gd as gdpins
 import test_oracle_gppr as gpins
 import test_oracle_series as spins
 import test_oracle_pins as pins
@@ -50,6 +51,8 @@ MUTANTS = {
     "series_theta_without_psi": ("return 1.0 / ((double)(N + 1) * c[0] * oracle_series_psi(c, N, t));",
                                  "return 1.0 / ((double)(N + 1) * c[0]);"),
     "series_result_unscaled": ("for (int64_t u = 0; u < n; u++) x[u] = c[0] * x[u];", ""),
+    "gd_stop_without_degree": ("double q = fabs(r[u]) / (double)(d > 0 ? d : 1);", "double q = fabs(r[u]);"),
+    "gd_stop_inclusive": ("if (worst < eps) break;", "if (worst <= eps * 1.5) break;"),
 }
 
 PIN_CASES = [
@@ -69,6 +72,7 @@ PIN_CASES = [
     (gpins.test_round_invariant, dict(beta=0.25)),
     (spins.test_ipr_bound_against_dense, dict(gi=0, theta=1.3)),
     (spins.test_heat_kernel_coefficients_give_the_heat_kernel, {}),
+    (gdpins.test_iteration_count_closed_form, dict(k=8, alpha=0.2, eps=3e-5)),
 ]
 
 
@@ -93,7 +97,8 @@ def test_mutant_is_caught(tmp_path, monkeypatch, name):
     for sym in ("oracle_ppr_round", "oracle_katz_round", "oracle_hk_round", "oracle_hk_terms",
                 "oracle_hk_psi", "oracle_hk_theta", "oracle_localgd_solve",
                 "oracle_localgd_solve_many", "oracle_push_fifo", "oracle_gppr_round", "oracle_gppr_solve",
-                "oracle_series_round", "oracle_series_psi", "oracle_series_theta", "oracle_series_solve"):
+                "oracle_series_round", "oracle_series_psi", "oracle_series_theta", "oracle_series_solve",
+                "oracle_gd_solve"):
         f, g = getattr(bad, sym), getattr(good, sym)
         f.argtypes, f.restype = g.argtypes, g.restype
     monkeypatch.setattr(oracle, "_lib", bad)
