@@ -94,6 +94,12 @@ typedef struct {
     double prop_beta;        /* GDE_GPPR: the exponent b in [0, 1] of M = D^-b A D^(b-1) */
     const double *series_coef; /* GDE_SERIES: c_0..c_N (host array, copied; all > 0) */
     int64_t series_terms;    /* GDE_SERIES: N + 1, in [1, 10^6] */
+    int32_t global_gd;       /* 1: the standard (global) GD LocalGD is compared with in Section 5:
+                                every node every iteration (a full SpMV), until
+                                ||D^-1 r||_inf < eps; PPR and Katz on an undirected graph, dense
+                                output only; stats: rounds = iterations, active_volume =
+                                iterations x nnz (its operation count), resid/mass = -1 */
+    int32_t reserved_opts;
 } gde_solve_opts;
 
 /* Per-seed result statistics (Definition 3.1 and Theorem 3.5). */

@@ -185,6 +185,17 @@ void batch_work_destroy(BatchWork *w);
 // per-round log of the last batched solve: rows of {candidates, volume, r_S mass, ns}
 int64_t batch_round_log(Graph &g, double *out, int64_t cap);
 
+// round-to-nearest add and FP64 -> storage conversion for FP64 / FP32 state
+template <typename real> __device__ __forceinline__ real radd(real a, real b);
+template <> __device__ __forceinline__ double radd<double>(double a, double b) { return __dadd_rn(a, b); }
+template <> __device__ __forceinline__ float radd<float>(float a, float b) { return __fadd_rn(a, b); }
+template <typename real> __device__ __forceinline__ real from_f64(double v);
+template <> __device__ __forceinline__ double from_f64<double>(double v) { return v; }
+template <> __device__ __forceinline__ float from_f64<float>(double v) { return __double2float_rn(v); }
+
+// standard global GD (global_gd.cu): x_out n values of p.precision
+void global_gd_solve(Graph &g, const SolveParams &p, int32_t seed, void *x_out, bool x_dev, gde_stats *st);
+
 // C entry points: exceptions become status codes (the message is kept for gde_last_error)
 #define API_BEGIN try { ::gde::clear_error();
 #define API_END                                                                 \

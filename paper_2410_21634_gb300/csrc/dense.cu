@@ -93,16 +93,10 @@ struct DenseWork {
 
 // ------------------------------------------------------------ device helpers --
 
-template <typename real> __device__ __forceinline__ real radd(real a, real b);
-template <> __device__ __forceinline__ double radd<double>(double a, double b) { return __dadd_rn(a, b); }
-template <> __device__ __forceinline__ float radd<float>(float a, float b) { return __fadd_rn(a, b); }
 
 __device__ __forceinline__ double rabs(double v) { return fabs(v); }
 __device__ __forceinline__ float rabs(float v) { return fabsf(v); }
 
-template <typename real> __device__ __forceinline__ real from_f64(double v);
-template <> __device__ __forceinline__ double from_f64<double>(double v) { return v; }
-template <> __device__ __forceinline__ float from_f64<float>(double v) { return __double2float_rn(v); }
 
 // threshold fl(eps_theta * d) in the storage type; FP32 rounds up so that for a float r,
 // r >= thr32  <=>  (double) r >= thr64
