@@ -60,6 +60,7 @@ def parse():
                     help="hash accumulator budget (0: the library default)")
     ap.add_argument("--serve-seconds", type=float, default=2.0,
                     help="seconds of the serving stream measured after the batched bench (0: skip)")
+    ap.add_argument("--no-gd", action="store_true", help="skip the global GD vs LocalGD comparison")
     return ap.parse_args()
 
 
@@ -327,6 +328,41 @@ def run_serving(gde, seconds, slots, rounds_per_step, g=None, beta=None, budget_
     }
 
 
+def run_gd_compare(gde, g=None):
+    """Global GD vs LocalGD (Section 5: Table 2's operation ratio, Figure 6's running time as a
+    function of eps) on R-MAT scale 22, PPR alpha=0.1, plain FP64, one seed per solve, 8 seeds
+    at degree quantiles; operation counts are iterations x nnz (GD) and sum_t vol(S_t)."""
+    import numpy as np
+    import torch
+
+    import synth
+    if g is None:
+        g = synth.workload_graph("rmat22")
+    G = gde.Graph.from_synth(g)
+    seeds = synth.seeds_quantile(g, 8)
+    out = torch.zeros((1, g.n), dtype=torch.float64, device="cuda")
+    rows = []
+    for eps in (1e-4, 1e-5, 1e-6, 1e-7):
+        res = {}
+        for name, kw in (("localgd", {}), ("gd", {"global_gd": 1})):
+            gde.solve(G, "ppr", 0.1, eps, torch.tensor(seeds[:1], dtype=torch.int32, device="cuda"), out, **kw)
+            torch.cuda.synchronize()
+            ops = 0
+            t0 = time.perf_counter()
+            for s in seeds:
+                _, st = gde.solve(G, "ppr", 0.1, eps, torch.tensor([s], dtype=torch.int32, device="cuda"), out, **kw)
+                ops += st[0]["active_volume"]
+            torch.cuda.synchronize()
+            res[name] = ((time.perf_counter() - t0) / len(seeds), ops / len(seeds))
+        rows.append({"eps": eps, "localgd_ms_per_seed": res["localgd"][0] * 1e3, "gd_ms_per_seed": res["gd"][0] * 1e3,
+                     "time_ratio_gd_over_localgd": res["gd"][0] / res["localgd"][0],
+                     "localgd_ops_per_seed": res["localgd"][1], "gd_ops_per_seed": res["gd"][1],
+                     "op_ratio_gd_over_localgd": res["gd"][1] / max(res["localgd"][1], 1)})
+    G.close()
+    return {"workload": f"R-MAT scale 22 ({g.n} nodes, {g.nnz} CSR entries), PPR alpha=0.1, plain FP64, "
+                        f"8 seeds at degree quantiles, one gde_solve per seed", "rows": rows}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -476,6 +512,10 @@ def main():
     if args.serve_seconds > 0 and rank == 0 and ws == 1:
         G.close()  # release the batched pool first
         serving = run_serving(gde, args.serve_seconds, SERVE_SLOTS, SERVE_ROUNDS_PER_STEP)
+    gd_compare = None
+    if not args.no_gd and rank == 0 and ws == 1:
+        G.close()
+        gd_compare = run_gd_compare(gde)
     line = {
         "metric": METRIC, "value": value, "unit": "seeds/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
@@ -495,6 +535,7 @@ def main():
         "tuning": tuning_used,
         "autotuned": tuning is not None,
         "serving": serving,
+        "global_gd_vs_localgd": gd_compare,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
