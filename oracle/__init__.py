@@ -101,6 +101,9 @@ def _load():
             lib.oracle_series_solve.argtypes = [I64, i64p, i32p, f64p, I64, D, ctypes.c_int32, I, I64, f64p,
                                                 ctypes.POINTER(_Solve)]
             lib.oracle_series_solve.restype = I
+            lib.oracle_localch_solve.argtypes = [I64, i64p, i32p, D, D, ctypes.c_int32, I64, f64p, f64p,
+                                                 ctypes.POINTER(ctypes.c_int64)]
+            lib.oracle_localch_solve.restype = I64
             lib.oracle_gd_solve.argtypes = [I64, i64p, i32p, I, D, D, ctypes.c_int32, I64, f64p]
             lib.oracle_gd_solve.restype = I64
             _lib = lib
@@ -286,6 +289,18 @@ def global_gd(g, kind, param: float, eps: float, seed: int, max_iter: int = 1_00
     if it < 0:
         raise MemoryError("oracle_gd_solve: allocation failed")
     return x, int(it)
+
+
+def localch(g, alpha: float, eps: float, seed: int, max_rounds: int = 1_000_000):
+    """LocalCH for PPR from e_seed.  Returns (x, r, rounds, volume)."""
+    lib = _load()
+    x = np.zeros(g.n, dtype=np.float64)
+    r = np.zeros(g.n, dtype=np.float64)
+    vol = ctypes.c_int64()
+    t = lib.oracle_localch_solve(g.n, g.offsets, g.cols, alpha, eps, int(seed), max_rounds, x, r, ctypes.byref(vol))
+    if t < 0:
+        raise MemoryError("oracle_localch_solve: allocation failed")
+    return x, r, int(t), int(vol.value)
 
 
 def series_round(g, coef, t: int, eps: float, x: np.ndarray, r: np.ndarray, r_next: np.ndarray,

@@ -302,6 +302,80 @@ int64_t oracle_gd_solve(int64_t n, const int64_t *off, const int32_t *col, int k
     return it;
 }
 
+/*
+ * LocalCH for PPR (Section 3.3's local Chebyshev method; its PPR updates in the appendix on
+ * implementation details), in the unit-mass variables of this file (x estimates f, the
+ * paper's D^1/2 r is alpha r).  Chebyshev on Q = I - (1-alpha) D^-1/2 A D^-1/2 with
+ * eigenvalues in [alpha, 2 - alpha]: delta_1 = 1 - alpha, delta_{t+1} = 1/(2/(1-alpha) - delta_t).
+ * Round 0 pushes S_0 as LocalGD does (xh = alpha r).  Round t >= 1, for u in
+ * S_t = { u : r_u != 0, |r_u| >= eps d_u } (ascending id, snapshot rho = r before any scatter):
+ *   xh_u = (2 delta_{t+1}/(1-alpha)) alpha rho_u + delta_t delta_{t+1} (x^t - x^{t-1})_u,
+ *   x_u += xh_u,  r_u = rho_u - xh_u/alpha,  r_v += ((1-alpha) xh_u/alpha)/d_u for v in N(u),
+ * i.e. x += xh_S and r -= Q_w xh_S / alpha with Q_w = I - (1-alpha) A D^-1, which keeps
+ * Q_w x / alpha + r = e_s.  The momentum is restricted to S_t; it stops when S_t is empty.
+ * Returns the number of rounds (or -1 on allocation failure).
+ */
+int64_t oracle_localch_solve(int64_t n, const int64_t *off, const int32_t *col, double alpha, double eps,
+                             int32_t seed, int64_t max_rounds, double *x, double *r_out, int64_t *volume) {
+    double *r = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    double *dx = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));   /* x^t - x^{t-1} */
+    double *dxn = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    int32_t *act = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    double *rho = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double *xh = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    if (!r || !dx || !dxn || !act || !rho || !xh) {
+        free(r); free(dx); free(dxn); free(act); free(rho); free(xh);
+        return -1;
+    }
+    memset(x, 0, sizeof(double) * (size_t)n);
+    r[seed] = 1.0;
+    const double c = 1.0 - alpha;
+    double delta = c;  /* delta_1 */
+    int64_t t = 0, vol = 0;
+    for (; t < max_rounds; t++) {
+        int64_t k = 0;
+        for (int64_t u = 0; u < n; u++) {
+            double th = eps * (double)deg_of(off, u);
+            if (r[u] != 0.0 && fabs(r[u]) >= th) act[k++] = (int32_t)u;
+        }
+        if (k == 0) break;
+        double dnext = 0.0, g1 = 0.0, g2 = 0.0;
+        if (t > 0) {
+            dnext = 1.0 / (2.0 / c - delta);
+            g1 = (2.0 * dnext) / c;
+            g2 = delta * dnext;
+        }
+        for (int64_t i = 0; i < k; i++) {
+            int32_t u = act[i];
+            rho[i] = r[u];
+            if (t == 0) xh[i] = alpha * rho[i];
+            else xh[i] = g1 * (alpha * rho[i]) + g2 * dx[u];
+        }
+        for (int64_t i = 0; i < k; i++) {
+            int32_t u = act[i];
+            x[u] = x[u] + xh[i];
+            r[u] = rho[i] - xh[i] / alpha;
+            dxn[u] = xh[i];
+            vol += deg_of(off, u);
+        }
+        for (int64_t i = 0; i < k; i++) {
+            int32_t u = act[i];
+            int64_t d = deg_of(off, u);
+            if (d == 0) continue;
+            double w = (c * (xh[i] / alpha)) / (double)d;
+            for (int64_t e = off[u]; e < off[u + 1]; e++) r[col[e]] = r[col[e]] + w;
+        }
+        /* the next round's momentum is this round's update, zero off S_t */
+        double *tmp = dx; dx = dxn; dxn = tmp;
+        memset(dxn, 0, sizeof(double) * (size_t)n);
+        if (t > 0) delta = dnext;
+    }
+    if (r_out) memcpy(r_out, r, sizeof(double) * (size_t)n);
+    if (volume) *volume = vol;
+    free(r); free(dx); free(dxn); free(act); free(rho); free(xh);
+    return t;
+}
+
 /* ------------------------------------------------------- heat-kernel terms */
 
 /*

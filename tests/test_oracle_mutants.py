@@ -14,6 +14,7 @@ import pytest
 import oracle
 import test_oracle_gd as gdpins
 import test_oracle_gppr as gpins
+import test_oracle_localch as chpins
 import test_oracle_series as spins
 import test_oracle_pins as pins
 
@@ -53,6 +54,9 @@ MUTANTS = {
     "series_result_unscaled": ("for (int64_t u = 0; u < n; u++) x[u] = c[0] * x[u];", ""),
     "gd_stop_without_degree": ("double q = fabs(r[u]) / (double)(d > 0 ? d : 1);", "double q = fabs(r[u]);"),
     "gd_stop_inclusive": ("if (worst < eps) break;", "if (worst <= eps * 1.5) break;"),
+    "localch_delta_recursion_sign": ("dnext = 1.0 / (2.0 / c - delta);", "dnext = 1.0 / (2.0 / c + delta);"),
+    "localch_residual_not_rescaled": ("r[u] = rho[i] - xh[i] / alpha;", "r[u] = rho[i] - xh[i];"),
+    "localch_share_drops_keep": ("double w = (c * (xh[i] / alpha)) / (double)d;", "double w = (xh[i] / alpha) / (double)d;"),
 }
 
 PIN_CASES = [
@@ -73,6 +77,8 @@ PIN_CASES = [
     (spins.test_ipr_bound_against_dense, dict(gi=0, theta=1.3)),
     (spins.test_heat_kernel_coefficients_give_the_heat_kernel, {}),
     (gdpins.test_iteration_count_closed_form, dict(k=8, alpha=0.2, eps=3e-5)),
+    (chpins.test_invariant_and_bound, dict(gi=0, eps=1e-5)),
+    (chpins.test_fewer_rounds_than_localgd, dict(gi=2)),
 ]
 
 
@@ -98,7 +104,7 @@ def test_mutant_is_caught(tmp_path, monkeypatch, name):
                 "oracle_hk_psi", "oracle_hk_theta", "oracle_localgd_solve",
                 "oracle_localgd_solve_many", "oracle_push_fifo", "oracle_gppr_round", "oracle_gppr_solve",
                 "oracle_series_round", "oracle_series_psi", "oracle_series_theta", "oracle_series_solve",
-                "oracle_gd_solve"):
+                "oracle_gd_solve", "oracle_localch_solve"):
         f, g = getattr(bad, sym), getattr(good, sym)
         f.argtypes, f.restype = g.argtypes, g.restype
     monkeypatch.setattr(oracle, "_lib", bad)
