@@ -99,7 +99,11 @@ typedef struct {
                                 ||D^-1 r||_inf < eps; PPR and Katz on an undirected graph, dense
                                 output only; stats: rounds = iterations, active_volume =
                                 iterations x nnz (its operation count), resid/mass = -1 */
-    int32_t reserved_opts;
+    int32_t chebyshev;       /* 1: LocalCH, Section 3.3's local Chebyshev method with momentum
+                                on S_t, for PPR on an undirected graph (Chebyshev on
+                                I - (1-alpha) D^-1/2 A D^-1/2, eigenvalues in [alpha, 2-alpha]);
+                                dense output only; residuals change sign, so at exit
+                                |f - x| < eps d (two-sided); resid/mass = -1 */
 } gde_solve_opts;
 
 /* Per-seed result statistics (Definition 3.1 and Theorem 3.5). */

@@ -352,7 +352,15 @@ gde_status gde_solve(gde_graph *h, gde_kind kind, double param, double eps, cons
             ids_dev = dev ? out_ids : (int32_t *)stage(4 * (size_t)nseeds * k, "top-k ids");
             vals_dev = dev ? (float *)out_x : (float *)stage(4 * (size_t)nseeds * k, "top-k values");
         }
-        if (o.global_gd) {
+        if (o.chebyshev) {
+            GDE_REQUIRE(o.chebyshev == 1 && !o.global_gd, GDE_EINVAL, "bad chebyshev flag");
+            GDE_REQUIRE(k == 0 && !o.batched && !o.deterministic, GDE_EINVAL,
+                        "LocalCH writes dense x (no topk, batched or deterministic mode)");
+            for (int32_t i = 0; i < nseeds; i++)
+                localch_solve(g, p, hs[i], (char *)out_x + rsz * (size_t)g.n * i, dev, &st[(size_t)i]);
+            if (stats) memcpy(stats, st.data(), sizeof(gde_stats) * (size_t)nseeds);
+            for (const gde_stats &one : st) if (one.status != GDE_OK) worst = (gde_status)one.status;
+        } else if (o.global_gd) {
             // the standard algorithm LocalGD is compared with: dense output, one seed at a time
             GDE_REQUIRE(o.global_gd == 1, GDE_EINVAL, "bad global_gd flag");
             GDE_REQUIRE(k == 0 && !o.batched && !o.deterministic, GDE_EINVAL,

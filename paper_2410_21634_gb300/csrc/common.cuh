@@ -195,6 +195,8 @@ template <> __device__ __forceinline__ float from_f64<float>(double v) { return 
 
 // standard global GD (global_gd.cu): x_out n values of p.precision
 void global_gd_solve(Graph &g, const SolveParams &p, int32_t seed, void *x_out, bool x_dev, gde_stats *st);
+// LocalCH for PPR (localch.cu)
+void localch_solve(Graph &g, const SolveParams &p, int32_t seed, void *x_out, bool x_dev, gde_stats *st);
 
 // C entry points: exceptions become status codes (the message is kept for gde_last_error)
 #define API_BEGIN try { ::gde::clear_error();
