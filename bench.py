@@ -330,8 +330,9 @@ def run_serving(gde, seconds, slots, rounds_per_step, g=None, beta=None, budget_
 
 def run_gd_compare(gde, g=None):
     """Global GD vs LocalGD (Section 5: Table 2's operation ratio, Figure 6's running time as a
-    function of eps) on R-MAT scale 22, PPR alpha=0.1, plain FP64, one seed per solve, 8 seeds
-    at degree quantiles; operation counts are iterations x nnz (GD) and sum_t vol(S_t)."""
+    function of eps), with LocalCH beside them, on R-MAT scale 22, PPR alpha=0.1, plain FP64,
+    one seed per solve, 8 seeds at degree quantiles; operation counts are iterations x nnz
+    (GD) and sum_t vol(S_t) (LocalGD, LocalCH)."""
     import numpy as np
     import torch
 
@@ -344,7 +345,7 @@ def run_gd_compare(gde, g=None):
     rows = []
     for eps in (1e-4, 1e-5, 1e-6, 1e-7):
         res = {}
-        for name, kw in (("localgd", {}), ("gd", {"global_gd": 1})):
+        for name, kw in (("localgd", {}), ("gd", {"global_gd": 1}), ("localch", {"chebyshev": 1})):
             gde.solve(G, "ppr", 0.1, eps, torch.tensor(seeds[:1], dtype=torch.int32, device="cuda"), out, **kw)
             torch.cuda.synchronize()
             ops = 0
@@ -357,7 +358,8 @@ def run_gd_compare(gde, g=None):
         rows.append({"eps": eps, "localgd_ms_per_seed": res["localgd"][0] * 1e3, "gd_ms_per_seed": res["gd"][0] * 1e3,
                      "time_ratio_gd_over_localgd": res["gd"][0] / res["localgd"][0],
                      "localgd_ops_per_seed": res["localgd"][1], "gd_ops_per_seed": res["gd"][1],
-                     "op_ratio_gd_over_localgd": res["gd"][1] / max(res["localgd"][1], 1)})
+                     "op_ratio_gd_over_localgd": res["gd"][1] / max(res["localgd"][1], 1),
+                     "localch_ms_per_seed": res["localch"][0] * 1e3, "localch_ops_per_seed": res["localch"][1]})
     G.close()
     return {"workload": f"R-MAT scale 22 ({g.n} nodes, {g.nnz} CSR entries), PPR alpha=0.1, plain FP64, "
                         f"8 seeds at degree quantiles, one gde_solve per seed", "rows": rows}
