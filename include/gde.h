@@ -325,8 +325,9 @@ gde_status gde_session_end(gde_session *s);
  * f_PPR, or (I - beta A)^-1 e_s for Katz, within the eps bound of Corollary 3.6 on the graph
  * as of the step that emitted it; t_done - t_submit is the latency (for an update: from the
  * step that applied the edge batch).  status GDE_ENOMEM: the query's table filled up (its
- * slot is released).  submit / insert_edges / poll may be called from other threads while a
- * step runs; steps are serialised.  Errors as elsewhere (GDE_EINVAL for bad arguments; a step
+ * slot is released).  submit / insert_edges / poll / info may be called from other threads
+ * while a step runs; steps are serialised; destroy must not overlap any other call on the
+ * server.  Errors as elsewhere (GDE_EINVAL for bad arguments; a step
  * that fails leaves the server unusable and reports the failure).
  */
 typedef struct gde_server gde_server;

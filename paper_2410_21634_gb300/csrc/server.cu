@@ -207,7 +207,6 @@ gde_status gde_server_step(gde_server *S, int32_t *running, int32_t *queued) {
     }
 
     // 2. admission: free slots first, then the slots answered longest ago
-    std::vector<Query> admit;
     {
         std::lock_guard<std::mutex> lock(S->mu);
         if (!S->queue.empty()) {

@@ -210,3 +210,42 @@ def test_queries_in_flight_are_corrected(gde, g0):
         fresh = oracle.localgd(g1, "ppr", 0.15, EPS[1], int(s)).x
         check_answer(g1, first[i], fresh, EPS[1], slack=2.0)
     S.close()
+
+
+def test_submit_and_poll_from_another_thread(gde, g0):
+    """submit and poll run on a second host thread while the main thread steps (the C calls
+    release the interpreter lock, so they really overlap); every query is answered once."""
+    import threading
+    G = gde.Graph.from_synth(g0)
+    S = gde.Server(G, slots=8, rounds_per_step=2, eps=EPS)
+    qs = queries(g0, 60, seed=21)
+    got = {}
+    stop = threading.Event()
+
+    def producer():
+        for q in qs:
+            S.submit(*q)
+        stop.set()
+
+    def consumer():
+        while not (stop.is_set() and len(got) == len(qs)):
+            for r in S.poll():
+                got.setdefault(r["qid"], r)
+            if len(got) == len(qs):
+                break
+
+    tp = threading.Thread(target=producer)
+    tc = threading.Thread(target=consumer)
+    tp.start()
+    tc.start()
+    for _ in range(100000):
+        S.step()
+        inf = S.info()
+        if stop.is_set() and inf["running"] == 0 and inf["queued"] == 0 and len(got) == len(qs):
+            break
+    tp.join()
+    tc.join(timeout=30)
+    assert sorted(got) == list(range(len(qs)))
+    for q in qs[::7]:
+        check_answer(g0, got[q[0]], oracle_x(g0, q), EPS[q[3]])
+    S.close()
