@@ -61,6 +61,13 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=2.0,
                     help="seconds of the serving stream measured after the batched bench (0: skip)")
     ap.add_argument("--no-gd", action="store_true", help="skip the global GD vs LocalGD comparison")
+    ap.add_argument("--no-random-probe", action="store_true",
+                    help="skip the random-access calibration of device memory")
+    ap.add_argument("--random-probe", action="store_true",
+                    help="only run the random-access calibration and print its JSON line")
+    ap.add_argument("--probe-gb", type=float, default=16.0, help="buffer of the random-access calibration")
+    ap.add_argument("--probe-l2-fetch", type=int, default=0,
+                    help="L2 fetch-granularity limit during the calibration (0: leave it alone)")
     return ap.parse_args()
 
 
@@ -365,10 +372,37 @@ def run_gd_compare(gde, g=None):
                         f"8 seeds at degree quantiles, one gde_solve per seed", "rows": rows}
 
 
+PROBE_GRID = 152 * 8
+PROBE_ACCESSES = 1 << 30
+
+
+def random_access_ceiling(gde, dev, gb=16.0, l2_fetch=0):
+    """Random 32-byte sector rates of device memory (gde_probe_random_access) over a buffer far
+    above the L2 size: reads, read + FP32 atomic add (the scatter's insert-or-add), and atomics
+    alone, in G accesses/s."""
+    import torch
+    buf = torch.empty(int(gb * (1 << 30)), dtype=torch.uint8, device=dev)
+    out = {"buffer_gb": gb, "accesses_per_launch": PROBE_ACCESSES, "grid": PROBE_GRID,
+           "l2_fetch_bytes": l2_fetch or "default"}
+    for name in ("load", "load_atomic", "atomic"):
+        ms = gde.probe_random_access(buf, PROBE_ACCESSES, name, grid=PROBE_GRID, reps=3, l2_fetch_bytes=l2_fetch)
+        out[f"{name}_gaccess_per_s"] = PROBE_ACCESSES / (ms / 1e3) / 1e9
+    del buf
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.random_probe:
+        import torch
+        import paper_2410_21634_gb300 as gde
+        gde.load()
+        ra = random_access_ceiling(gde, torch.device("cuda", 0), args.probe_gb, args.probe_l2_fetch)
+        print(json.dumps({"random_access": ra}), flush=True)
+        return 0
     import numpy as np
     import torch
 
@@ -481,6 +515,12 @@ def main():
            "d2h_bytes_per_step": 8 * nseeds * TOPK,
            "note": "host seed ids in, host top-k ids+values out, through gde_solve with host pointers"}
 
+    # the random-access ceiling of this GPU's memory, beside the round kernel's insert rate
+    random_access = None
+    if not args.no_random_probe and rank == 0:
+        random_access = random_access_ceiling(gde, dev, args.probe_gb, args.probe_l2_fetch)
+        random_access["round_kernel_inserts_gaccess_per_s"] = prof["edges"] / launches / (k_ms / 1e3) / 1e9
+
     # the plain FP64 local GD, one seed per launch, on the same GPU and seed mix
     plain = None
     if not args.no_plain and rank == 0:
@@ -527,6 +567,7 @@ def main():
         "plain_fp64_one_seed_per_launch": plain,
         "speedup_vs_plain_fp64": (value / ws) / plain["value"] if plain else None,
         "roofline": roofline,
+        "random_access": random_access,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": gpu_launches,

@@ -275,6 +275,31 @@ gde_status gde_autotune(gde_graph *g, gde_kind kind, double param, double eps, c
 gde_status gde_topk_f32_noalloc(const float *x, int64_t n, int32_t k, int32_t *out_ids,
                                 float *out_vals, void *cuda_stream);
 
+/*
+ * Random-access calibration of device memory (no counterpart in the paper: a second
+ * roofline denominator for the batched scatter, whose cost is set by random 32-byte accesses,
+ * not by streaming bandwidth).  Launches one untimed and `reps` timed kernels in which each
+ * access picks a pseudo-random 32-byte sector of buf (splitmix64 of the access index, a
+ * different salt per launch) and, by mode:
+ *   0  reads the sector (two 16-byte loads that bypass L1, as the scatter's probe does),
+ *   1  reads it, then atomically adds 1.0f to an FP32 word in it (the insert-or-add pattern),
+ *   2  atomically adds 1.0f to its first FP32 value without reading it first.
+ *   buf        device pointer, 256-byte aligned; its contents are zeroed and then overwritten
+ *   bytes      size of buf (>= 64); the probe uses the largest power-of-two number of sectors
+ *              that fits, so pass a buffer well above the L2 size to measure device memory
+ *   nops       accesses per launch (>= 1)
+ *   grid       blocks of 256 threads, 1 .. 65535
+ *   reps       timed launches, 1 .. 1000
+ *   l2_fetch_bytes  0 leaves the context's L2 fetch-granularity limit
+ *              (cudaLimitMaxL2FetchGranularity) alone; 32, 64 or 128 set it for the probe, and
+ *              the previous value is restored before returning
+ *   cuda_stream  cudaStream_t to launch on (NULL: the legacy default stream)
+ *   ms_out     receives the mean duration of one timed launch (CUDA events on cuda_stream)
+ * Synchronises cuda_stream.  Other arguments out of range return GDE_EINVAL.
+ */
+gde_status gde_probe_random_access(void *buf, uint64_t bytes, int64_t nops, int32_t mode, int32_t grid,
+                                   int32_t reps, int32_t l2_fetch_bytes, void *cuda_stream, double *ms_out);
+
 /* Thread-local description of the last failure of this thread ("" if none). */
 const char *gde_last_error(void);
 

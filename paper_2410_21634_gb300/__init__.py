@@ -33,7 +33,8 @@ EXPORTED = ["gde_solve_opts_init", "gde_graph_create", "gde_graph_destroy", "gde
             "gde_topk_f32_noalloc", "gde_profile_rounds", "gde_set_tuning", "gde_get_tuning",
             "gde_autotune", "gde_update_edges", "gde_graph_csr", "gde_server_opts_init",
             "gde_server_clock", "gde_server_create", "gde_server_destroy", "gde_server_submit",
-            "gde_server_insert_edges", "gde_server_step", "gde_server_poll", "gde_server_info"]
+            "gde_server_insert_edges", "gde_server_step", "gde_server_poll", "gde_server_info",
+            "gde_probe_random_access"]
 
 
 class GdeError(RuntimeError):
@@ -149,6 +150,8 @@ def load(path: str | None = None):
     lib.gde_server_step.argtypes = [vp, ctypes.POINTER(I32), ctypes.POINTER(I32)]
     lib.gde_server_poll.argtypes = [vp, ctypes.POINTER(ServerResult), I32, ctypes.POINTER(I32)]
     lib.gde_server_info.argtypes = [vp, ctypes.POINTER(ServerInfo)]
+    lib.gde_probe_random_access.argtypes = [vp, ctypes.c_uint64, I64, I32, I32, I32, I32, vp, ctypes.POINTER(D)]
+    lib.gde_probe_random_access.restype = ctypes.c_int
     for name in ("gde_server_create", "gde_server_destroy", "gde_server_submit", "gde_server_insert_edges",
                  "gde_server_step", "gde_server_poll", "gde_server_info"):
         getattr(lib, name).restype = ctypes.c_int
@@ -366,6 +369,25 @@ def topk_noalloc(x, k: int, out_ids, out_vals, stream=None):
         stream = _current_stream()
     _check(load().gde_topk_f32_noalloc(_ptr(x)[0], int(x.numel()), int(k), _ptr(out_ids)[0],
                                        _ptr(out_vals)[0], stream))
+
+
+PROBE_MODES = {"load": 0, "load_atomic": 1, "atomic": 2}
+
+
+def probe_random_access(buf, nops: int, mode="load_atomic", grid: int = 152 * 8, reps: int = 3,
+                        l2_fetch_bytes: int = 0, stream=None) -> float:
+    """gde_probe_random_access: mean ms of one launch of `nops` random 32-byte sector accesses
+    over the contiguous CUDA tensor `buf` (its contents are overwritten).  mode: "load",
+    "load_atomic" or "atomic" (or 0, 1, 2)."""
+    if not _is_cuda_tensor(buf):
+        raise ValueError("probe_random_access takes a CUDA tensor")
+    m = PROBE_MODES.get(mode, mode)
+    if stream is None:
+        stream = _current_stream()
+    ms = ctypes.c_double()
+    _check(load().gde_probe_random_access(_ptr(buf)[0], int(buf.numel() * buf.element_size()), int(nops), int(m),
+                                          int(grid), int(reps), int(l2_fetch_bytes), stream, ctypes.byref(ms)))
+    return ms.value
 
 
 class Session:
