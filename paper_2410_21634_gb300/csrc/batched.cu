@@ -117,6 +117,7 @@ struct BatchWork {
     float *b_w[3] = {nullptr, nullptr, nullptr};
     int32_t *b_seed[3] = {nullptr, nullptr, nullptr};
     int64_t *hub_vstart = nullptr;
+    uint32_t *hub_cstart = nullptr;  // first hub push of each scatter chunk (kHubChunkTab entries)
     // per-candidate push record of the round (frontier phase -> placement phase)
     int64_t *tmp_beg = nullptr;
     int32_t *tmp_deg = nullptr;
@@ -264,6 +265,7 @@ struct BArgs {
     float *b_w[3];
     int32_t *b_seed[3];
     int64_t *hub_vstart;
+    uint32_t *hub_cstart;
     int64_t *tmp_beg;
     int32_t *tmp_deg;
     float *tmp_w;
@@ -299,6 +301,7 @@ __device__ __forceinline__ void bappend(unsigned *counter, uint32_t *list, uint3
 constexpr uint32_t kMaxProbe = 256;
 constexpr int kStage = 256;            // staged candidates per warp (shared memory)
 constexpr int kMedGrab = 4;            // medium-degree entries a warp takes per grab
+constexpr int64_t kHubChunkTab = (int64_t)1 << 22;  // chunks whose first push is tabulated
 
 __device__ __forceinline__ unsigned long long slot_word(uint32_t key, float w) {
     return ((unsigned long long)__float_as_uint(w) << 32) | (unsigned long long)key;
@@ -494,6 +497,18 @@ __device__ T block_scan(const T *in, T *out, int64_t n, T *s_warp) {
         carry += block_total;
     }
     return carry;
+}
+
+// Hub pushes are scattered in chunks of consecutive columns of their concatenated adjacency.
+// Small rounds get shorter chunks so every warp has a share (a lone warp walking a long
+// chunk would set the round's latency): the chunk of a round is ceil(VH / 2 warps), rounded
+// up to a warp multiple, within [64, tuned chunk].
+__device__ __forceinline__ int64_t hub_chunk(int64_t vh, int64_t nwarps, int64_t tuned) {
+    int64_t chunk = (vh + 2 * nwarps - 1) / (2 * nwarps);
+    chunk = (chunk + 31) & ~(int64_t)31;
+    if (chunk < 64) chunk = 64;
+    if (chunk > tuned) chunk = tuned;
+    return chunk;
 }
 
 #ifndef GDE_ROUNDS_MIN_BLOCKS
@@ -699,7 +714,14 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
                 if (pos < a.list_cap) {
                     __stcg(a.b_beg[2] + pos, beg); __stcg(a.b_deg[2] + pos, d);
                     __stcg(a.b_w[2] + pos, w); __stcg(a.b_seed[2] + pos, j);
-                    __stcg(a.hub_vstart + pos, (int64_t)(__ldcg(a.vol_off + j) + (old & kBHubVolMask)));
+                    const int64_t vs = (int64_t)(__ldcg(a.vol_off + j) + (old & kBHubVolMask));
+                    __stcg(a.hub_vstart + pos, vs);
+                    // the chunks that start inside this push's columns begin at this push (the
+                    // pushes' column ranges tile [0, VH), so each chunk start is written once)
+                    const int64_t vh = (int64_t)(__ldcg(&ctl->hub_packed) & kBHubVolMask);
+                    const int64_t chunk = hub_chunk(vh, nw, a.chunk);
+                    for (int64_t c = (vs + chunk - 1) / chunk; c * chunk < vs + d && c < kHubChunkTab; c++)
+                        __stcg(a.hub_cstart + c, (uint32_t)pos);
                 } else {
                     atomicOr(&ctl->overflow, 1u);
                 }
@@ -726,12 +748,7 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
             // hubs: merge-path chunks of the concatenated hub adjacency, one warp per chunk,
             // consecutive lanes on consecutive columns
             if (VH > 0) {
-                // small rounds get shorter chunks so every warp has a share (a lone warp walking
-                // a long chunk would set the round's latency)
-                int64_t chunk = (VH + 2 * nw - 1) / (2 * nw);
-                chunk = (chunk + 31) & ~(int64_t)31;
-                if (chunk < 64) chunk = 64;
-                if (chunk > a.chunk) chunk = a.chunk;
+                const int64_t chunk = hub_chunk(VH, nw, a.chunk);
                 const int64_t nchunks = (VH + chunk - 1) / chunk;
                 // warps beyond the chunk count would only find the work gone: they stay out,
                 // so small rounds do not queue every warp on the hand-out counter
@@ -747,12 +764,17 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
                     if (c >= nchunks) break;
                     const int64_t e0 = c * chunk;
                     const int64_t e1 = min(e0 + chunk, VH);
-                    int64_t lo = 0, hi = H;
-                    while (hi - lo > 1) {
-                        const int64_t mid = (lo + hi) >> 1;
-                        if (__ldcg(a.hub_vstart + mid) <= e0) lo = mid; else hi = mid;
+                    int64_t h;
+                    if (c < kHubChunkTab) {
+                        h = (int64_t)__ldcg(a.hub_cstart + c);
+                    } else {  // past the table: the last push starting at or before e0
+                        int64_t lo = 0, hi = H;
+                        while (hi - lo > 1) {
+                            const int64_t mid = (lo + hi) >> 1;
+                            if (__ldcg(a.hub_vstart + mid) <= e0) lo = mid; else hi = mid;
+                        }
+                        h = lo;
                     }
-                    int64_t h = lo;
                     int64_t hs = __ldcg(a.hub_vstart + h);
                     int64_t he = hs + __ldcg(a.b_deg[2] + h);
                     int64_t hb = __ldcg(a.b_beg[2] + h);
@@ -1120,7 +1142,7 @@ static void batch_free(BatchWork *w) {
     dfree(w->kr); dfree(w->xs); dfree(w->thr32); dfree(w->colp);
     for (int k = 0; k < 2; k++) dfree(w->cand[k]);
     for (int b = 0; b < 3; b++) { dfree(w->b_beg[b]); dfree(w->b_deg[b]); dfree(w->b_w[b]); dfree(w->b_seed[b]); }
-    dfree(w->hub_vstart); dfree(w->tmp_beg); dfree(w->tmp_deg); dfree(w->tmp_w); dfree(w->tmp_jb);
+    dfree(w->hub_vstart); dfree(w->hub_cstart); dfree(w->tmp_beg); dfree(w->tmp_deg); dfree(w->tmp_w); dfree(w->tmp_jb);
     dfree(w->seg_cnt); dfree(w->seg_off); dfree(w->seg_cur); dfree(w->seg_hvol); dfree(w->vol_off);
     dfree(w->seg_hcur); dfree(w->seeds); dfree(w->status); dfree(w->inserts); dfree(w->svol);
     dfree(w->spushes); dfree(w->slast); dfree(w->spush); dfree(w->sscat); dfree(w->smass0); dfree(w->xlist); dfree(w->xcnt); dfree(w->glob); dfree(w->log);
@@ -1162,6 +1184,7 @@ static BatchWork *batch_work_alloc(int64_t nseeds, int64_t cap, int64_t list_cap
             w->b_seed[b] = (int32_t *)dmalloc(4 * (size_t)list_cap, "bins");
         }
         w->hub_vstart = (int64_t *)dmalloc(8 * (size_t)list_cap, "hub offsets");
+        w->hub_cstart = (uint32_t *)dmalloc(4 * (size_t)kHubChunkTab, "hub chunk starts");
         w->tmp_beg = (int64_t *)dmalloc(8 * (size_t)list_cap, "push records");
         w->tmp_deg = (int32_t *)dmalloc(4 * (size_t)list_cap, "push records");
         w->tmp_w = (float *)dmalloc(4 * (size_t)list_cap, "push records");
@@ -1252,7 +1275,7 @@ static BArgs bargs_base(Graph &g, BatchWork *w, int64_t cap, int64_t list_cap, i
     a.cand[0] = w->cand[0]; a.cand[1] = w->cand[1];
     a.list_cap = (unsigned)list_cap;
     for (int b = 0; b < 3; b++) { a.b_beg[b] = w->b_beg[b]; a.b_deg[b] = w->b_deg[b]; a.b_w[b] = w->b_w[b]; a.b_seed[b] = w->b_seed[b]; }
-    a.hub_vstart = w->hub_vstart;
+    a.hub_vstart = w->hub_vstart; a.hub_cstart = w->hub_cstart;
     a.tmp_beg = w->tmp_beg; a.tmp_deg = w->tmp_deg; a.tmp_w = w->tmp_w; a.tmp_jb = w->tmp_jb;
     a.seg_cnt = w->seg_cnt; a.seg_off = w->seg_off; a.seg_cur = w->seg_cur;
     a.seg_hvol = w->seg_hvol; a.vol_off = w->vol_off; a.seg_hcur = w->seg_hcur;
