@@ -103,6 +103,7 @@ void graph_validate(Graph &g, bool check_symmetric, unsigned *bits_out);
 // Directed adjacencies added by one insertion batch (device arrays; sorted by (u, v)), with
 // the rows that gained them and those rows' degrees before the batch.
 struct EdgeBatch {
+    bool owned = true;           // false: the arrays live in the graph's update scratch
     int64_t m = 0;               // adjacencies added
     int32_t *u = nullptr, *v = nullptr;
     int64_t rows = 0;            // rows that gained adjacencies (ascending)
@@ -114,7 +115,8 @@ struct EdgeBatch {
 
 // Inserts the undirected edges (src[i], dst[i]) into g (both directions; self-loops and
 // present adjacencies skipped) and returns the number of directed adjacencies added.  If out
-// is not NULL it receives the batch (free with edge_batch_free).  Derived per-graph state
+// is not NULL it receives the batch (free with edge_batch_free; its arrays stay valid until the
+// next insertion into g).  Derived per-graph state
 // (packed columns, thresholds, cached workspaces) is dropped through graph_changed.
 int64_t graph_insert_edges(Graph &g, const int32_t *src, const int32_t *dst, int64_t m, bool dev_ptrs,
                            EdgeBatch *out);

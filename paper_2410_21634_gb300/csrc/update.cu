@@ -46,51 +46,85 @@ __global__ void k_row_bounds(int64_t rows, const int32_t *__restrict__ row, cons
     re[i] = off[row[i] + 1];
 }
 
-// noff[u] = off[u] + (adjacencies added to rows before u): a binary search over the changed
-// rows (ascending) gives their count, and row_start is the running total of their additions
+// first index in [lo, hi) of the ascending array a whose value is >= x (hi if none)
+__device__ __forceinline__ int64_t lower_index(const int32_t *__restrict__ a, int64_t lo, int64_t hi, int64_t x) {
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (a[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+constexpr int kOffsetTile = 1024;  // offsets per warp tile
+
+// noff[u] = off[u] + (adjacencies added to rows before u): the number of changed rows below
+// u (a search over the ascending changed rows) indexes row_start, the running total of
+// their additions.  A warp searches once for its tile of consecutive u, then each u only
+// within the changed rows that fall inside the tile.
 __global__ void k_new_offsets(int64_t n, const int64_t *__restrict__ off, const int32_t *__restrict__ row,
                               const int64_t *__restrict__ row_start, int64_t rows, int64_t added,
                               int64_t *__restrict__ noff) {
-    const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (u > n) return;
-    int64_t lo = 0, hi = rows;  // first changed row >= u
-    while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (row[mid] < u) lo = mid + 1; else hi = mid;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t t0 = warp * kOffsetTile; t0 <= n; t0 += nwarps * kOffsetTile) {
+        const int64_t t1 = t0 + kOffsetTile < n + 1 ? t0 + kOffsetTile : n + 1;
+        const int64_t first = lower_index(row, 0, rows, t0);        // changed rows below t0
+        const int64_t last = lower_index(row, first, rows, t1);     // changed rows below t1
+        for (int64_t u = t0 + lane; u < t1; u += 32) {
+            const int64_t lo = lower_index(row, first, last, u);    // changed rows below u
+            noff[u] = off[u] + (lo < rows ? row_start[lo] : added);
+        }
     }
-    noff[u] = off[u] + (lo < rows ? row_start[lo] : added);
 }
 
-// One thread per old CSR entry e: it moves by the additions to earlier rows, plus, inside a
-// changed row, by that row's added columns that sort before it.  Rows are sorted, so the
-// copy is a shift that changes only at the changed rows: a coalesced streaming pass.
+// first index in [lo, hi) of the ascending array a whose value exceeds x (hi if none)
+__device__ __forceinline__ int64_t upper_index(const int64_t *__restrict__ a, int64_t lo, int64_t hi, int64_t x) {
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (a[mid] <= x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+constexpr int kShiftTile = 1024;  // CSR entries per warp tile of the column shift
+
+// Each old CSR entry e moves by the additions to earlier rows, plus, inside a changed row, by
+// that row's added columns that sort before it.  Rows are sorted, so the copy is a shift that
+// changes only at the changed rows: a coalesced streaming pass.  A warp takes a tile of
+// consecutive entries and finds the changed rows that reach into it once (one search over
+// the row starts); each entry then only searches that short range, which is empty unless a
+// changed row starts inside the tile.
 __global__ void k_shift_columns(int64_t nnz, const int32_t *__restrict__ col, const int64_t *__restrict__ rb,
                                 const int64_t *__restrict__ re, const int64_t *__restrict__ row_start,
                                 const int32_t *__restrict__ row_cnt, int64_t rows,
                                 const int32_t *__restrict__ added, int32_t *__restrict__ ncol) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t c = col[e];
-        int64_t lo = 0, hi = rows;  // first changed row starting after e
-        while (lo < hi) {
-            const int64_t mid = (lo + hi) >> 1;
-            if (rb[mid] <= e) lo = mid + 1; else hi = mid;
-        }
-        const int64_t i = lo - 1;  // last changed row starting at or before e
-        int64_t shift = 0;
-        if (i >= 0) {
-            if (e < re[i]) {
-                const int32_t *a = added + row_start[i];
-                int32_t l = 0, h = row_cnt[i];  // added columns of that row below c
-                while (l < h) {
-                    const int32_t m = (l + h) >> 1;
-                    if (a[m] < c) l = m + 1; else h = m;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t t0 = warp * kShiftTile; t0 < nnz; t0 += nwarps * kShiftTile) {
+        const int64_t t1 = t0 + kShiftTile < nnz ? t0 + kShiftTile : nnz;
+        const int64_t first = upper_index(rb, 0, rows, t0);          // rows starting after t0
+        const int64_t last = upper_index(rb, first, rows, t1 - 1);   // rows starting after t1 - 1
+        for (int64_t e = t0 + lane; e < t1; e += 32) {
+            const int32_t c = col[e];
+            const int64_t i = upper_index(rb, first, last, e) - 1;  // last changed row starting at or before e
+            int64_t shift = 0;
+            if (i >= 0) {
+                if (e < re[i]) {
+                    const int32_t *a = added + row_start[i];
+                    int32_t l = 0, h = row_cnt[i];  // added columns of that row below c
+                    while (l < h) {
+                        const int32_t m = (l + h) >> 1;
+                        if (a[m] < c) l = m + 1; else h = m;
+                    }
+                    shift = row_start[i] + l;
+                } else {
+                    shift = row_start[i] + row_cnt[i];
                 }
-                shift = row_start[i] + l;
-            } else {
-                shift = row_start[i] + row_cnt[i];
             }
+            ncol[e + shift] = c;
         }
-        ncol[e + shift] = c;
     }
 }
 
@@ -130,27 +164,49 @@ static unsigned blocks_for(int64_t m) {
     return (unsigned)(b > 0 ? b : 1);
 }
 
-// Buffers of the CSR rebuild, kept between batches so a batch allocates nothing large: the
+// Buffers of the CSR rebuild, kept between batches so that a batch allocates nothing: the
 // spare column array (the merge writes there, then it swaps with the graph's), the spare
-// offsets, the per-row counts and starts, and the scan's scratch.
+// offsets, and an arena for the batch's own arrays (its adjacencies, the changed rows and
+// their bounds), which grows only when a larger batch arrives.
 struct UpdateScratch {
     int32_t *col = nullptr;
     int64_t col_cap = 0;         // entries of the spare column array
     int64_t graph_col_cap = 0;   // entries of the array the graph's columns sit in
     int64_t *off = nullptr;      // n + 1
     int *dmax = nullptr;
+    uint8_t *arena = nullptr;
+    size_t arena_cap = 0;
     int64_t n = -1;
 };
 
 void update_scratch_free(Graph &g) {
     UpdateScratch *u = g.upd;
     if (!u) return;
-    dfree(u->col); dfree(u->off); dfree(u->dmax);
+    dfree(u->col); dfree(u->off); dfree(u->dmax); dfree(u->arena);
     delete u;
     g.upd = nullptr;
 }
 
-static UpdateScratch *update_scratch(Graph &g, int64_t nnz_new) {
+// Hands out 256-byte aligned pieces of the arena in order.
+struct Carver {
+    uint8_t *base;
+    size_t cap, used = 0;
+    template <typename T> T *take(int64_t count) {
+        const size_t at = (used + 255) & ~(size_t)255;
+        const size_t bytes = sizeof(T) * (size_t)(count > 0 ? count : 1);
+        GDE_REQUIRE(at + bytes <= cap, GDE_ECUDA, "edge batch arena too small");
+        used = at + bytes;
+        return reinterpret_cast<T *>(base + at);
+    }
+};
+
+// bytes of the arena a batch of mp directed adjacencies may need (every per-adjacency and
+// per-row array at its largest, plus alignment)
+static size_t arena_bytes(int64_t mp) {
+    return (size_t)mp * (4 + 4 + 1 + 4 + 4 + 4 + 4 + 8 + 4 + 8 + 8) + 12 * 256;
+}
+
+static UpdateScratch *update_scratch_base(Graph &g) {
     if (g.upd && g.upd->n != g.n) update_scratch_free(g);
     if (!g.upd) {
         UpdateScratch *u = new UpdateScratch();
@@ -161,7 +217,25 @@ static UpdateScratch *update_scratch(Graph &g, int64_t nnz_new) {
         u->dmax = (int *)dmalloc(sizeof(int), "max degree");
         u->graph_col_cap = g.nnz;  // the graph's columns were allocated to size
     }
-    UpdateScratch *u = g.upd;
+    return g.upd;
+}
+
+static Carver batch_arena(Graph &g, int64_t mp) {
+    UpdateScratch *u = update_scratch_base(g);
+    const size_t need = arena_bytes(mp);
+    if (u->arena_cap < need) {
+        const size_t cap = need + need / 2;
+        dfree(u->arena);
+        u->arena = nullptr;
+        u->arena_cap = 0;
+        u->arena = (uint8_t *)dmalloc(cap, "edge batch");
+        u->arena_cap = cap;
+    }
+    return Carver{u->arena, u->arena_cap};
+}
+
+static UpdateScratch *update_scratch(Graph &g, int64_t nnz_new) {
+    UpdateScratch *u = update_scratch_base(g);
     if (u->col_cap < nnz_new) {
         // room for growth: later batches reuse the buffer
         const int64_t cap = nnz_new + nnz_new / 4 + 1024;
@@ -174,8 +248,31 @@ static UpdateScratch *update_scratch(Graph &g, int64_t nnz_new) {
 }
 
 void edge_batch_free(EdgeBatch &b) {
-    dfree(b.u); dfree(b.v); dfree(b.row); dfree(b.row_cnt); dfree(b.row_start); dfree(b.old_deg);
+    if (b.owned) {
+        dfree(b.u); dfree(b.v); dfree(b.row); dfree(b.row_cnt); dfree(b.row_start); dfree(b.old_deg);
+    }
     b = EdgeBatch{};
+}
+
+// Sorts keys below `bound` ascending: least-significant-digit radix sort, 12-bit digits, as
+// many passes as bound has digits (a batch's keys are few, so counting passes beat comparisons).
+static void radix_sort_keys(std::vector<uint64_t> &k, uint64_t bound) {
+    constexpr int kBits = 12;
+    constexpr size_t kBuckets = (size_t)1 << kBits;
+    std::vector<uint64_t> tmp(k.size());
+    std::vector<size_t> cnt(kBuckets);
+    for (int shift = 0; shift < 64 && (shift == 0 || (bound - 1) >> shift); shift += kBits) {
+        std::fill(cnt.begin(), cnt.end(), 0);
+        for (uint64_t x : k) cnt[(x >> shift) & (kBuckets - 1)]++;
+        size_t sum = 0;
+        for (size_t b = 0; b < kBuckets; b++) {
+            const size_t c = cnt[b];
+            cnt[b] = sum;
+            sum += c;
+        }
+        for (uint64_t x : k) tmp[cnt[(x >> shift) & (kBuckets - 1)]++] = x;
+        k.swap(tmp);
+    }
 }
 
 int64_t graph_insert_edges(Graph &g, const int32_t *src, const int32_t *dst, int64_t m, bool dev_ptrs,
@@ -190,35 +287,34 @@ int64_t graph_insert_edges(Graph &g, const int32_t *src, const int32_t *dst, int
         GDE_CUDA(cudaMemcpyAsync(hd.data(), dst, 4 * (size_t)m, k, s));
         GDE_CUDA(cudaStreamSynchronize(s));
     }
-    // both directions, no self-loops, sorted by (u, v), unique
-    std::vector<std::pair<int32_t, int32_t>> p;
+    // both directions, no self-loops, sorted by (u, v), unique: (u, v) packed as u n + v
+    const uint64_t n64 = (uint64_t)g.n;
+    std::vector<uint64_t> p;
     p.reserve(2 * (size_t)m);
     for (int64_t i = 0; i < m; i++) {
         const int32_t a = hs[(size_t)i], b = hd[(size_t)i];
         GDE_REQUIRE(a >= 0 && a < g.n && b >= 0 && b < g.n, GDE_EINVAL, "edge endpoint out of range");
         if (a == b) continue;
-        p.emplace_back(a, b);
-        p.emplace_back(b, a);
+        p.push_back((uint64_t)a * n64 + (uint64_t)b);
+        p.push_back((uint64_t)b * n64 + (uint64_t)a);
     }
-    std::sort(p.begin(), p.end());
+    radix_sort_keys(p, n64 * n64);
     p.erase(std::unique(p.begin(), p.end()), p.end());
     const int64_t mp = (int64_t)p.size();
     if (out) *out = EdgeBatch{};
     if (mp == 0) return 0;
 
-    std::vector<void *> tmp;
-    auto alloc = [&](size_t bytes, const char *what) {
-        void *q = dmalloc(bytes, what);
-        tmp.push_back(q);
-        return q;
-    };
     int64_t added = 0;
-    try {
+    {
+        Carver arena = batch_arena(g, mp);
         std::vector<int32_t> pu((size_t)mp), pv((size_t)mp);
-        for (int64_t i = 0; i < mp; i++) { pu[(size_t)i] = p[(size_t)i].first; pv[(size_t)i] = p[(size_t)i].second; }
-        int32_t *du = (int32_t *)alloc(4 * (size_t)mp, "edge batch");
-        int32_t *dv = (int32_t *)alloc(4 * (size_t)mp, "edge batch");
-        uint8_t *keep = (uint8_t *)alloc((size_t)mp, "edge batch");
+        for (int64_t i = 0; i < mp; i++) {
+            pu[(size_t)i] = (int32_t)(p[(size_t)i] / n64);
+            pv[(size_t)i] = (int32_t)(p[(size_t)i] % n64);
+        }
+        int32_t *du = arena.take<int32_t>(mp);
+        int32_t *dv = arena.take<int32_t>(mp);
+        uint8_t *keep = arena.take<uint8_t>(mp);
         GDE_CUDA(cudaMemcpyAsync(du, pu.data(), 4 * (size_t)mp, cudaMemcpyHostToDevice, s));
         GDE_CUDA(cudaMemcpyAsync(dv, pv.data(), 4 * (size_t)mp, cudaMemcpyHostToDevice, s));
         k_mark_new<<<blocks_for(mp), kThreads, 0, s>>>(mp, du, dv, g.off, g.col, keep);
@@ -243,22 +339,20 @@ int64_t graph_insert_edges(Graph &g, const int32_t *src, const int32_t *dst, int
             nv.push_back(pv[(size_t)i]);
         }
         added = (int64_t)nu.size();
-        if (added == 0) {
-            for (void *q : tmp) dfree(q);
-            return 0;
-        }
+        if (added == 0) return 0;
         GDE_REQUIRE(g.nnz + added < ((int64_t)1 << 40), GDE_EINVAL, "graph too large");
         const int64_t nrows = (int64_t)rows.size();
         EdgeBatch eb{};
+        eb.owned = false;
         eb.m = added;
         eb.rows = nrows;
-        eb.u = (int32_t *)dmalloc(4 * (size_t)added, "edge batch");
-        eb.v = (int32_t *)dmalloc(4 * (size_t)added, "edge batch");
-        eb.row = (int32_t *)dmalloc(4 * (size_t)nrows, "edge batch");
-        eb.row_cnt = (int32_t *)dmalloc(4 * (size_t)nrows, "edge batch");
-        eb.row_start = (int64_t *)dmalloc(8 * (size_t)nrows, "edge batch");
-        eb.old_deg = (int32_t *)dmalloc(4 * (size_t)nrows, "edge batch");
-        try {
+        eb.u = arena.take<int32_t>(added);
+        eb.v = arena.take<int32_t>(added);
+        eb.row = arena.take<int32_t>(nrows);
+        eb.row_cnt = arena.take<int32_t>(nrows);
+        eb.row_start = arena.take<int64_t>(nrows);
+        eb.old_deg = arena.take<int32_t>(nrows);
+        {
             GDE_CUDA(cudaMemcpyAsync(eb.u, nu.data(), 4 * (size_t)added, cudaMemcpyHostToDevice, s));
             GDE_CUDA(cudaMemcpyAsync(eb.v, nv.data(), 4 * (size_t)added, cudaMemcpyHostToDevice, s));
             GDE_CUDA(cudaMemcpyAsync(eb.row, rows.data(), 4 * (size_t)nrows, cudaMemcpyHostToDevice, s));
@@ -269,14 +363,14 @@ int64_t graph_insert_edges(Graph &g, const int32_t *src, const int32_t *dst, int
             UpdateScratch *u = update_scratch(g, g.nnz + added);
             int64_t *noff = u->off;
             int *dmax = u->dmax;
-            int64_t *rb = (int64_t *)alloc(8 * (size_t)nrows, "row bounds");
-            int64_t *re = (int64_t *)alloc(8 * (size_t)nrows, "row bounds");
+            int64_t *rb = arena.take<int64_t>(nrows);
+            int64_t *re = arena.take<int64_t>(nrows);
             GDE_CUDA(cudaMemcpyAsync(dmax, &g.max_degree, sizeof(int), cudaMemcpyHostToDevice, s));
             k_gather_deg<<<blocks_for(nrows), kThreads, 0, s>>>(nrows, eb.row, g.deg, eb.old_deg);
             GDE_CUDA(cudaGetLastError());
             k_row_bounds<<<blocks_for(nrows), kThreads, 0, s>>>(nrows, eb.row, g.off, rb, re);
             GDE_CUDA(cudaGetLastError());
-            k_new_offsets<<<blocks_for(n + 1), kThreads, 0, s>>>(n, g.off, eb.row, eb.row_start, nrows, added, noff);
+            k_new_offsets<<<kSMs * 16, kThreads, 0, s>>>(n, g.off, eb.row, eb.row_start, nrows, added, noff);
             GDE_CUDA(cudaGetLastError());
             int32_t *ncol = u->col;
             if (g.nnz > 0) {
@@ -299,16 +393,9 @@ int64_t graph_insert_edges(Graph &g, const int32_t *src, const int32_t *dst, int
             std::swap(u->col_cap, u->graph_col_cap);
             g.nnz += added;
             g.max_degree = hmax;
-        } catch (...) {
-            edge_batch_free(eb);
-            throw;
         }
-        if (out) *out = eb; else edge_batch_free(eb);
-    } catch (...) {
-        for (void *q : tmp) dfree(q);
-        throw;
+        if (out) *out = eb;
     }
-    for (void *q : tmp) dfree(q);
     graph_changed(g);
     return added;
 }
