@@ -248,7 +248,7 @@ def run_serving(gde, seconds, slots, rounds_per_step, g=None, beta=None, budget_
         g = synth.workload_graph(SERVE["graph"])
     if beta is None:
         beta = 0.5 / synth.lambda_max(g)[0]
-    G = gde.Graph.from_synth(g)
+    G = gde.Graph.from_synth(g, check_symmetric=True)  # lets insertions keep the packed columns
     if budget_gb <= 0:
         # tables of 2n slots (the most a query can touch is n nodes, so no table passes half load)
         # (slot indices are 32-bit: slots * cap <= 2^32)

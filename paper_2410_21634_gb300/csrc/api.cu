@@ -263,6 +263,7 @@ gde_status gde_graph_destroy(gde_graph *h) {
     dfree(g.off);
     dfree(g.col);
     dfree(g.deg);
+    dfree(g.colp);
     if (g.stream) cudaStreamDestroy(g.stream);
     delete h;
     return GDE_OK;

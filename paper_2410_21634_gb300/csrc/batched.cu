@@ -105,12 +105,6 @@ struct BatchWork {
     float *thr32 = nullptr;
     int64_t thr_n = 0;
     double thr_eps = -1.0;
-    // columns with the neighbour's degree code in the bits above the node id (see pack_code)
-    uint32_t *colp = nullptr;
-    int colp_idbits = 0;     // 0: no packing (n too large), then thr32 is read for every edge
-    int colp_exact = 0;
-    int64_t colp_cap = 0;    // entries the packed array can hold
-    bool colp_valid = false; // packed from the current CSR
     uint32_t *cand[2] = {nullptr, nullptr};
     int64_t *b_beg[3] = {nullptr, nullptr, nullptr};
     int32_t *b_deg[3] = {nullptr, nullptr, nullptr};
@@ -335,17 +329,6 @@ __device__ __forceinline__ void stage_flush(uint32_t *buf, unsigned *n, bool for
     __syncwarp();
     if (lane == 0) *(volatile unsigned *)n = 0;
     __syncwarp();
-}
-
-// Degree code of a neighbour, stored above its id in the packed column array: the exact
-// degree when d < code_exact, else code_exact + floor(log2 d).  It brackets the neighbour's
-// threshold fl(eps d) (rounded up to float) without reading the per-node threshold array:
-// exact for small degrees, within [eps 2^k, eps (2^(k+1)-1)] for the log classes.
-__host__ __device__ __forceinline__ uint32_t degree_code(int32_t d, int code_exact) {
-    if (d < code_exact) return (uint32_t)d;
-    uint32_t k = 0;
-    while ((2ll << k) <= (long long)d) k++;
-    return (uint32_t)code_exact + k;
 }
 
 struct ThrBounds {
@@ -1139,7 +1122,7 @@ void topk_dense_f32(const float *x_dev, int64_t n, int k, int32_t *ids_dev, floa
 
 static void batch_free(BatchWork *w) {
     if (!w) return;
-    dfree(w->kr); dfree(w->xs); dfree(w->thr32); dfree(w->colp);
+    dfree(w->kr); dfree(w->xs); dfree(w->thr32);
     for (int k = 0; k < 2; k++) dfree(w->cand[k]);
     for (int b = 0; b < 3; b++) { dfree(w->b_beg[b]); dfree(w->b_deg[b]); dfree(w->b_w[b]); dfree(w->b_seed[b]); }
     dfree(w->hub_vstart); dfree(w->hub_cstart); dfree(w->tmp_beg); dfree(w->tmp_deg); dfree(w->tmp_w); dfree(w->tmp_jb);
@@ -1159,7 +1142,6 @@ void graph_changed(Graph &g) {
         g.dense[k] = nullptr;
     }
     if (BatchWork *w = g.batch) {
-        w->colp_valid = false;  // repacked (into the same buffer if it fits) on next use
         w->thr_eps = -1.0;
         w->thr_n = -1;
     }
@@ -1233,25 +1215,26 @@ static BatchWork *batch_work_get(Graph &g, int64_t nseeds, int64_t cap, int64_t 
 }
 
 // packed columns (id | degree code) of the current CSR, built on first use
-static void ensure_colp(Graph &g, BatchWork *w, cudaStream_t s) {
-    if ((w->colp && w->colp_valid) || g.nnz <= 0) return;
+void ensure_colp(Graph &g, cudaStream_t s) {
+    if ((g.colp && g.colp_valid) || g.nnz <= 0) return;
     int idbits = 1;
     while (((int64_t)1 << idbits) < g.n) idbits++;
     const int spare = 32 - idbits;
     if (spare < 5) return;
     const int codes = spare >= 8 ? 256 : (1 << spare);
-    if (w->colp_cap < g.nnz) {
-        dfree(w->colp);
-        w->colp = nullptr;
+    if (g.colp_cap < g.nnz) {
         // after edge insertions the graph has grown: leave room for more
-        const int64_t cap = w->colp_cap ? g.nnz + g.nnz / 4 + 1024 : g.nnz;
-        w->colp = (uint32_t *)dmalloc(4 * (size_t)cap, "packed columns");
-        w->colp_cap = cap;
+        const int64_t cap = g.colp_cap ? g.nnz + g.nnz / 4 + 1024 : g.nnz;
+        dfree(g.colp);
+        g.colp = nullptr;
+        g.colp_cap = 0;
+        g.colp = (uint32_t *)dmalloc(4 * (size_t)cap, "packed columns");
+        g.colp_cap = cap;
     }
-    w->colp_valid = true;
-    w->colp_idbits = idbits;
-    w->colp_exact = codes - 32;
-    k_pack_columns<<<kSMs * 8, kThreads, 0, s>>>(g.nnz, g.col, g.deg, w->colp, idbits, w->colp_exact);
+    g.colp_valid = true;
+    g.colp_idbits = idbits;
+    g.colp_exact = codes - 32;
+    k_pack_columns<<<kSMs * 8, kThreads, 0, s>>>(g.nnz, g.col, g.deg, g.colp, idbits, g.colp_exact);
     GDE_CUDA(cudaGetLastError());
     g.prof.launched();
 }
@@ -1261,9 +1244,9 @@ static BArgs bargs_base(Graph &g, BatchWork *w, int64_t cap, int64_t list_cap, i
                         uint32_t key_tag, uint32_t key_idmask) {
     BArgs a{};
     a.off = g.off; a.col = g.col; a.thr32 = w->thr32; a.kr = w->kr; a.xs = w->xs;
-    a.colp = w->colp_valid ? w->colp : nullptr; a.idbits = w->colp_idbits;
-    a.idmask = a.colp ? (uint32_t)(((uint64_t)1 << w->colp_idbits) - 1) : 0xFFFFFFFFu;
-    a.code_exact = w->colp_exact;
+    a.colp = g.colp_valid ? g.colp : nullptr; a.idbits = g.colp_idbits;
+    a.idmask = a.colp ? (uint32_t)(((uint64_t)1 << g.colp_idbits) - 1) : 0xFFFFFFFFu;
+    a.code_exact = g.colp_exact;
     a.thr_stride = g.n;
     a.key_idmask = key_idmask; a.key_tag = key_tag;
     a.xlist = w->xlist; a.xcnt = w->xcnt; a.xcap = (unsigned)w->xcap;
@@ -1352,7 +1335,7 @@ static void batch_solve_once(Graph &g, const SolveParams &p, const int32_t *seed
     cudaStream_t s = p.stream;
     GDE_CUDA(cudaMemcpyAsync(w->seeds, seeds_dev, 4 * (size_t)nseeds, cudaMemcpyDeviceToDevice, s));
     const int64_t pool = (int64_t)nseeds * cap;
-    ensure_colp(g, w, s);
+    ensure_colp(g, s);
     // epoch tags: keys carry the solve's tag above their id bits, so the previous solve's keys
     // read as empty; the tables are only reset on first use, after a failure, or when the tag
     // wraps (x is zeroed by the previous top-k through the x-lists)
@@ -1882,12 +1865,11 @@ void serve_pool_destroy(ServePool *P) {
 int64_t serve_pool_cap(const ServePool *P) { return P->cap; }
 
 void serve_pool_graph_changed(ServePool *P) {
-    P->w->colp_valid = false;
     P->thr_n = -1;
 }
 
 static void serve_ensure_graph_state(Graph &g, ServePool *P) {
-    ensure_colp(g, P->w, P->s);
+    ensure_colp(g, P->s);
     if (P->thr_n != g.n) {
         for (int c = 0; c < P->ncls; c++) {
             k_batch_thr<<<kSMs * 8, kThreads, 0, P->s>>>(g.n, g.deg, P->thr + (int64_t)c * g.n, P->eps[c]);

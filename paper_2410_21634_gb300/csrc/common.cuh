@@ -89,6 +89,15 @@ struct Graph {
     struct DenseWork *dense[2] = {nullptr, nullptr};     // cached single-seed workspace per precision
     struct BatchWork *batch = nullptr;                   // cached batched workspace
     struct UpdateScratch *upd = nullptr;                 // edge-insertion buffers, kept between batches
+    // The batched engines' edge stream: each column with its neighbour's degree code in the
+    // bits above the node id (degree_code).  Built on first use (ensure_colp); an insertion
+    // batch keeps it current when the graph was verified symmetric, else drops it.
+    uint32_t *colp = nullptr;
+    int64_t colp_cap = 0;      // entries the packed array can hold
+    int colp_idbits = 0;       // 0: no packing (n too large), thresholds are read per edge
+    int colp_exact = 0;
+    bool colp_valid = false;   // packed from the current CSR
+    bool symmetric = false;    // A = A^T verified at creation (insertions keep it)
     Profiler prof;
     Bins bins;                 // launch shape used by later solves
 };
@@ -99,6 +108,20 @@ enum : unsigned {
 };
 
 void graph_validate(Graph &g, bool check_symmetric, unsigned *bits_out);
+
+// Degree code of a neighbour, stored above its id in the packed column array: the exact
+// degree when d < code_exact, else code_exact + floor(log2 d).  It brackets the neighbour's
+// threshold fl(eps d) (rounded up to float) without reading the per-node threshold array:
+// exact for small degrees, within [eps 2^k, eps (2^(k+1)-1)] for the log classes.
+__host__ __device__ __forceinline__ uint32_t degree_code(int32_t d, int code_exact) {
+    if (d < code_exact) return (uint32_t)d;
+    uint32_t k = 0;
+    while ((2ll << k) <= (long long)d) k++;
+    return (uint32_t)code_exact + k;
+}
+
+// Builds g.colp from the CSR if it is not current (no-op when n leaves too few spare bits).
+void ensure_colp(Graph &g, cudaStream_t s);
 
 // Directed adjacencies added by one insertion batch (device arrays; sorted by (u, v)), with
 // the rows that gained them and those rows' degrees before the batch.

@@ -90,6 +90,7 @@ void graph_validate(Graph &g, bool check_symmetric, unsigned *bits_out) {
         }
         *bits_out = h[0];
         g.max_degree = (int32_t)h[1];
+        g.symmetric = h[0] == 0 && check_symmetric;
     } catch (...) {
         dfree(d_bits);
         throw;

@@ -95,10 +95,13 @@ constexpr int kShiftTile = 1024;  // CSR entries per warp tile of the column shi
 // consecutive entries and finds the changed rows that reach into it once (one search over
 // the row starts); each entry then only searches that short range, which is empty unless a
 // changed row starts inside the tile.
+// The packed columns (when colp is not NULL) move with their columns: a column's packed word
+// only changes if its node's degree changed, which k_fix_codes handles.
 __global__ void k_shift_columns(int64_t nnz, const int32_t *__restrict__ col, const int64_t *__restrict__ rb,
                                 const int64_t *__restrict__ re, const int64_t *__restrict__ row_start,
                                 const int32_t *__restrict__ row_cnt, int64_t rows,
-                                const int32_t *__restrict__ added, int32_t *__restrict__ ncol) {
+                                const int32_t *__restrict__ added, int32_t *__restrict__ ncol,
+                                const uint32_t *__restrict__ colp, uint32_t *__restrict__ ncolp) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -124,6 +127,7 @@ __global__ void k_shift_columns(int64_t nnz, const int32_t *__restrict__ col, co
                 }
             }
             ncol[e + shift] = c;
+            if (ncolp) ncolp[e + shift] = colp[e];
         }
     }
 }
@@ -138,11 +142,14 @@ __global__ void k_deg_add(int64_t rows, const int32_t *__restrict__ row, const i
 }
 
 // one thread per added adjacency i (row u, column v; the list is sorted by (u, v)): its place
-// is noff[u] + (its index among u's added) + (old columns of u below v)
+// is noff[u] + (its index among u's added) + (old columns of u below v).  With packed columns
+// (ncolp not NULL) it also writes v's packed word from v's degree after the batch.
 __global__ void k_place_added(int64_t m, const int32_t *__restrict__ u, const int32_t *__restrict__ v,
                               const int64_t *__restrict__ off, const int32_t *__restrict__ col,
                               const int64_t *__restrict__ noff, const int32_t *__restrict__ row,
-                              const int64_t *__restrict__ row_start, int64_t rows, int32_t *__restrict__ ncol) {
+                              const int64_t *__restrict__ row_start, int64_t rows, int32_t *__restrict__ ncol,
+                              const int32_t *__restrict__ deg, uint32_t *__restrict__ ncolp, int idbits,
+                              int code_exact) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= m) return;
     const int32_t a = u[i], c = v[i];
@@ -156,7 +163,39 @@ __global__ void k_place_added(int64_t m, const int32_t *__restrict__ u, const in
         const int64_t mid = (lo + hi) >> 1;
         if (col[mid] < c) lo = mid + 1; else hi = mid;
     }
-    ncol[noff[a] + (i - row_start[rl]) + (lo - off[a])] = c;
+    const int64_t at = noff[a] + (i - row_start[rl]) + (lo - off[a]);
+    ncol[at] = c;
+    if (ncolp) ncolp[at] = (uint32_t)c | (degree_code(deg[c], code_exact) << idbits);
+}
+
+// Packed words of the columns that name a node whose degree code the batch changed.  The
+// graph is symmetric, so the entries naming c sit in the rows of c's neighbours: one warp per
+// changed row c walks c's new row and, for each neighbour u, finds c in u's new row (binary
+// search) and rewrites its word.  An entry that is not found (the graph was not symmetric
+// after all) sets *missing, and the caller then drops the packed array.
+__global__ void k_fix_codes(int64_t rows, const int32_t *__restrict__ row, const int32_t *__restrict__ old_deg,
+                            const int32_t *__restrict__ deg, const int64_t *__restrict__ noff,
+                            const int32_t *__restrict__ ncol, uint32_t *__restrict__ ncolp, int idbits,
+                            int code_exact, unsigned *missing) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = warp; i < rows; i += nwarps) {
+        const int32_t c = row[i];
+        const uint32_t code = degree_code(deg[c], code_exact);
+        if (code == degree_code(old_deg[i], code_exact)) continue;
+        const uint32_t word = (uint32_t)c | (code << idbits);
+        for (int64_t k = noff[c] + lane; k < noff[c + 1]; k += 32) {
+            const int32_t u = ncol[k];
+            int64_t lo = noff[u], hi = noff[u + 1];
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (ncol[mid] < c) lo = mid + 1; else hi = mid;
+            }
+            if (lo < noff[u + 1] && ncol[lo] == c) ncolp[lo] = word;
+            else atomicOr(missing, 1u);
+        }
+    }
 }
 
 static unsigned blocks_for(int64_t m) {
@@ -173,7 +212,9 @@ struct UpdateScratch {
     int64_t col_cap = 0;         // entries of the spare column array
     int64_t graph_col_cap = 0;   // entries of the array the graph's columns sit in
     int64_t *off = nullptr;      // n + 1
-    int *dmax = nullptr;
+    int *dmax = nullptr;         // [0]: max degree, [1]: packed-word entries not found
+    uint32_t *colp = nullptr;    // spare packed columns
+    int64_t colp_cap = 0;
     uint8_t *arena = nullptr;
     size_t arena_cap = 0;
     int64_t n = -1;
@@ -182,7 +223,7 @@ struct UpdateScratch {
 void update_scratch_free(Graph &g) {
     UpdateScratch *u = g.upd;
     if (!u) return;
-    dfree(u->col); dfree(u->off); dfree(u->dmax); dfree(u->arena);
+    dfree(u->col); dfree(u->off); dfree(u->dmax); dfree(u->colp); dfree(u->arena);
     delete u;
     g.upd = nullptr;
 }
@@ -214,7 +255,7 @@ static UpdateScratch *update_scratch_base(Graph &g) {
         const int64_t n = g.n;
         u->n = n;
         u->off = (int64_t *)dmalloc(8 * (size_t)(n + 1), "CSR offsets");
-        u->dmax = (int *)dmalloc(sizeof(int), "max degree");
+        u->dmax = (int *)dmalloc(2 * sizeof(int), "max degree");
         u->graph_col_cap = g.nnz;  // the graph's columns were allocated to size
     }
     return g.upd;
@@ -358,14 +399,31 @@ int64_t graph_insert_edges(Graph &g, const int32_t *src, const int32_t *dst, int
             GDE_CUDA(cudaMemcpyAsync(eb.row, rows.data(), 4 * (size_t)nrows, cudaMemcpyHostToDevice, s));
             GDE_CUDA(cudaMemcpyAsync(eb.row_cnt, rcnt.data(), 4 * (size_t)nrows, cudaMemcpyHostToDevice, s));
             GDE_CUDA(cudaMemcpyAsync(eb.row_start, rstart.data(), 8 * (size_t)nrows, cudaMemcpyHostToDevice, s));
-            // new offsets, shifted columns, placed additions, then the degrees of the changed rows
+            // new offsets, shifted columns, the degrees of the changed rows, placed additions;
+            // on a symmetric graph the packed columns are carried along and then patched where
+            // a degree code changed, else they are dropped and rebuilt on next use
             const int64_t n = g.n;
             UpdateScratch *u = update_scratch(g, g.nnz + added);
             int64_t *noff = u->off;
             int *dmax = u->dmax;
+            const bool keep_colp = g.colp_valid && g.colp && g.symmetric && g.colp_idbits > 0;
+            uint32_t *ncolp = nullptr;
+            if (keep_colp) {
+                const int64_t need = g.nnz + added;
+                if (u->colp_cap < need) {
+                    const int64_t cap = need + need / 4 + 1024;
+                    dfree(u->colp);
+                    u->colp = nullptr;
+                    u->colp_cap = 0;
+                    u->colp = (uint32_t *)dmalloc(4 * (size_t)cap, "packed columns");
+                    u->colp_cap = cap;
+                }
+                ncolp = u->colp;
+            }
             int64_t *rb = arena.take<int64_t>(nrows);
             int64_t *re = arena.take<int64_t>(nrows);
-            GDE_CUDA(cudaMemcpyAsync(dmax, &g.max_degree, sizeof(int), cudaMemcpyHostToDevice, s));
+            const int hstate[2] = {g.max_degree, 0};
+            GDE_CUDA(cudaMemcpyAsync(dmax, hstate, sizeof(hstate), cudaMemcpyHostToDevice, s));
             k_gather_deg<<<blocks_for(nrows), kThreads, 0, s>>>(nrows, eb.row, g.deg, eb.old_deg);
             GDE_CUDA(cudaGetLastError());
             k_row_bounds<<<blocks_for(nrows), kThreads, 0, s>>>(nrows, eb.row, g.off, rb, re);
@@ -373,26 +431,43 @@ int64_t graph_insert_edges(Graph &g, const int32_t *src, const int32_t *dst, int
             k_new_offsets<<<kSMs * 16, kThreads, 0, s>>>(n, g.off, eb.row, eb.row_start, nrows, added, noff);
             GDE_CUDA(cudaGetLastError());
             int32_t *ncol = u->col;
+            int launched = 5;
             if (g.nnz > 0) {
                 k_shift_columns<<<kSMs * 16, kThreads, 0, s>>>(g.nnz, g.col, rb, re, eb.row_start, eb.row_cnt, nrows,
-                                                               eb.v, ncol);
+                                                               eb.v, ncol, keep_colp ? g.colp : nullptr, ncolp);
                 GDE_CUDA(cudaGetLastError());
+                launched++;
             }
-            k_place_added<<<blocks_for(added), kThreads, 0, s>>>(added, eb.u, eb.v, g.off, g.col, noff, eb.row,
-                                                                 eb.row_start, nrows, ncol);
-            GDE_CUDA(cudaGetLastError());
             k_deg_add<<<blocks_for(nrows), kThreads, 0, s>>>(nrows, eb.row, eb.row_cnt, g.deg, dmax);
             GDE_CUDA(cudaGetLastError());
-            int hmax = 0;
-            GDE_CUDA(cudaMemcpyAsync(&hmax, dmax, sizeof(int), cudaMemcpyDeviceToHost, s));
+            k_place_added<<<blocks_for(added), kThreads, 0, s>>>(added, eb.u, eb.v, g.off, g.col, noff, eb.row,
+                                                                 eb.row_start, nrows, ncol, g.deg, ncolp,
+                                                                 g.colp_idbits, g.colp_exact);
+            GDE_CUDA(cudaGetLastError());
+            if (keep_colp) {
+                k_fix_codes<<<blocks_for(32 * nrows), kThreads, 0, s>>>(nrows, eb.row, eb.old_deg, g.deg, noff, ncol,
+                                                                       ncolp, g.colp_idbits, g.colp_exact,
+                                                                       reinterpret_cast<unsigned *>(dmax + 1));
+                GDE_CUDA(cudaGetLastError());
+                launched++;
+            }
+            int hres[2] = {0, 0};
+            GDE_CUDA(cudaMemcpyAsync(hres, dmax, sizeof(hres), cudaMemcpyDeviceToHost, s));
             GDE_CUDA(cudaStreamSynchronize(s));
-            g.prof.launched(6);
+            g.prof.launched(launched);
             // the rebuilt arrays become the graph's, the old ones the next batch's spares
             std::swap(g.col, u->col);
             std::swap(g.off, u->off);
             std::swap(u->col_cap, u->graph_col_cap);
+            if (keep_colp && hres[1] == 0) {
+                std::swap(g.colp, u->colp);
+                std::swap(g.colp_cap, u->colp_cap);
+            } else {
+                g.colp_valid = false;
+                if (keep_colp) g.symmetric = false;  // an entry had no mirror
+            }
             g.nnz += added;
-            g.max_degree = hmax;
+            g.max_degree = hres[0];
         }
         if (out) *out = eb;
     }

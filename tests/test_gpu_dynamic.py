@@ -113,3 +113,48 @@ def test_batched_solve_after_insertions(gde):
         valid = ids[i] >= 0
         band = 1e-6 * d[ids[i][valid]] + 1e-5 * xs[n][ids[i][valid]] + 1e-12
         assert np.all(np.abs(vals[i][valid] - xs[n][ids[i][valid]]) <= band)
+
+
+def test_packed_columns_carried_through_insertions(gde):
+    """On a graph verified symmetric the batched engine's packed columns (node id plus the
+    neighbour's degree code) are shifted with the CSR and patched where a degree code changed,
+    instead of being rebuilt.  Several batches, one of which pushes the largest hub past the
+    next power of two (a change of its logarithmic code), must give the same answers as a
+    graph built from scratch on the union, and as the oracle."""
+    g = synth.rmat(16, 16, seed=21)
+    G = gde.Graph.from_synth(g, check_symmetric=True)
+    seeds = synth.seeds_mixed(g, 16, 16, seed=3)
+    k = 64
+    ids = np.zeros((32, k), np.int32)
+    vals = np.zeros((32, k), np.float32)
+    gde.solve(G, "ppr", 0.1, 1e-6, seeds, vals, ids, precision="fp32", topk=k, batched=1)  # packs
+    d = g.degrees()
+    hub = int(np.argmax(d))
+    need = (1 << int(np.floor(np.log2(d[hub])) + 1)) - int(d[hub]) + 3
+    nbr = set(g.cols[g.offsets[hub]:g.offsets[hub + 1]].tolist()) | {hub}
+    fresh = np.array([v for v in range(g.n) if v not in nbr][:need], dtype=np.int32)
+    batches = [synth.random_edges(g.n, 5000, seed=40 + b) for b in range(3)]
+    batches.insert(1, (np.full(fresh.shape, hub, np.int32), fresh))
+    g1 = g
+    for src, dst in batches:
+        G.update_edges(src, dst)
+        g1 = synth.with_edges(g1, src, dst)
+        st, _ = gde.solve(G, "ppr", 0.1, 1e-6, seeds, vals, ids, precision="fp32", topk=k, batched=1)
+        assert st == gde.OK
+    assert g1.degrees()[hub] >= 1 << (int(np.floor(np.log2(d[hub]))) + 1)
+    F = gde.Graph.from_synth(g1)
+    ids2 = np.zeros_like(ids)
+    vals2 = np.zeros_like(vals)
+    st, _ = gde.solve(F, "ppr", 0.1, 1e-6, seeds, vals2, ids2, precision="fp32", topk=k, batched=1)
+    assert st == gde.OK
+    d1 = g1.degrees().astype(float)
+    xs, _ = oracle.localgd_many(g1, "ppr", 0.1, 1e-6, seeds)
+    for i in range(32):
+        for I, V in ((ids[i], vals[i]), (ids2[i], vals2[i])):
+            valid = I >= 0
+            band = 1e-6 * d1[I[valid]] + 1e-5 * xs[i][I[valid]] + 1e-12
+            assert np.all(np.abs(V[valid] - xs[i][I[valid]]) <= band)
+        # the two graphs agree on the leaders up to FP32 summation order
+        assert np.allclose(vals[i], vals2[i], rtol=1e-4, atol=1e-6 * d1.max())
+    F.close()
+    G.close()
