@@ -84,11 +84,16 @@ typedef struct {
                                 psi_t = sum_{j<=N-t} tau^j t!/(t+j)!, which bounds
                                 0 <= f_N - e^-tau x <= eps d_u; 1: theta_t = 1 */
     int32_t batched;         /* 1: all seeds in one persistent launch with per-seed hash
-                                accumulators (PPR/Katz, FP32, topk > 0); 0 (default): one
-                                seed at a time with dense x and r */
+                                accumulators (FP32, topk > 0; every kind: the layered ones,
+                                HK and SERIES, keep one key tag per layer and x in a
+                                second table; layers + 1 must fit in the key tags: at
+                                most 253 layers up to 2^24 nodes, 2^(32-ceil(log2 n)) - 3
+                                else GDE_EINVAL); 0 (default): one seed
+                                at a time with dense x and r */
     uint32_t flags;          /* GDE_DEVICE_PTRS: seeds and outputs are device pointers */
     int64_t max_rounds;      /* round cap; 0 (default) means 1,000,000 */
-    int64_t mem_budget_bytes;/* batched: bytes for the hash accumulators; 0 = automatic */
+    int64_t mem_budget_bytes;/* batched: bytes for the hash accumulators (12 per slot, 18 for
+                                the layered kinds); 0 = automatic (16 GiB) */
     double hk_tol;           /* HK Taylor tail tolerance; 0 (default) means 1e-12 */
     void *cuda_stream;       /* borrowed cudaStream_t to run on; NULL = the graph's stream */
     double prop_beta;        /* GDE_GPPR: the exponent b in [0, 1] of M = D^-b A D^(b-1) */
@@ -165,13 +170,13 @@ gde_status gde_update_edges(gde_graph *g, const int32_t *src, const int32_t *dst
  * Approximate diffusion vectors for nseeds independent unit sources.
  *   kind, param  GDE_PPR with alpha in (0,1); GDE_KATZ with beta > 0 (LocalGD terminates
  *                when beta lambda_max(A) < 1); GDE_HK with tau > 0; GDE_GPPR with alpha in
- *                (0,1) and opts->prop_beta in [0,1] (plain and batched modes); GDE_SERIES
- *                with opts->series_coef (param unused; plain mode)
+ *                (0,1) and opts->prop_beta in [0,1]; GDE_SERIES with opts->series_coef
+ *                (param unused); every kind in both the plain and the batched mode
  *   eps          tolerance > 0 of the active-set test
  *   seeds        nseeds source node ids in [0, n)
  *   out_x        topk == 0: nseeds x n values, row-major (double for GDE_FP64, float for
  *                GDE_FP32): x for PPR, x = (I - beta A)^-1 e_s approximately for Katz,
- *                e^-tau x (the heat-kernel vector) for HK.
+ *                e^-tau x (the heat-kernel vector) for HK, c_0 x for SERIES.
  *                topk == k: nseeds x k values, largest first (ties: lower id first), and
  *                out_ids receives the matching nseeds x k node ids (-1 pads seeds whose
  *                support is smaller than k)

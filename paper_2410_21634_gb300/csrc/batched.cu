@@ -143,6 +143,14 @@ struct BatchWork {
     int64_t last_rounds = 0;
     bool need_clear = true;   // reset every table before the next solve
     bool list_overflowed = false;  // the last solve ran out of candidate / bin list entries
+    // layered solves: per-seed x tables (keys in the low half of xkr, values in xxs) and the
+    // per-round threshold and share coefficients
+    unsigned long long *xkr = nullptr;
+    float *xxs = nullptr;
+    int64_t xt_seeds = 0, xt_cap = 0;
+    int xt_log2cap = 0;
+    double *layer_eps = nullptr, *layer_coef = nullptr;
+    int64_t layer_cap = 0;
     uint32_t epoch = 0;       // tag of the current solve's keys
 };
 
@@ -279,6 +287,17 @@ struct BArgs {
     int64_t max_rounds;
     int32_t t1, t2, chunk;
     int32_t schedule;   // 0: all bins handed out in order; 1: hubs in order, others strided; 2: all strided
+    // layered kinds (heat kernel, general series): round t reads layer t and writes layer t+1;
+    // the keys of layer t carry key_tag + t * tag_step, so a layer's keys read as free slots
+    // once the next layer is written, and x lives in a separate per-seed table keyed by node
+    const double *layer_eps;   // theta_t eps of round t, t = 0 .. nlayers
+    const double *layer_coef;  // share coefficient of round t (divided by d_u)
+    int64_t nlayers;           // rounds t < nlayers scatter; round nlayers only adds to x
+    uint32_t tag_step;
+    unsigned long long *xkr;   // x table: keys in the low half of each word
+    float *xxs;                // x table: values
+    int xlog2cap;
+    uint32_t xmask;
 };
 
 __device__ __forceinline__ void bappend(unsigned *counter, uint32_t *list, uint32_t v, unsigned cap,
@@ -355,10 +374,14 @@ __device__ __forceinline__ ThrBounds thr_bounds(const BArgs &a, double eps, uint
 // class's threshold array only when the bracket cannot decide.  (With nonnegative residuals
 // this happens once per node and round; when corrections made some residuals negative a node
 // can cross more than once, and the frontier phase drops the repeats.)
+template <bool LAYERED>
 __device__ __forceinline__ bool crossed(const float *thr32c, int32_t v, ThrBounds tb, float old, float nv) {
     const float ao = fabsf(old), an = fabsf(nv);
     if (an < tb.lo || ao >= tb.hi) return false;
-    const float thr = tb.lo == tb.hi ? tb.lo : thr32c[v];
+    // a layered round has no per-node array (its threshold changes every round): crossing the
+    // bracket's lower bound lists the node; residuals only grow there, so a node that reaches
+    // its threshold is listed exactly once, and the frontier's exact test drops the others
+    const float thr = tb.lo == tb.hi ? tb.lo : (LAYERED ? tb.lo : thr32c[v]);
     return ao < thr && an >= thr;
 }
 
@@ -368,8 +391,15 @@ struct SlotMeta {
     uint32_t tag;
 };
 
-__device__ __forceinline__ SlotMeta slot_meta(const BArgs &a, int32_t j) {
-    if (!a.sparam) return SlotMeta{0, a.key_tag};
+// the keys round t's scatter writes: the next layer's (layered kinds) or the solve's
+template <bool LAYERED>
+__device__ __forceinline__ uint32_t write_tag(const BArgs &a, int64_t t) {
+    return LAYERED ? a.key_tag + (uint32_t)(t + 1) * a.tag_step : a.key_tag;
+}
+
+template <bool LAYERED>
+__device__ __forceinline__ SlotMeta slot_meta(const BArgs &a, int32_t j, int64_t t) {
+    if (!a.sparam) return SlotMeta{0, write_tag<LAYERED>(a, t)};
     const SlotParam &sp = a.sparam[j];
     return SlotMeta{sp.cls, sp.tag};
 }
@@ -379,13 +409,14 @@ __device__ __forceinline__ SlotMeta slot_meta(const BArgs &a, int32_t j) {
 // examined in order, so the first empty slot ends the search (keys are never removed).  A
 // residual that crosses its threshold from below (exactly once: contributions are positive)
 // is staged as a candidate of the next round.  Returns 1 if v was a new key.
+template <bool LAYERED>
 __device__ __forceinline__ unsigned bscatter(const BArgs &a, int32_t j, SlotMeta m, uint32_t packed, float w,
                                              uint32_t *sbuf, unsigned *sn) {
     const uint64_t base = (uint64_t)j << a.log2cap;
     const int32_t v = (int32_t)(packed & a.idmask);
     const uint32_t kcur = (uint32_t)v | m.tag;
     const int cls = m.cls;
-    const float *thr32c = a.thr32 + (int64_t)cls * a.thr_stride;
+    const float *thr32c = LAYERED ? nullptr : a.thr32 + (int64_t)cls * a.thr_stride;
     ThrBounds tb;
     if (a.colp) {
         const float2 br = s_thr_br[cls][packed >> a.idbits];
@@ -414,14 +445,14 @@ __device__ __forceinline__ unsigned bscatter(const BArgs &a, int32_t j, SlotMeta
                 const uint32_t key = (uint32_t)(wk & 0xFFFFFFFFull);
                 if (key == kcur) {
                     const float old = atomicAdd(r_of(a.kr, slot), w);
-                    if (crossed(thr32c, v, tb, old, __fadd_rn(old, w))) stage_push(sbuf, sn, (uint32_t)slot);
+                    if (crossed<LAYERED>(thr32c, v, tb, old, __fadd_rn(old, w))) stage_push(sbuf, sn, (uint32_t)slot);
                     return 0;
                 }
                 // another node of this solve: next slot (empty and stale-tag slots are free)
                 if (key != kEmpty && (key & ~a.key_idmask) == m.tag) break;
                 const unsigned long long prev = atomicCAS(a.kr + slot, wk, slot_word(kcur, w));
                 if (prev == wk) {
-                    if (crossed(thr32c, v, tb, 0.0f, w)) stage_push(sbuf, sn, (uint32_t)slot);
+                    if (crossed<LAYERED>(thr32c, v, tb, 0.0f, w)) stage_push(sbuf, sn, (uint32_t)slot);
                     return 1;
                 }
                 wk = prev;  // lost the race: look at what was written into this slot
@@ -431,6 +462,38 @@ __device__ __forceinline__ unsigned bscatter(const BArgs &a, int32_t j, SlotMeta
     }
     atomicExch(a.status + j, kSeedOverflow);  // table full
     return 0;
+}
+
+// Insert-or-add inc at node v of seed j's x table (layered solves; keys carry the solve's
+// tag, slots are probed linearly).  A node is pushed at most once per round, so its slot's
+// value has one writer per round.  Returns 1 if v was new (*slot_out then enters the seed's
+// x-list), 0 if it was present, -1 if the probe found no room.
+__device__ __forceinline__ int xt_add(const BArgs &a, int32_t j, int32_t v, float inc, uint64_t *slot_out) {
+    const uint64_t base = (uint64_t)j << a.xlog2cap;
+    const uint32_t kcur = (uint32_t)v | a.key_tag;
+    uint32_t h = mix32((uint32_t)v) & a.xmask;
+    for (uint32_t probes = 0; probes <= a.xmask && probes < kMaxProbe; probes++) {
+        const uint64_t slot = base + h;
+        unsigned long long wk = ld_relaxed_u64(a.xkr + slot);
+        for (;;) {
+            const uint32_t key = (uint32_t)(wk & 0xFFFFFFFFull);
+            if (key == kcur) {
+                atomicAdd(a.xxs + slot, inc);
+                *slot_out = slot;
+                return 0;
+            }
+            if (key != kEmpty && (key & ~a.key_idmask) == a.key_tag) break;  // another node of this solve
+            const unsigned long long prev = atomicCAS(a.xkr + slot, wk, (unsigned long long)kcur);
+            if (prev == wk) {
+                atomicAdd(a.xxs + slot, inc);
+                *slot_out = slot;
+                return 1;
+            }
+            wk = prev;
+        }
+        h = (h + 1) & a.xmask;
+    }
+    return -1;
 }
 
 // columns of the push: packed (id | code) when available, else plain ids
@@ -497,6 +560,7 @@ __device__ __forceinline__ int64_t hub_chunk(int64_t vh, int64_t nwarps, int64_t
 #ifndef GDE_ROUNDS_MIN_BLOCKS
 #define GDE_ROUNDS_MIN_BLOCKS 6  // 40 registers, 48 warps per SM (the kernel is latency-bound)
 #endif
+template <bool LAYERED>
 __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_rounds(BArgs a) {
     const unsigned nblocks = gridDim.x;
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -538,6 +602,7 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
         BCtl *prev = &G->ctl[p ^ 1];
         const unsigned ncand = min(__ldcg(&prev->cand_out), a.list_cap);
         const uint32_t *cand = a.cand[p];
+        const bool last_layer = LAYERED && t >= a.nlayers;
 
         // ---------------- phase A1: S_t for every seed ----------------
         // threshold test, r_S -> 0, x_S += c r_S, per-edge share; the push record is kept per
@@ -559,7 +624,13 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
                 const SlotParam sp = a.sparam[j];
                 cx = sp.cx; coef = sp.coef; divide = sp.divide != 0; cls = sp.cls;
             }
-            const float thr = a.thr32[(int64_t)cls * a.thr_stride + v];
+            float thr;
+            if (LAYERED) {
+                const double dv = (double)(a.off[v + 1] - a.off[v]);
+                thr = __double2float_ru(__dmul_rn(a.layer_eps[t < a.nlayers ? t : a.nlayers], dv));
+            } else {
+                thr = a.thr32[(int64_t)cls * a.thr_stride + v];
+            }
             if (!(rho != 0.0f && fabsf(rho) >= thr)) { __stcg(a.tmp_deg + ci, 0); continue; }
             // take the residual: a slot listed twice (possible once residuals can be negative)
             // is pushed by one taker only
@@ -567,11 +638,23 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
             if (!(rho != 0.0f && fabsf(rho) >= thr)) { __stcg(a.tmp_deg + ci, 0); continue; }
             const double rho64 = (double)rho;
             const int64_t beg = a.off[v];
-            const int32_t d = (int32_t)(a.off[v + 1] - beg);
-            const float xold = __ldcg(a.xs + slot);
+            // vol(S_t) counts d_u; the last layer of a layered kind only adds to x (no scatter)
+            const int32_t dvol = (int32_t)(a.off[v + 1] - beg);
+            const int32_t d = last_layer ? 0 : dvol;
             double xinc = __dmul_rn(cx, rho64);
             if (a.gbeta != 0.0) xinc = __ddiv_rn(xinc, pow((double)(d > 0 ? d : 1), a.gbeta));
-            __stcg(a.xs + slot, __fadd_rn(xold, __double2float_rn(xinc)));
+            bool xfirst;
+            uint64_t xslot = slot;
+            if (LAYERED) {
+                const int xr = xt_add(a, j, v, __double2float_rn(xinc), &xslot);
+                if (xr < 0) atomicExch(a.status + j, kSeedOverflow);  // x table full
+                xfirst = xr == 1;
+                coef = a.layer_coef[t < a.nlayers ? t : a.nlayers];
+            } else {
+                const float xold = __ldcg(a.xs + slot);
+                __stcg(a.xs + slot, __fadd_rn(xold, __double2float_rn(xinc)));
+                xfirst = xold == 0.0f;
+            }
             float w = 0.0f;
             if (d > 0) {
                 if (divide)
@@ -580,12 +663,12 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
                     w = __double2float_rn(__dmul_rn(coef, rho64));
             }
             my_rs += fabs(rho64);
-            my_vol += (unsigned long long)d;
+            my_vol += (unsigned long long)dvol;
             {
                 // per-seed counters and FP64 mass: one atomic per group of lanes with the same seed
                 const unsigned am = __activemask();
                 const unsigned peers = __match_any_sync(am, j);
-                const unsigned dsum = __reduce_add_sync(peers, (unsigned)d);
+                const unsigned dsum = __reduce_add_sync(peers, (unsigned)dvol);
                 double psum = 0.0, ssum = 0.0;
                 const double scat = d > 0 ? __dmul_rn((double)w, (double)d) : 0.0;
                 for (unsigned m = peers; m; m &= m - 1) {
@@ -601,14 +684,14 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
                     atomicAdd(a.sscat + j, ssum);
                 }
             }
-            if (xold == 0.0f) {
+            if (xfirst) {
                 // first activation of this node in this solve: remember the slot for the top-k
                 const unsigned xpeers = __match_any_sync(__activemask(), j);
                 const int xl = __ffs(xpeers) - 1;
                 unsigned xb = 0;
                 if (lane == xl) xb = atomicAdd(a.xcnt + j, (unsigned)__popc(xpeers));
                 xb = __shfl_sync(xpeers, xb, xl) + __popc(xpeers & ((1u << lane) - 1u));
-                if (xb < a.xcap) __stcg(a.xlist + (uint64_t)j * a.xcap + xb, slot);
+                if (xb < a.xcap) __stcg(a.xlist + (uint64_t)j * a.xcap + xb, (uint32_t)xslot);
             }
             if (d == 0) { __stcg(a.tmp_deg + ci, 0); continue; }
             const int bin = d <= a.t1 ? 0 : (d <= a.t2 ? 1 : 2);
@@ -715,6 +798,19 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
         const unsigned long long tb0 = globaltimer();
 
         // ---------------- phase B: scatter ----------------
+        if (LAYERED && a.colp) {
+            // the crossings of this scatter are tested against the next layer's threshold
+            const double en = a.layer_eps[t + 1 <= a.nlayers ? t + 1 : a.nlayers];
+            for (int c = threadIdx.x; c < 256; c += kThreads) {
+                if (c >= a.code_exact && c - a.code_exact > 32) {
+                    s_thr_br[0][c] = make_float2(__int_as_float(0x7f800000), __int_as_float(0x7f800000));
+                    continue;
+                }
+                const ThrBounds tb = thr_bounds(a, en, (uint32_t)c);
+                s_thr_br[0][c] = make_float2(tb.lo, tb.hi);
+            }
+            __syncthreads();
+        }
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             // the other parity's counters were last read in phase A of this round
             prev->hub_packed = 0; prev->cnt_small = 0; prev->cnt_med = 0; prev->cand_out = 0;
@@ -763,7 +859,7 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
                     int64_t hb = __ldcg(a.b_beg[2] + h);
                     float hw = __ldcg(a.b_w[2] + h);
                     int32_t hj = __ldcg(a.b_seed[2] + h);
-                    SlotMeta hm = slot_meta(a, hj);
+                    SlotMeta hm = slot_meta<LAYERED>(a, hj, t);
                     for (int64_t eb = e0; eb < e1; eb += 32) {
                         const int64_t e = eb + lane;
                         if (e < e1) {
@@ -774,9 +870,9 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
                                 hb = __ldcg(a.b_beg[2] + h);
                                 hw = __ldcg(a.b_w[2] + h);
                                 hj = __ldcg(a.b_seed[2] + h);
-                                hm = slot_meta(a, hj);
+                                hm = slot_meta<LAYERED>(a, hj, t);
                             }
-                            bscatter(a, hj, hm, push_col(a, hb + (e - hs)), hw, sbuf, sn);
+                            bscatter<LAYERED>(a, hj, hm, push_col(a, hb + (e - hs)), hw, sbuf, sn);
                         }
                         stage_flush(sbuf, sn, false, ctl, cand_out, a.list_cap);
                     }
@@ -802,10 +898,10 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
                 const int32_t d = __ldcg(a.b_deg[1] + i);
                 const float w = __ldcg(a.b_w[1] + i);
                 const int32_t j = __ldcg(a.b_seed[1] + i);
-                const SlotMeta m = slot_meta(a, j);
+                const SlotMeta m = slot_meta<LAYERED>(a, j, t);
                 for (int32_t k0 = 0; k0 < d; k0 += 32) {
                     const int32_t k = k0 + lane;
-                    if (k < d) bscatter(a, j, m, push_col(a, b + k), w, sbuf, sn);
+                    if (k < d) bscatter<LAYERED>(a, j, m, push_col(a, b + k), w, sbuf, sn);
                     stage_flush(sbuf, sn, false, ctl, cand_out, a.list_cap);
                 }
                 }
@@ -833,9 +929,9 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
                     j = __ldcg(a.b_seed[0] + i);
                 }
                 const int32_t dmax = (int32_t)__reduce_max_sync(0xffffffffu, (unsigned)d);
-                const SlotMeta m = d > 0 ? slot_meta(a, j) : SlotMeta{0, a.key_tag};
+                const SlotMeta m = d > 0 ? slot_meta<LAYERED>(a, j, t) : SlotMeta{0, write_tag<LAYERED>(a, t)};
                 for (int32_t k = 0; k < dmax; k++) {
-                    if (k < d) bscatter(a, j, m, push_col(a, b + k), w, sbuf, sn);
+                    if (k < d) bscatter<LAYERED>(a, j, m, push_col(a, b + k), w, sbuf, sn);
                     stage_flush(sbuf, sn, false, ctl, cand_out, a.list_cap);
                 }
             }
@@ -983,6 +1079,7 @@ struct TopkArgs {
     unsigned *ssupport;         // |supp(x)| per seed
     const int32_t *slots;       // block b reads seed slots[b] (NULL: seed b); output row b
     int keep;                   // nonzero: leave x in place (a server's resident queries)
+    float scale;                // output values are x * scale (0 reads as 1)
 };
 
 // One block per seed: the top-k of (x desc, id asc) over the slots of the seed's x-list (every
@@ -1035,7 +1132,8 @@ __global__ void __launch_bounds__(kThreads) k_batch_topk(TopkArgs a) {
             if (pos < k) {
                 const bool valid = key != 0;
                 a.out_ids[orow * k + pos] = valid ? (int32_t)(0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFull)) : -1;
-                a.out_vals[orow * k + pos] = valid ? __uint_as_float((uint32_t)(key >> 32)) : 0.0f;
+                const float sc = a.scale != 0.0f ? a.scale : 1.0f;
+                a.out_vals[orow * k + pos] = valid ? __fmul_rn(__uint_as_float((uint32_t)(key >> 32)), sc) : 0.0f;
             }
         }
     }
@@ -1129,6 +1227,7 @@ static void batch_free(BatchWork *w) {
     dfree(w->seg_cnt); dfree(w->seg_off); dfree(w->seg_cur); dfree(w->seg_hvol); dfree(w->vol_off);
     dfree(w->seg_hcur); dfree(w->seeds); dfree(w->status); dfree(w->inserts); dfree(w->svol);
     dfree(w->spushes); dfree(w->slast); dfree(w->spush); dfree(w->sscat); dfree(w->smass0); dfree(w->xlist); dfree(w->xcnt); dfree(w->glob); dfree(w->log);
+    dfree(w->xkr); dfree(w->xxs); dfree(w->layer_eps); dfree(w->layer_coef);
     delete w;
 }
 
@@ -1192,7 +1291,10 @@ static BatchWork *batch_work_alloc(int64_t nseeds, int64_t cap, int64_t list_cap
         w->glob = (BGlobal *)dmalloc(sizeof(BGlobal), "batch control");
         w->log = (RoundLog *)dmalloc(sizeof(RoundLog) * kLogCap, "round log");
         int per_sm = 0;
-        GDE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_rounds, kThreads, 0));
+        GDE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_rounds<false>, kThreads, 0));
+        int per_sm_layered = 0;
+        GDE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_layered, k_batch_rounds<true>, kThreads, 0));
+        if (per_sm_layered < per_sm) per_sm = per_sm_layered;  // one grid serves both
         int dev = 0, sms = 0;
         GDE_CUDA(cudaGetDevice(&dev));
         GDE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -1283,7 +1385,8 @@ static void launch_rounds(Graph &g, BatchWork *w, const BArgs &a, cudaStream_t s
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     const int pr = g.prof.start(kProfBatchRounds, s);
-    GDE_CUDA(cudaLaunchKernelEx(&cfg, k_batch_rounds, a));
+    if (a.layer_eps) GDE_CUDA(cudaLaunchKernelEx(&cfg, k_batch_rounds<true>, a));
+    else GDE_CUDA(cudaLaunchKernelEx(&cfg, k_batch_rounds<false>, a));
     g.prof.launched();
     g.prof.stop(pr, s);
 }
@@ -1308,12 +1411,14 @@ static void batch_solve_once(Graph &g, const SolveParams &p, const int32_t *seed
                              int32_t *overflow_seeds_host, int32_t *n_overflow, int list_scale,
                              bool *list_full) {
     GDE_REQUIRE(k >= 1 && k <= kTopMax, GDE_EINVAL, "batched mode needs 1 <= topk <= 64");
-    GDE_REQUIRE(p.kind == GDE_PPR || p.kind == GDE_KATZ || p.kind == GDE_GPPR, GDE_EINVAL,
-                "batched mode supports PPR, Katz and the generalised propagation");
+    GDE_REQUIRE(p.kind == GDE_PPR || p.kind == GDE_KATZ || p.kind == GDE_GPPR || layered(p.kind), GDE_EINVAL,
+                "batched mode supports PPR, Katz, the generalised propagation, the heat kernel and series");
     GDE_REQUIRE(p.precision == GDE_FP32, GDE_EINVAL, "batched mode stores x and r in FP32");
     GDE_REQUIRE(g.n < ((int64_t)1 << 31) - 1, GDE_EINVAL, "graph too large for 32-bit keys");
+    const bool lay = layered(p.kind);
     const int64_t budget = mem_budget > 0 ? mem_budget : ((int64_t)16 << 30);
-    int64_t cap = floor_pow2(budget / (12 * (int64_t)nseeds));
+    // layered kinds add an x table of half the residual table's slots (12 + 6 bytes per slot)
+    int64_t cap = floor_pow2(budget / ((lay ? 18 : 12) * (int64_t)nseeds));
     // a table of 2n slots never exceeds half load (at most n keys)
     // (at most 2^31 slots per table: slot indices are 32-bit and carry the seed above log2(cap))
     const int64_t cap_max = std::min<int64_t>(ceil_pow2(2 * (g.n > 0 ? g.n : 1)), (int64_t)1 << 31);
@@ -1343,20 +1448,67 @@ static void batch_solve_once(Graph &g, const SolveParams &p, const int32_t *seed
     while (((int64_t)1 << key_idbits) < g.n) key_idbits++;
     const int tag_bits = 32 - key_idbits < 8 ? 32 - key_idbits : 8;
     const uint32_t max_tag = tag_bits >= 2 ? (1u << tag_bits) - 2u : 0u;  // never all ones
+    // a layered solve gives every layer its own tag: nlayers + 1 layers, and the keys the last
+    // layer's (empty) scatter would write
+    const int64_t nlayers = lay ? p.hk_N : 0;
+    const uint32_t tags = lay ? (uint32_t)(nlayers + 2) : 1u;
+    GDE_REQUIRE(!lay || (nlayers + 2 <= (int64_t)max_tag), GDE_EINVAL,
+                "batched layered solve: more layers than this graph's key tags can tell apart");
+    bool fresh_x = false;
+    if (lay && (w->xt_seeds != (int64_t)nseeds || w->xt_cap != cap / 2)) {
+        dfree(w->xkr); w->xkr = nullptr;
+        dfree(w->xxs); w->xxs = nullptr;
+        w->xt_seeds = w->xt_cap = 0;
+        const int64_t xcap = cap / 2;
+        w->xkr = (unsigned long long *)dmalloc(8 * (size_t)nseeds * (size_t)xcap, "x tables");
+        w->xxs = (float *)dmalloc(4 * (size_t)nseeds * (size_t)xcap, "x tables");
+        w->xt_seeds = nseeds;
+        w->xt_cap = xcap;
+        w->xt_log2cap = 0;
+        while (((int64_t)1 << w->xt_log2cap) < xcap) w->xt_log2cap++;
+        fresh_x = true;
+    }
     w->epoch = w->epoch + 1;
-    if (w->need_clear || w->epoch > max_tag) {
+    if (w->need_clear || w->epoch + tags - 1 > max_tag || fresh_x) {
         const int pc = g.prof.start(kProfBatchClear, s);
         k_batch_clear<<<kSMs * 8, kThreads, 0, s>>>(w->pool, w->kr, w->xs);
         GDE_CUDA(cudaGetLastError());
         g.prof.launched();
+        if (w->xkr) {
+            k_batch_clear<<<kSMs * 8, kThreads, 0, s>>>(w->xt_seeds * w->xt_cap, w->xkr, w->xxs);
+            GDE_CUDA(cudaGetLastError());
+            g.prof.launched();
+        }
         g.prof.stop(pc, s);
         w->epoch = max_tag >= 1 ? 1u : 0u;
     }
     w->need_clear = true;  // until this solve completes
     const uint32_t key_tag = w->epoch << key_idbits;
+    w->epoch += tags - 1;  // the last tag this solve uses
     const uint32_t key_idmask = (uint32_t)(((uint64_t)1 << key_idbits) - 1);
     (void)pool;
-    if (w->thr_eps != p.eps || w->thr_n != g.n || !w->thr32) {
+    if (lay) {
+        // per-round constants: theta_t eps and the share coefficient of round t
+        GDE_REQUIRE(g.colp_valid && g.colp_idbits > 0, GDE_EINVAL,
+                    "batched layered solve: graph too large for packed columns");
+        const int64_t nl1 = nlayers + 1;
+        if (w->layer_cap < nl1) {
+            dfree(w->layer_eps); w->layer_eps = nullptr;
+            dfree(w->layer_coef); w->layer_coef = nullptr;
+            w->layer_cap = 0;
+            w->layer_eps = (double *)dmalloc(8 * (size_t)nl1, "layer constants");
+            w->layer_coef = (double *)dmalloc(8 * (size_t)nl1, "layer constants");
+            w->layer_cap = nl1;
+        }
+        std::vector<double> le((size_t)nl1), lc((size_t)nl1);
+        for (int64_t t = 0; t < nl1; t++) {
+            le[(size_t)t] = layer_theta(p, t) * p.eps;
+            lc[(size_t)t] = layer_ratio(p, t);
+        }
+        GDE_CUDA(cudaMemcpyAsync(w->layer_eps, le.data(), 8 * (size_t)nl1, cudaMemcpyHostToDevice, s));
+        GDE_CUDA(cudaMemcpyAsync(w->layer_coef, lc.data(), 8 * (size_t)nl1, cudaMemcpyHostToDevice, s));
+        GDE_CUDA(cudaStreamSynchronize(s));  // the host vectors go out of scope
+    } else if (w->thr_eps != p.eps || w->thr_n != g.n || !w->thr32) {
         if (!w->thr32) w->thr32 = (float *)dmalloc(4 * (size_t)(g.n > 0 ? g.n : 1), "thresholds");
         k_batch_thr<<<kSMs * 8, kThreads, 0, s>>>(g.n, g.deg, w->thr32, p.eps);
         GDE_CUDA(cudaGetLastError());
@@ -1382,12 +1534,31 @@ static void batch_solve_once(Graph &g, const SolveParams &p, const int32_t *seed
     a.coef = a.kind == GDE_PPR ? 1.0 - p.param : p.param;
     a.gbeta = p.gbeta;
     a.max_rounds = p.max_rounds;
+    if (lay) {
+        a.kind = GDE_HK;  // shares divided by d_u, x += r_u
+        a.cx = 1.0;
+        a.coef = 0.0;
+        a.gbeta = 0.0;
+        a.layer_eps = w->layer_eps;
+        a.layer_coef = w->layer_coef;
+        a.nlayers = nlayers;
+        a.tag_step = 1u << key_idbits;
+        a.xkr = w->xkr;
+        a.xxs = w->xxs;
+        a.xlog2cap = w->xt_log2cap;
+        a.xmask = (uint32_t)(w->xt_cap - 1);
+    }
     launch_rounds(g, w, a, s);
 
     TopkArgs ta{};
     ta.kr = w->kr; ta.xs = w->xs; ta.log2cap = w->log2cap; ta.cap = cap; ta.k = k;
     ta.key_idmask = key_idmask; ta.xlist = w->xlist; ta.xcnt = w->xcnt; ta.xcap = (unsigned)w->xcap;
     ta.out_ids = ids_dev; ta.out_vals = vals_dev; ta.ssupport = w->inserts;
+    if (lay) {
+        // x lives in the x tables; the output is e^-tau x (heat kernel) or c_0 x (series)
+        ta.kr = w->xkr; ta.xs = w->xxs; ta.log2cap = w->xt_log2cap; ta.cap = w->xt_cap;
+        ta.scale = (float)(p.kind == GDE_SERIES ? p.series[0] : std::exp(-p.param));
+    }
     const int pt = g.prof.start(kProfBatchTopk, s);
     k_batch_topk<<<nseeds, kThreads, 0, s>>>(ta);
     GDE_CUDA(cudaGetLastError());
@@ -1445,9 +1616,10 @@ static void batch_solve_once(Graph &g, const SolveParams &p, const int32_t *seed
             o.rounds = last[j] + 1;
             o.active_volume = (int64_t)vol[j];
             o.pushes = pushes[j];
-            // unit source: ||r||_1 = 1 - pushed + scattered; ||x||_1 = c_x * pushed
-            o.resid_l1 = m0[j] - pushed[j] + scat[j];
-            o.mass_l1 = (p.kind == GDE_KATZ ? 1.0 : p.param) * pushed[j];
+            // unit source: ||r||_1 = 1 - pushed + scattered; ||x||_1 = c_x * pushed (layered
+            // kinds leave each layer's remainder behind: not reported)
+            o.resid_l1 = lay ? -1.0 : m0[j] - pushed[j] + scat[j];
+            o.mass_l1 = lay ? -1.0 : (p.kind == GDE_KATZ ? 1.0 : p.param) * pushed[j];
             o.status = of ? GDE_ENOMEM : ((capped && last[j] + 1 >= (int64_t)hg.rounds) ? GDE_ENOTCONV : GDE_OK);
             o.reserved = 0;
         }

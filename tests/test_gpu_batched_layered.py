@@ -1,0 +1,132 @@
+"""Batched FP32 LocalGD for the layered kinds (the heat kernel's Taylor layers and a general
+series f = sum_k c_k (A D^-1)^k e_s): every seed of the batch in one persistent launch, layer t
+pushed into layer t+1 with the per-layer threshold theta_t eps d_u, x in a per-seed table,
+top-k out; against the FP64 oracle through the C ABI.
+
+Both sides satisfy 0 <= f_u - x_u <= eps d_u (the layered bound of Section 3), so a top-k entry
+is compared with the oracle's value within eps d_u plus 1e-5 relative (FP32), as for PPR."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from test_gpu_batched import check_topk, run_batched
+from test_gpu_series import ipr_coef
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gde():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_2410_21634_gb300 as m
+    m.load()
+    return m
+
+
+@pytest.fixture(scope="module")
+def c1():
+    return synth.workload_graph("chung_lu_1e4")
+
+
+@pytest.fixture(scope="module")
+def rmat16():
+    return synth.rmat(16, 16, seed=21)
+
+
+@pytest.mark.parametrize("hk_mode", [0, 1])
+def test_batched_hk(gde, c1, rmat16, hk_mode):
+    tau, eps = 5.0, 1e-6
+    for g in (c1, rmat16):
+        G = gde.Graph.from_synth(g)
+        seeds = synth.seeds_mixed(g, 12, 12, seed=5)
+        st, stats, ids, vals = run_batched(gde, G, "hk", tau, eps, seeds, hk_threshold=hk_mode)
+        assert st == gde.OK
+        for i in range(0, len(seeds), 3):
+            ref = oracle.localgd(g, "hk", tau, eps, int(seeds[i]), hk_mode=hk_mode)
+            check_topk(g, ids[i], vals[i], ref.x, eps)
+            assert stats[i]["rounds"] <= oracle.hk_terms(tau) + 1
+            assert stats[i]["active_volume"] == pytest.approx(ref.volume, rel=0.02, abs=64)
+        G.close()
+
+
+def test_batched_series(gde, rmat16):
+    g = rmat16
+    c = ipr_coef(1.5)
+    eps = 1e-3 * c[0]
+    G = gde.Graph.from_synth(g)
+    seeds = synth.seeds_mixed(g, 8, 8, seed=6)
+    st, _, ids, vals = run_batched(gde, G, "series", 0.0, eps, seeds, series_coef=c)
+    assert st == gde.OK
+    for i in range(0, len(seeds), 3):
+        ref = oracle.series(g, c, eps, int(seeds[i]))
+        check_topk(g, ids[i], vals[i], ref.x, eps)
+    G.close()
+
+
+def test_hk_equals_its_series(gde, c1):
+    """The heat kernel and the series of its Taylor coefficients take the same rounds on
+    the batched engine, so their top-k lists agree within FP32 summation order."""
+    g = c1
+    tau = 5.0
+    N = oracle.hk_terms(tau)
+    c = [math.exp(-tau)]
+    for k in range(N):
+        c.append(c[-1] * tau / (k + 1))
+    G = gde.Graph.from_synth(g)
+    seeds = synth.seeds_quantile(g, 6)
+    _, _, ids_a, vals_a = run_batched(gde, G, "hk", tau, 1e-6, seeds)
+    _, _, ids_b, vals_b = run_batched(gde, G, "series", 0.0, 1e-6, seeds, series_coef=np.array(c))
+    d = g.degrees().astype(np.float64)
+    assert np.allclose(vals_a, vals_b, rtol=1e-5, atol=1e-7 * d.max())
+    G.close()
+
+
+def test_alone_equals_in_mix(gde, rmat16):
+    g = rmat16
+    seeds = synth.seeds_mixed(g, 16, 16, seed=9)
+    G = gde.Graph.from_synth(g)
+    _, _, ids_b, vals_b = run_batched(gde, G, "hk", 5.0, 1e-6, seeds)
+    d = g.degrees().astype(np.float64)
+    for i in (0, 7, 20, 31):
+        _, _, ids_1, vals_1 = run_batched(gde, G, "hk", 5.0, 1e-6, seeds[i:i + 1])
+        assert np.allclose(vals_1[0], vals_b[i], rtol=1e-5, atol=1e-6 * d.max())
+        same = ids_1[0] == ids_b[i]
+        assert np.all(same | np.isclose(vals_1[0], vals_b[i], rtol=1e-5))
+    G.close()
+
+
+def test_tag_wrap_and_mixed_kinds(gde, rmat16):
+    """Every layer takes its own key tag, so a run of layered solves wraps the tag space and
+    clears the tables; PPR solves in between share the same workspace.  Every repeat gives
+    the first answer again."""
+    g = rmat16
+    G = gde.Graph.from_synth(g)
+    seeds = synth.seeds_mixed(g, 8, 8, seed=12)
+    d = g.degrees().astype(np.float64)
+    _, _, ids0, vals0 = run_batched(gde, G, "hk", 5.0, 1e-6, seeds)
+    _, _, pids0, pvals0 = run_batched(gde, G, "ppr", 0.1, 1e-6, seeds)
+    for rep in range(14):
+        _, _, ids, vals = run_batched(gde, G, "hk", 5.0, 1e-6, seeds)
+        assert np.allclose(vals, vals0, rtol=1e-5, atol=1e-6 * d.max()), rep
+        if rep % 4 == 3:
+            _, _, pids, pvals = run_batched(gde, G, "ppr", 0.1, 1e-6, seeds)
+            assert np.allclose(pvals, pvals0, rtol=1e-5, atol=1e-6 * d.max()), rep
+    G.close()
+
+
+def test_overflow_falls_back(gde, rmat16):
+    """A budget too small for the touched sets: overflowing seeds are re-solved with dense
+    state and the outputs stay correct."""
+    g = rmat16
+    seeds = synth.seeds_mixed(g, 4, 4, seed=4)
+    G = gde.Graph.from_synth(g)
+    st, stats, ids, vals = run_batched(gde, G, "hk", 5.0, 1e-6, seeds, mem_budget_bytes=8 * 18 * 4096)
+    assert st == gde.OK
+    for i in (0, 5):
+        ref = oracle.localgd(g, "hk", 5.0, 1e-6, int(seeds[i]))
+        check_topk(g, ids[i], vals[i], ref.x, 1e-6)
+    G.close()
