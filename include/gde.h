@@ -86,10 +86,9 @@ typedef struct {
     int32_t batched;         /* 1: all seeds in one persistent launch with per-seed hash
                                 accumulators (FP32, topk > 0; every kind: the layered ones,
                                 HK and SERIES, keep one key tag per layer and x in a
-                                second table; layers + 1 must fit in the key tags: at
-                                most 253 layers up to 2^24 nodes, 2^(32-ceil(log2 n)) - 3
-                                else GDE_EINVAL); 0 (default): one seed
-                                at a time with dense x and r */
+                                second table: at most 253 layers up to 2^24 nodes and
+                                2^(32-ceil(log2 n)) - 3 above, more is GDE_EINVAL);
+                                0 (default): one seed at a time with dense x and r */
     uint32_t flags;          /* GDE_DEVICE_PTRS: seeds and outputs are device pointers */
     int64_t max_rounds;      /* round cap; 0 (default) means 1,000,000 */
     int64_t mem_budget_bytes;/* batched: bytes for the hash accumulators (12 per slot, 18 for
