@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=2.0,
                     help="seconds of the serving stream measured after the batched bench (0: skip)")
     ap.add_argument("--no-gd", action="store_true", help="skip the global GD vs LocalGD comparison")
+    ap.add_argument("--no-kinds", action="store_true", help="skip the batched heat-kernel line")
     ap.add_argument("--no-random-probe", action="store_true",
                     help="skip the random-access calibration of device memory")
     ap.add_argument("--random-probe", action="store_true",
@@ -335,6 +336,56 @@ def run_serving(gde, seconds, slots, rounds_per_step, g=None, beta=None, budget_
     }
 
 
+def run_batched_kinds(gde, G, g, seeds_np, dev, budget_gb=64.0, sample=32):
+    """The batched engine on the other kinds of the paper, on the benchmark's graph and seeds:
+    the heat kernel (tau = 5, Taylor layers, eps = 1e-6).  Each row: batched FP32 seeds/s and
+    GTEPS (CUDA events around 3 solves after one warm-up), and the plain FP64 one-seed-per-
+    launch path on `sample` of the seeds (half uniform, half hubs)."""
+    import numpy as np
+    import torch
+    rows = []
+    nseeds = len(seeds_np)
+    seeds = torch.from_numpy(seeds_np).to(dev)
+    ids = torch.zeros((nseeds, TOPK), dtype=torch.int32, device=dev)
+    vals = torch.zeros((nseeds, TOPK), dtype=torch.float32, device=dev)
+    budget = int(budget_gb * (1 << 30))
+    for kind, param, eps in (("hk", 5.0, 1e-6),):
+        def solve():
+            return gde.solve(G, kind, param, eps, seeds, vals, ids, precision="fp32", topk=TOPK, batched=1,
+                             mem_budget_bytes=budget)
+        solve()
+        torch.cuda.synchronize()
+        G.profile_enable(True)
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        reps = 3
+        for _ in range(reps):
+            st, stats = solve()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        prof = G.profile_read()
+        G.profile_enable(False)
+        sec = e0.elapsed_time(e1) / 1e3 / reps
+        overflow = sum(1 for x in stats if x["fallback"])
+        half = nseeds // 2
+        smp = np.concatenate([seeds_np[: sample // 2], seeds_np[half: half + sample // 2]])
+        out = torch.zeros((1, g.n), dtype=torch.float64, device=dev)
+        gde.solve(G, kind, param, eps, torch.tensor([int(smp[0])], dtype=torch.int32, device=dev), out)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for sd in smp:
+            gde.solve(G, kind, param, eps, torch.tensor([int(sd)], dtype=torch.int32, device=dev), out)
+        torch.cuda.synchronize()
+        plain = len(smp) / (time.perf_counter() - t0)
+        rows.append({"kind": kind, "param": param, "eps": eps, "seeds": nseeds,
+                     "batched_fp32_seeds_per_s": nseeds / sec, "ms_per_solve": sec * 1e3,
+                     "gteps": prof["edges"] / reps / sec / 1e9, "fallback_seeds": overflow,
+                     "plain_fp64_seeds_per_s": plain, "plain_sample": len(smp),
+                     "speedup_vs_plain_fp64": nseeds / sec / plain})
+    return {"graph": g.name, "budget_gb": budget_gb, "rows": rows}
+
+
 def run_gd_compare(gde, g=None):
     """Global GD vs LocalGD (Section 5: Table 2's operation ratio, Figure 6's running time as a
     function of eps), with LocalCH beside them, on R-MAT scale 22, PPR alpha=0.1, plain FP64,
@@ -441,7 +492,7 @@ def main():
         log(f"[bench] autotune: {tuning} ({tune_ms:.1f} ms) in {time.time() - t0:.1f}s")
     for _ in range(max(args.warmup, 3)):
         st, stats = step()
-    overflow = sum(1 for s in stats if s["status"] == gde.ENOMEM)
+    overflow = sum(1 for s in stats if s["fallback"])
     torch.cuda.synchronize()
     G.profile_enable(True)
     stream = torch.cuda.current_stream()
@@ -549,6 +600,10 @@ def main():
     gpu_launches = prof["launches"]  # counted by the library for the timed steps
     tuning_used = G.get_tuning()
 
+    kinds = None
+    if not args.no_kinds and rank == 0:
+        kinds = run_batched_kinds(gde, G, g, seeds_np, dev)
+
     # the serving workload (continuous batching with edge insertions), on its own graph
     serving = None
     if args.serve_seconds > 0 and rank == 0 and ws == 1:
@@ -577,6 +632,7 @@ def main():
         "rounds_per_step": prof["rounds"] / launches,
         "tuning": tuning_used,
         "autotuned": tuning is not None,
+        "batched_kinds": kinds,
         "serving": serving,
         "global_gd_vs_localgd": gd_compare,
     }

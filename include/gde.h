@@ -119,7 +119,10 @@ typedef struct {
                                 scaled residual y, with mass_l1 the matching ||S x||_1) */
     double mass_l1;          /* ||x^(T)||_1 before any output scaling */
     int32_t status;          /* gde_status of this seed */
-    int32_t reserved;
+    int32_t fallback;        /* batched seeds whose hash table overflowed: 2 when re-solved
+                                in a smaller batch with larger tables (same memory budget),
+                                1 when re-solved by the one-seed engine with dense state
+                                (overflow at the largest table); else 0 */
 } gde_stats;
 
 void gde_solve_opts_init(gde_solve_opts *opts);

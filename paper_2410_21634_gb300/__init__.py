@@ -57,10 +57,10 @@ class Stats(ctypes.Structure):
     _fields_ = [("rounds", ctypes.c_int64), ("active_volume", ctypes.c_int64),
                 ("pushes", ctypes.c_int64), ("resid_l1", ctypes.c_double),
                 ("mass_l1", ctypes.c_double), ("status", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("fallback", ctypes.c_int32)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class Profile(ctypes.Structure):

@@ -380,8 +380,8 @@ gde_status gde_solve(gde_graph *h, gde_kind kind, double param, double eps, cons
             }
             std::vector<int32_t> of((size_t)nseeds);
             int32_t nof = 0;
-            batch_solve(g, p, seeds_dev, nseeds, k, o.mem_budget_bytes, ids_dev, vals_dev, st.data(),
-                        of.data(), &nof);
+            batch_solve_rebatch(g, p, seeds_dev, hs.data(), nseeds, k, o.mem_budget_bytes, ids_dev, vals_dev,
+                                st.data(), of.data(), &nof);
             for (int32_t i = 0; i < nof; i++) todo.push_back(of[i]);
         } else {
             for (int32_t i = 0; i < nseeds; i++) todo.push_back(i);
@@ -417,6 +417,7 @@ gde_status gde_solve(gde_graph *h, gde_kind kind, double param, double eps, cons
                 one.resid_l1 = rl1;
                 one.mass_l1 = xl1;
                 one.status = converged ? GDE_OK : GDE_ENOTCONV;
+                one.fallback = o.batched ? 1 : 0;  // only overflowed seeds come here in batched mode
                 void *dst = vec ? vec : (char *)out_x + rsz * (size_t)g.n * i;
                 dense_output(g, w, p, dst);
                 if (k > 0) {

@@ -1437,6 +1437,11 @@ static void batch_solve_once(Graph &g, const SolveParams &p, const int32_t *seed
     GDE_REQUIRE(nseeds <= list_cap, GDE_EINVAL, "too many seeds for one batch");
     *list_full = list_cap == (int64_t)nseeds * cap;
     BatchWork *w = batch_work_get(g, nseeds, cap, list_cap);
+    if (w->list_cap > list_cap) {
+        // a workspace that an earlier solve left larger keeps its longer lists
+        list_cap = std::min<int64_t>(w->list_cap, std::min<int64_t>((int64_t)nseeds * cap, 0xFFFFFFFFll));
+        *list_full = list_cap == (int64_t)nseeds * cap;
+    }
     cudaStream_t s = p.stream;
     GDE_CUDA(cudaMemcpyAsync(w->seeds, seeds_dev, 4 * (size_t)nseeds, cudaMemcpyDeviceToDevice, s));
     const int64_t pool = (int64_t)nseeds * cap;
@@ -1621,7 +1626,7 @@ static void batch_solve_once(Graph &g, const SolveParams &p, const int32_t *seed
             o.resid_l1 = lay ? -1.0 : m0[j] - pushed[j] + scat[j];
             o.mass_l1 = lay ? -1.0 : (p.kind == GDE_KATZ ? 1.0 : p.param) * pushed[j];
             o.status = of ? GDE_ENOMEM : ((capped && last[j] + 1 >= (int64_t)hg.rounds) ? GDE_ENOTCONV : GDE_OK);
-            o.reserved = 0;
+            o.fallback = 0;
         }
     }
     if (n_overflow) *n_overflow = nof;
@@ -2223,6 +2228,92 @@ void batch_solve(Graph &g, const SolveParams &p, const int32_t *seeds_dev, int32
             g.batch->list_overflowed = false;
         }
     }
+}
+
+// rows[i] of the output receives row i of the chunk's output
+__global__ void k_put_rows(int32_t m, int k, const int32_t *rows, const int32_t *src_ids, const float *src_vals,
+                           int32_t *dst_ids, float *dst_vals) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= (int64_t)m * k) return;
+    const int64_t r = i / k, c = i % k;
+    dst_ids[(int64_t)rows[r] * k + c] = src_ids[i];
+    dst_vals[(int64_t)rows[r] * k + c] = src_vals[i];
+}
+
+void batch_solve_rebatch(Graph &g, const SolveParams &p, const int32_t *seeds_dev, const int32_t *seeds_host,
+                         int32_t nseeds, int k, int64_t mem_budget, int32_t *ids_dev, float *vals_dev,
+                         gde_stats *stats_host, int32_t *overflow_seeds_host, int32_t *n_overflow) {
+    batch_solve(g, p, seeds_dev, nseeds, k, mem_budget, ids_dev, vals_dev, stats_host, overflow_seeds_host,
+                n_overflow);
+    if (*n_overflow == 0) return;
+    const int64_t budget = mem_budget > 0 ? mem_budget : ((int64_t)16 << 30);
+    const int64_t per_slot = layered(p.kind) ? 18 : 12;
+    const int64_t cap_max = std::min<int64_t>(ceil_pow2(2 * (g.n > 0 ? g.n : 1)), (int64_t)1 << 31);
+    int64_t cap = floor_pow2(budget / (per_slot * (int64_t)nseeds));
+    std::vector<int32_t> pending(overflow_seeds_host, overflow_seeds_host + *n_overflow);
+    std::vector<void *> tmp;
+    auto alloc = [&](size_t bytes, const char *what) {
+        void *q = dmalloc(bytes, what);
+        tmp.push_back(q);
+        return q;
+    };
+    try {
+        cudaStream_t s = p.stream;
+        while (!pending.empty() && cap < cap_max) {
+            cap *= 2;
+            const int64_t chunk = budget / (per_slot * cap);  // seeds per batch at this table size
+            if (chunk < 1) break;
+            const int32_t m0 = (int32_t)std::min<int64_t>(chunk, (int64_t)pending.size());
+            if (tmp.empty()) {
+                alloc(4 * (size_t)pending.size(), "re-batched seeds");
+                alloc(4 * (size_t)pending.size(), "re-batched rows");
+                alloc(4 * (size_t)pending.size() * (size_t)k, "re-batched ids");
+                alloc(4 * (size_t)pending.size() * (size_t)k, "re-batched values");
+            }
+            int32_t *d_seeds = (int32_t *)tmp[0], *d_rows = (int32_t *)tmp[1];
+            int32_t *d_ids = (int32_t *)tmp[2];
+            float *d_vals = (float *)tmp[3];
+            std::vector<int32_t> next;
+            std::vector<gde_stats> cst((size_t)m0);
+            std::vector<int32_t> cof((size_t)m0);
+            for (size_t c0 = 0; c0 < pending.size(); c0 += (size_t)m0) {
+                const int32_t m = (int32_t)std::min<size_t>((size_t)m0, pending.size() - c0);
+                std::vector<int32_t> hseeds((size_t)m), hrows((size_t)m);
+                for (int32_t i = 0; i < m; i++) {
+                    hrows[(size_t)i] = pending[c0 + (size_t)i];
+                    hseeds[(size_t)i] = seeds_host[hrows[(size_t)i]];
+                }
+                GDE_CUDA(cudaMemcpyAsync(d_seeds, hseeds.data(), 4 * (size_t)m, cudaMemcpyHostToDevice, s));
+                GDE_CUDA(cudaMemcpyAsync(d_rows, hrows.data(), 4 * (size_t)m, cudaMemcpyHostToDevice, s));
+                int32_t cn = 0;
+                // the same budget over m seeds gives tables of at least `cap` slots
+                batch_solve(g, p, d_seeds, m, k, budget, d_ids, d_vals, cst.data(), cof.data(), &cn);
+                const int64_t items = (int64_t)m * k;
+                k_put_rows<<<(unsigned)((items + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+                    m, k, d_rows, d_ids, d_vals, ids_dev, vals_dev);
+                GDE_CUDA(cudaGetLastError());
+                g.prof.launched();
+                GDE_CUDA(cudaStreamSynchronize(s));  // the host vectors go out of scope
+                std::vector<bool> of((size_t)m, false);
+                for (int32_t i = 0; i < cn; i++) of[(size_t)cof[(size_t)i]] = true;
+                for (int32_t i = 0; i < m; i++) {
+                    if (of[(size_t)i]) next.push_back(hrows[(size_t)i]);
+                    if (stats_host) {
+                        gde_stats one = cst[(size_t)i];
+                        one.fallback = of[(size_t)i] ? 0 : 2;
+                        stats_host[hrows[(size_t)i]] = one;
+                    }
+                }
+            }
+            pending.swap(next);
+        }
+    } catch (...) {
+        for (void *q : tmp) dfree(q);
+        throw;
+    }
+    for (void *q : tmp) dfree(q);
+    for (size_t i = 0; i < pending.size(); i++) overflow_seeds_host[i] = pending[i];
+    *n_overflow = (int32_t)pending.size();
 }
 
 int64_t batch_round_log(Graph &g, double *out, int64_t cap) {

@@ -252,6 +252,12 @@ void serve_pool_results(Graph &g, ServePool *P, int32_t n, const int32_t *slots,
 void batch_solve(Graph &g, const SolveParams &p, const int32_t *seeds_dev, int32_t nseeds, int k,
                  int64_t mem_budget, int32_t *ids_dev, float *vals_dev, gde_stats *stats_host,
                  int32_t *overflow_seeds_host, int32_t *n_overflow);
+// batch_solve, then the seeds whose table overflowed again in smaller batches with tables of
+// twice, four times, ... the slots under the same budget; those still overflowing at the
+// largest table are left in overflow_seeds_host / *n_overflow.  seeds_host: the same ids.
+void batch_solve_rebatch(Graph &g, const SolveParams &p, const int32_t *seeds_dev, const int32_t *seeds_host,
+                         int32_t nseeds, int k, int64_t mem_budget, int32_t *ids_dev, float *vals_dev,
+                         gde_stats *stats_host, int32_t *overflow_seeds_host, int32_t *n_overflow);
 // top-k (x desc, id asc) of a dense float vector on the device
 void topk_dense_f32(const float *x_dev, int64_t n, int k, int32_t *ids_dev, float *vals_dev,
                     cudaStream_t s);

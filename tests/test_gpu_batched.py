@@ -138,9 +138,27 @@ def test_overflow_falls_back(gde, rmat16):
     G = gde.Graph.from_synth(g)
     st, stats, ids, vals = run_batched(gde, G, "ppr", 0.1, 1e-6, seeds, mem_budget_bytes=16 * 12 * 4096)
     assert st == gde.OK
+    assert any(s["fallback"] for s in stats) and all(s["status"] == gde.OK for s in stats)
     for i in (0, 9):
         ref = oracle.localgd(g, "ppr", 0.1, 1e-6, int(seeds[i]))
         check_topk(g, ids[i], vals[i], ref.x, 1e-6)
+
+
+def test_overflow_rebatched_with_larger_tables(gde, rmat16):
+    """Seeds that overflow their tables are solved again in smaller batches, whose tables
+    are larger under the same budget, before any falls back to dense state."""
+    g = rmat16
+    seeds = synth.seeds_mixed(g, 8, 8, seed=4)
+    G = gde.Graph.from_synth(g)
+    budget = 16 * 12 * (1 << 13)  # 8K slots per seed for the whole batch
+    st, stats, ids, vals = run_batched(gde, G, "ppr", 0.1, 1e-6, seeds, mem_budget_bytes=budget)
+    assert st == gde.OK
+    fb = [s["fallback"] for s in stats]
+    assert 2 in fb, fb
+    for i in range(16):
+        ref = oracle.localgd(g, "ppr", 0.1, 1e-6, int(seeds[i]))
+        check_topk(g, ids[i], vals[i], ref.x, 1e-6)
+    G.close()
 
 
 def test_batched_device_pointers(gde, c1):

@@ -44,7 +44,7 @@ def test_batched_hk(gde, c1, rmat16, hk_mode):
         G = gde.Graph.from_synth(g)
         seeds = synth.seeds_mixed(g, 12, 12, seed=5)
         st, stats, ids, vals = run_batched(gde, G, "hk", tau, eps, seeds, hk_threshold=hk_mode)
-        assert st == gde.OK
+        assert st == gde.OK and not any(s["fallback"] for s in stats)
         for i in range(0, len(seeds), 3):
             ref = oracle.localgd(g, "hk", tau, eps, int(seeds[i]), hk_mode=hk_mode)
             check_topk(g, ids[i], vals[i], ref.x, eps)
@@ -126,6 +126,7 @@ def test_overflow_falls_back(gde, rmat16):
     G = gde.Graph.from_synth(g)
     st, stats, ids, vals = run_batched(gde, G, "hk", 5.0, 1e-6, seeds, mem_budget_bytes=8 * 18 * 4096)
     assert st == gde.OK
+    assert any(s["fallback"] for s in stats)
     for i in (0, 5):
         ref = oracle.localgd(g, "hk", 5.0, 1e-6, int(seeds[i]))
         check_topk(g, ids[i], vals[i], ref.x, 1e-6)
