@@ -624,22 +624,19 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
                 const SlotParam sp = a.sparam[j];
                 cx = sp.cx; coef = sp.coef; divide = sp.divide != 0; cls = sp.cls;
             }
-            float thr;
-            if (LAYERED) {
-                const double dv = (double)(a.off[v + 1] - a.off[v]);
-                thr = __double2float_ru(__dmul_rn(a.layer_eps[t < a.nlayers ? t : a.nlayers], dv));
-            } else {
-                thr = a.thr32[(int64_t)cls * a.thr_stride + v];
-            }
+            // the threshold fl(eps d_v) rounded up to float (the per-node arrays hold the same
+            // values), from the row bounds the push needs anyway
+            const int64_t beg = a.off[v];
+            const int32_t dvol = (int32_t)(a.off[v + 1] - beg);
+            const double eps_t = LAYERED ? a.layer_eps[t < a.nlayers ? t : a.nlayers] : a.eps_cls[cls];
+            const float thr = __double2float_ru(__dmul_rn(eps_t, (double)dvol));
             if (!(rho != 0.0f && fabsf(rho) >= thr)) { __stcg(a.tmp_deg + ci, 0); continue; }
             // take the residual: a slot listed twice (possible once residuals can be negative)
             // is pushed by one taker only
             rho = atomicExch(r_of(a.kr, slot), 0.0f);
             if (!(rho != 0.0f && fabsf(rho) >= thr)) { __stcg(a.tmp_deg + ci, 0); continue; }
             const double rho64 = (double)rho;
-            const int64_t beg = a.off[v];
             // vol(S_t) counts d_u; the last layer of a layered kind only adds to x (no scatter)
-            const int32_t dvol = (int32_t)(a.off[v + 1] - beg);
             const int32_t d = last_layer ? 0 : dvol;
             double xinc = __dmul_rn(cx, rho64);
             if (a.gbeta != 0.0) xinc = __ddiv_rn(xinc, pow((double)(d > 0 ? d : 1), a.gbeta));
