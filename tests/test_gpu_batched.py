@@ -235,3 +235,26 @@ def test_autotune_picks_a_valid_tuning(gde, rmat16):
     for i in (0, 31):
         ref = oracle.localgd(g, "ppr", 0.1, 1e-6, int(seeds[i]))
         check_topk(g, ids[i], vals[i], ref.x, 1e-6)
+
+
+def test_many_seeds_small_graph(gde, c1):
+    """5,000 seeds on a 10^4-node graph (more seeds than nodes, repeats included): the
+    per-seed segments, lists and tables at a seed count well past the benchmark's."""
+    g = c1
+    rng = np.random.Generator(np.random.PCG64(17))
+    seeds = rng.integers(0, g.n, size=5000).astype(np.int32)
+    G = gde.Graph.from_synth(g)
+    st, stats, ids, vals = run_batched(gde, G, "ppr", 0.15, 1e-5, seeds, k=8)
+    assert st == gde.OK
+    for i in rng.choice(5000, size=12, replace=False):
+        ref = oracle.localgd(g, "ppr", 0.15, 1e-5, int(seeds[i]))
+        check_topk(g, ids[i], vals[i], ref.x, 1e-5, k=8)
+    # the same seed anywhere in the batch gives the same list
+    first = {}
+    for i, s in enumerate(seeds.tolist()):
+        if s in first:
+            j = first[s]
+            assert np.allclose(vals[i], vals[j], rtol=1e-5, atol=1e-7)
+        else:
+            first[s] = i
+    G.close()
