@@ -236,7 +236,8 @@ SERVE = {"graph": "chung_lu_2p23", "rate_qps": 2000.0, "batch_edges": 10000, "ba
          "eps": (1e-5, 1e-6, 1e-7), "alpha": 0.15}
 
 
-def run_serving(gde, seconds, slots, rounds_per_step, g=None, beta=None, budget_gb=0.0, trace=None):
+def run_serving(gde, seconds, slots, rounds_per_step, g=None, beta=None, budget_gb=0.0, trace=None,
+                defer_volume=0):
     """The serving workload: PPR (alpha 0.15) and Katz (beta = 0.5 / lambda_max) queries
     arriving as a Poisson stream at 2,000/s with eps drawn from {1e-5, 1e-6, 1e-7}, while
     batches of 10,000 uniformly random edges are inserted every 50 ms, on Chung-Lu n=2^23
@@ -257,7 +258,8 @@ def run_serving(gde, seconds, slots, rounds_per_step, g=None, beta=None, budget_
         budget = slots * cap * 12
     else:
         budget = int(budget_gb * (1 << 30))
-    S = gde.Server(G, slots=slots, rounds_per_step=rounds_per_step, eps=SERVE["eps"], mem_budget_bytes=budget)
+    S = gde.Server(G, slots=slots, rounds_per_step=rounds_per_step, eps=SERVE["eps"], mem_budget_bytes=budget,
+                   defer_volume=defer_volume)
     arrivals = synth.poisson_arrivals(SERVE["rate_qps"], seconds, seed=7)
     nq = len(arrivals)
     rng = np.random.Generator(np.random.PCG64(11))

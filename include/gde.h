@@ -373,6 +373,10 @@ typedef struct {
     int32_t n_eps;            /* tolerance classes, 1..4 (default 1) */
     double eps[4];            /* their tolerances (default eps[0] = 1e-6) */
     int64_t mem_budget_bytes; /* hash pool bytes, 0 = 16 GB */
+    int64_t defer_volume;     /* a query whose last step pushed more edges than this runs one
+                                 round per step (its rounds are unchanged, only spread out) so
+                                 the other queries' rounds in a step are not each held up by
+                                 its scatter; 0 = 2^23, < 0 = never */
 } gde_server_opts;
 
 typedef struct {

@@ -82,7 +82,8 @@ class Tuning(ctypes.Structure):
 
 class ServerOpts(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int32), ("rounds_per_step", ctypes.c_int32), ("topk", ctypes.c_int32),
-                ("n_eps", ctypes.c_int32), ("eps", ctypes.c_double * 4), ("mem_budget_bytes", ctypes.c_int64)]
+                ("n_eps", ctypes.c_int32), ("eps", ctypes.c_double * 4), ("mem_budget_bytes", ctypes.c_int64),
+                ("defer_volume", ctypes.c_int64)]
 
 
 class ServerResult(ctypes.Structure):
@@ -443,7 +444,7 @@ class Server:
     poll() returns the results emitted so far as dicts."""
 
     def __init__(self, graph: Graph, slots: int = 256, rounds_per_step: int = 4, topk: int = 64,
-                 eps=(1e-6,), mem_budget_bytes: int = 0):
+                 eps=(1e-6,), mem_budget_bytes: int = 0, defer_volume: int = 0):
         lib = load()
         o = ServerOpts()
         lib.gde_server_opts_init(ctypes.byref(o))
@@ -455,6 +456,7 @@ class Server:
         for i, e in enumerate(eps):
             o.eps[i] = float(e)
         o.mem_budget_bytes = int(mem_budget_bytes)
+        o.defer_volume = int(defer_volume)
         h = ctypes.c_void_p()
         _check(lib.gde_server_create(graph.handle, ctypes.byref(o), ctypes.byref(h)))
         self._h = h

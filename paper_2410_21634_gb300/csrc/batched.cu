@@ -51,8 +51,15 @@ struct SlotParam {
     int32_t divide;
     int32_t cls;
     uint32_t tag;    // the slot's key tag (shifted above the id bits): a server retags a slot
-    uint32_t pad;    // for every query, so the previous query's keys read as free
+                     // for every query, so the previous query's keys read as free
+    uint32_t flags;  // kSlotDefer: the slot runs only the first round of a launch
 };
+
+// A slot whose last launch pushed many edges (a query in its heavy rounds) runs one round
+// per launch and passes its candidates on unchanged in the launch's later rounds, so the
+// other slots' rounds in that launch are not each held up by its scatter.  Its own rounds
+// are unchanged, only spread over more launches.
+constexpr uint32_t kSlotDefer = 1u;
 
 struct BCtl {  // per-round counters (one set per round parity)
     unsigned long long hub_packed;
@@ -623,6 +630,12 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
             if (a.sparam) {
                 const SlotParam sp = a.sparam[j];
                 cx = sp.cx; coef = sp.coef; divide = sp.divide != 0; cls = sp.cls;
+                if ((sp.flags & kSlotDefer) && t != a.t0) {
+                    // sits this round out: the candidate carries over to the next round
+                    bappend(&ctl->cand_out, a.cand[p ^ 1], slot, a.list_cap, &ctl->overflow);
+                    __stcg(a.tmp_deg + ci, 0);
+                    continue;
+                }
             }
             // the threshold fl(eps d_v) rounded up to float (the per-node arrays hold the same
             // values), from the row bounds the push needs anyway
@@ -1662,6 +1675,10 @@ struct ServePool {
     float *d_vals = nullptr;
     unsigned long long *d_partial = nullptr;  // top-k parts
     cudaStream_t s = nullptr;
+    // slots whose last launch pushed more than defer_vol edges run one round per launch
+    int64_t defer_vol = (int64_t)1 << 23;
+    std::vector<unsigned long long> last_vol;  // per slot: its pushed volume after the last launch
+    std::vector<uint8_t> heavy;
 };
 
 // device view of one slot table's probing, shared by the admission and correction kernels
@@ -1996,6 +2013,8 @@ ServePool *serve_pool_create(Graph &g, int32_t slots, int64_t budget, const doub
         P->thr = (float *)dmalloc(4 * (size_t)ncls * (size_t)(g.n > 0 ? g.n : 1), "class thresholds");
         P->d_param = (SlotParam *)dmalloc(sizeof(SlotParam) * (size_t)slots, "slot parameters");
         P->h_param.assign((size_t)slots, SlotParam{0.15, 0.85, 1, 0});
+        P->last_vol.assign((size_t)slots, 0ull);
+        P->heavy.assign((size_t)slots, 0);
         P->pend = (unsigned *)dmalloc(4 * (size_t)slots, "pending counts");
         P->d_list = (int32_t *)dmalloc(4 * (size_t)slots, "slot list");
         P->d_seeds = (int32_t *)dmalloc(4 * (size_t)slots, "slot seeds");
@@ -2037,6 +2056,8 @@ void serve_pool_destroy(ServePool *P) {
 }
 
 int64_t serve_pool_cap(const ServePool *P) { return P->cap; }
+
+void serve_pool_set_defer(ServePool *P, int64_t v) { P->defer_vol = v; }
 
 void serve_pool_graph_changed(ServePool *P) {
     P->thr_n = -1;
@@ -2086,7 +2107,9 @@ void serve_pool_admit(Graph &g, ServePool *P, int32_t n, const int32_t *slots, c
         }
         tags[(size_t)i] = e << P->key_idbits;
         P->h_param[(size_t)slots[i]].tag = tags[(size_t)i];
-        P->h_param[(size_t)slots[i]].pad = 0;
+        P->h_param[(size_t)slots[i]].flags = 0;
+        P->last_vol[(size_t)slots[i]] = 0;
+        P->heavy[(size_t)slots[i]] = 0;
     }
     GDE_CUDA(cudaMemcpyAsync(P->d_param, P->h_param.data(), sizeof(SlotParam) * (size_t)P->slots,
                              cudaMemcpyHostToDevice, s));
@@ -2138,6 +2161,18 @@ void serve_pool_correct(Graph &g, ServePool *P, const EdgeBatch &eb, int32_t nre
 int64_t serve_pool_run(Graph &g, ServePool *P, int64_t rounds) {
     serve_ensure_graph_state(g, P);
     BatchWork *w = P->w;
+    // heavy slots (by their volume in the last launch) run one round of this launch
+    bool changed = false;
+    for (int32_t j = 0; j < P->slots; j++) {
+        const uint32_t want = (rounds > 1 && P->heavy[(size_t)j]) ? kSlotDefer : 0u;
+        if ((P->h_param[(size_t)j].flags & kSlotDefer) != want) {
+            P->h_param[(size_t)j].flags = (P->h_param[(size_t)j].flags & ~kSlotDefer) | want;
+            changed = true;
+        }
+    }
+    if (changed)
+        GDE_CUDA(cudaMemcpyAsync(P->d_param, P->h_param.data(), sizeof(SlotParam) * (size_t)P->slots,
+                                 cudaMemcpyHostToDevice, P->s));
     BArgs a = bargs_base(g, w, P->cap, P->list_cap, P->slots, 1u << P->key_idbits, P->key_idmask);
     a.thr32 = P->thr;
     a.thr_stride = g.n;
@@ -2153,7 +2188,15 @@ int64_t serve_pool_run(Graph &g, ServePool *P, int64_t rounds) {
     launch_rounds(g, w, a, P->s);
     BGlobal hg;
     GDE_CUDA(cudaMemcpyAsync(&hg, w->glob, sizeof(BGlobal), cudaMemcpyDeviceToHost, P->s));
+    std::vector<unsigned long long> vol((size_t)P->slots);
+    GDE_CUDA(cudaMemcpyAsync(vol.data(), w->svol, 8 * (size_t)P->slots, cudaMemcpyDeviceToHost, P->s));
     GDE_CUDA(cudaStreamSynchronize(P->s));
+    for (int32_t j = 0; j < P->slots; j++) {
+        const unsigned long long prev = P->last_vol[(size_t)j], now = vol[(size_t)j];
+        const unsigned long long delta = now >= prev ? now - prev : now;  // re-admitted: counted anew
+        P->heavy[(size_t)j] = P->defer_vol >= 0 && delta > (unsigned long long)P->defer_vol ? 1 : 0;
+        P->last_vol[(size_t)j] = now;
+    }
     if (hg.error != 0) serve_check_error(P);
     const int64_t ran = (int64_t)hg.rounds - P->T;
     P->T = hg.rounds;

@@ -237,6 +237,8 @@ double server_clock();
 // serving pool (batched.cu): slots whose solves continue across launches
 struct ServePool;
 ServePool *serve_pool_create(Graph &g, int32_t slots, int64_t budget, const double *eps, int ncls);
+// slots whose last launch pushed more than v edges run one round per launch (v < 0: never)
+void serve_pool_set_defer(ServePool *P, int64_t v);
 void serve_pool_destroy(ServePool *P);
 int64_t serve_pool_cap(const ServePool *P);
 int64_t serve_pool_round(const ServePool *P);

@@ -80,6 +80,7 @@ void gde_server_opts_init(gde_server_opts *o) {
     o->n_eps = 1;
     o->eps[0] = 1e-6;
     o->mem_budget_bytes = 0;
+    o->defer_volume = 0;
 }
 
 double gde_server_clock(void) { return server_clock(); }
@@ -102,6 +103,7 @@ gde_status gde_server_create(gde_graph *g, const gde_server_opts *o, gde_server 
         S->graph = g;
         S->opts = op;
         S->pool = serve_pool_create(G, op.slots, op.mem_budget_bytes, op.eps, op.n_eps);
+        serve_pool_set_defer(S->pool, op.defer_volume == 0 ? ((int64_t)1 << 23) : op.defer_volume);
         S->slots.resize((size_t)op.slots);
     } catch (...) {
         if (S->pool) serve_pool_destroy(S->pool);

@@ -249,3 +249,34 @@ def test_submit_and_poll_from_another_thread(gde, g0):
     for q in qs[::7]:
         check_answer(g0, got[q[0]], oracle_x(g0, q), EPS[q[3]])
     S.close()
+
+
+@pytest.mark.parametrize("defer", [1, 2000])
+def test_deferred_heavy_queries(gde, g0, defer):
+    """Queries whose last step pushed more than defer_volume edges run one round per step;
+    their answers are those of the oracle, and a deferred query needs more steps, never
+    different rounds.  defer_volume = 1 defers every query after its first step."""
+    G = gde.Graph.from_synth(g0)
+    qs = queries(g0, 24, seed=5)
+    S = gde.Server(G, slots=8, rounds_per_step=4, eps=EPS, defer_volume=defer)
+    for q in qs:
+        S.submit(*q)
+    out = S.run_until_idle()
+    steps_deferred = S.info()["steps"]
+    first = {r["qid"]: r for r in out if not r["update"]}
+    assert sorted(first) == list(range(24))
+    for q in qs:
+        check_answer(g0, first[q[0]], oracle_x(g0, q), EPS[q[3]])
+    S.close()
+    # the same stream without deferral takes no more steps
+    S = gde.Server(G, slots=8, rounds_per_step=4, eps=EPS, defer_volume=-1)
+    for q in qs:
+        S.submit(*q)
+    out2 = S.run_until_idle()
+    assert S.info()["steps"] <= steps_deferred
+    second = {r["qid"]: r for r in out2 if not r["update"]}
+    d = g0.degrees().astype(np.float64)
+    for q in qs:
+        a, b = first[q[0]], second[q[0]]
+        assert np.allclose(a["vals"], b["vals"], rtol=1e-5, atol=1e-6 * d.max())
+    S.close()
