@@ -338,20 +338,26 @@ def run_serving(gde, seconds, slots, rounds_per_step, g=None, beta=None, budget_
     }
 
 
-def run_batched_kinds(gde, G, g, seeds_np, dev, budget_gb=64.0, sample=32):
+def run_batched_kinds(gde, G, g, seeds_np, dev, sample=32):
     """The batched engine on the other kinds of the paper, on the benchmark's graph and seeds:
-    the heat kernel (tau = 5, Taylor layers, eps = 1e-6).  Each row: batched FP32 seeds/s and
-    GTEPS (CUDA events around 3 solves after one warm-up), and the plain FP64 one-seed-per-
-    launch path on `sample` of the seeds (half uniform, half hubs)."""
+    Katz (beta = 0.5 / lambda_max, eps = 1e-7, 16 GB tables) and the heat kernel (tau = 5,
+    Taylor layers, eps = 1e-6, 64 GB tables: its first layers touch more nodes than PPR's
+    rounds).  Each row: batched FP32 seeds/s and GTEPS (CUDA events around 3 solves after
+    one warm-up), and the plain FP64 one-seed-per-launch path on `sample` of the seeds (half
+    uniform, half hubs)."""
     import numpy as np
     import torch
+
+    import synth
     rows = []
+    lam, _ = synth.lambda_max(g, rel_tol=1e-4, max_iter=200)
     nseeds = len(seeds_np)
     seeds = torch.from_numpy(seeds_np).to(dev)
     ids = torch.zeros((nseeds, TOPK), dtype=torch.int32, device=dev)
     vals = torch.zeros((nseeds, TOPK), dtype=torch.float32, device=dev)
-    budget = int(budget_gb * (1 << 30))
-    for kind, param, eps in (("hk", 5.0, 1e-6),):
+    for kind, param, eps, budget_gb in (("katz", 0.5 / lam, 1e-7, 16.0), ("hk", 5.0, 1e-6, 64.0)):
+        budget = int(budget_gb * (1 << 30))
+
         def solve():
             return gde.solve(G, kind, param, eps, seeds, vals, ids, precision="fp32", topk=TOPK, batched=1,
                              mem_budget_bytes=budget)
@@ -380,12 +386,12 @@ def run_batched_kinds(gde, G, g, seeds_np, dev, budget_gb=64.0, sample=32):
             gde.solve(G, kind, param, eps, torch.tensor([int(sd)], dtype=torch.int32, device=dev), out)
         torch.cuda.synchronize()
         plain = len(smp) / (time.perf_counter() - t0)
-        rows.append({"kind": kind, "param": param, "eps": eps, "seeds": nseeds,
+        rows.append({"kind": kind, "param": param, "eps": eps, "seeds": nseeds, "budget_gb": budget_gb,
                      "batched_fp32_seeds_per_s": nseeds / sec, "ms_per_solve": sec * 1e3,
                      "gteps": prof["edges"] / reps / sec / 1e9, "fallback_seeds": overflow,
                      "plain_fp64_seeds_per_s": plain, "plain_sample": len(smp),
                      "speedup_vs_plain_fp64": nseeds / sec / plain})
-    return {"graph": g.name, "budget_gb": budget_gb, "rows": rows}
+    return {"graph": g.name, "lambda_max": lam, "rows": rows}
 
 
 def run_gd_compare(gde, g=None):
