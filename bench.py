@@ -340,11 +340,11 @@ def run_serving(gde, seconds, slots, rounds_per_step, g=None, beta=None, budget_
 
 def run_batched_kinds(gde, G, g, seeds_np, dev, sample=32):
     """The batched engine on the other kinds of the paper, on the benchmark's graph and seeds:
-    Katz (beta = 0.5 / lambda_max, eps = 1e-7, 16 GB tables) and the heat kernel (tau = 5,
-    Taylor layers, eps = 1e-6, 64 GB tables: its first layers touch more nodes than PPR's
-    rounds).  Each row: batched FP32 seeds/s and GTEPS (CUDA events around 3 solves after
-    one warm-up), and the plain FP64 one-seed-per-launch path on `sample` of the seeds (half
-    uniform, half hubs)."""
+    Katz (beta = 0.5 / lambda_max, eps = 1e-7) and the heat kernel (tau = 5, Taylor layers,
+    eps = 1e-6), both with 64 GB of tables (a Katz hub seed and the first heat-kernel layers
+    touch more nodes than PPR).  Each row: batched FP32 seeds/s and GTEPS (CUDA events around
+    3 solves after one warm-up), and the plain FP64 one-seed-per-launch path on `sample` of
+    the seeds (half uniform, half hubs)."""
     import numpy as np
     import torch
 
@@ -355,7 +355,7 @@ def run_batched_kinds(gde, G, g, seeds_np, dev, sample=32):
     seeds = torch.from_numpy(seeds_np).to(dev)
     ids = torch.zeros((nseeds, TOPK), dtype=torch.int32, device=dev)
     vals = torch.zeros((nseeds, TOPK), dtype=torch.float32, device=dev)
-    for kind, param, eps, budget_gb in (("katz", 0.5 / lam, 1e-7, 16.0), ("hk", 5.0, 1e-6, 64.0)):
+    for kind, param, eps, budget_gb in (("katz", 0.5 / lam, 1e-7, 64.0), ("hk", 5.0, 1e-6, 64.0)):
         budget = int(budget_gb * (1 << 30))
 
         def solve():
