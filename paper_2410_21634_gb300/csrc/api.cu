@@ -177,7 +177,7 @@ static void tuning_from_bins(const Bins &b, gde_tuning *t) {
     t->t2 = b.t2;
     t->chunk = b.chunk;
     t->blocks_per_sm = b.blocks_per_sm;
-    t->schedule = b.schedule == 1 ? 1 : (b.schedule == 0 ? 2 : 3);
+    t->schedule = b.schedule == 1 ? 1 : (b.schedule == 0 ? 2 : (b.schedule == 2 ? 3 : 4));
 }
 
 }  // namespace gde
@@ -491,8 +491,8 @@ gde_status gde_set_tuning(gde_graph *h, const gde_tuning *t) {
     if (t->t2 > 0) b.t2 = t->t2;
     if (t->chunk > 0) b.chunk = t->chunk;
     if (t->blocks_per_sm > 0) b.blocks_per_sm = t->blocks_per_sm;
-    if (t->schedule > 0) b.schedule = t->schedule == 1 ? 1 : (t->schedule == 2 ? 0 : 2);
-    GDE_REQUIRE(t->schedule <= 3, GDE_EINVAL, "tuning: schedule must be 0..3");
+    if (t->schedule > 0) b.schedule = t->schedule == 1 ? 1 : (t->schedule == 2 ? 0 : (t->schedule == 3 ? 2 : 3));
+    GDE_REQUIRE(t->schedule <= 4, GDE_EINVAL, "tuning: schedule must be 0..4");
     GDE_REQUIRE(b.t1 <= b.t2, GDE_EINVAL, "tuning: t1 must be <= t2");
     GDE_REQUIRE(b.chunk >= 32 && b.chunk <= (1 << 24), GDE_EINVAL, "tuning: chunk must be in [32, 2^24]");
     GDE_REQUIRE(b.blocks_per_sm <= 32, GDE_EINVAL, "tuning: blocks_per_sm must be <= 32");
@@ -564,7 +564,7 @@ gde_status gde_autotune(gde_graph *h, gde_kind kind, double param, double eps, c
         const int t1s[] = {4, 8, 16, 32};
         const int t2s[] = {128, 256, 512, 1024, 2048};
         const int chunks[] = {256, 512, 1024, 2048, 4096};
-        const int scheds[] = {0, 1, 2};
+        const int scheds[] = {0, 1, 2, 3};
         const int bpss[] = {0, 3, 2};
         auto sweep = [&](const int *vals_, int nv, int Bins::*field, bool need_order) {
             for (int i = 0; i < nv; i++) {
@@ -579,7 +579,7 @@ gde_status gde_autotune(gde_graph *h, gde_kind kind, double param, double eps, c
         sweep(t1s, 4, &Bins::t1, true);
         sweep(t2s, 5, &Bins::t2, true);
         sweep(chunks, 5, &Bins::chunk, false);
-        sweep(scheds, 3, &Bins::schedule, false);
+        sweep(scheds, 4, &Bins::schedule, false);
         sweep(bpss, 3, &Bins::blocks_per_sm, false);
         g.bins = cur;
         for (int k = 0; k < 2; k++)

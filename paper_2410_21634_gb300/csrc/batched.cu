@@ -76,7 +76,15 @@ struct BCtl {  // per-round counters (one set per round parity)
     unsigned long long hub_next;
     unsigned int med_next;
     unsigned int small_next;
+    // seed-grouped order: work units of all three bins, group by group
+    unsigned long long unit_next;
+    unsigned long long units_total;
 };
+
+#ifndef GDE_SEED_GROUP
+#define GDE_SEED_GROUP 8
+#endif
+constexpr int kSeedGroup = GDE_SEED_GROUP;  // seeds whose bins are scattered together (schedule 3)
 
 struct BGlobal {
     BCtl ctl[2];
@@ -119,6 +127,7 @@ struct BatchWork {
     int32_t *b_seed[3] = {nullptr, nullptr, nullptr};
     int64_t *hub_vstart = nullptr;
     uint32_t *hub_cstart = nullptr;  // first hub push of each scatter chunk (kHubChunkTab entries)
+    unsigned long long *grp_units = nullptr, *grp_off = nullptr;  // per seed group (schedule 3)
     // per-candidate push record of the round (frontier phase -> placement phase)
     int64_t *tmp_beg = nullptr;
     int32_t *tmp_deg = nullptr;
@@ -293,7 +302,11 @@ struct BArgs {
     double gbeta; // generalised propagation: x += (cx * rho) / max(d_u, 1)^gbeta (0: none)
     int64_t max_rounds;
     int32_t t1, t2, chunk;
-    int32_t schedule;   // 0: all bins handed out in order; 1: hubs in order, others strided; 2: all strided
+    int32_t schedule;   // 0: all bins handed out in order; 1: hubs in order, others strided; 2: all strided;
+                        // 3: group by group of kSeedGroup seeds, each group's hubs, medium and small
+                        // entries together, so a seed's table is brought into L2 once per round
+    unsigned long long *grp_units;  // per seed group: its work units (schedule 3)
+    unsigned long long *grp_off;    // their exclusive prefix sums
     // layered kinds (heat kernel, general series): round t reads layer t and writes layer t+1;
     // the keys of layer t carry key_tag + t * tag_step, so a layer's keys read as free slots
     // once the next layer is written, and x lives in a separate per-seed table keyed by node
@@ -756,6 +769,23 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
                 ctl->hub_packed = ((unsigned long long)n2 << kBHubVolBits) | vh;
                 if ((unsigned long long)n0 + n1 + n2 > a.list_cap) ctl->overflow = 1;
             }
+            if (a.schedule == 3) {
+                // work units of each seed group: its hub chunks, medium grabs and small groups
+                const int64_t chunk = hub_chunk((int64_t)vh, nw, a.chunk);
+                const int64_t ngroups = (ns + kSeedGroup - 1) / kSeedGroup;
+                __syncthreads();  // seg_off / vol_off of every seed are written
+                for (int64_t gi = threadIdx.x; gi < ngroups; gi += kThreads) {
+                    const int64_t j0 = gi * kSeedGroup, j1 = j0 + kSeedGroup < ns ? j0 + kSeedGroup : ns;
+                    const unsigned long long hv = (j1 < ns ? __ldcg(a.vol_off + j1) : vh) - __ldcg(a.vol_off + j0);
+                    const unsigned nm = (j1 < ns ? __ldcg(a.seg_off + ns + j1) : n1) - __ldcg(a.seg_off + ns + j0);
+                    const unsigned nsm = (j1 < ns ? __ldcg(a.seg_off + j1) : n0) - __ldcg(a.seg_off + j0);
+                    a.grp_units[gi] = (hv + (unsigned long long)chunk - 1) / (unsigned long long)chunk +
+                                      (nm + kMedGrab - 1) / kMedGrab + (nsm + 31) / 32;
+                }
+                __syncthreads();
+                const unsigned long long tot = block_scan<unsigned long long>(a.grp_units, a.grp_off, ngroups, s_scan64);
+                if (threadIdx.x == 0) ctl->units_total = tot;
+            }
         }
         if (!grid_sync(G, nblocks)) return;
 
@@ -826,6 +856,7 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
             prev->hub_packed = 0; prev->cnt_small = 0; prev->cnt_med = 0; prev->cand_out = 0;
             prev->n_active = 0; prev->vol = 0; prev->rS_l1 = 0.0; prev->overflow = 0;
             prev->hub_next = 0; prev->med_next = 0; prev->small_next = 0;
+            prev->unit_next = 0; prev->units_total = 0;
         }
         uint32_t *cand_out = a.cand[p ^ 1];
         if (__ldcg(&ctl->overflow)) {
@@ -834,76 +865,45 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
             const unsigned long long hp = __ldcg(&ctl->hub_packed);
             const int64_t H = (int64_t)(hp >> kBHubVolBits);
             const int64_t VH = (int64_t)(hp & kBHubVolMask);
-            // hubs: merge-path chunks of the concatenated hub adjacency, one warp per chunk,
-            // consecutive lanes on consecutive columns
-            if (VH > 0) {
-                const int64_t chunk = hub_chunk(VH, nw, a.chunk);
-                const int64_t nchunks = (VH + chunk - 1) / chunk;
-                // warps beyond the chunk count would only find the work gone: they stay out,
-                // so small rounds do not queue every warp on the hand-out counter
-                for (int64_t it = 0; gw < nchunks; it++) {
-                    int64_t c;
-                    if (a.schedule <= 1) {
-                        unsigned long long cg_ = 0;
-                        if (lane == 0) cg_ = atomicAdd(&ctl->hub_next, 1ull);
-                        c = (int64_t)__shfl_sync(0xffffffffu, cg_, 0);
-                    } else {
-                        c = gw + it * nw;
-                    }
-                    if (c >= nchunks) break;
-                    const int64_t e0 = c * chunk;
-                    const int64_t e1 = min(e0 + chunk, VH);
-                    int64_t h;
-                    if (c < kHubChunkTab) {
-                        h = (int64_t)__ldcg(a.hub_cstart + c);
-                    } else {  // past the table: the last push starting at or before e0
-                        int64_t lo = 0, hi = H;
-                        while (hi - lo > 1) {
-                            const int64_t mid = (lo + hi) >> 1;
-                            if (__ldcg(a.hub_vstart + mid) <= e0) lo = mid; else hi = mid;
-                        }
-                        h = lo;
-                    }
-                    int64_t hs = __ldcg(a.hub_vstart + h);
-                    int64_t he = hs + __ldcg(a.b_deg[2] + h);
-                    int64_t hb = __ldcg(a.b_beg[2] + h);
-                    float hw = __ldcg(a.b_w[2] + h);
-                    int32_t hj = __ldcg(a.b_seed[2] + h);
-                    SlotMeta hm = slot_meta<LAYERED>(a, hj, t);
-                    for (int64_t eb = e0; eb < e1; eb += 32) {
-                        const int64_t e = eb + lane;
-                        if (e < e1) {
-                            while (e >= he) {
-                                ++h;
-                                hs = __ldcg(a.hub_vstart + h);
-                                he = hs + __ldcg(a.b_deg[2] + h);
-                                hb = __ldcg(a.b_beg[2] + h);
-                                hw = __ldcg(a.b_w[2] + h);
-                                hj = __ldcg(a.b_seed[2] + h);
-                                hm = slot_meta<LAYERED>(a, hj, t);
-                            }
-                            bscatter<LAYERED>(a, hj, hm, push_col(a, hb + (e - hs)), hw, sbuf, sn);
-                        }
-                        stage_flush(sbuf, sn, false, ctl, cand_out, a.list_cap);
-                    }
-                }
-            }
-            // medium degrees: one warp per node
+            const int64_t chunk = hub_chunk(VH, nw, a.chunk);
             const unsigned nmed = min(__ldcg(&ctl->cnt_med), a.list_cap);
-            // descending: the hub sweep ends at the last seeds, the medium sweep starts there
-            for (int64_t it = 0; gw * kMedGrab < (int64_t)nmed; it++) {
-                unsigned got = 0;
-                if (a.schedule == 0) {
-                    if (lane == 0) got = atomicAdd(&ctl->med_next, (unsigned)kMedGrab);
-                    got = __shfl_sync(0xffffffffu, got, 0);
-                } else {
-                    const int64_t g0 = (gw + it * nw) * kMedGrab;
-                    got = g0 < nmed ? (unsigned)g0 : nmed;
+            const unsigned nsm = min(__ldcg(&ctl->cnt_small), a.list_cap);
+            // hub columns [e0, e1) of the concatenated hub adjacency, h the push holding e0:
+            // consecutive lanes on consecutive columns, walking the pushes forward
+            auto hub_range = [&](int64_t e0, int64_t e1, int64_t h) {
+                int64_t hs = __ldcg(a.hub_vstart + h);
+                int64_t he = hs + __ldcg(a.b_deg[2] + h);
+                int64_t hb = __ldcg(a.b_beg[2] + h);
+                float hw = __ldcg(a.b_w[2] + h);
+                int32_t hj = __ldcg(a.b_seed[2] + h);
+                SlotMeta hm = slot_meta<LAYERED>(a, hj, t);
+                for (int64_t eb = e0; eb < e1; eb += 32) {
+                    const int64_t e = eb + lane;
+                    if (e < e1) {
+                        while (e >= he) {
+                            ++h;
+                            hs = __ldcg(a.hub_vstart + h);
+                            he = hs + __ldcg(a.b_deg[2] + h);
+                            hb = __ldcg(a.b_beg[2] + h);
+                            hw = __ldcg(a.b_w[2] + h);
+                            hj = __ldcg(a.b_seed[2] + h);
+                            hm = slot_meta<LAYERED>(a, hj, t);
+                        }
+                        bscatter<LAYERED>(a, hj, hm, push_col(a, hb + (e - hs)), hw, sbuf, sn);
+                    }
+                    stage_flush(sbuf, sn, false, ctl, cand_out, a.list_cap);
                 }
-                if (got >= nmed) break;
-                const unsigned gend = min(got + (unsigned)kMedGrab, nmed);
-                for (unsigned ii = got; ii < gend; ii++) {
-                const int64_t i = (int64_t)nmed - 1 - ii;
+            };
+            // the last hub push in [lo, hi) starting at or before e0
+            auto hub_find = [&](int64_t e0, int64_t lo, int64_t hi) {
+                while (hi - lo > 1) {
+                    const int64_t mid = (lo + hi) >> 1;
+                    if (__ldcg(a.hub_vstart + mid) <= e0) lo = mid; else hi = mid;
+                }
+                return lo;
+            };
+            // one medium-degree push: the whole warp on its columns
+            auto med_entry = [&](int64_t i) {
                 const int64_t b = __ldcg(a.b_beg[1] + i);
                 const int32_t d = __ldcg(a.b_deg[1] + i);
                 const float w = __ldcg(a.b_w[1] + i);
@@ -914,25 +914,15 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
                     if (k < d) bscatter<LAYERED>(a, j, m, push_col(a, b + k), w, sbuf, sn);
                     stage_flush(sbuf, sn, false, ctl, cand_out, a.list_cap);
                 }
-                }
-            }
-            // small degrees: one thread per node (warp-uniform loops so the warp can flush)
-            const unsigned nsm = min(__ldcg(&ctl->cnt_small), a.list_cap);
-            for (int64_t it = 0; gw * 32 < (int64_t)nsm; it++) {
-                int64_t i0;
-                if (a.schedule == 0) {
-                    unsigned got = 0;
-                    if (lane == 0) got = atomicAdd(&ctl->small_next, 32u);
-                    i0 = (int64_t)__shfl_sync(0xffffffffu, got, 0);
-                } else {
-                    i0 = (gw + it * nw) * 32;
-                }
-                if (i0 >= nsm) break;
+            };
+            // small-degree pushes [i0, min(i0 + 32, iend)): one thread each (warp-uniform loops
+            // so the warp can flush)
+            auto small_group = [&](int64_t i0, int64_t iend) {
                 const int64_t i = i0 + lane;
                 int64_t b = 0;
                 int32_t d = 0, j = 0;
                 float w = 0.0f;
-                if (i < nsm) {
+                if (i < iend) {
                     b = __ldcg(a.b_beg[0] + i);
                     d = __ldcg(a.b_deg[0] + i);
                     w = __ldcg(a.b_w[0] + i);
@@ -943,6 +933,103 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
                 for (int32_t k = 0; k < dmax; k++) {
                     if (k < d) bscatter<LAYERED>(a, j, m, push_col(a, b + k), w, sbuf, sn);
                     stage_flush(sbuf, sn, false, ctl, cand_out, a.list_cap);
+                }
+            };
+            if (a.schedule == 3) {
+                // group by group of seeds: each group's hub chunks, medium grabs and small
+                // groups are consecutive work units, so a seed's table is brought into L2 once
+                // per round instead of once per bin
+                // (units handed out in order, one at a time: with static striding the warps that
+                // drew long hub chunks fell behind and held the round)
+                const unsigned long long total = __ldcg(&ctl->units_total);
+                const int64_t ngroups = (ns + kSeedGroup - 1) / kSeedGroup;
+                for (int64_t it = 0; (unsigned long long)gw < total; it++) {
+                    unsigned long long u = 0;
+                    if (lane == 0) u = atomicAdd(&ctl->unit_next, 1ull);
+                    u = __shfl_sync(0xffffffffu, u, 0);
+                    if (u >= total) break;
+                    int64_t glo = 0, ghi = ngroups;  // the last group starting at or before u
+                    while (ghi - glo > 1) {
+                        const int64_t mid = (glo + ghi) >> 1;
+                        if (__ldcg(a.grp_off + mid) <= u) glo = mid; else ghi = mid;
+                    }
+                    const int64_t j0 = glo * kSeedGroup, j1 = j0 + kSeedGroup < ns ? j0 + kSeedGroup : ns;
+                    int64_t r = (int64_t)(u - __ldcg(a.grp_off + glo));
+                    const int64_t hv0 = (int64_t)__ldcg(a.vol_off + j0);
+                    const int64_t hv1 = j1 < ns ? (int64_t)__ldcg(a.vol_off + j1) : VH;
+                    const int64_t nch = (hv1 - hv0 + chunk - 1) / chunk;
+                    if (r < nch) {
+                        const int64_t e0 = hv0 + r * chunk;
+                        const int64_t e1 = min(e0 + chunk, hv1);
+                        const int64_t h0 = (int64_t)__ldcg(a.seg_off + 2 * ns + j0);
+                        const int64_t h1 = j1 < ns ? (int64_t)__ldcg(a.seg_off + 2 * ns + j1) : H;
+                        hub_range(e0, e1, hub_find(e0, h0, h1));
+                        continue;
+                    }
+                    r -= nch;
+                    const int64_t m0 = (int64_t)__ldcg(a.seg_off + ns + j0);
+                    const int64_t m1 = j1 < ns ? (int64_t)__ldcg(a.seg_off + ns + j1) : (int64_t)nmed;
+                    const int64_t nmg = (m1 - m0 + kMedGrab - 1) / kMedGrab;
+                    if (r < nmg) {
+                        const int64_t gend = min(m0 + (r + 1) * kMedGrab, m1);
+                        for (int64_t i = m0 + r * kMedGrab; i < gend; i++) med_entry(i);
+                        continue;
+                    }
+                    r -= nmg;
+                    const int64_t s0 = (int64_t)__ldcg(a.seg_off + j0);
+                    const int64_t s1 = j1 < ns ? (int64_t)__ldcg(a.seg_off + j1) : (int64_t)nsm;
+                    small_group(s0 + r * 32, s1);
+                }
+            } else {
+                // hubs: merge-path chunks of the concatenated hub adjacency, one warp per chunk
+                if (VH > 0) {
+                    const int64_t nchunks = (VH + chunk - 1) / chunk;
+                    // warps beyond the chunk count would only find the work gone: they stay out,
+                    // so small rounds do not queue every warp on the hand-out counter
+                    for (int64_t it = 0; gw < nchunks; it++) {
+                        int64_t c;
+                        if (a.schedule <= 1) {
+                            unsigned long long cg_ = 0;
+                            if (lane == 0) cg_ = atomicAdd(&ctl->hub_next, 1ull);
+                            c = (int64_t)__shfl_sync(0xffffffffu, cg_, 0);
+                        } else {
+                            c = gw + it * nw;
+                        }
+                        if (c >= nchunks) break;
+                        const int64_t e0 = c * chunk;
+                        const int64_t e1 = min(e0 + chunk, VH);
+                        // past the table: the last push starting at or before e0
+                        const int64_t h = c < kHubChunkTab ? (int64_t)__ldcg(a.hub_cstart + c) : hub_find(e0, 0, H);
+                        hub_range(e0, e1, h);
+                    }
+                }
+                // medium degrees: one warp per node; descending: the hub sweep ends at the last
+                // seeds, the medium sweep starts there
+                for (int64_t it = 0; gw * kMedGrab < (int64_t)nmed; it++) {
+                    unsigned got = 0;
+                    if (a.schedule == 0) {
+                        if (lane == 0) got = atomicAdd(&ctl->med_next, (unsigned)kMedGrab);
+                        got = __shfl_sync(0xffffffffu, got, 0);
+                    } else {
+                        const int64_t g0 = (gw + it * nw) * kMedGrab;
+                        got = g0 < nmed ? (unsigned)g0 : nmed;
+                    }
+                    if (got >= nmed) break;
+                    const unsigned gend = min(got + (unsigned)kMedGrab, nmed);
+                    for (unsigned ii = got; ii < gend; ii++) med_entry((int64_t)nmed - 1 - ii);
+                }
+                // small degrees: one thread per node
+                for (int64_t it = 0; gw * 32 < (int64_t)nsm; it++) {
+                    int64_t i0;
+                    if (a.schedule == 0) {
+                        unsigned got = 0;
+                        if (lane == 0) got = atomicAdd(&ctl->small_next, 32u);
+                        i0 = (int64_t)__shfl_sync(0xffffffffu, got, 0);
+                    } else {
+                        i0 = (gw + it * nw) * 32;
+                    }
+                    if (i0 >= nsm) break;
+                    small_group(i0, nsm);
                 }
             }
         }
@@ -1233,7 +1320,7 @@ static void batch_free(BatchWork *w) {
     dfree(w->kr); dfree(w->xs); dfree(w->thr32);
     for (int k = 0; k < 2; k++) dfree(w->cand[k]);
     for (int b = 0; b < 3; b++) { dfree(w->b_beg[b]); dfree(w->b_deg[b]); dfree(w->b_w[b]); dfree(w->b_seed[b]); }
-    dfree(w->hub_vstart); dfree(w->hub_cstart); dfree(w->tmp_beg); dfree(w->tmp_deg); dfree(w->tmp_w); dfree(w->tmp_jb);
+    dfree(w->hub_vstart); dfree(w->hub_cstart); dfree(w->grp_units); dfree(w->grp_off); dfree(w->tmp_beg); dfree(w->tmp_deg); dfree(w->tmp_w); dfree(w->tmp_jb);
     dfree(w->seg_cnt); dfree(w->seg_off); dfree(w->seg_cur); dfree(w->seg_hvol); dfree(w->vol_off);
     dfree(w->seg_hcur); dfree(w->seeds); dfree(w->status); dfree(w->inserts); dfree(w->svol);
     dfree(w->spushes); dfree(w->slast); dfree(w->spush); dfree(w->sscat); dfree(w->smass0); dfree(w->xlist); dfree(w->xcnt); dfree(w->glob); dfree(w->log);
@@ -1276,6 +1363,9 @@ static BatchWork *batch_work_alloc(int64_t nseeds, int64_t cap, int64_t list_cap
         }
         w->hub_vstart = (int64_t *)dmalloc(8 * (size_t)list_cap, "hub offsets");
         w->hub_cstart = (uint32_t *)dmalloc(4 * (size_t)kHubChunkTab, "hub chunk starts");
+        const size_t ngroups = (size_t)(nseeds + kSeedGroup - 1) / kSeedGroup + 1;
+        w->grp_units = (unsigned long long *)dmalloc(8 * ngroups, "seed group units");
+        w->grp_off = (unsigned long long *)dmalloc(8 * ngroups, "seed group units");
         w->tmp_beg = (int64_t *)dmalloc(8 * (size_t)list_cap, "push records");
         w->tmp_deg = (int32_t *)dmalloc(4 * (size_t)list_cap, "push records");
         w->tmp_w = (float *)dmalloc(4 * (size_t)list_cap, "push records");
@@ -1371,6 +1461,7 @@ static BArgs bargs_base(Graph &g, BatchWork *w, int64_t cap, int64_t list_cap, i
     a.list_cap = (unsigned)list_cap;
     for (int b = 0; b < 3; b++) { a.b_beg[b] = w->b_beg[b]; a.b_deg[b] = w->b_deg[b]; a.b_w[b] = w->b_w[b]; a.b_seed[b] = w->b_seed[b]; }
     a.hub_vstart = w->hub_vstart; a.hub_cstart = w->hub_cstart;
+    a.grp_units = w->grp_units; a.grp_off = w->grp_off;
     a.tmp_beg = w->tmp_beg; a.tmp_deg = w->tmp_deg; a.tmp_w = w->tmp_w; a.tmp_jb = w->tmp_jb;
     a.seg_cnt = w->seg_cnt; a.seg_off = w->seg_off; a.seg_cur = w->seg_cur;
     a.seg_hvol = w->seg_hvol; a.vol_off = w->vol_off; a.seg_hcur = w->seg_hcur;

@@ -229,7 +229,7 @@ def test_autotune_picks_a_valid_tuning(gde, rmat16):
     assert ms > 0
     assert best["t1"] in (4, 8, 16, 32) and best["t2"] in (128, 256, 512, 1024, 2048)
     assert best["t1"] <= best["t2"] and best["chunk"] in (256, 512, 1024, 2048, 4096)
-    assert best["schedule"] in (1, 2, 3) and best["blocks_per_sm"] in (0, 2, 3)
+    assert best["schedule"] in (1, 2, 3, 4) and best["blocks_per_sm"] in (0, 2, 3)
     assert G.get_tuning() == best and set(before) == set(best)
     st, stats, ids, vals = run_batched(gde, G, "ppr", 0.1, 1e-6, seeds)
     for i in (0, 31):
@@ -257,4 +257,22 @@ def test_many_seeds_small_graph(gde, c1):
             assert np.allclose(vals[i], vals[j], rtol=1e-5, atol=1e-7)
         else:
             first[s] = i
+    G.close()
+
+
+@pytest.mark.parametrize("schedule", [1, 2, 3, 4])
+def test_every_scatter_schedule(gde, rmat16, schedule):
+    """Every scatter order of the tuning (hub chunks handed out in order, all bins in order,
+    all strided, group by group of seeds) gives the oracle's answers, for PPR and the
+    layered heat kernel."""
+    g = rmat16
+    G = gde.Graph.from_synth(g)
+    G.set_tuning(t1=8, t2=64, chunk=256, schedule=schedule)
+    seeds = synth.seeds_mixed(g, 20, 20, seed=13)
+    for kind, param in (("ppr", 0.1), ("hk", 5.0)):
+        st, stats, ids, vals = run_batched(gde, G, kind, param, 1e-6, seeds)
+        assert st == gde.OK
+        for i in range(0, 40, 7):
+            ref = oracle.localgd(g, kind, param, 1e-6, int(seeds[i]))
+            check_topk(g, ids[i], vals[i], ref.x, 1e-6)
     G.close()
