@@ -79,7 +79,16 @@ struct BCtl {  // per-round counters (one set per round parity)
     // seed-grouped order: work units of all three bins, group by group
     unsigned long long unit_next;
     unsigned long long units_total;
+    unsigned int dmax_push;  // largest degree pushed this round
+    unsigned int pad2;
 };
+
+// A round with at most kDirectCand candidates, none of degree above kDirectMaxDeg, skips the
+// seed-ordered binning (two grid barriers and a one-block scan): each warp scatters whole
+// push records straight from the frontier's output.  The tail of a solve is dozens of such
+// rounds, where the fixed cost of the binning outweighs its locality.
+constexpr unsigned kDirectCand = 1u << 15;
+constexpr unsigned kDirectMaxDeg = 1u << 12;
 
 #ifndef GDE_SEED_GROUP
 #define GDE_SEED_GROUP 8
@@ -629,6 +638,7 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
         // candidate and counted per (degree bin, seed)
         double my_rs = 0.0;
         unsigned long long my_vol = 0;
+        unsigned my_dmax = 0;
         const int64_t ns = a.nseeds;
         for (int64_t ci = tid; ci < ncand; ci += nthreads) {
             const uint32_t slot = __ldcg(cand + ci);
@@ -717,6 +727,7 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
                 if (xb < a.xcap) __stcg(a.xlist + (uint64_t)j * a.xcap + xb, (uint32_t)xslot);
             }
             if (d == 0) { __stcg(a.tmp_deg + ci, 0); continue; }
+            my_dmax = my_dmax > (unsigned)d ? my_dmax : (unsigned)d;
             const int bin = d <= a.t1 ? 0 : (d <= a.t2 ? 1 : 2);
             __stcg(a.tmp_beg + ci, beg);
             __stcg(a.tmp_deg + ci, d);
@@ -734,20 +745,26 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
         {
             double rs = bwarp_sum(my_rs);
             unsigned long long vv = bwarp_sum(my_vol);
-            if (lane == 0) { s_rs[wid] = rs; s_vol[wid] = vv; }
+            unsigned dm = __reduce_max_sync(0xffffffffu, my_dmax);
+            if (lane == 0) { s_rs[wid] = rs; s_vol[wid] = vv; s_busy[wid] = dm; }
             __syncthreads();
             if (wid == 0) {
                 rs = lane < kWarps ? s_rs[lane] : 0.0;
                 vv = lane < kWarps ? s_vol[lane] : 0ull;
+                dm = lane < kWarps ? (unsigned)s_busy[lane] : 0u;
                 rs = bwarp_sum(rs);
                 vv = bwarp_sum(vv);
+                dm = __reduce_max_sync(0xffffffffu, dm);
                 if (lane == 0 && vv + (rs != 0.0)) {
                     atomicAdd(&ctl->rS_l1, rs);
                     atomicAdd(&ctl->vol, vv);
                 }
+                if (lane == 0 && dm > 0) atomicMax(&ctl->dmax_push, dm);
             }
         }
         if (!grid_sync(G, nblocks)) return;
+        const bool direct = ncand <= kDirectCand && __ldcg(&ctl->dmax_push) <= kDirectMaxDeg;
+        if (!direct) {
 
         // ---------------- phase S: segment offsets (one block) ----------------
         // the degree bins are laid out seed by seed, so the scatter phase sweeps the seeds
@@ -834,6 +851,7 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
             }
         }
         if (!grid_sync(G, nblocks)) return;
+        }  // !direct
         if (tid == 0 && lt < kLogCap) a.log[lt].tA_ns = globaltimer() - t_start;
         const unsigned long long tb0 = globaltimer();
 
@@ -856,7 +874,7 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
             prev->hub_packed = 0; prev->cnt_small = 0; prev->cnt_med = 0; prev->cand_out = 0;
             prev->n_active = 0; prev->vol = 0; prev->rS_l1 = 0.0; prev->overflow = 0;
             prev->hub_next = 0; prev->med_next = 0; prev->small_next = 0;
-            prev->unit_next = 0; prev->units_total = 0;
+            prev->unit_next = 0; prev->units_total = 0; prev->dmax_push = 0;
         }
         uint32_t *cand_out = a.cand[p ^ 1];
         if (__ldcg(&ctl->overflow)) {
@@ -935,7 +953,24 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
                     stage_flush(sbuf, sn, false, ctl, cand_out, a.list_cap);
                 }
             };
-            if (a.schedule == 3) {
+            if (direct) {
+                // the per-(bin, seed) counts of the frontier phase are not scanned this round
+                for (int64_t i = tid; i < 3 * ns; i += nthreads) a.seg_cnt[i] = 0;
+                for (int64_t i = tid; i < ns; i += nthreads) a.seg_hvol[i] = 0;
+                for (int64_t ci = gw; ci < ncand; ci += nw) {
+                    const int32_t d = __ldcg(a.tmp_deg + ci);
+                    if (d == 0) continue;
+                    const int64_t b = __ldcg(a.tmp_beg + ci);
+                    const float w = __ldcg(a.tmp_w + ci);
+                    const int32_t j = (int32_t)(__ldcg(a.tmp_jb + ci) & ((1u << 30) - 1u));
+                    const SlotMeta m = slot_meta<LAYERED>(a, j, t);
+                    for (int32_t k0 = 0; k0 < d; k0 += 32) {
+                        const int32_t k = k0 + lane;
+                        if (k < d) bscatter<LAYERED>(a, j, m, push_col(a, b + k), w, sbuf, sn);
+                        stage_flush(sbuf, sn, false, ctl, cand_out, a.list_cap);
+                    }
+                }
+            } else if (a.schedule == 3) {
                 // group by group of seeds: each group's hub chunks, medium grabs and small
                 // groups are consecutive work units, so a seed's table is brought into L2 once
                 // per round instead of once per bin
