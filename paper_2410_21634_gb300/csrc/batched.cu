@@ -159,6 +159,7 @@ struct BatchWork {
     double *sscat = nullptr;         // per seed: sum of scattered mass d_u w_u (FP64)
     double *smass0 = nullptr;        // per seed: the source's residual (1, or S_s when scaled)
     uint32_t *xlist = nullptr;       // per seed: xcap slots whose x is nonzero
+    uint32_t *xnode = nullptr;       // the node of each x-list entry (the top-k reads no key word)
     unsigned *xcnt = nullptr;        // per seed: x-list length (may exceed xcap: overflow)
     int64_t xcap = 0;
     BGlobal *glob = nullptr;
@@ -270,6 +271,7 @@ struct BArgs {
     uint32_t key_idmask;    // node-id bits of a table key
     uint32_t key_tag;       // this solve's epoch tag, already shifted above the id bits
     uint32_t *xlist;
+    uint32_t *xnode;
     unsigned *xcnt;
     unsigned xcap;
     double *spush;
@@ -724,7 +726,10 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
                 unsigned xb = 0;
                 if (lane == xl) xb = atomicAdd(a.xcnt + j, (unsigned)__popc(xpeers));
                 xb = __shfl_sync(xpeers, xb, xl) + __popc(xpeers & ((1u << lane) - 1u));
-                if (xb < a.xcap) __stcg(a.xlist + (uint64_t)j * a.xcap + xb, (uint32_t)xslot);
+                if (xb < a.xcap) {
+                    __stcg(a.xlist + (uint64_t)j * a.xcap + xb, (uint32_t)xslot);
+                    __stcg(a.xnode + (uint64_t)j * a.xcap + xb, (uint32_t)v);
+                }
             }
             if (d == 0) { __stcg(a.tmp_deg + ci, 0); continue; }
             my_dmax = my_dmax > (unsigned)d ? my_dmax : (unsigned)d;
@@ -1203,6 +1208,7 @@ struct TopkArgs {
     int64_t cap;
     uint32_t key_idmask;
     const uint32_t *xlist;
+    const uint32_t *xnode;      // node of each x-list entry
     const unsigned *xcnt;
     unsigned xcap;
     int k;
@@ -1231,10 +1237,11 @@ __global__ void __launch_bounds__(kThreads) k_batch_topk(TopkArgs a) {
         const int64_t i = i0 + lane;
         unsigned long long key = 0;
         if (i < n) {
-            const uint64_t slot = use_list ? (uint64_t)a.xlist[(uint64_t)j * a.xcap + i] : base + (uint64_t)i;
+            const uint64_t li = (uint64_t)j * a.xcap + i;
+            const uint64_t slot = use_list ? (uint64_t)a.xlist[li] : base + (uint64_t)i;
             const float x = a.xs[slot];
             if (x > 0.0f) {
-                const uint32_t v = (uint32_t)(a.kr[slot] & 0xFFFFFFFFull) & a.key_idmask;
+                const uint32_t v = use_list ? a.xnode[li] : (uint32_t)(a.kr[slot] & 0xFFFFFFFFull) & a.key_idmask;
                 key = ((unsigned long long)__float_as_uint(x) << 32) | (unsigned long long)(0xFFFFFFFFu - v);
                 if (!a.keep) a.xs[slot] = 0.0f;
                 support++;
@@ -1358,7 +1365,7 @@ static void batch_free(BatchWork *w) {
     dfree(w->hub_vstart); dfree(w->hub_cstart); dfree(w->grp_units); dfree(w->grp_off); dfree(w->tmp_beg); dfree(w->tmp_deg); dfree(w->tmp_w); dfree(w->tmp_jb);
     dfree(w->seg_cnt); dfree(w->seg_off); dfree(w->seg_cur); dfree(w->seg_hvol); dfree(w->vol_off);
     dfree(w->seg_hcur); dfree(w->seeds); dfree(w->status); dfree(w->inserts); dfree(w->svol);
-    dfree(w->spushes); dfree(w->slast); dfree(w->spush); dfree(w->sscat); dfree(w->smass0); dfree(w->xlist); dfree(w->xcnt); dfree(w->glob); dfree(w->log);
+    dfree(w->spushes); dfree(w->slast); dfree(w->spush); dfree(w->sscat); dfree(w->smass0); dfree(w->xlist); dfree(w->xnode); dfree(w->xcnt); dfree(w->glob); dfree(w->log);
     dfree(w->xkr); dfree(w->xxs); dfree(w->layer_eps); dfree(w->layer_coef);
     delete w;
 }
@@ -1422,6 +1429,7 @@ static BatchWork *batch_work_alloc(int64_t nseeds, int64_t cap, int64_t list_cap
         w->smass0 = (double *)dmalloc(8 * (size_t)nseeds, "seed source mass");
         w->xcap = cap < xcap_max ? cap : xcap_max;
         w->xlist = (uint32_t *)dmalloc(4 * (size_t)nseeds * (size_t)w->xcap, "x lists");
+        w->xnode = (uint32_t *)dmalloc(4 * (size_t)nseeds * (size_t)w->xcap, "x lists");
         w->xcnt = (unsigned *)dmalloc(4 * (size_t)nseeds, "x list lengths");
         w->glob = (BGlobal *)dmalloc(sizeof(BGlobal), "batch control");
         w->log = (RoundLog *)dmalloc(sizeof(RoundLog) * kLogCap, "round log");
@@ -1486,7 +1494,7 @@ static BArgs bargs_base(Graph &g, BatchWork *w, int64_t cap, int64_t list_cap, i
     a.code_exact = g.colp_exact;
     a.thr_stride = g.n;
     a.key_idmask = key_idmask; a.key_tag = key_tag;
-    a.xlist = w->xlist; a.xcnt = w->xcnt; a.xcap = (unsigned)w->xcap;
+    a.xlist = w->xlist; a.xnode = w->xnode; a.xcnt = w->xcnt; a.xcap = (unsigned)w->xcap;
     a.spush = w->spush; a.sscat = w->sscat;
     a.log2cap = w->log2cap; a.mask = (uint32_t)(cap - 1); a.nseeds = nseeds;
     a.status = w->status; a.inserts = w->inserts;
@@ -1693,7 +1701,8 @@ static void batch_solve_once(Graph &g, const SolveParams &p, const int32_t *seed
 
     TopkArgs ta{};
     ta.kr = w->kr; ta.xs = w->xs; ta.log2cap = w->log2cap; ta.cap = cap; ta.k = k;
-    ta.key_idmask = key_idmask; ta.xlist = w->xlist; ta.xcnt = w->xcnt; ta.xcap = (unsigned)w->xcap;
+    ta.key_idmask = key_idmask; ta.xlist = w->xlist; ta.xnode = w->xnode; ta.xcnt = w->xcnt;
+    ta.xcap = (unsigned)w->xcap;
     ta.out_ids = ids_dev; ta.out_vals = vals_dev; ta.ssupport = w->inserts;
     if (lay) {
         // x lives in the x tables; the output is e^-tau x (heat kernel) or c_0 x (series)
@@ -2059,10 +2068,11 @@ __global__ void __launch_bounds__(kThreads) k_serve_topk_partial(TopkArgs a, uns
         const int64_t i = i0 + lane;
         unsigned long long key = 0;
         if (i < hi) {
-            const uint64_t slot = use_list ? (uint64_t)a.xlist[(uint64_t)j * a.xcap + i] : base + (uint64_t)i;
+            const uint64_t li = (uint64_t)j * a.xcap + i;
+            const uint64_t slot = use_list ? (uint64_t)a.xlist[li] : base + (uint64_t)i;
             const float x = a.xs[slot];
             if (x > 0.0f) {
-                const uint32_t v = (uint32_t)(a.kr[slot] & 0xFFFFFFFFull) & a.key_idmask;
+                const uint32_t v = use_list ? a.xnode[li] : (uint32_t)(a.kr[slot] & 0xFFFFFFFFull) & a.key_idmask;
                 key = ((unsigned long long)__float_as_uint(x) << 32) | (unsigned long long)(0xFFFFFFFFu - v);
             }
         }
@@ -2350,7 +2360,8 @@ void serve_pool_results(Graph &g, ServePool *P, int32_t n, const int32_t *slots,
     GDE_CUDA(cudaMemcpyAsync(P->d_list, slots, 4 * (size_t)n, cudaMemcpyHostToDevice, s));
     TopkArgs ta{};
     ta.kr = P->w->kr; ta.xs = P->w->xs; ta.log2cap = P->w->log2cap; ta.cap = P->cap; ta.k = k;
-    ta.key_idmask = P->key_idmask; ta.xlist = P->w->xlist; ta.xcnt = P->w->xcnt; ta.xcap = (unsigned)P->w->xcap;
+    ta.key_idmask = P->key_idmask; ta.xlist = P->w->xlist; ta.xnode = P->w->xnode; ta.xcnt = P->w->xcnt;
+    ta.xcap = (unsigned)P->w->xcap;
     ta.out_ids = P->d_ids; ta.out_vals = P->d_vals; ta.ssupport = P->w->inserts;
     ta.slots = P->d_list; ta.keep = 1;
     k_serve_topk_partial<<<(unsigned)(n * kServeTopkParts), kThreads, 0, s>>>(ta, P->d_partial);
