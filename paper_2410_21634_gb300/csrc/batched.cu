@@ -8,17 +8,22 @@
 //             key = node id | epoch tag << idbits; a slot whose tag is not the current
 //             solve's (or 0xFFFFFFFF) is empty, so tables need no reset between solves
 //   xs[slot]  float x of that node (zero outside the current solve's x-lists)
-//   xlist     per seed, the slots whose x became nonzero (appended on first activation);
-//             the top-k reads only these and zeroes their x
+//   xlist     per seed, the slots whose x became nonzero (appended on first activation),
+//             with each one's node id beside it (xnode); the top-k reads only these and
+//             zeroes their x
 // seed j owns slots [j*cap, (j+1)*cap); a slot index therefore names its seed (slot >> log2cap).
-// thr32[v] = fl(eps d_v) rounded up to float (one array shared by all seeds).
+// thr32[v] = fl(eps d_v) rounded up to float (one array per tolerance class, all seeds).
+// The layered kinds (heat kernel, series) give each layer its own key tag and keep x in a
+// second per-seed table (xkr / xxs), since a layer's slots are reused by the next layer.
 //
-// Rounds run inside one cooperative kernel: phase A builds S_t for every seed from the
+// Rounds run inside one cooperative kernel: phase A1 builds S_t for every seed from the
 // candidate list (slots whose residual crossed its threshold in the previous round), zeroes
-// r on S_t, adds to x and bins the pushes by degree into lists pooled over all seeds; a grid
-// barrier; phase B scatters every push into its seed's table (insert-or-add) and appends
-// threshold crossings to the next candidate list; a grid barrier.  Every grid-barrier wait
-// is bounded by a time limit after which the kernel records GDE_ETIMEOUT and returns.
+// r on S_t, adds to x and records the pushes; phases S and A2 count, scan and place them by
+// degree bin, seed by seed, into lists pooled over all seeds (skipped in small rounds, which
+// scatter straight from the records); phase B scatters every push into its seed's table
+// (insert-or-add) and appends threshold crossings to the next candidate list.  Grid
+// barriers separate the phases; every wait is bounded by a time limit after which the
+// kernel records GDE_ETIMEOUT and returns.
 #include <cooperative_groups.h>
 #include <cooperative_groups/scan.h>
 
