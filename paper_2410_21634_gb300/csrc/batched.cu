@@ -92,8 +92,14 @@ struct BCtl {  // per-round counters (one set per round parity)
 // seed-ordered binning (two grid barriers and a one-block scan): each warp scatters whole
 // push records straight from the frontier's output.  The tail of a solve is dozens of such
 // rounds, where the fixed cost of the binning outweighs its locality.
-constexpr unsigned kDirectCand = 1u << 15;
-constexpr unsigned kDirectMaxDeg = 1u << 12;
+#ifndef GDE_DIRECT_CAND_LOG2
+#define GDE_DIRECT_CAND_LOG2 15
+#endif
+#ifndef GDE_DIRECT_DEG_LOG2
+#define GDE_DIRECT_DEG_LOG2 12
+#endif
+constexpr unsigned kDirectCand = 1u << GDE_DIRECT_CAND_LOG2;
+constexpr unsigned kDirectMaxDeg = 1u << GDE_DIRECT_DEG_LOG2;
 
 #ifndef GDE_SEED_GROUP
 #define GDE_SEED_GROUP 8
