@@ -333,6 +333,7 @@ def run_serving(gde, seconds, slots, rounds_per_step, g=None, beta=None, budget_
         "throughput_qps": lat.size / elapsed, "offered_qps": SERVE["rate_qps"],
         "elapsed_s": elapsed, "edge_batches": info["edge_batches"], "steps": steps,
         "rounds": info["rounds"], "slots": slots, "rounds_per_step": rounds_per_step,
+        "defer_volume": defer_volume if defer_volume != 0 else 1 << 23,
         "slot_cap": info["cap"], "pool_gb": round(budget / 2**30, 1), "pushed_edges": info["volume"],
         "step_seconds": {k: round(info[k], 4) for k in ("t_graph", "t_correct", "t_admit", "t_rounds", "t_results")}, "pushed_edges_first_answers": int(vol),
     }
