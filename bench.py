@@ -66,6 +66,8 @@ def parse():
                     help="skip the random-access calibration of device memory")
     ap.add_argument("--random-probe", action="store_true",
                     help="only run the random-access calibration and print its JSON line")
+    ap.add_argument("--serving-only", action="store_true",
+                    help="only run the serving workload (--serve-seconds of arrivals) and print its JSON line")
     ap.add_argument("--probe-gb", type=float, default=16.0, help="buffer of the random-access calibration")
     ap.add_argument("--probe-l2-fetch", type=int, default=0,
                     help="L2 fetch-granularity limit during the calibration (0: leave it alone)")
@@ -456,6 +458,14 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.serving_only:
+        import torch
+        import paper_2410_21634_gb300 as gde
+        torch.cuda.set_device(0)
+        gde.load()
+        serving = run_serving(gde, args.serve_seconds, SERVE_SLOTS, SERVE_ROUNDS_PER_STEP)
+        print(json.dumps({"serving": serving}), flush=True)
+        return 0
     if args.random_probe:
         import torch
         import paper_2410_21634_gb300 as gde
