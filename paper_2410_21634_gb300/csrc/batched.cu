@@ -329,6 +329,7 @@ struct BArgs {
                         // entries together, so a seed's table is brought into L2 once per round
     unsigned long long *grp_units;  // per seed group: its work units (schedule 3)
     unsigned long long *grp_off;    // their exclusive prefix sums
+    unsigned *pend;     // not NULL: receives per seed the candidates left for the next launch
     // layered kinds (heat kernel, general series): round t reads layer t and writes layer t+1;
     // the keys of layer t carry key_tag + t * tag_step, so a layer's keys read as free slots
     // once the next layer is written, and x lives in a separate per-seed table keyed by node
@@ -637,6 +638,13 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
     }
     __syncthreads();
 
+    // per-seed count of the candidates this launch leaves behind (a server's unfinished
+    // queries): zeroed here, filled after the last round; every round's grid barriers order
+    // the two
+    if (a.pend && a.max_rounds > 0)
+        for (int64_t j = tid; j < a.nseeds; j += nthreads) a.pend[j] = 0u;
+    int last_p = -1;         // parity of the last round run
+    unsigned last_next = 0;  // its candidates for the next round
     for (int64_t t = a.t0; t < a.t0 + a.max_rounds; t++) {
         const int64_t lt = t - a.t0;  // round of this launch (log row)
         const int p = (int)(t & 1);
@@ -1114,7 +1122,13 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
             }
             if (ovf || next > a.list_cap) atomicCAS(&G->error, 0u, (unsigned)GDE_ENOMEM);
         }
+        last_p = p;
+        last_next = next <= a.list_cap ? next : a.list_cap;
         if (next == 0 || next > a.list_cap || ovf) break;
+    }
+    if (a.pend && last_p >= 0) {
+        const uint32_t *left = a.cand[last_p ^ 1];
+        for (int64_t i = tid; i < (int64_t)last_next; i += nthreads) atomicAdd(a.pend + (__ldcg(left + i) >> a.log2cap), 1u);
     }
 }
 
@@ -1825,6 +1839,8 @@ struct ServePool {
     int64_t defer_vol = (int64_t)1 << 23;
     std::vector<unsigned long long> last_vol;  // per slot: its pushed volume after the last launch
     std::vector<uint8_t> heavy;
+    std::vector<unsigned> h_pend;  // per slot: candidates the last launch left (when pend_valid)
+    bool pend_valid = false;       // cleared by anything that changes the candidate list
 };
 
 // device view of one slot table's probing, shared by the admission and correction kernels
@@ -2224,6 +2240,7 @@ static void serve_ensure_graph_state(Graph &g, ServePool *P) {
 void serve_pool_admit(Graph &g, ServePool *P, int32_t n, const int32_t *slots, const int32_t *seeds,
                       const gde_kind *kinds, const double *params, const int32_t *cls) {
     if (n <= 0) return;
+    P->pend_valid = false;
     cudaStream_t s = P->s;
     for (int32_t i = 0; i < n; i++) {
         GDE_REQUIRE(slots[i] >= 0 && slots[i] < P->slots, GDE_EINVAL, "slot out of range");
@@ -2289,6 +2306,7 @@ void serve_pool_admit(Graph &g, ServePool *P, int32_t n, const int32_t *slots, c
 
 void serve_pool_correct(Graph &g, ServePool *P, const EdgeBatch &eb, int32_t nres, const int32_t *res) {
     if (nres <= 0 || eb.rows <= 0) return;
+    P->pend_valid = false;
     serve_ensure_graph_state(g, P);
     GDE_CUDA(cudaMemcpyAsync(P->d_list, res, 4 * (size_t)nres, cudaMemcpyHostToDevice, P->s));
     CorrectArgs a{};
@@ -2306,6 +2324,7 @@ void serve_pool_correct(Graph &g, ServePool *P, const EdgeBatch &eb, int32_t nre
 }
 
 int64_t serve_pool_run(Graph &g, ServePool *P, int64_t rounds) {
+    P->pend_valid = false;
     serve_ensure_graph_state(g, P);
     BatchWork *w = P->w;
     // heavy slots (by their volume in the last launch) run one round of this launch
@@ -2329,6 +2348,7 @@ int64_t serve_pool_run(Graph &g, ServePool *P, int64_t rounds) {
     a.sparam = P->d_param;
     a.t0 = P->T;
     a.max_rounds = rounds;
+    a.pend = P->pend;
     a.kind = GDE_PPR;
     a.cx = 0.0;
     a.coef = 0.0;
@@ -2337,7 +2357,10 @@ int64_t serve_pool_run(Graph &g, ServePool *P, int64_t rounds) {
     GDE_CUDA(cudaMemcpyAsync(&hg, w->glob, sizeof(BGlobal), cudaMemcpyDeviceToHost, P->s));
     std::vector<unsigned long long> vol((size_t)P->slots);
     GDE_CUDA(cudaMemcpyAsync(vol.data(), w->svol, 8 * (size_t)P->slots, cudaMemcpyDeviceToHost, P->s));
+    P->h_pend.resize((size_t)P->slots);
+    GDE_CUDA(cudaMemcpyAsync(P->h_pend.data(), P->pend, 4 * (size_t)P->slots, cudaMemcpyDeviceToHost, P->s));
     GDE_CUDA(cudaStreamSynchronize(P->s));
+    P->pend_valid = true;
     for (int32_t j = 0; j < P->slots; j++) {
         const unsigned long long prev = P->last_vol[(size_t)j], now = vol[(size_t)j];
         const unsigned long long delta = now >= prev ? now - prev : now;  // re-admitted: counted anew
@@ -2354,6 +2377,10 @@ int64_t serve_pool_run(Graph &g, ServePool *P, int64_t rounds) {
 int64_t serve_pool_volume(const ServePool *P) { return P->volume; }
 
 void serve_pool_pending(Graph &g, ServePool *P, unsigned *pend_host) {
+    if (P->pend_valid) {  // counted by the launch that just ran
+        std::copy(P->h_pend.begin(), P->h_pend.end(), pend_host);
+        return;
+    }
     GDE_CUDA(cudaMemsetAsync(P->pend, 0, 4 * (size_t)P->slots, P->s));
     k_serve_pending<<<kSMs * 2, kThreads, 0, P->s>>>(next_count(P), (unsigned)P->list_cap, P->w->cand[P->T & 1],
                                                       P->w->log2cap, P->pend);
