@@ -573,7 +573,7 @@ def main():
     ids_h = torch.zeros((nseeds, TOPK), dtype=torch.int32).pin_memory()
     vals_h = torch.zeros((nseeds, TOPK), dtype=torch.float32).pin_memory()
     ids_hn, vals_hn, seeds_hn = ids_h.numpy(), vals_h.numpy(), seeds_host.numpy()
-    e2e_steps = max(3, min(args.steps, 10))
+    e2e_steps = max(3, min(args.steps, 20))
     gde.solve(G, "ppr", ALPHA, EPS, seeds_hn, vals_hn, ids_hn, precision="fp32", topk=TOPK, batched=1,
               mem_budget_bytes=budget)
     t0 = time.perf_counter()

@@ -264,6 +264,7 @@ gde_status gde_graph_destroy(gde_graph *h) {
     dfree(g.col);
     dfree(g.deg);
     dfree(g.colp);
+    for (void *q : g.stage_buf) dfree(q);
     if (g.stream) cudaStreamDestroy(g.stream);
     delete h;
     return GDE_OK;
@@ -336,15 +337,26 @@ gde_status gde_solve(gde_graph *h, gde_kind kind, double param, double eps, cons
 
     const size_t rsz = p.precision == GDE_FP64 ? 8 : 4;
     const int k = o.topk;
-    // device views of the outputs (staging buffers for host pointers)
-    std::vector<void *> owned;
+    // device views of the outputs (staging buffers for host pointers, reused across calls:
+    // the graph's lock is held, so no other call on g uses them meanwhile)
+    size_t nstaged = 0;
     auto stage = [&](size_t bytes, const char *what) {
-        void *q = dmalloc(bytes, what);
-        owned.push_back(q);
-        return q;
+        const size_t i = nstaged++;
+        if (g.stage_buf.size() <= i) {
+            g.stage_buf.push_back(nullptr);
+            g.stage_cap.push_back(0);
+        }
+        if (g.stage_cap[i] < bytes) {
+            dfree(g.stage_buf[i]);
+            g.stage_buf[i] = nullptr;
+            g.stage_cap[i] = 0;
+            g.stage_buf[i] = dmalloc(bytes, what);
+            g.stage_cap[i] = bytes;
+        }
+        return g.stage_buf[i];
     };
     gde_status worst = GDE_OK;
-    try {
+    {
         std::vector<gde_stats> st((size_t)nseeds);
         std::vector<int32_t> todo;  // seeds solved one at a time with dense x and r
         int32_t *ids_dev = nullptr;
@@ -440,11 +452,7 @@ gde_status gde_solve(gde_graph *h, gde_kind kind, double param, double eps, cons
             if (st[(size_t)i].status != GDE_OK) worst = (gde_status)st[(size_t)i].status;
             if (stats) stats[i] = st[(size_t)i];
         }
-    } catch (...) {
-        for (void *q : owned) dfree(q);
-        throw;
     }
-    for (void *q : owned) dfree(q);
     if (worst != GDE_OK) {
         set_error("round cap reached before the active set became empty");
         return worst;

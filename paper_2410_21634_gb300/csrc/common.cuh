@@ -94,6 +94,10 @@ struct Graph {
     // batch keeps it current when the graph was verified symmetric, else drops it.
     uint32_t *colp = nullptr;
     int64_t colp_cap = 0;      // entries the packed array can hold
+    // device staging for gde_solve calls with host pointers, kept between calls (a call
+    // takes its buffers in a fixed order, growing one only when a larger call needs it)
+    std::vector<void *> stage_buf;
+    std::vector<size_t> stage_cap;
     int colp_idbits = 0;       // 0: no packing (n too large), thresholds are read per edge
     int colp_exact = 0;
     bool colp_valid = false;   // packed from the current CSR
