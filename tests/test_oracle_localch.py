@@ -31,7 +31,9 @@ def test_invariant_and_bound(gi, eps):
     Q = np.eye(g.n) - (1 - alpha) * dense.walk_matrix(g)
     for s in (int(np.argmax(g.degrees())), 0):
         x, r, rounds, vol = oracle.localch(g, alpha, eps, s)
-        assert np.max(np.abs(Q @ x / alpha + r - dense.unit(g.n, s))) < 1e-12
+        with np.errstate(invalid="ignore", over="ignore"):  # a planted mistake may diverge
+            err = np.max(np.abs(Q @ x / alpha + r - dense.unit(g.n, s)))
+        assert err < 1e-12
         assert np.all((np.abs(r) < eps * g.degrees()) | (r == 0))
         f = dense.ppr(g, alpha, s)
         assert np.all(np.abs(f - x) < eps * d)
