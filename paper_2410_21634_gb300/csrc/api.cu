@@ -393,10 +393,10 @@ gde_status gde_solve(gde_graph *h, gde_kind kind, double param, double eps, cons
             std::vector<int32_t> of((size_t)nseeds);
             int32_t nof = 0;
             int64_t budget = o.mem_budget_bytes;
-            if (budget <= 0 && layered(kind)) {
-                // the first layers of the layered kinds touch several times the nodes of a
-                // PPR round: up to 64 GiB of tables, half the free device memory, at least
-                // the 16 GiB that the other kinds default to
+            if (budget <= 0 && (layered(kind) || kind == GDE_KATZ)) {
+                // the first layers of the layered kinds, and a Katz vector from a hub, touch
+                // several times the nodes of a PPR solve: up to 64 GiB of tables, half the
+                // free device memory, at least the 16 GiB that PPR defaults to
                 size_t free_b = 0, total_b = 0;
                 GDE_CUDA(cudaMemGetInfo(&free_b, &total_b));
                 budget = std::min<int64_t>((int64_t)64 << 30, (int64_t)(free_b / 2));
