@@ -131,3 +131,26 @@ def test_overflow_falls_back(gde, rmat16):
         ref = oracle.localgd(g, "hk", 5.0, 1e-6, int(seeds[i]))
         check_topk(g, ids[i], vals[i], ref.x, 1e-6)
     G.close()
+
+
+def test_isolated_duplicate_and_padding(gde):
+    """An isolated seed keeps its unit mass: e^-tau at the seed for the heat kernel and c_0
+    for a series, nothing else.  A repeated seed gives the same list twice, and a support
+    smaller than k pads with -1."""
+    g = synth.with_isolated(synth.star(5), 2)  # nodes 6, 7 isolated
+    G = gde.Graph.from_synth(g)
+    seeds = np.array([6, 0, 0, 3], dtype=np.int32)
+    tau = 2.0
+    st, stats, ids, vals = run_batched(gde, G, "hk", tau, 1e-4, seeds, k=8)
+    assert st == gde.OK
+    assert ids[0, 0] == 6 and vals[0, 0] == pytest.approx(math.exp(-tau), rel=1e-6)
+    assert np.all(ids[0, 1:] == -1) and np.all(vals[0, 1:] == 0)
+    assert np.array_equal(ids[1], ids[2]) and np.allclose(vals[1], vals[2])
+    for i in (1, 3):
+        ref = oracle.localgd(g, "hk", tau, 1e-4, int(seeds[i]))
+        check_topk(g, ids[i], vals[i], ref.x, 1e-4, k=8)
+        assert np.all(ids[i, 6:] == -1)  # the star has 6 nodes
+    c = np.array([0.5, 0.25, 0.125, 0.0625])
+    st, stats, ids, vals = run_batched(gde, G, "series", 0.0, 1e-4, seeds[:1], k=8, series_coef=c)
+    assert st == gde.OK and ids[0, 0] == 6 and vals[0, 0] == pytest.approx(0.5, rel=1e-6)
+    G.close()
