@@ -92,9 +92,10 @@ typedef struct {
     uint32_t flags;          /* GDE_DEVICE_PTRS: seeds and outputs are device pointers */
     int64_t max_rounds;      /* round cap; 0 (default) means 1,000,000 */
     int64_t mem_budget_bytes;/* batched: bytes for the hash accumulators (12 per slot, 18 for
-                                the layered kinds); 0 = automatic: 16 GiB for PPR and the
-                                generalised propagation, up to 64 GiB (half the free device
-                                memory) for Katz and the layered kinds */
+                                the layered kinds); 0 = automatic: up to 32 GiB for PPR and
+                                the generalised propagation, up to 64 GiB for Katz and the
+                                layered kinds (half the free device memory at most, 16 GiB
+                                at least) */
     double hk_tol;           /* HK Taylor tail tolerance; 0 (default) means 1e-12 */
     void *cuda_stream;       /* borrowed cudaStream_t to run on; NULL = the graph's stream */
     double prop_beta;        /* GDE_GPPR: the exponent b in [0, 1] of M = D^-b A D^(b-1) */

