@@ -560,6 +560,7 @@ def main():
         tj = json.load(open(tp))
         src = open(os.path.join(ROOT, "paper_2410_21634_gb300", "csrc", "batched.cu"), "rb").read()
         if (tj.get("kernel") == "k_batch_rounds" and tj.get("graph") == g.name and tj.get("seeds") == nseeds
+                and tj.get("budget_arg_gb") == args.budget_gb
                 and tj.get("source_sha256") == hashlib.sha256(src).hexdigest()):
             traffic = tj.get("bytes_per_launch")
     roofline = {"bound": "hbm", "kernel": "k_batch_rounds", "achieved": achieved, "peak": peak,
