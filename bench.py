@@ -33,12 +33,18 @@ if ROOT not in sys.path:
 
 METRIC = "GTEPS & seeds/s at eps=1e-7, % HBM peak; batched FP32 vs plain FP64 on same GPU"
 ALPHA, EPS, TOPK = 0.1, 1e-7, 64
-# algorithmic bytes of the persistent round kernel (hash accumulators, FP32):
-# per pushed edge: column id 4 + slot word read 8 + residual write 4 + threshold 4
-BYTES_PER_EDGE = 20
-# per pushed node: candidate 4 + slot word 8 + residual zero 4 + x read/write 8 + threshold 4
-# + row offsets 16 + degree-bin entry written and read 2*20 + candidate append 4
-BYTES_PER_PUSH = 88
+# algorithmic bytes of the persistent round kernel (FP32 hash accumulators), the method's own
+# traffic: sum over rounds of |S_t| B_node + vol(S_t) B_edge + |C_t| B_cand
+# per pushed edge: column id 4 + the 8-byte slot word read and its residual written back 4
+BYTES_PER_EDGE = 16
+# per pushed node: row offsets 16 + frontier record written and read 2 x 12 + x read and
+# written 8 + residual zeroed 8 + candidate entry 4 + its append 4
+BYTES_PER_PUSH = 64
+# per candidate test: its slot word 8 + row offsets 16
+BYTES_PER_CAND = 24
+# the kernel's own finer model (threshold reads per edge, the degree-bin entries written and
+# read by the seed-ordered placement), reported beside it
+KERNEL_BYTES_PER_EDGE, KERNEL_BYTES_PER_PUSH = 20, 88
 
 
 def log(*a):
@@ -550,8 +556,13 @@ def main():
     peak, peak_kind = measured_peaks()
     launches = max(prof["batch_launches"], 1)
     k_ms = prof["batch_rounds_ms"] / launches
-    alg_bytes = (BYTES_PER_EDGE * prof["edges"] + BYTES_PER_PUSH * prof["pushes"]) / launches
+    # candidates tested per launch: the kernel's round log of the last solve (all steps are the
+    # same solve)
+    cands = float(G.profile_rounds()[:, 0].sum())
+    alg_bytes = (BYTES_PER_EDGE * prof["edges"] + BYTES_PER_PUSH * prof["pushes"]) / launches \
+        + BYTES_PER_CAND * cands
     achieved = alg_bytes / (k_ms / 1e3) / 1e9
+    kernel_bytes = (KERNEL_BYTES_PER_EDGE * prof["edges"] + KERNEL_BYTES_PER_PUSH * prof["pushes"]) / launches
     traffic = None
     tp = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tp):
@@ -567,6 +578,12 @@ def main():
                 "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                 "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
                 "kernel_ms": k_ms, "alg_bytes_per_launch": alg_bytes,
+                "bytes_model": f"{BYTES_PER_EDGE} B per pushed edge, {BYTES_PER_PUSH} B per pushed node, "
+                               f"{BYTES_PER_CAND} B per candidate",
+                "edges_per_launch": prof["edges"] / launches, "pushes_per_launch": prof["pushes"] / launches,
+                "candidates_per_launch": cands,
+                "frac_kernel_model": kernel_bytes / (k_ms / 1e3) / 1e9 / peak,
+                "traffic_over_alg": traffic / alg_bytes if traffic else None,
                 "share_of_step": prof["batch_rounds_ms"] / ms if ms > 0 else None}
 
     # end to end through the public API with host buffers (seeds in, top-k out)

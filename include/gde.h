@@ -331,6 +331,41 @@ gde_status gde_session_read(gde_session *s, void *x, void *r, int32_t *active, i
 gde_status gde_session_end(gde_session *s);
 
 /*
+ * Batched stepping interface: one round of the batched engine per call, for every seed of a
+ * batch at once (Eq. local-gd, Section 3.3, run for all seeds together), with the per-seed
+ * hash tables copied to the host between rounds, so that the batched engine can be compared
+ * with the CPU oracle round by round.  It launches the persistent round kernel of
+ * gde_solve's batched mode with a one-round cap, from the state the previous launch left.
+ *   kind, param, eps, opts  as for gde_solve's batched mode: opts->precision must be GDE_FP32;
+ *                hk_threshold, hk_tol, prop_beta, series_coef are honoured;
+ *                opts->mem_budget_bytes sizes the tables (0: 4 GiB; at most 2n slots a table)
+ *   seeds        nseeds >= 1 node ids in [0, n), a host array (GDE_DEVICE_PTRS: GDE_EINVAL)
+ *   gde_bsession_begin  x = 0, r = e_s (the heat kernel and series: layer 0) for every seed
+ *   gde_bsession_step   runs the next round t of every seed; *n_candidates (may be NULL)
+ *                       receives the candidates of round t + 1, all seeds together (0: every
+ *                       active set is empty and further steps change nothing)
+ *   gde_bsession_read   seed index j in [0, nseeds): x (n floats: the engine's x before any
+ *                       output scaling), r (n floats: the residual, for the heat kernel and
+ *                       series the layer the next round reads) as of the last step, and the
+ *                       node ids the last step pushed (S_t of seed j, unordered, up to n ints;
+ *                       *n_pushed receives how many); host buffers, any pointer may be NULL.
+ *                       Returns GDE_ENOMEM when that seed's table overflowed (its state is
+ *                       then incomplete).
+ * The session owns its device workspace (the graph's cached batched workspace is not
+ * touched) and borrows the graph, which must outlive it and must not change while it runs
+ * (a step after an edge insertion returns GDE_EINVAL).  Every step synchronises and copies
+ * the whole pool (12 bytes per table slot, 18 for the layered kinds) to the host: a testing
+ * interface, not a fast path.  gde_bsession_end releases everything (NULL is a no-op).
+ */
+typedef struct gde_bsession gde_bsession;
+gde_status gde_bsession_begin(gde_graph *g, gde_kind kind, double param, double eps, const int32_t *seeds,
+                              int32_t nseeds, const gde_solve_opts *opts, gde_bsession **out);
+gde_status gde_bsession_step(gde_bsession *s, int64_t *n_candidates);
+gde_status gde_bsession_read(gde_bsession *s, int32_t seed_index, float *x, float *r, int32_t *pushed,
+                             int64_t *n_pushed);
+gde_status gde_bsession_end(gde_bsession *s);
+
+/*
  * Serving (continuous batching of PPR and Katz queries on a graph that receives edge
  * insertions; the dynamic setting of Section 4).  A server owns a pool of `slots` resident
  * queries, each a per-query hash table of FP32 x and r in device memory (12 bytes per

@@ -34,7 +34,8 @@ EXPORTED = ["gde_solve_opts_init", "gde_graph_create", "gde_graph_destroy", "gde
             "gde_autotune", "gde_update_edges", "gde_graph_csr", "gde_server_opts_init",
             "gde_server_clock", "gde_server_create", "gde_server_destroy", "gde_server_submit",
             "gde_server_insert_edges", "gde_server_step", "gde_server_poll", "gde_server_info",
-            "gde_probe_random_access"]
+            "gde_probe_random_access", "gde_bsession_begin", "gde_bsession_step", "gde_bsession_read",
+            "gde_bsession_end"]
 
 
 class GdeError(RuntimeError):
@@ -131,6 +132,13 @@ def load(path: str | None = None):
     lib.gde_session_step.argtypes = [vp, ctypes.POINTER(I64)]
     lib.gde_session_read.argtypes = [vp, vp, vp, vp, ctypes.POINTER(I64)]
     lib.gde_session_end.argtypes = [vp]
+    lib.gde_bsession_begin.argtypes = [vp, ctypes.c_int, D, D, vp, I32, ctypes.POINTER(SolveOpts),
+                                       ctypes.POINTER(vp)]
+    lib.gde_bsession_step.argtypes = [vp, ctypes.POINTER(I64)]
+    lib.gde_bsession_read.argtypes = [vp, I32, vp, vp, vp, ctypes.POINTER(I64)]
+    lib.gde_bsession_end.argtypes = [vp]
+    for name in ("gde_bsession_begin", "gde_bsession_step", "gde_bsession_read", "gde_bsession_end"):
+        getattr(lib, name).restype = ctypes.c_int
     lib.gde_topk_f32_noalloc.argtypes = [vp, I64, I32, vp, vp, vp]
     lib.gde_topk_f32_noalloc.restype = ctypes.c_int
     lib.gde_profile_rounds.argtypes = [vp, vp, I64, ctypes.POINTER(I64)]
@@ -359,17 +367,37 @@ def solve(graph: Graph, kind, param: float, eps: float, seeds, out_x, out_ids=No
     return st, ([st_arr[i].as_dict() for i in range(nseeds)] if stats else [])
 
 
+def _check_topk_noalloc_args(x, k, out_ids, out_vals):
+    """The checks the C entry point cannot make (it sees only pointers): tensor kinds, dtypes,
+    output sizes and one common device.  Raises ValueError."""
+    for name, a in (("x", x), ("out_ids", out_ids), ("out_vals", out_vals)):
+        if not _is_cuda_tensor(a):
+            raise ValueError(f"topk_noalloc: {name} must be a CUDA tensor")
+        if not a.is_contiguous():
+            raise ValueError(f"topk_noalloc: {name} must be contiguous")
+    if str(x.dtype) != "torch.float32" or str(out_vals.dtype) != "torch.float32":
+        raise ValueError("topk_noalloc: x and out_vals must be float32")
+    if str(out_ids.dtype) != "torch.int32":
+        raise ValueError("topk_noalloc: out_ids must be int32")
+    k = int(k)
+    if out_ids.numel() < k or out_vals.numel() < k:
+        raise ValueError(f"topk_noalloc: out_ids and out_vals need at least k = {k} elements")
+    if not (x.device == out_ids.device == out_vals.device):
+        raise ValueError("topk_noalloc: x, out_ids and out_vals must be on one device")
+
+
 def topk_noalloc(x, k: int, out_ids, out_vals, stream=None):
     """gde_topk_f32_noalloc: top-k of a dense float CUDA vector without device allocation.
-    x, out_ids (int32, k) and out_vals (float32, k) must be contiguous CUDA tensors; the call
-    is asynchronous on `stream` (default: torch's current stream)."""
-    for a in (x, out_ids, out_vals):
-        if not _is_cuda_tensor(a):
-            raise ValueError("topk_noalloc takes CUDA tensors")
-    if stream is None:
-        stream = _current_stream()
-    _check(load().gde_topk_f32_noalloc(_ptr(x)[0], int(x.numel()), int(k), _ptr(out_ids)[0],
-                                       _ptr(out_vals)[0], stream))
+    x (float32), out_ids (int32, >= k elements) and out_vals (float32, >= k elements) must be
+    contiguous CUDA tensors on one device; the call runs with that device current and is
+    asynchronous on `stream` (default: that device's current torch stream)."""
+    _check_topk_noalloc_args(x, k, out_ids, out_vals)
+    import torch
+    with torch.cuda.device(x.device):
+        if stream is None:
+            stream = torch.cuda.current_stream(x.device).cuda_stream
+        _check(load().gde_topk_f32_noalloc(_ptr(x)[0], int(x.numel()), int(k), _ptr(out_ids)[0],
+                                           _ptr(out_vals)[0], stream))
 
 
 PROBE_MODES = {"load": 0, "load_atomic": 1, "atomic": 2}
@@ -424,6 +452,53 @@ class Session:
     def close(self):
         if getattr(self, "_h", None):
             load().gde_session_end(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BatchSession:
+    """Batched stepping interface (gde_bsession_*): one round of the batched engine per step()
+    for every seed of the batch, with each seed's state readable between rounds."""
+
+    def __init__(self, graph: Graph, kind, param: float, eps: float, seeds, **opt_kw):
+        lib = load()
+        self.graph = graph
+        seeds = np.ascontiguousarray(seeds, dtype=np.int32)
+        if seeds.ndim != 1 or seeds.shape[0] < 1:
+            raise ValueError("seeds must be a non-empty 1-d array")
+        self.nseeds = int(seeds.shape[0])
+        opt_kw.setdefault("precision", FP32)
+        o = make_opts(**opt_kw)
+        h = ctypes.c_void_p()
+        _check(lib.gde_bsession_begin(graph.handle, _kind(kind), float(param), float(eps), seeds.ctypes.data,
+                                      self.nseeds, ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+
+    def step(self) -> int:
+        """Runs the next round of every seed; returns the candidates of the round after it."""
+        k = ctypes.c_int64()
+        _check(load().gde_bsession_step(self._h, ctypes.byref(k)))
+        return k.value
+
+    def read(self, j: int):
+        """(x, r, nodes pushed by the last step) of seed index j, as float32 / int32 arrays."""
+        n = self.graph.n
+        x = np.empty(n, dtype=np.float32)
+        r = np.empty(n, dtype=np.float32)
+        pushed = np.empty(max(n, 1), dtype=np.int32)
+        k = ctypes.c_int64()
+        _check(load().gde_bsession_read(self._h, int(j), x.ctypes.data, r.ctypes.data, pushed.ctypes.data,
+                                        ctypes.byref(k)))
+        return x, r, np.sort(pushed[:k.value])
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().gde_bsession_end(self._h)
             self._h = None
 
     def __del__(self):

@@ -206,6 +206,11 @@ struct gde_session {
     uint32_t flags = 0;
 };
 
+struct gde_bsession {
+    gde_graph *graph = nullptr;
+    BatchSession *s = nullptr;
+};
+
 
 extern "C" {
 
@@ -679,6 +684,61 @@ gde_status gde_session_end(gde_session *s) {
         dense_work_destroy(s->w);
     }
     delete s;
+    return GDE_OK;
+}
+
+gde_status gde_bsession_begin(gde_graph *h, gde_kind kind, double param, double eps, const int32_t *seeds,
+                              int32_t nseeds, const gde_solve_opts *opts, gde_bsession **out) {
+    API_BEGIN
+    GDE_REQUIRE(h != nullptr && out != nullptr, GDE_EINVAL, "graph or out is NULL");
+    *out = nullptr;
+    gde_solve_opts o;
+    gde_solve_opts_init(&o);
+    if (opts) o = *opts;
+    GDE_REQUIRE((o.flags & GDE_DEVICE_PTRS) == 0, GDE_EINVAL, "batched session: seeds are a host array");
+    Graph &g = h->g;
+    std::lock_guard<std::mutex> lock(g.mu);
+    SolveParams p = make_params(g, kind, param, eps, o);
+    gde_bsession *b = new gde_bsession();
+    try {
+        b->graph = h;
+        b->s = bsession_begin(g, p, seeds, nseeds, o.mem_budget_bytes);
+    } catch (...) {
+        delete b;
+        throw;
+    }
+    *out = b;
+    API_END
+}
+
+gde_status gde_bsession_step(gde_bsession *b, int64_t *n_candidates) {
+    API_BEGIN
+    GDE_REQUIRE(b != nullptr, GDE_EINVAL, "session is NULL");
+    Graph &g = b->graph->g;
+    std::lock_guard<std::mutex> lock(g.mu);
+    const int64_t c = bsession_step(b->s);
+    if (n_candidates) *n_candidates = c;
+    API_END
+}
+
+gde_status gde_bsession_read(gde_bsession *b, int32_t seed_index, float *x, float *r, int32_t *pushed,
+                             int64_t *n_pushed) {
+    API_BEGIN
+    GDE_REQUIRE(b != nullptr, GDE_EINVAL, "session is NULL");
+    Graph &g = b->graph->g;
+    std::lock_guard<std::mutex> lock(g.mu);
+    const gde_status st = bsession_read(b->s, seed_index, x, r, pushed, n_pushed);
+    if (st != GDE_OK) {
+        set_error("batched session: this seed's table overflowed");
+        return st;
+    }
+    API_END
+}
+
+gde_status gde_bsession_end(gde_bsession *b) {
+    if (!b) return GDE_OK;
+    bsession_destroy(b->s);
+    delete b;
     return GDE_OK;
 }
 

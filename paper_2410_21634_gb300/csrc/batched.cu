@@ -330,6 +330,7 @@ struct BArgs {
     unsigned long long *grp_units;  // per seed group: its work units (schedule 3)
     unsigned long long *grp_off;    // their exclusive prefix sums
     unsigned *pend;     // not NULL: receives per seed the candidates left for the next launch
+    uint32_t *pushed;   // not NULL (stepping sessions): per candidate of the round, 1 if it was pushed
     // layered kinds (heat kernel, general series): round t reads layer t and writes layer t+1;
     // the keys of layer t carry key_tag + t * tag_step, so a layer's keys read as free slots
     // once the next layer is written, and x lives in a separate per-seed table keyed by node
@@ -664,6 +665,7 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
         for (int64_t ci = tid; ci < ncand; ci += nthreads) {
             const uint32_t slot = __ldcg(cand + ci);
             const int32_t j = (int32_t)(slot >> a.log2cap);
+            if (a.pushed) a.pushed[ci] = 0u;
             if (__ldcg(a.status + j) != kSeedOk) { __stcg(a.tmp_deg + ci, 0); continue; }
             const unsigned long long word = __ldcg(a.kr + slot);
             const int32_t v = (int32_t)((uint32_t)(word & 0xFFFFFFFFull) & a.key_idmask);
@@ -692,6 +694,7 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
             // is pushed by one taker only
             rho = atomicExch(r_of(a.kr, slot), 0.0f);
             if (!(rho != 0.0f && fabsf(rho) >= thr)) { __stcg(a.tmp_deg + ci, 0); continue; }
+            if (a.pushed) a.pushed[ci] = 1u;
             const double rho64 = (double)rho;
             // vol(S_t) counts d_u; the last layer of a layered kind only adds to x (no scatter)
             const int32_t d = last_layer ? 0 : dvol;
@@ -1572,48 +1575,16 @@ static inline int64_t ceil_pow2(int64_t v) {
     return p;
 }
 
-// Runs a batched PPR/Katz solve.  seeds_dev: device seed ids.  Outputs (device): ids[nseeds*k],
-// vals[nseeds*k] (float).  stats_host may be NULL.  Seeds whose table overflowed are reported
-// with status GDE_ENOMEM in stats and in *n_overflow; their outputs are not valid.
-static void batch_solve_once(Graph &g, const SolveParams &p, const int32_t *seeds_dev, int32_t nseeds, int k,
-                             int64_t mem_budget, int32_t *ids_dev, float *vals_dev, gde_stats *stats_host,
-                             int32_t *overflow_seeds_host, int32_t *n_overflow, int list_scale,
-                             bool *list_full) {
-    GDE_REQUIRE(k >= 1 && k <= kTopMax, GDE_EINVAL, "batched mode needs 1 <= topk <= 64");
-    GDE_REQUIRE(p.kind == GDE_PPR || p.kind == GDE_KATZ || p.kind == GDE_GPPR || layered(p.kind), GDE_EINVAL,
-                "batched mode supports PPR, Katz, the generalised propagation, the heat kernel and series");
-    GDE_REQUIRE(p.precision == GDE_FP32, GDE_EINVAL, "batched mode stores x and r in FP32");
-    GDE_REQUIRE(g.n < ((int64_t)1 << 31) - 1, GDE_EINVAL, "graph too large for 32-bit keys");
+// Prepares a batched solve of nseeds seeds on workspace w (tables of cap slots, candidate and
+// bin lists of list_cap entries): copies the seed ids, builds the packed columns, takes the
+// solve's epoch tag (clearing the pool on first use, after a failure or when the tag wraps),
+// the layered kinds' x tables and per-round constants or the per-node thresholds, and seeds
+// every table.  Returns the round kernel's arguments for round 0.
+static BArgs batch_setup(Graph &g, const SolveParams &p, BatchWork *w, const int32_t *seeds_dev, int32_t nseeds,
+                         int64_t cap, int64_t list_cap, uint32_t *key_tag_out, uint32_t *key_idmask_out) {
     const bool lay = layered(p.kind);
-    const int64_t budget = mem_budget > 0 ? mem_budget : ((int64_t)16 << 30);
-    // layered kinds add an x table of half the residual table's slots (12 + 6 bytes per slot)
-    int64_t cap = floor_pow2(budget / ((lay ? 18 : 12) * (int64_t)nseeds));
-    // a table of 2n slots never exceeds half load (at most n keys)
-    // (at most 2^31 slots per table: slot indices are 32-bit and carry the seed above log2(cap))
-    const int64_t cap_max = std::min<int64_t>(ceil_pow2(2 * (g.n > 0 ? g.n : 1)), (int64_t)1 << 31);
-    if (cap > cap_max) cap = cap_max;
-    GDE_REQUIRE(cap >= 64 || cap == cap_max, GDE_ENOMEM, "memory budget too small for the batch");
-    GDE_REQUIRE((int64_t)nseeds * cap <= ((int64_t)1 << 32), GDE_EINVAL, "batch pool exceeds 2^32 slots");
-    // candidate and bin lists: every slot can enter a list at most once per round, but the
-    // per-round frontier of all seeds together is far smaller than the pool; past this
-    // capacity the solve reports GDE_ENOMEM
-    int64_t list_cap = (int64_t)nseeds * cap;
-    int64_t list_max = (int64_t)nseeds << 14;
-    if (list_max < ((int64_t)1 << 22)) list_max = (int64_t)1 << 22;
-    if (list_max > ((int64_t)1 << 24)) list_max = (int64_t)1 << 24;
-    list_max <<= 2 * list_scale;  // a retry after an overflow: four times larger
-    if (list_cap > list_max) list_cap = list_max;
-    GDE_REQUIRE(nseeds <= list_cap, GDE_EINVAL, "too many seeds for one batch");
-    *list_full = list_cap == (int64_t)nseeds * cap;
-    BatchWork *w = batch_work_get(g, nseeds, cap, list_cap);
-    if (w->list_cap > list_cap) {
-        // a workspace that an earlier solve left larger keeps its longer lists
-        list_cap = std::min<int64_t>(w->list_cap, std::min<int64_t>((int64_t)nseeds * cap, 0xFFFFFFFFll));
-        *list_full = list_cap == (int64_t)nseeds * cap;
-    }
     cudaStream_t s = p.stream;
     GDE_CUDA(cudaMemcpyAsync(w->seeds, seeds_dev, 4 * (size_t)nseeds, cudaMemcpyDeviceToDevice, s));
-    const int64_t pool = (int64_t)nseeds * cap;
     ensure_colp(g, s);
     // epoch tags: keys carry the solve's tag above their id bits, so the previous solve's keys
     // read as empty; the tables are only reset on first use, after a failure, or when the tag
@@ -1660,7 +1631,6 @@ static void batch_solve_once(Graph &g, const SolveParams &p, const int32_t *seed
     const uint32_t key_tag = w->epoch << key_idbits;
     w->epoch += tags - 1;  // the last tag this solve uses
     const uint32_t key_idmask = (uint32_t)(((uint64_t)1 << key_idbits) - 1);
-    (void)pool;
     if (lay) {
         // per-round constants: theta_t eps and the share coefficient of round t
         GDE_REQUIRE(g.colp_valid && g.colp_idbits > 0, GDE_EINVAL,
@@ -1722,6 +1692,54 @@ static void batch_solve_once(Graph &g, const SolveParams &p, const int32_t *seed
         a.xlog2cap = w->xt_log2cap;
         a.xmask = (uint32_t)(w->xt_cap - 1);
     }
+    *key_tag_out = key_tag;
+    *key_idmask_out = key_idmask;
+    return a;
+}
+
+// Runs a batched PPR/Katz solve.  seeds_dev: device seed ids.  Outputs (device): ids[nseeds*k],
+// vals[nseeds*k] (float).  stats_host may be NULL.  Seeds whose table overflowed are reported
+// with status GDE_ENOMEM in stats and in *n_overflow; their outputs are not valid.
+static void batch_solve_once(Graph &g, const SolveParams &p, const int32_t *seeds_dev, int32_t nseeds, int k,
+                             int64_t mem_budget, int32_t *ids_dev, float *vals_dev, gde_stats *stats_host,
+                             int32_t *overflow_seeds_host, int32_t *n_overflow, int list_scale,
+                             bool *list_full) {
+    GDE_REQUIRE(k >= 1 && k <= kTopMax, GDE_EINVAL, "batched mode needs 1 <= topk <= 64");
+    GDE_REQUIRE(p.kind == GDE_PPR || p.kind == GDE_KATZ || p.kind == GDE_GPPR || layered(p.kind), GDE_EINVAL,
+                "batched mode supports PPR, Katz, the generalised propagation, the heat kernel and series");
+    GDE_REQUIRE(p.precision == GDE_FP32, GDE_EINVAL, "batched mode stores x and r in FP32");
+    GDE_REQUIRE(g.n < ((int64_t)1 << 31) - 1, GDE_EINVAL, "graph too large for 32-bit keys");
+    const bool lay = layered(p.kind);
+    const int64_t budget = mem_budget > 0 ? mem_budget : ((int64_t)16 << 30);
+    // layered kinds add an x table of half the residual table's slots (12 + 6 bytes per slot)
+    int64_t cap = floor_pow2(budget / ((lay ? 18 : 12) * (int64_t)nseeds));
+    // a table of 2n slots never exceeds half load (at most n keys)
+    // (at most 2^31 slots per table: slot indices are 32-bit and carry the seed above log2(cap))
+    const int64_t cap_max = std::min<int64_t>(ceil_pow2(2 * (g.n > 0 ? g.n : 1)), (int64_t)1 << 31);
+    if (cap > cap_max) cap = cap_max;
+    GDE_REQUIRE(cap >= 64 || cap == cap_max, GDE_ENOMEM, "memory budget too small for the batch");
+    GDE_REQUIRE((int64_t)nseeds * cap <= ((int64_t)1 << 32), GDE_EINVAL, "batch pool exceeds 2^32 slots");
+    // candidate and bin lists: every slot can enter a list at most once per round, but the
+    // per-round frontier of all seeds together is far smaller than the pool; past this
+    // capacity the solve reports GDE_ENOMEM
+    int64_t list_cap = (int64_t)nseeds * cap;
+    int64_t list_max = (int64_t)nseeds << 14;
+    if (list_max < ((int64_t)1 << 22)) list_max = (int64_t)1 << 22;
+    if (list_max > ((int64_t)1 << 24)) list_max = (int64_t)1 << 24;
+    list_max <<= 2 * list_scale;  // a retry after an overflow: four times larger
+    if (list_cap > list_max) list_cap = list_max;
+    GDE_REQUIRE(nseeds <= list_cap, GDE_EINVAL, "too many seeds for one batch");
+    *list_full = list_cap == (int64_t)nseeds * cap;
+    BatchWork *w = batch_work_get(g, nseeds, cap, list_cap);
+    if (w->list_cap > list_cap) {
+        // a workspace that an earlier solve left larger keeps its longer lists
+        list_cap = std::min<int64_t>(w->list_cap, std::min<int64_t>((int64_t)nseeds * cap, 0xFFFFFFFFll));
+        *list_full = list_cap == (int64_t)nseeds * cap;
+    }
+    cudaStream_t s = p.stream;
+    uint32_t key_tag = 0, key_idmask = 0;
+    BArgs a = batch_setup(g, p, w, seeds_dev, nseeds, cap, list_cap, &key_tag, &key_idmask);
+    (void)key_tag;
     launch_rounds(g, w, a, s);
 
     TopkArgs ta{};
@@ -2551,5 +2569,195 @@ int64_t batch_round_log(Graph &g, double *out, int64_t cap) {
     }
     return r;
 }
+
+
+// ======================================================= stepping session ====
+// The batched engine run one round per launch, with every seed's table read back between
+// rounds, so that its rounds (Eq. local-gd for all seeds of a batch at once) can be compared
+// with the oracle's from exactly the same state.  The round kernel, its arguments and the
+// set-up are the batched solve's; only max_rounds = 1 and the per-candidate push flags differ.
+// The session owns its workspace (the graph's cached one is untouched); the graph must not
+// change while it runs.
+
+struct BatchSession {
+    Graph *g = nullptr;
+    SolveParams p;
+    BatchWork *w = nullptr;
+    int32_t nseeds = 0;
+    int64_t cap = 0, list_cap = 0;
+    uint32_t key_tag = 0, key_idmask = 0, tag_step = 0;
+    BArgs a{};
+    int64_t T = 0;                       // the next round
+    int32_t *d_seeds = nullptr;
+    uint32_t *d_pushed = nullptr;        // per candidate of the last round: pushed or not
+    const int64_t *off0 = nullptr;       // the CSR as of begin (an insertion swaps the arrays)
+    const int32_t *col0 = nullptr;
+    int64_t nnz0 = 0;
+    std::vector<unsigned long long> h_kr, h_xkr;  // host copies of the tables after the last step
+    std::vector<float> h_xs, h_xxs;
+    std::vector<int32_t> h_status;
+    std::vector<std::vector<int32_t>> pushed;     // per seed: the nodes pushed in the last round
+};
+
+static float host_bits_to_float(uint32_t b) {
+    float f;
+    std::memcpy(&f, &b, sizeof f);
+    return f;
+}
+
+static void bsession_mirror(BatchSession *S) {
+    BatchWork *w = S->w;
+    cudaStream_t s = S->p.stream;
+    const size_t pool = (size_t)S->nseeds * (size_t)S->cap;
+    S->h_kr.resize(pool);
+    S->h_xs.resize(pool);
+    S->h_status.resize((size_t)S->nseeds);
+    GDE_CUDA(cudaMemcpyAsync(S->h_kr.data(), w->kr, 8 * pool, cudaMemcpyDeviceToHost, s));
+    GDE_CUDA(cudaMemcpyAsync(S->h_xs.data(), w->xs, 4 * pool, cudaMemcpyDeviceToHost, s));
+    GDE_CUDA(cudaMemcpyAsync(S->h_status.data(), w->status, 4 * (size_t)S->nseeds, cudaMemcpyDeviceToHost, s));
+    if (layered(S->p.kind)) {
+        const size_t xp = (size_t)w->xt_seeds * (size_t)w->xt_cap;
+        S->h_xkr.resize(xp);
+        S->h_xxs.resize(xp);
+        GDE_CUDA(cudaMemcpyAsync(S->h_xkr.data(), w->xkr, 8 * xp, cudaMemcpyDeviceToHost, s));
+        GDE_CUDA(cudaMemcpyAsync(S->h_xxs.data(), w->xxs, 4 * xp, cudaMemcpyDeviceToHost, s));
+    }
+    GDE_CUDA(cudaStreamSynchronize(s));
+}
+
+static void bsession_free(BatchSession *S) {
+    if (!S) return;
+    if (S->p.stream) cudaStreamSynchronize(S->p.stream);
+    batch_free(S->w);
+    dfree(S->d_seeds);
+    dfree(S->d_pushed);
+    delete S;
+}
+
+void bsession_destroy(BatchSession *S) { bsession_free(S); }
+
+BatchSession *bsession_begin(Graph &g, const SolveParams &p, const int32_t *seeds_host, int32_t nseeds,
+                             int64_t budget) {
+    GDE_REQUIRE(p.kind == GDE_PPR || p.kind == GDE_KATZ || p.kind == GDE_GPPR || layered(p.kind), GDE_EINVAL,
+                "batched session: PPR, Katz, the generalised propagation, the heat kernel or a series");
+    GDE_REQUIRE(p.precision == GDE_FP32, GDE_EINVAL, "batched session: the batched engine stores x and r in FP32");
+    GDE_REQUIRE(nseeds >= 1 && seeds_host != nullptr, GDE_EINVAL, "batched session: needs at least one seed");
+    GDE_REQUIRE(g.n >= 1 && g.n < ((int64_t)1 << 31) - 1, GDE_EINVAL, "batched session: graph size out of range");
+    for (int32_t i = 0; i < nseeds; i++)
+        GDE_REQUIRE(seeds_host[i] >= 0 && seeds_host[i] < g.n, GDE_EINVAL, "seed id out of range");
+    const bool lay = layered(p.kind);
+    if (budget <= 0) budget = (int64_t)4 << 30;
+    int64_t cap = floor_pow2(budget / ((lay ? 18 : 12) * (int64_t)nseeds));
+    const int64_t cap_max = std::min<int64_t>(ceil_pow2(2 * g.n), (int64_t)1 << 31);
+    if (cap > cap_max) cap = cap_max;
+    GDE_REQUIRE(cap >= 64 || cap == cap_max, GDE_ENOMEM, "batched session: memory budget too small");
+    GDE_REQUIRE((int64_t)nseeds * cap <= ((int64_t)1 << 32), GDE_EINVAL, "batched session: pool exceeds 2^32 slots");
+    int64_t list_cap = std::min<int64_t>((int64_t)nseeds * cap, (int64_t)1 << 24);
+    GDE_REQUIRE(nseeds <= list_cap, GDE_EINVAL, "batched session: too many seeds");
+    BatchSession *S = new BatchSession();
+    try {
+        S->g = &g;
+        S->p = p;
+        S->nseeds = nseeds;
+        S->cap = cap;
+        S->list_cap = list_cap;
+        S->w = batch_work_alloc(nseeds, cap, list_cap);
+        S->d_seeds = (int32_t *)dmalloc(4 * (size_t)nseeds, "session seeds");
+        S->d_pushed = (uint32_t *)dmalloc(4 * (size_t)list_cap, "session push flags");
+        cudaStream_t s = p.stream;
+        GDE_CUDA(cudaMemcpyAsync(S->d_seeds, seeds_host, 4 * (size_t)nseeds, cudaMemcpyHostToDevice, s));
+        S->a = batch_setup(g, p, S->w, S->d_seeds, nseeds, cap, list_cap, &S->key_tag, &S->key_idmask);
+        S->a.max_rounds = 1;
+        S->a.pushed = S->d_pushed;
+        S->tag_step = S->a.tag_step;
+        S->off0 = g.off;
+        S->col0 = g.col;
+        S->nnz0 = g.nnz;
+        S->pushed.assign((size_t)nseeds, std::vector<int32_t>());
+        bsession_mirror(S);
+    } catch (...) {
+        bsession_free(S);
+        throw;
+    }
+    return S;
+}
+
+// candidates of round T: in cand[T & 1], counted by the other parity's cand_out
+static unsigned bsession_ncand(BatchSession *S) {
+    unsigned c = 0;
+    GDE_CUDA(cudaMemcpyAsync(&c, &S->w->glob->ctl[(S->T & 1) ^ 1].cand_out, sizeof(unsigned),
+                             cudaMemcpyDeviceToHost, S->p.stream));
+    GDE_CUDA(cudaStreamSynchronize(S->p.stream));
+    return c;
+}
+
+int64_t bsession_step(BatchSession *S) {
+    Graph &g = *S->g;
+    GDE_REQUIRE(g.off == S->off0 && g.col == S->col0 && g.nnz == S->nnz0, GDE_EINVAL,
+                "batched session: the graph changed since the session began");
+    for (auto &v : S->pushed) v.clear();
+    unsigned ncand = bsession_ncand(S);
+    if (ncand == 0) return 0;
+    GDE_REQUIRE(ncand <= (unsigned)S->list_cap, GDE_ENOMEM, "batched session: candidate list overflowed");
+    cudaStream_t s = S->p.stream;
+    std::vector<uint32_t> cand(ncand), flag(ncand);
+    GDE_CUDA(cudaMemcpyAsync(cand.data(), S->w->cand[S->T & 1], 4 * (size_t)ncand, cudaMemcpyDeviceToHost, s));
+    S->a.t0 = S->T;
+    launch_rounds(g, S->w, S->a, s);
+    BGlobal hg;
+    GDE_CUDA(cudaMemcpyAsync(&hg, S->w->glob, sizeof(BGlobal), cudaMemcpyDeviceToHost, s));
+    GDE_CUDA(cudaMemcpyAsync(flag.data(), S->d_pushed, 4 * (size_t)ncand, cudaMemcpyDeviceToHost, s));
+    GDE_CUDA(cudaStreamSynchronize(s));
+    if (hg.error == GDE_ETIMEOUT) {
+        set_error("batched session: a grid barrier wait timed out");
+        throw Fail{GDE_ETIMEOUT};
+    }
+    GDE_REQUIRE(hg.error == 0, (gde_status)hg.error, "batched session: candidate or bin list capacity exceeded");
+    // the pushed candidates' nodes, decoded from the tables as they were before the round
+    for (unsigned i = 0; i < ncand; i++) {
+        if (!flag[i]) continue;
+        const uint32_t slot = cand[i];
+        const int32_t j = (int32_t)(slot >> S->w->log2cap);
+        const uint32_t key = (uint32_t)(S->h_kr[slot] & 0xFFFFFFFFull);
+        S->pushed[(size_t)j].push_back((int32_t)(key & S->key_idmask));
+    }
+    S->T = S->T + 1;
+    bsession_mirror(S);
+    return (int64_t)bsession_ncand(S);
+}
+
+// x (n floats: the unscaled x of the engine), r (n floats: the residual, for the layered kinds
+// the current layer) of seed j after the last step, and the nodes pushed in that step
+gde_status bsession_read(BatchSession *S, int32_t j, float *x, float *r, int32_t *pushed, int64_t *n_pushed) {
+    GDE_REQUIRE(j >= 0 && j < S->nseeds, GDE_EINVAL, "batched session: seed index out of range");
+    const int64_t n = S->g->n;
+    const uint64_t base = (uint64_t)j << S->w->log2cap;
+    const bool lay = layered(S->p.kind);
+    const uint32_t rtag = lay ? S->key_tag + (uint32_t)S->T * S->tag_step : S->key_tag;
+    if (x) std::fill(x, x + n, 0.0f);
+    if (r) std::fill(r, r + n, 0.0f);
+    for (int64_t i = 0; i < S->cap; i++) {
+        const unsigned long long word = S->h_kr[base + (uint64_t)i];
+        const uint32_t key = (uint32_t)(word & 0xFFFFFFFFull);
+        if (key == kEmpty || (key & ~S->key_idmask) != rtag) continue;
+        const uint32_t v = key & S->key_idmask;
+        if (r) r[v] = host_bits_to_float((uint32_t)(word >> 32));
+        if (x && !lay) x[v] = S->h_xs[base + (uint64_t)i];
+    }
+    if (x && lay) {
+        const uint64_t xb = (uint64_t)j << S->w->xt_log2cap;
+        for (int64_t i = 0; i < S->w->xt_cap; i++) {
+            const uint32_t key = (uint32_t)(S->h_xkr[xb + (uint64_t)i] & 0xFFFFFFFFull);
+            if (key == kEmpty || (key & ~S->key_idmask) != S->key_tag) continue;
+            x[key & S->key_idmask] = S->h_xxs[xb + (uint64_t)i];
+        }
+    }
+    const std::vector<int32_t> &pl = S->pushed[(size_t)j];
+    if (pushed) std::copy(pl.begin(), pl.end(), pushed);
+    if (n_pushed) *n_pushed = (int64_t)pl.size();
+    return S->h_status[(size_t)j] == kSeedOk ? GDE_OK : GDE_ENOMEM;
+}
+
+int64_t bsession_round(const BatchSession *S) { return S->T; }
 
 }  // namespace gde

@@ -264,6 +264,15 @@ void batch_solve(Graph &g, const SolveParams &p, const int32_t *seeds_dev, int32
 void batch_solve_rebatch(Graph &g, const SolveParams &p, const int32_t *seeds_dev, const int32_t *seeds_host,
                          int32_t nseeds, int k, int64_t mem_budget, int32_t *ids_dev, float *vals_dev,
                          gde_stats *stats_host, int32_t *overflow_seeds_host, int32_t *n_overflow);
+// batched engine stepped one round per launch, with the tables read back between rounds
+struct BatchSession;
+BatchSession *bsession_begin(Graph &g, const SolveParams &p, const int32_t *seeds_host, int32_t nseeds,
+                             int64_t budget);
+// runs the next round of every seed; returns the candidates of the round after it (0: done)
+int64_t bsession_step(BatchSession *S);
+gde_status bsession_read(BatchSession *S, int32_t j, float *x, float *r, int32_t *pushed, int64_t *n_pushed);
+int64_t bsession_round(const BatchSession *S);
+void bsession_destroy(BatchSession *S);
 // top-k (x desc, id asc) of a dense float vector on the device
 void topk_dense_f32(const float *x_dev, int64_t n, int k, int32_t *ids_dev, float *vals_dev,
                     cudaStream_t s);

@@ -11,6 +11,7 @@ import pytest
 
 import oracle
 import synth
+from topk_check import check_bands
 
 pytestmark = pytest.mark.gpu
 
@@ -27,24 +28,13 @@ def gde():
 
 
 def check_topk(g, ids, vals, xref, eps, k=K):
+    """Top-k list of a free-running FP32 solve against the oracle's x, each node u with its
+    own band b_u = eps d_u + 1e-5 x_u (both solutions satisfy 0 <= f_u - x_u < eps d_u,
+    Corollary 3.6, and may push different near-threshold nodes; tests/topk_check.py)."""
     d = g.degrees().astype(np.float64)
     nz = int((xref > 0).sum())
-    valid = ids >= 0
-    assert valid.sum() == min(k, nz) or valid.sum() <= min(k, nz)
-    ids_v = ids[valid]
-    vals_v = vals[valid].astype(np.float64)
-    assert np.all(np.diff(vals_v) <= 0), "values not descending"
-    band = eps * d[ids_v] + 1e-5 * xref[ids_v] + 1e-12
-    assert np.all(np.abs(vals_v - xref[ids_v]) <= band), "value outside the error band"
-    # ranking: the oracle's i-th largest value and the device's i-th value agree within the band
-    ref_ids, ref_vals = oracle.topk(xref, len(ids_v))
-    tol = eps * d.max() + 1e-5 * ref_vals + 1e-12
-    assert np.all(np.abs(np.sort(vals_v)[::-1] - ref_vals[: len(vals_v)]) <= tol)
-    # ids whose oracle value is clearly inside the top-k (beyond the band) must be present
-    if len(ids_v) == k and len(ref_vals) == k:
-        kth = ref_vals[-1]
-        sure = ref_ids[ref_vals > kth + 2 * (eps * d[ref_ids] + 1e-5 * ref_vals)]
-        assert set(sure.tolist()) <= set(ids_v.tolist())
+    assert (ids >= 0).sum() <= min(k, nz)
+    check_bands(ids, vals, xref, eps * d + 1e-5 * xref + 1e-12, k)
 
 
 def run_batched(gde, G, kind, param, eps, seeds, k=K, **kw):
@@ -108,13 +98,14 @@ def test_alone_equals_in_mix(gde, rmat16):
     seeds = synth.seeds_mixed(g, 32, 32, seed=9)
     G = gde.Graph.from_synth(g)
     _, _, ids_b, vals_b = run_batched(gde, G, "ppr", 0.1, 1e-6, seeds)
-    d = g.degrees().astype(np.float64)
     for i in (0, 5, 33, 60):
         _, _, ids_1, vals_1 = run_batched(gde, G, "ppr", 0.1, 1e-6, seeds[i:i + 1])
-        assert np.allclose(vals_1[0], vals_b[i], rtol=1e-5, atol=1e-6 * d.max())
+        # the seed's arithmetic does not depend on the other seeds; only the order of its
+        # float atomics does, so the values agree to FP32 summation rounding
+        assert np.allclose(vals_1[0], vals_b[i], rtol=1e-5, atol=0)
         same = ids_1[0] == ids_b[i]
         # positions may swap only between near-equal values
-        assert np.all(same | np.isclose(vals_1[0], vals_b[i], rtol=1e-5))
+        assert np.all(same | np.isclose(vals_1[0], vals_b[i], rtol=1e-5, atol=0))
 
 
 def test_duplicate_isolated_and_padding(gde):

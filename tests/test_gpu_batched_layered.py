@@ -80,8 +80,7 @@ def test_hk_equals_its_series(gde, c1):
     seeds = synth.seeds_quantile(g, 6)
     _, _, ids_a, vals_a = run_batched(gde, G, "hk", tau, 1e-6, seeds)
     _, _, ids_b, vals_b = run_batched(gde, G, "series", 0.0, 1e-6, seeds, series_coef=np.array(c))
-    d = g.degrees().astype(np.float64)
-    assert np.allclose(vals_a, vals_b, rtol=1e-5, atol=1e-7 * d.max())
+    assert np.allclose(vals_a, vals_b, rtol=1e-5, atol=0)
     G.close()
 
 
@@ -90,12 +89,12 @@ def test_alone_equals_in_mix(gde, rmat16):
     seeds = synth.seeds_mixed(g, 16, 16, seed=9)
     G = gde.Graph.from_synth(g)
     _, _, ids_b, vals_b = run_batched(gde, G, "hk", 5.0, 1e-6, seeds)
-    d = g.degrees().astype(np.float64)
     for i in (0, 7, 20, 31):
         _, _, ids_1, vals_1 = run_batched(gde, G, "hk", 5.0, 1e-6, seeds[i:i + 1])
-        assert np.allclose(vals_1[0], vals_b[i], rtol=1e-5, atol=1e-6 * d.max())
+        # only the order of the seed's float atomics differs: FP32 summation rounding
+        assert np.allclose(vals_1[0], vals_b[i], rtol=1e-5, atol=0)
         same = ids_1[0] == ids_b[i]
-        assert np.all(same | np.isclose(vals_1[0], vals_b[i], rtol=1e-5))
+        assert np.all(same | np.isclose(vals_1[0], vals_b[i], rtol=1e-5, atol=0))
     G.close()
 
 
@@ -106,15 +105,14 @@ def test_tag_wrap_and_mixed_kinds(gde, rmat16):
     g = rmat16
     G = gde.Graph.from_synth(g)
     seeds = synth.seeds_mixed(g, 8, 8, seed=12)
-    d = g.degrees().astype(np.float64)
     _, _, ids0, vals0 = run_batched(gde, G, "hk", 5.0, 1e-6, seeds)
     _, _, pids0, pvals0 = run_batched(gde, G, "ppr", 0.1, 1e-6, seeds)
     for rep in range(14):
         _, _, ids, vals = run_batched(gde, G, "hk", 5.0, 1e-6, seeds)
-        assert np.allclose(vals, vals0, rtol=1e-5, atol=1e-6 * d.max()), rep
+        assert np.allclose(vals, vals0, rtol=1e-5, atol=0), rep
         if rep % 4 == 3:
             _, _, pids, pvals = run_batched(gde, G, "ppr", 0.1, 1e-6, seeds)
-            assert np.allclose(pvals, pvals0, rtol=1e-5, atol=1e-6 * d.max()), rep
+            assert np.allclose(pvals, pvals0, rtol=1e-5, atol=0), rep
     G.close()
 
 

@@ -1,0 +1,151 @@
+"""Round-by-round parity of the batched FP32 engine (the headline path: Eq. local-gd,
+Section 3.3, run for every seed of a batch inside one persistent launch, per-seed hash
+accumulators) with the FP64 oracle, through the batched stepping interface (gde_bsession_*).
+
+At every round each seed's device state is widened exactly to FP64, the oracle runs that
+round from it, and the device's pushed set, x and r must match: S_t identical (up to nodes
+within one ulp of their threshold), every entry >= eps d_u within 1e-5 relative, relative L1
+within 1e-5.  The heat kernel's literal threshold (theta_t = 1, most of the graph active)
+keeps the float-summation widening for entries with many contributions; every other case is
+held to the plain 1e-5 bar.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from lockstep import run_batched
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gde():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_2410_21634_gb300 as m
+    m.load()
+    return m
+
+
+@pytest.fixture(scope="module")
+def rmat16():
+    return synth.rmat(16, 16, seed=21)
+
+
+@pytest.fixture(scope="module")
+def c1():
+    return synth.workload_graph("chung_lu_1e4")
+
+
+def _report(name, rep):
+    print(f"\n{name}: {rep}")
+    assert rep["rounds"] > 2 and rep["pushes"] > 0 and rep["entries"] > 0
+
+
+def test_batched_lockstep_ppr_rmat_64_mixed(gde, rmat16):
+    """64 seeds (32 uniform, 32 from the top 1% by degree) on R-MAT 16, whose hubs are pushed
+    by the merge-path chunks; PPR alpha = 0.1, eps = 1e-6."""
+    g = rmat16
+    assert g.degrees().max() > 4096
+    seeds = synth.seeds_mixed(g, 32, 32, seed=3)
+    G = gde.Graph.from_synth(g)
+    rep = run_batched(G, g, "ppr", 0.1, 1e-6, seeds)
+    _report("ppr rmat16 64 seeds", rep)
+    assert rep["widened"] == 0
+    G.close()
+
+
+def test_batched_lockstep_ppr_c1(gde, c1):
+    seeds = synth.seeds_by_degree(c1, 64, seed=5)
+    G = gde.Graph.from_synth(c1)
+    rep = run_batched(G, c1, "ppr", 0.15, 1e-6, seeds)
+    _report("ppr c1 64 seeds", rep)
+    G.close()
+
+
+def test_batched_lockstep_katz(gde, rmat16):
+    g = rmat16
+    lam, _ = synth.lambda_max(g)
+    seeds = synth.seeds_mixed(g, 8, 8, seed=7)
+    G = gde.Graph.from_synth(g)
+    rep = run_batched(G, g, "katz", 0.5 / lam, 1e-6, seeds)
+    _report("katz rmat16", rep)
+    G.close()
+
+
+def test_batched_lockstep_hk_error_bound(gde, rmat16):
+    g = rmat16
+    seeds = synth.seeds_mixed(g, 8, 8, seed=8)
+    G = gde.Graph.from_synth(g)
+    rep = run_batched(G, g, "hk", 5.0, 1e-6, seeds, hk_mode=0)
+    _report("hk theta rmat16", rep)
+    G.close()
+
+
+def test_batched_lockstep_hk_literal(gde, rmat16):
+    """theta_t = 1: most of the graph is active in the middle layers, so hub entries receive
+    thousands of float additions in one round; those get the summation bound."""
+    g = rmat16
+    seeds = synth.seeds_mixed(g, 4, 4, seed=9)
+    G = gde.Graph.from_synth(g)
+    rep = run_batched(G, g, "hk", 5.0, 1e-6, seeds, hk_mode=1, widen=True)
+    _report("hk literal rmat16", rep)
+    G.close()
+
+
+def test_batched_lockstep_series(gde, c1):
+    """Table 1's IPR coefficients theta^k/(theta^k + theta^10)^2 on the layered engine."""
+    theta = 1.5
+    k = np.arange(40, dtype=np.float64)
+    coef = theta ** k / (theta ** k + theta ** 10) ** 2
+    seeds = synth.seeds_by_degree(c1, 16, seed=6)
+    G = gde.Graph.from_synth(c1)
+    rep = run_batched(G, c1, "series", 0.0, 1e-7, seeds, coef=coef)
+    _report("series c1", rep)
+    G.close()
+
+
+def test_batched_session_rejects_bad_use(gde, c1):
+    G = gde.Graph.from_synth(c1)
+    with pytest.raises(gde.GdeError) as e:
+        gde.BatchSession(G, "ppr", 0.15, 1e-6, np.array([0, c1.n], dtype=np.int32))
+    assert e.value.status == gde.EINVAL
+    with pytest.raises(gde.GdeError) as e:
+        gde.BatchSession(G, "ppr", 0.15, 1e-6, np.array([0], dtype=np.int32), precision="fp64")
+    assert e.value.status == gde.EINVAL
+    S = gde.BatchSession(G, "ppr", 0.15, 1e-6, np.array([0, 1], dtype=np.int32))
+    S.step()
+    with pytest.raises(gde.GdeError) as e:
+        S.read(2)
+    assert e.value.status == gde.EINVAL
+    # the graph changes under the session: the next step is refused
+    G.update_edges(np.array([0], dtype=np.int32), np.array([c1.n - 1], dtype=np.int32))
+    with pytest.raises(gde.GdeError) as e:
+        S.step()
+    assert e.value.status == gde.EINVAL
+    S.close()
+    G.close()
+
+
+def test_batched_session_runs_the_solve(gde, rmat16):
+    """Stepping the session to the end gives the same top values as the one-launch solve
+    (the same kernel, the same round count) within FP32 atomic-order rounding."""
+    g = rmat16
+    seeds = synth.seeds_mixed(g, 6, 6, seed=11)
+    G = gde.Graph.from_synth(g)
+    S = gde.BatchSession(G, "ppr", 0.1, 1e-6, seeds)
+    rounds = 0
+    while S.step() > 0:
+        rounds += 1
+    ids = np.zeros((len(seeds), 64), dtype=np.int32)
+    vals = np.zeros((len(seeds), 64), dtype=np.float32)
+    st, stats = gde.solve(G, "ppr", 0.1, 1e-6, seeds, vals, ids, precision="fp32", topk=64, batched=1)
+    assert st == gde.OK
+    for j in range(len(seeds)):
+        x, _, _ = S.read(j)
+        ref_ids, ref_vals = oracle.topk(x.astype(np.float64), 64)
+        assert np.allclose(vals[j], ref_vals, rtol=1e-5, atol=0)
+    assert max(s["rounds"] for s in stats) == rounds + 1
+    S.close()
+    G.close()

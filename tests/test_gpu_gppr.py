@@ -12,6 +12,7 @@ import pytest
 import oracle
 import oracle.dense as dense
 import synth
+from topk_check import check_bands
 
 pytestmark = pytest.mark.gpu
 
@@ -129,13 +130,9 @@ def test_batched_fp32_topk(gde, rmat16):
     d = g.degrees().astype(np.float64)
     for i in range(0, 24, 5):
         ref, *_ = oracle.gppr(g, 0.1, beta, eps, int(seeds[i]))
-        valid = ids[i] >= 0
-        v = vals[i][valid].astype(np.float64)
-        assert np.all(np.diff(v) <= 0)
-        band = eps * np.maximum(d[ids[i][valid]], 1) ** (1 - beta) + 1e-5 * ref[ids[i][valid]] + 1e-12
-        assert np.all(np.abs(v - ref[ids[i][valid]]) <= band)
-        ref_ids, ref_vals = oracle.topk(ref, int(valid.sum()))
-        assert np.all(np.abs(v - ref_vals) <= eps * d.max() + 1e-5 * ref_vals + 1e-12)
+        # the dense bound of this propagation is eps d_u^(1-b) (degree 0 read as 1)
+        b = eps * np.maximum(d, 1) ** (1 - beta) + 1e-5 * ref + 1e-12
+        check_bands(ids[i], vals[i], ref, b, k)
 
 
 def test_bad_beta_rejected(gde, c1):

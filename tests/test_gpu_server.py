@@ -15,6 +15,7 @@ import pytest
 import oracle
 import oracle.dense as dense
 import synth
+from topk_check import check_bands
 
 pytestmark = pytest.mark.gpu
 
@@ -40,18 +41,10 @@ def beta_of(g):
 
 
 def check_answer(g, res, xref, eps, slack=1.0):
-    """top-k of the device against the oracle's x: values within the band, descending,
-    ranking consistent (the same check as the batched tests)"""
+    """top-k of the device against the oracle's x, each node within its own band
+    slack eps d_u + 1e-5 |x_u| (the same check as the batched tests, tests/topk_check.py)"""
     d = g.degrees().astype(np.float64)
-    ids, vals = res["ids"], res["vals"].astype(np.float64)
-    valid = ids >= 0
-    ids_v, vals_v = ids[valid], vals[valid]
-    assert np.all(np.diff(vals_v) <= 0)
-    band = slack * eps * d[ids_v] + 1e-5 * np.abs(xref[ids_v]) + 1e-12
-    assert np.all(np.abs(vals_v - xref[ids_v]) <= band), np.max(np.abs(vals_v - xref[ids_v]) - band)
-    ref_ids, ref_vals = oracle.topk(xref, len(ids_v))
-    tol = slack * eps * d.max() + 1e-5 * np.abs(ref_vals) + 1e-12
-    assert np.all(np.abs(vals_v - ref_vals[: len(vals_v)]) <= tol)
+    check_bands(res["ids"], res["vals"], xref, slack * eps * d + 1e-5 * np.abs(xref) + 1e-12, len(res["ids"]))
 
 
 def queries(g, n, seed):
@@ -117,13 +110,13 @@ def test_same_alone_and_in_the_mix(gde, g0):
                 mixed[r["qid"]] = r
     S.close()
     assert len(mixed) == len(qs)
-    d = g0.degrees().astype(np.float64)
     for qid, a in alone.items():
         m = mixed[qid]
-        eps = EPS[qs[qid][3]]
-        assert np.allclose(a["vals"], m["vals"], rtol=1e-5, atol=eps * d.max())
+        # a query's rounds do not depend on the others in the pool; only the order of its
+        # float atomics does, so its answer agrees to FP32 summation rounding
+        assert np.allclose(a["vals"], m["vals"], rtol=1e-5, atol=0)
         same = a["ids"] == m["ids"]
-        assert np.all(same | np.isclose(a["vals"], m["vals"], rtol=1e-5))
+        assert np.all(same | np.isclose(a["vals"], m["vals"], rtol=1e-5, atol=0))
 
 
 @pytest.mark.parametrize("kind", ["ppr", "katz"])
@@ -275,8 +268,8 @@ def test_deferred_heavy_queries(gde, g0, defer):
     out2 = S.run_until_idle()
     assert S.info()["steps"] <= steps_deferred
     second = {r["qid"]: r for r in out2 if not r["update"]}
-    d = g0.degrees().astype(np.float64)
     for q in qs:
         a, b = first[q[0]], second[q[0]]
-        assert np.allclose(a["vals"], b["vals"], rtol=1e-5, atol=1e-6 * d.max())
+        # deferral spreads a query's rounds over more steps without changing them
+        assert np.allclose(a["vals"], b["vals"], rtol=1e-5, atol=0)
     S.close()
