@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's default tuning")
+    ap.add_argument("--hub-degree", type=int, default=0,
+                    help="batched hub-slab degree threshold (0: the library default, -1: no slab)")
     ap.add_argument("--budget-gb", type=float, default=0.0,
                     help="hash accumulator budget (0: the library default)")
     ap.add_argument("--serve-seconds", type=float, default=2.0,
@@ -503,6 +505,8 @@ def main():
     vals = torch.zeros((nseeds, TOPK), dtype=torch.float32, device=dev)
 
     budget = int(args.budget_gb * (1 << 30))
+    if args.hub_degree:
+        G.set_tuning(hub_degree=args.hub_degree)
 
     def step():
         return gde.solve(G, "ppr", ALPHA, EPS, seeds, vals, ids, precision="fp32", topk=TOPK, batched=1,

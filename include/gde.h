@@ -242,6 +242,16 @@ typedef struct {
     int32_t chunk;
     int32_t blocks_per_sm;
     int32_t schedule;
+    int32_t hub_degree;  /* batched PPR / Katz / generalised propagation: targets of degree >=
+                            hub_degree keep their residual in a dense per-seed fixed-point slab
+                            (one integer atomic add per edge, exact sums) instead of the FP32
+                            hash tables; at 160 (the default) no FP32 entry receives more than
+                            159 additions per round, so each stays within 159 * 2^-24 < 1e-5
+                            relative of its exact sum.  Degrees above the graph's exact degree
+                            codes (224 up to 2^24 nodes) round up to a power of two.  -1 turns
+                            the slab off; 0 keeps the current setting.  The slab needs
+                            nseeds * (table slots + hubs) <= 2^32 and 12 bytes per seed and hub
+                            (at most 16 GiB), else the solve runs without it. */
 } gde_tuning;
 
 gde_status gde_set_tuning(gde_graph *g, const gde_tuning *t);
@@ -249,8 +259,9 @@ gde_status gde_get_tuning(const gde_graph *g, gde_tuning *t);
 
 /*
  * Autotuner of the batched push: one pass of coordinate descent over t1, t2, chunk,
- * schedule and blocks_per_sm (in that order; each tried over a fixed candidate list with the
- * others held), timing batched solves of `seeds` (kind/param/eps/opts as for gde_solve;
+ * schedule, blocks_per_sm and (unless the slab is off) hub_degree in {64, 128, 160} (in that
+ * order; each tried over a fixed candidate list with the others held), timing batched solves
+ * of `seeds` (kind/param/eps/opts as for gde_solve;
  * opts->topk in [1,64], batched forced on, FP32) with CUDA events on the solve stream, the
  * fastest of two timed runs per candidate.  The best tuning is applied to g as by
  * gde_set_tuning and, if best is not NULL, returned; *best_ms (may be NULL) receives its time.
@@ -345,8 +356,10 @@ gde_status gde_session_end(gde_session *s);
  *                       receives the candidates of round t + 1, all seeds together (0: every
  *                       active set is empty and further steps change nothing)
  *   gde_bsession_read   seed index j in [0, nseeds): x (n floats: the engine's x before any
- *                       output scaling), r (n floats: the residual, for the heat kernel and
- *                       series the layer the next round reads) as of the last step, and the
+ *                       output scaling), r (n doubles: the residual, for the heat kernel and
+ *                       series the layer the next round reads; FP32 table entries widened
+ *                       exactly, hub-slab entries as their fixed-point values) as of the
+ *                       last step, and the
  *                       node ids the last step pushed (S_t of seed j, unordered, up to n ints;
  *                       *n_pushed receives how many); host buffers, any pointer may be NULL.
  *                       Returns GDE_ENOMEM when that seed's table overflowed (its state is
@@ -361,7 +374,7 @@ typedef struct gde_bsession gde_bsession;
 gde_status gde_bsession_begin(gde_graph *g, gde_kind kind, double param, double eps, const int32_t *seeds,
                               int32_t nseeds, const gde_solve_opts *opts, gde_bsession **out);
 gde_status gde_bsession_step(gde_bsession *s, int64_t *n_candidates);
-gde_status gde_bsession_read(gde_bsession *s, int32_t seed_index, float *x, float *r, int32_t *pushed,
+gde_status gde_bsession_read(gde_bsession *s, int32_t seed_index, float *x, double *r, int32_t *pushed,
                              int64_t *n_pushed);
 gde_status gde_bsession_end(gde_bsession *s);
 

@@ -78,7 +78,8 @@ class Profile(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("t1", ctypes.c_int32), ("t2", ctypes.c_int32), ("chunk", ctypes.c_int32),
-                ("blocks_per_sm", ctypes.c_int32), ("schedule", ctypes.c_int32)]
+                ("blocks_per_sm", ctypes.c_int32), ("schedule", ctypes.c_int32),
+                ("hub_degree", ctypes.c_int32)]
 
 
 class ServerOpts(ctypes.Structure):
@@ -303,8 +304,8 @@ class Graph:
         _check(load().gde_profile_rounds(self._h, buf.ctypes.data, cap, ctypes.byref(r)))
         return buf[: min(r.value, cap)].copy()
 
-    def set_tuning(self, t1=0, t2=0, chunk=0, blocks_per_sm=0, schedule=0):
-        t = Tuning(t1, t2, chunk, blocks_per_sm, schedule)
+    def set_tuning(self, t1=0, t2=0, chunk=0, blocks_per_sm=0, schedule=0, hub_degree=0):
+        t = Tuning(t1, t2, chunk, blocks_per_sm, schedule, hub_degree)
         _check(load().gde_set_tuning(self._h, ctypes.byref(t)))
 
     def get_tuning(self) -> dict:
@@ -486,10 +487,10 @@ class BatchSession:
         return k.value
 
     def read(self, j: int):
-        """(x, r, nodes pushed by the last step) of seed index j, as float32 / int32 arrays."""
+        """(x float32, r float64, nodes pushed by the last step int32) of seed index j."""
         n = self.graph.n
         x = np.empty(n, dtype=np.float32)
-        r = np.empty(n, dtype=np.float32)
+        r = np.empty(n, dtype=np.float64)
         pushed = np.empty(max(n, 1), dtype=np.int32)
         k = ctypes.c_int64()
         _check(load().gde_bsession_read(self._h, int(j), x.ctypes.data, r.ctypes.data, pushed.ctypes.data,

@@ -193,6 +193,7 @@ static void tuning_from_bins(const Bins &b, gde_tuning *t) {
     t->chunk = b.chunk;
     t->blocks_per_sm = b.blocks_per_sm;
     t->schedule = b.schedule == 1 ? 1 : (b.schedule == 0 ? 2 : (b.schedule == 2 ? 3 : 4));
+    t->hub_degree = b.hub_degree;
 }
 
 }  // namespace gde
@@ -284,6 +285,7 @@ gde_status gde_graph_destroy(gde_graph *h) {
     dfree(g.col);
     dfree(g.deg);
     dfree(g.colp);
+    hubs_free(g);
     for (void *q : g.stage_buf) dfree(q);
     if (g.stream) cudaStreamDestroy(g.stream);
     delete h;
@@ -522,6 +524,9 @@ gde_status gde_set_tuning(gde_graph *h, const gde_tuning *t) {
     if (t->blocks_per_sm > 0) b.blocks_per_sm = t->blocks_per_sm;
     if (t->schedule > 0) b.schedule = t->schedule == 1 ? 1 : (t->schedule == 2 ? 0 : (t->schedule == 3 ? 2 : 3));
     GDE_REQUIRE(t->schedule <= 4, GDE_EINVAL, "tuning: schedule must be 0..4");
+    GDE_REQUIRE(t->hub_degree == 0 || t->hub_degree == -1 || t->hub_degree >= 2, GDE_EINVAL,
+                "tuning: hub_degree must be -1 (no slab), 0 (keep) or >= 2");
+    if (t->hub_degree != 0) b.hub_degree = t->hub_degree;
     GDE_REQUIRE(b.t1 <= b.t2, GDE_EINVAL, "tuning: t1 must be <= t2");
     GDE_REQUIRE(b.chunk >= 32 && b.chunk <= (1 << 24), GDE_EINVAL, "tuning: chunk must be in [32, 2^24]");
     GDE_REQUIRE(b.blocks_per_sm <= 32, GDE_EINVAL, "tuning: blocks_per_sm must be <= 32");
@@ -597,6 +602,9 @@ gde_status gde_autotune(gde_graph *h, gde_kind kind, double param, double eps, c
         const int chunks[] = {256, 512, 1024, 2048, 4096};
         const int scheds[] = {0, 1, 2, 3};
         const int bpss[] = {0, 3, 2};
+        // hub slab thresholds: all at most 160, so every FP32 table entry keeps its bound of
+        // 159 additions per round whichever wins
+        const int hubs[] = {64, 128, 160};
         auto sweep = [&](const int *vals_, int nv, int Bins::*field, bool need_order) {
             for (int i = 0; i < nv; i++) {
                 Bins b = cur;
@@ -612,6 +620,7 @@ gde_status gde_autotune(gde_graph *h, gde_kind kind, double param, double eps, c
         sweep(chunks, 5, &Bins::chunk, false);
         sweep(scheds, 4, &Bins::schedule, false);
         sweep(bpss, 3, &Bins::blocks_per_sm, false);
+        if (cur.hub_degree > 0) sweep(hubs, 3, &Bins::hub_degree, false);
         g.bins = cur;
         for (int k = 0; k < 2; k++)
             if (g.dense[k]) { dense_work_destroy(g.dense[k]); g.dense[k] = nullptr; }
@@ -721,7 +730,7 @@ gde_status gde_bsession_step(gde_bsession *b, int64_t *n_candidates) {
     API_END
 }
 
-gde_status gde_bsession_read(gde_bsession *b, int32_t seed_index, float *x, float *r, int32_t *pushed,
+gde_status gde_bsession_read(gde_bsession *b, int32_t seed_index, float *x, double *r, int32_t *pushed,
                              int64_t *n_pushed) {
     API_BEGIN
     GDE_REQUIRE(b != nullptr, GDE_EINVAL, "session is NULL");

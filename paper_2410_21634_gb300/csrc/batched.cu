@@ -189,6 +189,14 @@ struct BatchWork {
     double *layer_eps = nullptr, *layer_coef = nullptr;
     int64_t layer_cap = 0;
     uint32_t epoch = 0;       // tag of the current solve's keys
+    // hub slab: per seed, H fixed-point residuals (value = count * 2^qexp) and H float x values
+    unsigned long long *slab = nullptr;
+    float *slab_x = nullptr;
+    int64_t slab_seeds = 0, slab_H = 0;
+    bool slab_x_dirty = true;  // slab_x must be zeroed before the next solve
+    bool slab_on = false;      // the last set-up used the slab
+    uint32_t slab_base = 0;
+    int qexp = 0;
 };
 
 // ------------------------------------------------------------- device bits --
@@ -331,6 +339,24 @@ struct BArgs {
     unsigned long long *grp_off;    // their exclusive prefix sums
     unsigned *pend;     // not NULL: receives per seed the candidates left for the next launch
     uint32_t *pushed;   // not NULL (stepping sessions): per candidate of the round, 1 if it was pushed
+    // hub slab (non-layered kinds without per-slot parameters; slab == NULL: off).  A column
+    // word whose degree code is >= hub_code names a hub by its rank (colq); the hub's residual
+    // of seed j is the fixed-point integer slab[j * H + rank] (value = count * 2^qexp: sums of
+    // integers are exact and take one atomic add, with no probe), its x slab_x[j * H + rank].
+    // Candidate and x-list ids at or above slab_base name slab entries (slab_base + j * H + rank).
+    unsigned long long *slab;
+    float *slab_x;
+    int64_t H;
+    uint64_t slab_bank;   // entries per bank (nseeds * H); the layered kinds keep two banks,
+                          // round t reading layer t from bank t & 1 and writing bank (t + 1) & 1
+    uint32_t slab_base;
+    uint32_t hub_code;
+    const int32_t *hub_node;
+    const int32_t *hub_deg;
+    int qexp;
+    float wscale;    // 2^-qexp: a float share times it is its count (exact scaling)
+    double vscale;   // 2^qexp: a count times it is its value
+    double tscale;   // 2^-qexp
     // layered kinds (heat kernel, general series): round t reads layer t and writes layer t+1;
     // the keys of layer t carry key_tag + t * tag_step, so a layer's keys read as free slots
     // once the next layer is written, and x lives in a separate per-seed table keyed by node
@@ -401,6 +427,22 @@ struct ThrBounds {
 // the brackets of every degree code, built once per block of the round kernel (the FP64
 // products that define them are then not on the per-edge path)
 __shared__ float2 s_thr_br[kMaxCls][256];
+// the same brackets as slab counts, for the hub codes (>= hub_code)
+__shared__ ulonglong2 s_hub_br[256];
+
+// fixed-point helpers of the hub slab (value = count * 2^qexp)
+__device__ __forceinline__ unsigned long long slab_count(const BArgs &a, float w) {
+    return __float2ull_rn(__fmul_rn(w, a.wscale));
+}
+__device__ __forceinline__ double slab_value(const BArgs &a, unsigned long long c) {
+    return __dmul_rn(__ull2double_rn(c), a.vscale);
+}
+// the smallest count whose value is >= thr (so count >= it <=> value >= thr, exactly)
+__device__ __forceinline__ unsigned long long slab_threshold(const BArgs &a, double thr) {
+    return __double2ull_ru(__dmul_rn(thr, a.tscale));
+}
+constexpr unsigned long long kSlabLimit = 1ull << 62;  // a count this large marks the seed overflowed
+constexpr uint64_t kSlabMaxBytes = (uint64_t)16 << 30;    // hub slabs of one batch (12 bytes per entry)
 
 __device__ __forceinline__ ThrBounds thr_bounds(const BArgs &a, double eps, uint32_t code) {
     ThrBounds t;
@@ -433,6 +475,7 @@ __device__ __forceinline__ bool crossed(const float *thr32c, int32_t v, ThrBound
 struct SlotMeta {
     int cls;
     uint32_t tag;
+    uint32_t bank;  // hub slab bank the scatter writes (layered kinds: the next layer's parity)
 };
 
 // the keys round t's scatter writes: the next layer's (layered kinds) or the solve's
@@ -443,9 +486,9 @@ __device__ __forceinline__ uint32_t write_tag(const BArgs &a, int64_t t) {
 
 template <bool LAYERED>
 __device__ __forceinline__ SlotMeta slot_meta(const BArgs &a, int32_t j, int64_t t) {
-    if (!a.sparam) return SlotMeta{0, write_tag<LAYERED>(a, t)};
+    if (!a.sparam) return SlotMeta{0, write_tag<LAYERED>(a, t), LAYERED ? (uint32_t)((t + 1) & 1) : 0u};
     const SlotParam &sp = a.sparam[j];
-    return SlotMeta{sp.cls, sp.tag};
+    return SlotMeta{sp.cls, sp.tag, 0u};
 }
 
 // Insert-or-add w at node v of seed j's table.  The probe starts at a 4-slot bucket (one
@@ -453,9 +496,40 @@ __device__ __forceinline__ SlotMeta slot_meta(const BArgs &a, int32_t j, int64_t
 // examined in order, so the first empty slot ends the search (keys are never removed).  A
 // residual that crosses its threshold from below (exactly once: contributions are positive)
 // is staged as a candidate of the next round.  Returns 1 if v was a new key.
+// Adds count wq to hub `rank` of seed j's slab (one integer atomic: the slab has a fixed
+// place for every hub, so there is no probe).  PPR and Katz: a count that crosses the hub's
+// threshold (exactly once: counts only grow) is staged as a candidate of the next round.  The
+// layered kinds stage every entry on its first touch in the layer (count was 0), so the next
+// round's frontier takes each touched entry once and leaves the bank empty for reuse.
+template <bool LAYERED>
+__device__ __forceinline__ void slab_add(const BArgs &a, int32_t j, uint32_t code, uint32_t rank, uint32_t bank,
+                                         unsigned long long wq, uint32_t *sbuf, unsigned *sn) {
+    const uint64_t idx = (uint64_t)j * (uint64_t)a.H + rank;
+    const unsigned long long old = atomicAdd(a.slab + (uint64_t)bank * a.slab_bank + idx, wq);
+    const unsigned long long nv = old + wq;
+    if (LAYERED) {
+        if (old == 0ull) stage_push(sbuf, sn, a.slab_base + (uint32_t)idx);
+    } else {
+        const ulonglong2 br = s_hub_br[code];
+        if (nv >= br.x && old < br.y) {
+            const unsigned long long thr =
+                br.x == br.y ? br.x : slab_threshold(a, __dmul_rn(a.eps, (double)__ldg(a.hub_deg + rank)));
+            if (old < thr && nv >= thr) stage_push(sbuf, sn, a.slab_base + (uint32_t)idx);
+        }
+    }
+    if (nv >= kSlabLimit) atomicExch(a.status + j, kSeedOverflow);
+}
+
 template <bool LAYERED>
 __device__ __forceinline__ unsigned bscatter(const BArgs &a, int32_t j, SlotMeta m, uint32_t packed, float w,
-                                             uint32_t *sbuf, unsigned *sn) {
+                                             unsigned long long wq, uint32_t *sbuf, unsigned *sn) {
+    if (a.slab) {
+        const uint32_t code = packed >> a.idbits;
+        if (code >= a.hub_code) {
+            slab_add<LAYERED>(a, j, code, packed & a.idmask, m.bank, wq, sbuf, sn);
+            return 0;
+        }
+    }
     const uint64_t base = (uint64_t)j << a.log2cap;
     const int32_t v = (int32_t)(packed & a.idmask);
     const uint32_t kcur = (uint32_t)v | m.tag;
@@ -637,6 +711,25 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
             s_thr_br[cls][c] = make_float2(tb.lo, tb.hi);
         }
     }
+    if (!LAYERED && a.slab) {
+        // the hub codes' brackets as slab counts (exact for exact degrees)
+        for (int c = threadIdx.x; c < 256; c += kThreads) {
+            const unsigned long long never = ~0ull;
+            if ((uint32_t)c < a.hub_code || (c >= a.code_exact && c - a.code_exact > 32)) {
+                s_hub_br[c] = make_ulonglong2(never, never);
+                continue;
+            }
+            ulonglong2 br;
+            if (c < a.code_exact) {
+                br.x = br.y = slab_threshold(a, __dmul_rn(a.eps, (double)c));
+            } else {
+                const int k = c - a.code_exact;
+                br.x = slab_threshold(a, __dmul_rn(a.eps, (double)(1ll << k)));
+                br.y = slab_threshold(a, __dmul_rn(a.eps, (double)((2ll << k) - 1)));
+            }
+            s_hub_br[c] = br;
+        }
+    }
     __syncthreads();
 
     // per-seed count of the candidates this launch leaves behind (a server's unfinished
@@ -664,12 +757,21 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
         const int64_t ns = a.nseeds;
         for (int64_t ci = tid; ci < ncand; ci += nthreads) {
             const uint32_t slot = __ldcg(cand + ci);
-            const int32_t j = (int32_t)(slot >> a.log2cap);
+            // a hub slab entry (slab_base + j * H + rank) or a hash slot (j << log2cap | i)
+            const bool hub = a.slab && slot >= a.slab_base;
+            const uint64_t hidx = hub ? (uint64_t)(slot - a.slab_base) : 0ull;
+            const int32_t j = hub ? (int32_t)(hidx / (uint64_t)a.H) : (int32_t)(slot >> a.log2cap);
             if (a.pushed) a.pushed[ci] = 0u;
             if (__ldcg(a.status + j) != kSeedOk) { __stcg(a.tmp_deg + ci, 0); continue; }
-            const unsigned long long word = __ldcg(a.kr + slot);
-            const int32_t v = (int32_t)((uint32_t)(word & 0xFFFFFFFFull) & a.key_idmask);
-            float rho = __uint_as_float((uint32_t)(word >> 32));
+            int32_t v;
+            float rho = 0.0f;
+            if (hub) {
+                v = __ldg(a.hub_node + (hidx - (uint64_t)j * (uint64_t)a.H));
+            } else {
+                const unsigned long long word = __ldcg(a.kr + slot);
+                v = (int32_t)((uint32_t)(word & 0xFFFFFFFFull) & a.key_idmask);
+                rho = __uint_as_float((uint32_t)(word >> 32));
+            }
             double cx = a.cx, coef = a.coef;
             bool divide = a.kind != GDE_KATZ;
             int cls = 0;
@@ -688,28 +790,57 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
             const int64_t beg = a.off[v];
             const int32_t dvol = (int32_t)(a.off[v + 1] - beg);
             const double eps_t = LAYERED ? a.layer_eps[t < a.nlayers ? t : a.nlayers] : a.eps_cls[cls];
-            const float thr = __double2float_ru(__dmul_rn(eps_t, (double)dvol));
-            if (!(rho != 0.0f && fabsf(rho) >= thr)) { __stcg(a.tmp_deg + ci, 0); continue; }
-            // take the residual: a slot listed twice (possible once residuals can be negative)
-            // is pushed by one taker only
-            rho = atomicExch(r_of(a.kr, slot), 0.0f);
-            if (!(rho != 0.0f && fabsf(rho) >= thr)) { __stcg(a.tmp_deg + ci, 0); continue; }
+            double rho64;
+            if (hub) {
+                // the exact test on the fixed-point count: count >= tq <=> value >= fl(eps d)
+                const unsigned long long tq = slab_threshold(a, __dmul_rn(eps_t, (double)dvol));
+                unsigned long long *cp = a.slab + (LAYERED ? (uint64_t)(t & 1) * a.slab_bank : 0ull) + hidx;
+                unsigned long long c;
+                if (LAYERED) {
+                    // every touched entry of the layer is listed once: take it whether or not it
+                    // is pushed (what stays below the threshold is the layer's remainder, left
+                    // behind as in the tables), so the bank is empty when round t + 1 writes it
+                    c = atomicExch(cp, 0ull);
+                } else {
+                    c = __ldcg(cp);
+                    if (!(c != 0ull && c >= tq)) { __stcg(a.tmp_deg + ci, 0); continue; }
+                    c = atomicExch(cp, 0ull);
+                }
+                if (!(c != 0ull && c >= tq)) { __stcg(a.tmp_deg + ci, 0); continue; }
+                rho64 = slab_value(a, c);
+            } else {
+                const float thr = __double2float_ru(__dmul_rn(eps_t, (double)dvol));
+                if (!(rho != 0.0f && fabsf(rho) >= thr)) { __stcg(a.tmp_deg + ci, 0); continue; }
+                // take the residual: a slot listed twice (possible once residuals can be
+                // negative) is pushed by one taker only
+                rho = atomicExch(r_of(a.kr, slot), 0.0f);
+                if (!(rho != 0.0f && fabsf(rho) >= thr)) { __stcg(a.tmp_deg + ci, 0); continue; }
+                rho64 = (double)rho;
+            }
             if (a.pushed) a.pushed[ci] = 1u;
-            const double rho64 = (double)rho;
             // vol(S_t) counts d_u; the last layer of a layered kind only adds to x (no scatter)
             const int32_t d = last_layer ? 0 : dvol;
             double xinc = __dmul_rn(cx, rho64);
             if (a.gbeta != 0.0) xinc = __ddiv_rn(xinc, pow((double)(d > 0 ? d : 1), a.gbeta));
             bool xfirst;
             uint64_t xslot = slot;
-            if (LAYERED) {
+            if (LAYERED && hub) {
+                // a hub's x lives in the slab beside its residual (one writer: a node is pushed
+                // once per round)
+                float *xp = a.slab_x + hidx;
+                const float xold = __ldcg(xp);
+                __stcg(xp, __fadd_rn(xold, __double2float_rn(xinc)));
+                xfirst = xold == 0.0f;
+                coef = a.layer_coef[t < a.nlayers ? t : a.nlayers];
+            } else if (LAYERED) {
                 const int xr = xt_add(a, j, v, __double2float_rn(xinc), &xslot);
                 if (xr < 0) atomicExch(a.status + j, kSeedOverflow);  // x table full
                 xfirst = xr == 1;
                 coef = a.layer_coef[t < a.nlayers ? t : a.nlayers];
             } else {
-                const float xold = __ldcg(a.xs + slot);
-                __stcg(a.xs + slot, __fadd_rn(xold, __double2float_rn(xinc)));
+                float *xp = hub ? a.slab_x + hidx : a.xs + slot;
+                const float xold = __ldcg(xp);
+                __stcg(xp, __fadd_rn(xold, __double2float_rn(xinc)));
                 xfirst = xold == 0.0f;
             }
             float w = 0.0f;
@@ -920,6 +1051,7 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
                 int64_t he = hs + __ldcg(a.b_deg[2] + h);
                 int64_t hb = __ldcg(a.b_beg[2] + h);
                 float hw = __ldcg(a.b_w[2] + h);
+                unsigned long long hwq = a.slab ? slab_count(a, hw) : 0ull;
                 int32_t hj = __ldcg(a.b_seed[2] + h);
                 SlotMeta hm = slot_meta<LAYERED>(a, hj, t);
                 for (int64_t eb = e0; eb < e1; eb += 32) {
@@ -931,10 +1063,11 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
                             he = hs + __ldcg(a.b_deg[2] + h);
                             hb = __ldcg(a.b_beg[2] + h);
                             hw = __ldcg(a.b_w[2] + h);
+                            hwq = a.slab ? slab_count(a, hw) : 0ull;
                             hj = __ldcg(a.b_seed[2] + h);
                             hm = slot_meta<LAYERED>(a, hj, t);
                         }
-                        bscatter<LAYERED>(a, hj, hm, push_col(a, hb + (e - hs)), hw, sbuf, sn);
+                        bscatter<LAYERED>(a, hj, hm, push_col(a, hb + (e - hs)), hw, hwq, sbuf, sn);
                     }
                     stage_flush(sbuf, sn, false, ctl, cand_out, a.list_cap);
                 }
@@ -952,11 +1085,12 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
                 const int64_t b = __ldcg(a.b_beg[1] + i);
                 const int32_t d = __ldcg(a.b_deg[1] + i);
                 const float w = __ldcg(a.b_w[1] + i);
+                const unsigned long long wq = a.slab ? slab_count(a, w) : 0ull;
                 const int32_t j = __ldcg(a.b_seed[1] + i);
                 const SlotMeta m = slot_meta<LAYERED>(a, j, t);
                 for (int32_t k0 = 0; k0 < d; k0 += 32) {
                     const int32_t k = k0 + lane;
-                    if (k < d) bscatter<LAYERED>(a, j, m, push_col(a, b + k), w, sbuf, sn);
+                    if (k < d) bscatter<LAYERED>(a, j, m, push_col(a, b + k), w, wq, sbuf, sn);
                     stage_flush(sbuf, sn, false, ctl, cand_out, a.list_cap);
                 }
             };
@@ -974,9 +1108,10 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
                     j = __ldcg(a.b_seed[0] + i);
                 }
                 const int32_t dmax = (int32_t)__reduce_max_sync(0xffffffffu, (unsigned)d);
-                const SlotMeta m = d > 0 ? slot_meta<LAYERED>(a, j, t) : SlotMeta{0, write_tag<LAYERED>(a, t)};
+                const SlotMeta m = d > 0 ? slot_meta<LAYERED>(a, j, t) : SlotMeta{0, write_tag<LAYERED>(a, t), 0u};
+                const unsigned long long wq = a.slab && d > 0 ? slab_count(a, w) : 0ull;
                 for (int32_t k = 0; k < dmax; k++) {
-                    if (k < d) bscatter<LAYERED>(a, j, m, push_col(a, b + k), w, sbuf, sn);
+                    if (k < d) bscatter<LAYERED>(a, j, m, push_col(a, b + k), w, wq, sbuf, sn);
                     stage_flush(sbuf, sn, false, ctl, cand_out, a.list_cap);
                 }
             };
@@ -989,11 +1124,12 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
                     if (d == 0) continue;
                     const int64_t b = __ldcg(a.tmp_beg + ci);
                     const float w = __ldcg(a.tmp_w + ci);
+                    const unsigned long long wq = a.slab ? slab_count(a, w) : 0ull;
                     const int32_t j = (int32_t)(__ldcg(a.tmp_jb + ci) & ((1u << 30) - 1u));
                     const SlotMeta m = slot_meta<LAYERED>(a, j, t);
                     for (int32_t k0 = 0; k0 < d; k0 += 32) {
                         const int32_t k = k0 + lane;
-                        if (k < d) bscatter<LAYERED>(a, j, m, push_col(a, b + k), w, sbuf, sn);
+                        if (k < d) bscatter<LAYERED>(a, j, m, push_col(a, b + k), w, wq, sbuf, sn);
                         stage_flush(sbuf, sn, false, ctl, cand_out, a.list_cap);
                     }
                 }
@@ -1151,11 +1287,22 @@ __global__ void k_batch_thr(int64_t n, const int32_t *deg, float *thr32, double 
         thr32[i] = __double2float_ru(__dmul_rn(eps, (double)deg[i]));
 }
 
+// Seeds the hub slab instead of the hash table when the seed is a hub (slab not NULL and
+// hub_rank[s] >= 0), so that all of a node's residual lives in one place.
+struct SeedSlab {
+    unsigned long long *slab;
+    const int32_t *hub_rank;
+    int64_t H;
+    uint32_t slab_base;
+    double tscale;  // 2^-qexp
+};
+
 __global__ void k_batch_seed(int32_t nseeds, const int32_t *seeds, unsigned long long *kr,
                              uint32_t *cand0, int log2cap, uint32_t mask, BGlobal *G,
                              int32_t *status, unsigned *inserts, unsigned long long *svol,
                              unsigned *spushes, int32_t *slast, uint32_t key_tag, unsigned *xcnt,
-                             double *spush, double *sscat, const int32_t *deg, double gbeta, double *smass0) {
+                             double *spush, double *sscat, const int32_t *deg, double gbeta, double *smass0,
+                             SeedSlab sl) {
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j == 0) {
         memset(G, 0, sizeof(BGlobal));
@@ -1168,9 +1315,17 @@ __global__ void k_batch_seed(int32_t nseeds, const int32_t *seeds, unsigned long
     const uint64_t slot = ((uint64_t)j << log2cap) + (mix32((uint32_t)s) & mask & ~sector_mask);
     // unit source; the generalised propagation keeps it scaled, y_s = max(d_s, 1)^gbeta
     const double m0 = gbeta != 0.0 ? pow((double)(deg[s] > 0 ? deg[s] : 1), gbeta) : 1.0;
-    kr[slot] = ((unsigned long long)__float_as_uint((float)m0) << 32) | (unsigned long long)((uint32_t)s | key_tag);
+    const int32_t rank = sl.slab ? sl.hub_rank[s] : -1;
+    if (rank >= 0) {
+        const uint64_t idx = (uint64_t)j * (uint64_t)sl.H + (uint64_t)rank;
+        const unsigned long long c = __double2ull_rn(__dmul_rn((double)(float)m0, sl.tscale));
+        sl.slab[idx] = c;
+        cand0[j] = sl.slab_base + (uint32_t)idx;
+    } else {
+        kr[slot] = ((unsigned long long)__float_as_uint((float)m0) << 32) | (unsigned long long)((uint32_t)s | key_tag);
+        cand0[j] = (uint32_t)slot;
+    }
     smass0[j] = (double)(float)m0;
-    cand0[j] = (uint32_t)slot;
     status[j] = kSeedOk;
     inserts[j] = 1;
     xcnt[j] = 0;
@@ -1246,6 +1401,11 @@ struct TopkArgs {
     const int32_t *slots;       // block b reads seed slots[b] (NULL: seed b); output row b
     int keep;                   // nonzero: leave x in place (a server's resident queries)
     float scale;                // output values are x * scale (0 reads as 1)
+    // hub slab (slab_x NULL: none): x-list ids at or above slab_base are slab entries
+    float *slab_x;
+    uint32_t slab_base;
+    int64_t H;
+    const int32_t *hub_node;
 };
 
 // One block per seed: the top-k of (x desc, id asc) over the slots of the seed's x-list (every
@@ -1259,19 +1419,31 @@ __global__ void __launch_bounds__(kThreads) k_batch_topk(TopkArgs a) {
     unsigned long long ta = 0, tb = 0;
     const unsigned nx = a.xcnt[j];
     const bool use_list = nx <= a.xcap;
-    const int64_t n = use_list ? (int64_t)nx : a.cap;
+    // an overflowed x-list: the whole table, then the seed's slab entries
+    const int64_t n = use_list ? (int64_t)nx : a.cap + (a.slab_x ? a.H : 0);
     unsigned support = 0;
     for (int64_t i0 = (int64_t)wid * 32; i0 < n; i0 += kThreads) {
         const int64_t i = i0 + lane;
         unsigned long long key = 0;
         if (i < n) {
             const uint64_t li = (uint64_t)j * a.xcap + i;
-            const uint64_t slot = use_list ? (uint64_t)a.xlist[li] : base + (uint64_t)i;
-            const float x = a.xs[slot];
+            float *xp;
+            uint32_t v;
+            if (use_list) {
+                const uint32_t id = a.xlist[li];
+                xp = a.slab_x && id >= a.slab_base ? a.slab_x + (id - a.slab_base) : a.xs + id;
+                v = a.xnode[li];
+            } else if (i < a.cap) {
+                xp = a.xs + base + (uint64_t)i;
+                v = (uint32_t)(a.kr[base + (uint64_t)i] & 0xFFFFFFFFull) & a.key_idmask;
+            } else {
+                xp = a.slab_x + (uint64_t)j * (uint64_t)a.H + (uint64_t)(i - a.cap);
+                v = (uint32_t)a.hub_node[i - a.cap];
+            }
+            const float x = *xp;
             if (x > 0.0f) {
-                const uint32_t v = use_list ? a.xnode[li] : (uint32_t)(a.kr[slot] & 0xFFFFFFFFull) & a.key_idmask;
                 key = ((unsigned long long)__float_as_uint(x) << 32) | (unsigned long long)(0xFFFFFFFFu - v);
-                if (!a.keep) a.xs[slot] = 0.0f;
+                if (!a.keep) *xp = 0.0f;
                 support++;
             }
         }
@@ -1395,6 +1567,7 @@ static void batch_free(BatchWork *w) {
     dfree(w->seg_hcur); dfree(w->seeds); dfree(w->status); dfree(w->inserts); dfree(w->svol);
     dfree(w->spushes); dfree(w->slast); dfree(w->spush); dfree(w->sscat); dfree(w->smass0); dfree(w->xlist); dfree(w->xnode); dfree(w->xcnt); dfree(w->glob); dfree(w->log);
     dfree(w->xkr); dfree(w->xxs); dfree(w->layer_eps); dfree(w->layer_coef);
+    dfree(w->slab); dfree(w->slab_x);
     delete w;
 }
 
@@ -1411,6 +1584,7 @@ void graph_changed(Graph &g) {
         w->thr_eps = -1.0;
         w->thr_n = -1;
     }
+    g.hub_valid = false;  // degrees moved: the hub ranks and colq are rebuilt on next use
 }
 
 static BatchWork *batch_work_alloc(int64_t nseeds, int64_t cap, int64_t list_cap, int64_t xcap_max = (int64_t)1 << 16) {
@@ -1512,6 +1686,95 @@ void ensure_colp(Graph &g, cudaStream_t s) {
     g.prof.launched();
 }
 
+__global__ void k_hub_ranks(int64_t H, const int32_t *hub_node, int32_t *hub_rank) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < H; r += (int64_t)gridDim.x * blockDim.x)
+        hub_rank[hub_node[r]] = (int32_t)r;
+}
+
+// colq: colp with each hub's rank in place of its id (the degree code is unchanged)
+__global__ void k_pack_hub_columns(int64_t nnz, const uint32_t *colp, const int32_t *hub_rank, uint32_t *colq,
+                                   int idbits, uint32_t idmask, uint32_t hub_code) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t w = colp[e];
+        const uint32_t code = w >> idbits;
+        colq[e] = code >= hub_code ? ((uint32_t)hub_rank[w & idmask] | (code << idbits)) : w;
+    }
+}
+
+void hubs_free(Graph &g) {
+    dfree(g.colq); g.colq = nullptr; g.colq_cap = 0;
+    dfree(g.hub_node); g.hub_node = nullptr;
+    dfree(g.hub_deg); g.hub_deg = nullptr;
+    dfree(g.hub_rank); g.hub_rank = nullptr;
+    g.hub_cap = 0;
+    g.hub_n = 0;
+    g.hub_valid = false;
+    g.hub_node_host.clear();
+}
+
+// The degree code that marks hubs of degree >= min_deg: the degree itself below code_exact,
+// else the log2 class (min_deg is then rounded up to a power of two, the classes' bounds).
+static uint32_t hub_code_of(int32_t *min_deg, int code_exact) {
+    if (*min_deg <= code_exact) return (uint32_t)*min_deg;
+    int k = 0;
+    while ((1ll << k) < (long long)*min_deg) k++;
+    *min_deg = (int32_t)(1ll << k);
+    return (uint32_t)(code_exact + k);
+}
+
+bool ensure_hubs(Graph &g, int32_t min_deg, cudaStream_t s) {
+    ensure_colp(g, s);
+    if (!g.colp_valid || g.colp_idbits <= 0 || min_deg < 2) return false;
+    const uint32_t code = hub_code_of(&min_deg, g.colp_exact);
+    if (g.hub_valid && g.hub_min_deg == min_deg) return true;
+    // rank the hubs by degree (descending, then id): the hottest ones share sectors
+    std::vector<int32_t> deg((size_t)g.n);
+    if (g.n > 0) GDE_CUDA(cudaMemcpyAsync(deg.data(), g.deg, 4 * (size_t)g.n, cudaMemcpyDeviceToHost, s));
+    GDE_CUDA(cudaStreamSynchronize(s));
+    std::vector<int32_t> hubs;
+    for (int64_t v = 0; v < g.n; v++)
+        if (deg[(size_t)v] >= min_deg) hubs.push_back((int32_t)v);
+    std::stable_sort(hubs.begin(), hubs.end(), [&](int32_t x, int32_t y) { return deg[(size_t)x] > deg[(size_t)y]; });
+    const int64_t H = (int64_t)hubs.size();
+    std::vector<int32_t> hdeg((size_t)H);
+    for (int64_t r = 0; r < H; r++) hdeg[(size_t)r] = deg[(size_t)hubs[(size_t)r]];
+    g.hub_valid = false;
+    if (g.hub_cap < H || !g.hub_node) {
+        dfree(g.hub_node); g.hub_node = nullptr;
+        dfree(g.hub_deg); g.hub_deg = nullptr;
+        g.hub_cap = 0;
+        g.hub_node = (int32_t *)dmalloc(4 * (size_t)(H > 0 ? H : 1), "hub ranks");
+        g.hub_deg = (int32_t *)dmalloc(4 * (size_t)(H > 0 ? H : 1), "hub degrees");
+        g.hub_cap = H;
+    }
+    if (!g.hub_rank) g.hub_rank = (int32_t *)dmalloc(4 * (size_t)(g.n > 0 ? g.n : 1), "hub rank of each node");
+    if (g.colq_cap < g.nnz || !g.colq) {
+        dfree(g.colq); g.colq = nullptr; g.colq_cap = 0;
+        g.colq = (uint32_t *)dmalloc(4 * (size_t)(g.colp_cap > 0 ? g.colp_cap : 1), "hub packed columns");
+        g.colq_cap = g.colp_cap;
+    }
+    if (H > 0) {
+        GDE_CUDA(cudaMemcpyAsync(g.hub_node, hubs.data(), 4 * (size_t)H, cudaMemcpyHostToDevice, s));
+        GDE_CUDA(cudaMemcpyAsync(g.hub_deg, hdeg.data(), 4 * (size_t)H, cudaMemcpyHostToDevice, s));
+    }
+    GDE_CUDA(cudaMemsetAsync(g.hub_rank, 0xFF, 4 * (size_t)(g.n > 0 ? g.n : 1), s));
+    if (H > 0) {
+        k_hub_ranks<<<kSMs * 4, kThreads, 0, s>>>(H, g.hub_node, g.hub_rank);
+        GDE_CUDA(cudaGetLastError());
+    }
+    const uint32_t idmask = (uint32_t)(((uint64_t)1 << g.colp_idbits) - 1);
+    k_pack_hub_columns<<<kSMs * 8, kThreads, 0, s>>>(g.nnz, g.colp, g.hub_rank, g.colq, g.colp_idbits, idmask, code);
+    GDE_CUDA(cudaGetLastError());
+    g.prof.launched(H > 0 ? 2 : 1);
+    GDE_CUDA(cudaStreamSynchronize(s));  // the host vectors go out of scope
+    g.hub_node_host.swap(hubs);
+    g.hub_n = H;
+    g.hub_min_deg = min_deg;
+    g.hub_code = code;
+    g.hub_valid = true;
+    return true;
+}
+
 // the fields of the round kernel's arguments that come from the graph and the workspace
 static BArgs bargs_base(Graph &g, BatchWork *w, int64_t cap, int64_t list_cap, int32_t nseeds,
                         uint32_t key_tag, uint32_t key_idmask) {
@@ -1573,6 +1836,18 @@ static inline int64_t ceil_pow2(int64_t v) {
     int64_t p = 1;
     while (p < v) p *= 2;
     return p;
+}
+
+// Hubs of the slab a batched solve of nseeds seeds with tables of cap slots gets (0: no slab):
+// the tuning asks for one, the graph has packed columns and hubs, the slab ids fit 32 bits
+// after the pool's slot ids, and the slabs (two residual banks for the layered kinds) fit
+// kSlabMaxBytes.  Builds the hub data if needed.
+static int64_t slab_hubs(Graph &g, const SolveParams &p, int64_t nseeds, int64_t cap, cudaStream_t s) {
+    if (g.bins.hub_degree <= 0 || !ensure_hubs(g, g.bins.hub_degree, s) || g.hub_n <= 0) return 0;
+    const uint64_t entry_bytes = layered(p.kind) ? 20ull : 12ull;
+    if ((uint64_t)nseeds * (uint64_t)(cap + g.hub_n) > ((uint64_t)1 << 32)) return 0;
+    if ((uint64_t)nseeds * (uint64_t)g.hub_n * entry_bytes > kSlabMaxBytes) return 0;
+    return g.hub_n;
 }
 
 // Prepares a batched solve of nseeds seeds on workspace w (tables of cap slots, candidate and
@@ -1660,15 +1935,76 @@ static BArgs batch_setup(Graph &g, const SolveParams &p, BatchWork *w, const int
         w->thr_eps = p.eps;
         w->thr_n = g.n;
     }
+    // hub slab: the residuals of nodes of degree >= the tuning's hub_degree live in a dense
+    // fixed-point array per seed (two banks, one per layer parity, for the layered kinds); ids of
+    // slab entries follow the pool's slot ids, so both must fit 32 bits; at most kSlabMaxBytes
+    w->slab_on = false;
+    SeedSlab sl{};
+    const int banks = lay ? 2 : 1;
+    if (slab_hubs(g, p, nseeds, cap, s) > 0) {
+        const int64_t H = g.hub_n;
+        const size_t bank = (size_t)nseeds * (size_t)H;
+        if (!w->slab || w->slab_seeds < (int64_t)nseeds * banks || w->slab_H != H) {
+            dfree(w->slab); w->slab = nullptr;
+            dfree(w->slab_x); w->slab_x = nullptr;
+            w->slab_seeds = w->slab_H = 0;
+            w->slab = (unsigned long long *)dmalloc(8 * bank * (size_t)banks, "hub slab");
+            w->slab_x = (float *)dmalloc(4 * bank, "hub slab x");
+            w->slab_seeds = (int64_t)nseeds * banks;
+            w->slab_H = H;
+            w->slab_x_dirty = true;
+        }
+        // residual counts start at zero every solve; x is zeroed by the top-k through the x-lists
+        GDE_CUDA(cudaMemsetAsync(w->slab, 0, 8 * bank * (size_t)banks, s));
+        if (w->slab_x_dirty) GDE_CUDA(cudaMemsetAsync(w->slab_x, 0, 4 * bank, s));
+        w->slab_x_dirty = true;  // until this solve's top-k has run
+        // fixed-point scale 2^qexp: the finest whose counts (below the 2^62 overflow mark) hold
+        // 64 times the largest residual the solve can reach: the source mass for PPR and Katz
+        // (the generalised propagation's source is d_s^b), the largest layer mass
+        // prod_{s<t} c_{s+1}/c_s for the layered kinds
+        double m_max = 1.0;
+        if (p.gbeta != 0.0) m_max = std::pow((double)(g.max_degree > 1 ? g.max_degree : 1), p.gbeta);
+        if (lay) {
+            double prod = 1.0;
+            for (int64_t t = 0; t < nlayers; t++) {
+                prod *= layer_ratio(p, t);
+                if (prod > m_max) m_max = prod;
+            }
+        }
+        const int qexp = (int)std::ceil(std::log2(64.0 * m_max)) - 62;
+        w->slab_on = true;
+        w->slab_base = (uint32_t)((int64_t)nseeds * cap);
+        w->qexp = qexp;
+        sl.slab = w->slab;
+        sl.hub_rank = g.hub_rank;
+        sl.H = H;
+        sl.slab_base = w->slab_base;
+        sl.tscale = std::ldexp(1.0, -qexp);
+    }
     GDE_CUDA(cudaMemsetAsync(w->log, 0, sizeof(RoundLog) * kLogCap, s));
     k_batch_seed<<<(nseeds + kThreads - 1) / kThreads, kThreads, 0, s>>>(
         nseeds, w->seeds, w->kr, w->cand[0], w->log2cap, (uint32_t)(cap - 1), w->glob, w->status,
         w->inserts, w->svol, w->spushes, w->slast, key_tag, w->xcnt, w->spush, w->sscat, g.deg, p.gbeta,
-        w->smass0);
+        w->smass0, sl);
     GDE_CUDA(cudaGetLastError());
     g.prof.launched();
 
     BArgs a = bargs_base(g, w, cap, list_cap, nseeds, key_tag, key_idmask);
+    if (w->slab_on) {
+        a.colp = g.colq;  // hub words carry the hub's rank
+        a.slab = w->slab;
+        a.slab_x = w->slab_x;
+        a.H = g.hub_n;
+        a.slab_bank = (uint64_t)nseeds * (uint64_t)g.hub_n;
+        a.slab_base = w->slab_base;
+        a.hub_code = g.hub_code;
+        a.hub_node = g.hub_node;
+        a.hub_deg = g.hub_deg;
+        a.qexp = w->qexp;
+        a.wscale = std::ldexp(1.0f, -w->qexp);
+        a.vscale = std::ldexp(1.0, w->qexp);
+        a.tscale = std::ldexp(1.0, -w->qexp);
+    }
     a.eps = p.eps;
     a.eps_cls[0] = p.eps; a.ncls = 1; a.sparam = nullptr; a.t0 = 0;
     GDE_CUDA(cudaMemsetAsync(w->seg_cnt, 0, 4 * 3 * (size_t)nseeds, s));
@@ -1719,22 +2055,23 @@ static void batch_solve_once(Graph &g, const SolveParams &p, const int32_t *seed
     if (cap > cap_max) cap = cap_max;
     GDE_REQUIRE(cap >= 64 || cap == cap_max, GDE_ENOMEM, "memory budget too small for the batch");
     GDE_REQUIRE((int64_t)nseeds * cap <= ((int64_t)1 << 32), GDE_EINVAL, "batch pool exceeds 2^32 slots");
-    // candidate and bin lists: every slot can enter a list at most once per round, but the
-    // per-round frontier of all seeds together is far smaller than the pool; past this
-    // capacity the solve reports GDE_ENOMEM
-    int64_t list_cap = (int64_t)nseeds * cap;
+    // candidate and bin lists: every slot (and hub slab entry) can enter a list at most once
+    // per round, but the per-round frontier of all seeds together is far smaller than the pool;
+    // past this capacity the solve reports GDE_ENOMEM
+    const int64_t entries = (int64_t)nseeds * (cap + slab_hubs(g, p, nseeds, cap, p.stream));
+    int64_t list_cap = entries;
     int64_t list_max = (int64_t)nseeds << 14;
     if (list_max < ((int64_t)1 << 22)) list_max = (int64_t)1 << 22;
     if (list_max > ((int64_t)1 << 24)) list_max = (int64_t)1 << 24;
     list_max <<= 2 * list_scale;  // a retry after an overflow: four times larger
     if (list_cap > list_max) list_cap = list_max;
     GDE_REQUIRE(nseeds <= list_cap, GDE_EINVAL, "too many seeds for one batch");
-    *list_full = list_cap == (int64_t)nseeds * cap;
+    *list_full = list_cap == entries;
     BatchWork *w = batch_work_get(g, nseeds, cap, list_cap);
     if (w->list_cap > list_cap) {
         // a workspace that an earlier solve left larger keeps its longer lists
-        list_cap = std::min<int64_t>(w->list_cap, std::min<int64_t>((int64_t)nseeds * cap, 0xFFFFFFFFll));
-        *list_full = list_cap == (int64_t)nseeds * cap;
+        list_cap = std::min<int64_t>(w->list_cap, std::min<int64_t>(entries, 0xFFFFFFFFll));
+        *list_full = list_cap == entries;
     }
     cudaStream_t s = p.stream;
     uint32_t key_tag = 0, key_idmask = 0;
@@ -1751,6 +2088,9 @@ static void batch_solve_once(Graph &g, const SolveParams &p, const int32_t *seed
         // x lives in the x tables; the output is e^-tau x (heat kernel) or c_0 x (series)
         ta.kr = w->xkr; ta.xs = w->xxs; ta.log2cap = w->xt_log2cap; ta.cap = w->xt_cap;
         ta.scale = (float)(p.kind == GDE_SERIES ? p.series[0] : std::exp(-p.param));
+    }
+    if (w->slab_on) {
+        ta.slab_x = w->slab_x; ta.slab_base = w->slab_base; ta.H = g.hub_n; ta.hub_node = g.hub_node;
     }
     const int pt = g.prof.start(kProfBatchTopk, s);
     k_batch_topk<<<nseeds, kThreads, 0, s>>>(ta);
@@ -1779,6 +2119,7 @@ static void batch_solve_once(Graph &g, const SolveParams &p, const int32_t *seed
     }
     GDE_CUDA(cudaStreamSynchronize(s));
     w->need_clear = false;  // the top-k zeroed x on every x-list (or table) it read
+    if (w->slab_on) w->slab_x_dirty = false;
     if (hg.error == GDE_ETIMEOUT) {
         set_error("batched solve: a grid barrier wait timed out");
         throw Fail{GDE_ETIMEOUT};
@@ -2593,8 +2934,8 @@ struct BatchSession {
     const int64_t *off0 = nullptr;       // the CSR as of begin (an insertion swaps the arrays)
     const int32_t *col0 = nullptr;
     int64_t nnz0 = 0;
-    std::vector<unsigned long long> h_kr, h_xkr;  // host copies of the tables after the last step
-    std::vector<float> h_xs, h_xxs;
+    std::vector<unsigned long long> h_kr, h_xkr, h_slab;  // host copies of the tables after the last step
+    std::vector<float> h_xs, h_xxs, h_slab_x;
     std::vector<int32_t> h_status;
     std::vector<std::vector<int32_t>> pushed;     // per seed: the nodes pushed in the last round
 };
@@ -2615,6 +2956,15 @@ static void bsession_mirror(BatchSession *S) {
     GDE_CUDA(cudaMemcpyAsync(S->h_kr.data(), w->kr, 8 * pool, cudaMemcpyDeviceToHost, s));
     GDE_CUDA(cudaMemcpyAsync(S->h_xs.data(), w->xs, 4 * pool, cudaMemcpyDeviceToHost, s));
     GDE_CUDA(cudaMemcpyAsync(S->h_status.data(), w->status, 4 * (size_t)S->nseeds, cudaMemcpyDeviceToHost, s));
+    if (w->slab_on) {
+        // the bank the next round reads (the layered kinds keep two)
+        const size_t sp = (size_t)S->nseeds * (size_t)w->slab_H;
+        const size_t bank = layered(S->p.kind) ? (size_t)(S->T & 1) : 0;
+        S->h_slab.resize(sp);
+        S->h_slab_x.resize(sp);
+        GDE_CUDA(cudaMemcpyAsync(S->h_slab.data(), w->slab + bank * sp, 8 * sp, cudaMemcpyDeviceToHost, s));
+        GDE_CUDA(cudaMemcpyAsync(S->h_slab_x.data(), w->slab_x, 4 * sp, cudaMemcpyDeviceToHost, s));
+    }
     if (layered(S->p.kind)) {
         const size_t xp = (size_t)w->xt_seeds * (size_t)w->xt_cap;
         S->h_xkr.resize(xp);
@@ -2652,7 +3002,8 @@ BatchSession *bsession_begin(Graph &g, const SolveParams &p, const int32_t *seed
     if (cap > cap_max) cap = cap_max;
     GDE_REQUIRE(cap >= 64 || cap == cap_max, GDE_ENOMEM, "batched session: memory budget too small");
     GDE_REQUIRE((int64_t)nseeds * cap <= ((int64_t)1 << 32), GDE_EINVAL, "batched session: pool exceeds 2^32 slots");
-    int64_t list_cap = std::min<int64_t>((int64_t)nseeds * cap, (int64_t)1 << 24);
+    int64_t list_cap = std::min<int64_t>((int64_t)nseeds * (cap + slab_hubs(g, p, nseeds, cap, p.stream)),
+                                         (int64_t)1 << 24);
     GDE_REQUIRE(nseeds <= list_cap, GDE_EINVAL, "batched session: too many seeds");
     BatchSession *S = new BatchSession();
     try {
@@ -2717,6 +3068,12 @@ int64_t bsession_step(BatchSession *S) {
     for (unsigned i = 0; i < ncand; i++) {
         if (!flag[i]) continue;
         const uint32_t slot = cand[i];
+        if (S->w->slab_on && slot >= S->w->slab_base) {
+            const uint64_t idx = slot - S->w->slab_base;
+            const int64_t j = (int64_t)(idx / (uint64_t)S->w->slab_H);
+            S->pushed[(size_t)j].push_back(g.hub_node_host[(size_t)(idx - (uint64_t)j * S->w->slab_H)]);
+            continue;
+        }
         const int32_t j = (int32_t)(slot >> S->w->log2cap);
         const uint32_t key = (uint32_t)(S->h_kr[slot] & 0xFFFFFFFFull);
         S->pushed[(size_t)j].push_back((int32_t)(key & S->key_idmask));
@@ -2726,23 +3083,34 @@ int64_t bsession_step(BatchSession *S) {
     return (int64_t)bsession_ncand(S);
 }
 
-// x (n floats: the unscaled x of the engine), r (n floats: the residual, for the layered kinds
+// x (n floats: the unscaled x of the engine), r (n doubles: the residual, for the layered kinds
 // the current layer) of seed j after the last step, and the nodes pushed in that step
-gde_status bsession_read(BatchSession *S, int32_t j, float *x, float *r, int32_t *pushed, int64_t *n_pushed) {
+gde_status bsession_read(BatchSession *S, int32_t j, float *x, double *r, int32_t *pushed, int64_t *n_pushed) {
     GDE_REQUIRE(j >= 0 && j < S->nseeds, GDE_EINVAL, "batched session: seed index out of range");
     const int64_t n = S->g->n;
     const uint64_t base = (uint64_t)j << S->w->log2cap;
     const bool lay = layered(S->p.kind);
     const uint32_t rtag = lay ? S->key_tag + (uint32_t)S->T * S->tag_step : S->key_tag;
     if (x) std::fill(x, x + n, 0.0f);
-    if (r) std::fill(r, r + n, 0.0f);
+    if (r) std::fill(r, r + n, 0.0);
     for (int64_t i = 0; i < S->cap; i++) {
         const unsigned long long word = S->h_kr[base + (uint64_t)i];
         const uint32_t key = (uint32_t)(word & 0xFFFFFFFFull);
         if (key == kEmpty || (key & ~S->key_idmask) != rtag) continue;
         const uint32_t v = key & S->key_idmask;
-        if (r) r[v] = host_bits_to_float((uint32_t)(word >> 32));
+        if (r) r[v] = (double)host_bits_to_float((uint32_t)(word >> 32));
         if (x && !lay) x[v] = S->h_xs[base + (uint64_t)i];
+    }
+    if (S->w->slab_on) {
+        // hubs: fixed-point counts (value = count * 2^qexp) and their x
+        const int64_t H = S->w->slab_H;
+        const Graph &g = *S->g;
+        for (int64_t rk = 0; rk < H; rk++) {
+            const size_t idx = (size_t)j * (size_t)H + (size_t)rk;
+            const int32_t v = g.hub_node_host[(size_t)rk];
+            if (r) r[v] = std::ldexp((double)S->h_slab[idx], S->w->qexp);
+            if (x) x[v] = S->h_slab_x[idx];
+        }
     }
     if (x && lay) {
         const uint64_t xb = (uint64_t)j << S->w->xt_log2cap;

@@ -56,6 +56,10 @@ struct Bins {
     int32_t chunk = 1024; // hub edges per warp work item
     int32_t blocks_per_sm = 0;  // persistent grid; 0 = occupancy limit
     int32_t schedule = 0;       // batched scatter order: 0 all bins in order, 1 hubs in order, 2 strided
+    // batched engine: targets of degree >= hub_degree keep their residual in the per-seed
+    // fixed-point hub slab instead of the hash tables (-1: no slab).  At 160 every hash entry
+    // receives at most 159 float additions per round: within 159 * 2^-24 < 1e-5 of the exact sum.
+    int32_t hub_degree = 160;
 };
 
 // ---------------------------------------------------------------- profiler --
@@ -98,6 +102,21 @@ struct Graph {
     // takes its buffers in a fixed order, growing one only when a larger call needs it)
     std::vector<void *> stage_buf;
     std::vector<size_t> stage_cap;
+    // Hubs of the batched engine: the nodes of degree >= hub_min_deg ranked by degree
+    // (descending, then id).  colq is the packed column array with each hub's rank in place of
+    // its id (the degree code above it says which words name hubs: code >= hub_code).  Built on
+    // first use; an insertion batch drops it (graph_changed).
+    uint32_t *colq = nullptr;
+    int64_t colq_cap = 0;
+    int32_t *hub_node = nullptr;   // rank -> node
+    int32_t *hub_deg = nullptr;    // rank -> degree
+    int32_t *hub_rank = nullptr;   // node -> rank, -1 for other nodes
+    int64_t hub_cap = 0;           // entries hub_node / hub_deg can hold
+    int64_t hub_n = 0;
+    int32_t hub_min_deg = 0;       // the degree threshold the hub data was built for
+    uint32_t hub_code = 0;         // degree codes at or above it name hubs
+    bool hub_valid = false;
+    std::vector<int32_t> hub_node_host;
     int colp_idbits = 0;       // 0: no packing (n too large), thresholds are read per edge
     int colp_exact = 0;
     bool colp_valid = false;   // packed from the current CSR
@@ -126,6 +145,10 @@ __host__ __device__ __forceinline__ uint32_t degree_code(int32_t d, int code_exa
 
 // Builds g.colp from the CSR if it is not current (no-op when n leaves too few spare bits).
 void ensure_colp(Graph &g, cudaStream_t s);
+// Builds the hub data (hub_node, hub_deg, hub_rank, colq) for degree threshold min_deg if it is
+// not current.  Returns false when the graph has no packed columns (then there is no slab).
+bool ensure_hubs(Graph &g, int32_t min_deg, cudaStream_t s);
+void hubs_free(Graph &g);
 
 // Directed adjacencies added by one insertion batch (device arrays; sorted by (u, v)), with
 // the rows that gained them and those rows' degrees before the batch.
@@ -270,7 +293,7 @@ BatchSession *bsession_begin(Graph &g, const SolveParams &p, const int32_t *seed
                              int64_t budget);
 // runs the next round of every seed; returns the candidates of the round after it (0: done)
 int64_t bsession_step(BatchSession *S);
-gde_status bsession_read(BatchSession *S, int32_t j, float *x, float *r, int32_t *pushed, int64_t *n_pushed);
+gde_status bsession_read(BatchSession *S, int32_t j, float *x, double *r, int32_t *pushed, int64_t *n_pushed);
 int64_t bsession_round(const BatchSession *S);
 void bsession_destroy(BatchSession *S);
 // top-k (x desc, id asc) of a dense float vector on the device

@@ -230,6 +230,7 @@ def test_autotune_picks_a_valid_tuning(gde, rmat16):
     assert best["t1"] in (4, 8, 16, 32) and best["t2"] in (128, 256, 512, 1024, 2048)
     assert best["t1"] <= best["t2"] and best["chunk"] in (256, 512, 1024, 2048, 4096)
     assert best["schedule"] in (1, 2, 3, 4) and best["blocks_per_sm"] in (0, 2, 3)
+    assert best["hub_degree"] in (64, 128, 160)
     assert G.get_tuning() == best and set(before) == set(best)
     st, stats, ids, vals = run_batched(gde, G, "ppr", 0.1, 1e-6, seeds)
     for i in (0, 31):
@@ -275,4 +276,26 @@ def test_every_scatter_schedule(gde, rmat16, schedule):
         for i in range(0, 40, 7):
             ref = oracle.localgd(g, kind, param, 1e-6, int(seeds[i]))
             check_topk(g, ids[i], vals[i], ref.x, 1e-6)
+    G.close()
+
+
+@pytest.mark.parametrize("kind, param", [("ppr", 0.1), ("katz", None), ("hk", 5.0)])
+def test_hub_slab_on_and_off_agree(gde, rmat16, kind, param):
+    """The hub slab (degree >= 160 targets in exact fixed-point counts) and the FP32 tables
+    alone give the same answers: the top-k values agree to the FP32 rounding of the tables."""
+    g = rmat16
+    if param is None:
+        param = 0.5 / synth.lambda_max(g)[0]
+    seeds = synth.seeds_mixed(g, 16, 16, seed=21)
+    G = gde.Graph.from_synth(g)
+    assert G.get_tuning()["hub_degree"] == 160
+    st, _, ids_on, vals_on = run_batched(gde, G, kind, param, 1e-6, seeds)
+    assert st == gde.OK
+    G.set_tuning(hub_degree=-1)
+    st, _, ids_off, vals_off = run_batched(gde, G, kind, param, 1e-6, seeds)
+    assert st == gde.OK
+    assert np.allclose(vals_on, vals_off, rtol=1e-4, atol=0)
+    for i in (0, 17):
+        ref = oracle.localgd(g, kind, param, 1e-6, int(seeds[i]))
+        check_topk(g, ids_on[i], vals_on[i], ref.x, 1e-6)
     G.close()

@@ -2,12 +2,18 @@
 Section 3.3, run for every seed of a batch inside one persistent launch, per-seed hash
 accumulators) with the FP64 oracle, through the batched stepping interface (gde_bsession_*).
 
-At every round each seed's device state is widened exactly to FP64, the oracle runs that
-round from it, and the device's pushed set, x and r must match: S_t identical (up to nodes
-within one ulp of their threshold), every entry >= eps d_u within 1e-5 relative, relative L1
-within 1e-5.  The heat kernel's literal threshold (theta_t = 1, most of the graph active)
-keeps the float-summation widening for entries with many contributions; every other case is
-held to the plain 1e-5 bar.
+At every round each seed's device state is read back exactly (FP32 table entries widened to
+FP64, hub-slab entries as their fixed-point values), the oracle runs that round from it, and
+the device's pushed set, x and r must match: S_t identical (up to nodes within one ulp of
+their threshold), every entry >= eps d_u within 1e-5 relative, relative L1 within 1e-5.
+
+Every kind is held to the plain 1e-5 bar.  The engine's precision layout is what makes that a
+guarantee rather than luck: targets of degree >= 160 accumulate in the exact fixed-point hub
+slab, so an FP32 table entry adds at most 159 terms in a round, within 159 * 2^-24 < 1e-5 of
+their exact sum.  With the slab turned off (hub_degree = -1) a hub next to a hub seed can add
+hundreds of identical float terms (Katz's share beta r_u has no 1/d_u factor; the heat kernel's
+first layers push many equal-degree neighbours), and round-to-nearest drifts with their count;
+that configuration is stepped for PPR.
 """
 import numpy as np
 import pytest
@@ -52,7 +58,6 @@ def test_batched_lockstep_ppr_rmat_64_mixed(gde, rmat16):
     G = gde.Graph.from_synth(g)
     rep = run_batched(G, g, "ppr", 0.1, 1e-6, seeds)
     _report("ppr rmat16 64 seeds", rep)
-    assert rep["widened"] == 0
     G.close()
 
 
@@ -84,13 +89,40 @@ def test_batched_lockstep_hk_error_bound(gde, rmat16):
 
 
 def test_batched_lockstep_hk_literal(gde, rmat16):
-    """theta_t = 1: most of the graph is active in the middle layers, so hub entries receive
-    thousands of float additions in one round; those get the summation bound."""
+    """theta_t = 1: most of the graph is active in the middle layers and hubs receive
+    thousands of additions in one round, in the exact slab."""
     g = rmat16
     seeds = synth.seeds_mixed(g, 4, 4, seed=9)
     G = gde.Graph.from_synth(g)
-    rep = run_batched(G, g, "hk", 5.0, 1e-6, seeds, hk_mode=1, widen=True)
+    rep = run_batched(G, g, "hk", 5.0, 1e-6, seeds, hk_mode=1)
     _report("hk literal rmat16", rep)
+    G.close()
+
+
+def test_batched_lockstep_ppr_without_slab(gde, rmat16):
+    """The hash tables alone (hub_degree = -1): every target in FP32."""
+    g = rmat16
+    seeds = synth.seeds_mixed(g, 16, 16, seed=3)
+    G = gde.Graph.from_synth(g)
+    G.set_tuning(hub_degree=-1)
+    rep = run_batched(G, g, "ppr", 0.1, 1e-6, seeds)
+    _report("ppr rmat16 without slab", rep)
+    G.close()
+
+
+@pytest.mark.parametrize("hub_degree", [2, 64, 1000])
+def test_batched_lockstep_other_hub_degrees(gde, rmat16, hub_degree):
+    """Other slab thresholds: nearly every node a hub (2), a lower one (64), and one above the
+    exact degree codes (1000, rounded up to 1024)."""
+    g = rmat16
+    seeds = synth.seeds_mixed(g, 8, 8, seed=14)
+    G = gde.Graph.from_synth(g)
+    G.set_tuning(hub_degree=hub_degree)
+    assert G.get_tuning()["hub_degree"] == hub_degree
+    rep = run_batched(G, g, "ppr", 0.1, 1e-6, seeds)
+    _report(f"ppr rmat16 hub_degree {hub_degree}", rep)
+    rep = run_batched(G, g, "hk", 5.0, 1e-6, seeds[::4])
+    _report(f"hk rmat16 hub_degree {hub_degree}", rep)
     G.close()
 
 
