@@ -111,6 +111,12 @@ typedef struct {
                                 I - (1-alpha) D^-1/2 A D^-1/2, eigenvalues in [alpha, 2-alpha]);
                                 dense output only; residuals change sign, so at exit
                                 |f - x| < eps d (two-sided); resid/mass = -1 */
+    int32_t katz_minus_source; /* GDE_KATZ: 1 returns the Katz vector f_Katz = x - e_s (Eq. f-katz)
+                                instead of x.  The source entry x_s = 1 + (residual returned to
+                                s) is kept as x_s - 1 in an FP64 word, so f_Katz,s has full
+                                relative precision in FP32 too, where x_s - 1 read from an FP32
+                                x_s would keep only about 6e-8 absolute.  Plain and batched
+                                LocalGD; GDE_EINVAL with other kinds or methods. */
 } gde_solve_opts;
 
 /* Per-seed result statistics (Definition 3.1 and Theorem 3.5). */

@@ -51,7 +51,8 @@ class SolveOpts(ctypes.Structure):
                 ("max_rounds", ctypes.c_int64), ("mem_budget_bytes", ctypes.c_int64),
                 ("hk_tol", ctypes.c_double), ("cuda_stream", ctypes.c_void_p), ("prop_beta", ctypes.c_double),
                 ("series_coef", ctypes.c_void_p), ("series_terms", ctypes.c_int64),
-                ("global_gd", ctypes.c_int32), ("chebyshev", ctypes.c_int32)]
+                ("global_gd", ctypes.c_int32), ("chebyshev", ctypes.c_int32),
+                ("katz_minus_source", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -221,7 +222,7 @@ def _current_stream():
 
 def make_opts(precision=FP64, topk=0, hk_threshold=0, batched=0, deterministic=0, flags=0,
               max_rounds=0, mem_budget_bytes=0, hk_tol=0.0, stream=None, prop_beta=0.0,
-              series_coef=None, global_gd=0, chebyshev=0) -> SolveOpts:
+              series_coef=None, global_gd=0, chebyshev=0, katz_minus_source=0) -> SolveOpts:
     o = SolveOpts()
     load().gde_solve_opts_init(ctypes.byref(o))
     o.precision = FP32 if precision in (FP32, "fp32", "float32") else FP64
@@ -231,6 +232,7 @@ def make_opts(precision=FP64, topk=0, hk_threshold=0, batched=0, deterministic=0
     o.prop_beta = float(prop_beta)
     o.global_gd = int(global_gd)
     o.chebyshev = int(chebyshev)
+    o.katz_minus_source = int(katz_minus_source)
     if series_coef is not None:
         c = np.ascontiguousarray(series_coef, dtype=np.float64)
         o._series = c  # kept alive with the options

@@ -178,6 +178,11 @@ static SolveParams make_params(Graph &g, gde_kind kind, double param, double eps
     p.deterministic = o.deterministic;
     p.stream = o.cuda_stream ? (cudaStream_t)o.cuda_stream : g.stream;
     p.gbeta = kind == GDE_GPPR ? o.prop_beta : 0.0;
+    GDE_REQUIRE(o.katz_minus_source == 0 || (o.katz_minus_source == 1 && kind == GDE_KATZ), GDE_EINVAL,
+                "katz_minus_source: 0, or 1 with GDE_KATZ");
+    GDE_REQUIRE(!(o.katz_minus_source && (o.global_gd || o.chebyshev)), GDE_EINVAL,
+                "katz_minus_source: LocalGD only (not global_gd)");
+    p.katz_minus_source = o.katz_minus_source;
     return p;
 }
 

@@ -194,6 +194,7 @@ struct BatchWork {
     float *slab_x = nullptr;
     int64_t slab_seeds = 0, slab_H = 0;
     bool slab_x_dirty = true;  // slab_x must be zeroed before the next solve
+    double *xsrc = nullptr;    // Katz with f_Katz output: per seed x_s - 1 in FP64
     bool slab_on = false;      // the last set-up used the slab
     uint32_t slab_base = 0;
     int qexp = 0;
@@ -354,6 +355,10 @@ struct BArgs {
     const int32_t *hub_node;
     const int32_t *hub_deg;
     int qexp;
+    // Katz with f_Katz output (xsrc not NULL): x_s - 1 of seed j in FP64 in xsrc[j] (starts at -1
+    // and gains every residual pushed at the seed s = seed_ids[j])
+    double *xsrc;
+    const int32_t *seed_ids;
     float wscale;    // 2^-qexp: a float share times it is its count (exact scaling)
     double vscale;   // 2^qexp: a count times it is its value
     double tscale;   // 2^-qexp
@@ -850,6 +855,7 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
                 else
                     w = __double2float_rn(__dmul_rn(coef, rho64));
             }
+            if (!LAYERED && a.xsrc && v == __ldg(a.seed_ids + j)) a.xsrc[j] = __dadd_rn(a.xsrc[j], rho64);
             my_rs += fabs(rho64);
             my_vol += (unsigned long long)dvol;
             {
@@ -1302,7 +1308,7 @@ __global__ void k_batch_seed(int32_t nseeds, const int32_t *seeds, unsigned long
                              int32_t *status, unsigned *inserts, unsigned long long *svol,
                              unsigned *spushes, int32_t *slast, uint32_t key_tag, unsigned *xcnt,
                              double *spush, double *sscat, const int32_t *deg, double gbeta, double *smass0,
-                             SeedSlab sl) {
+                             SeedSlab sl, double *xsrc) {
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j == 0) {
         memset(G, 0, sizeof(BGlobal));
@@ -1326,6 +1332,7 @@ __global__ void k_batch_seed(int32_t nseeds, const int32_t *seeds, unsigned long
         cand0[j] = (uint32_t)slot;
     }
     smass0[j] = (double)(float)m0;
+    if (xsrc) xsrc[j] = -1.0;
     status[j] = kSeedOk;
     inserts[j] = 1;
     xcnt[j] = 0;
@@ -1401,6 +1408,9 @@ struct TopkArgs {
     const int32_t *slots;       // block b reads seed slots[b] (NULL: seed b); output row b
     int keep;                   // nonzero: leave x in place (a server's resident queries)
     float scale;                // output values are x * scale (0 reads as 1)
+    // Katz with f_Katz output (xsrc not NULL): the seed's entry is xsrc[j] = x_s - 1 (FP64)
+    const double *xsrc;
+    const int32_t *seed_ids;
     // hub slab (slab_x NULL: none): x-list ids at or above slab_base are slab entries
     float *slab_x;
     uint32_t slab_base;
@@ -1440,11 +1450,13 @@ __global__ void __launch_bounds__(kThreads) k_batch_topk(TopkArgs a) {
                 xp = a.slab_x + (uint64_t)j * (uint64_t)a.H + (uint64_t)(i - a.cap);
                 v = (uint32_t)a.hub_node[i - a.cap];
             }
-            const float x = *xp;
+            float x = *xp;
             if (x > 0.0f) {
-                key = ((unsigned long long)__float_as_uint(x) << 32) | (unsigned long long)(0xFFFFFFFFu - v);
                 if (!a.keep) *xp = 0.0f;
                 support++;
+                if (a.xsrc && (int32_t)v == a.seed_ids[j]) x = __double2float_rn(a.xsrc[j]);
+                if (x > 0.0f)
+                    key = ((unsigned long long)__float_as_uint(x) << 32) | (unsigned long long)(0xFFFFFFFFu - v);
             }
         }
         top64_insert(ta, tb, key, lane);
@@ -1567,7 +1579,7 @@ static void batch_free(BatchWork *w) {
     dfree(w->seg_hcur); dfree(w->seeds); dfree(w->status); dfree(w->inserts); dfree(w->svol);
     dfree(w->spushes); dfree(w->slast); dfree(w->spush); dfree(w->sscat); dfree(w->smass0); dfree(w->xlist); dfree(w->xnode); dfree(w->xcnt); dfree(w->glob); dfree(w->log);
     dfree(w->xkr); dfree(w->xxs); dfree(w->layer_eps); dfree(w->layer_coef);
-    dfree(w->slab); dfree(w->slab_x);
+    dfree(w->slab); dfree(w->slab_x); dfree(w->xsrc);
     delete w;
 }
 
@@ -1629,6 +1641,7 @@ static BatchWork *batch_work_alloc(int64_t nseeds, int64_t cap, int64_t list_cap
         w->spush = (double *)dmalloc(8 * (size_t)nseeds, "seed pushed mass");
         w->sscat = (double *)dmalloc(8 * (size_t)nseeds, "seed scattered mass");
         w->smass0 = (double *)dmalloc(8 * (size_t)nseeds, "seed source mass");
+        w->xsrc = (double *)dmalloc(8 * (size_t)nseeds, "seed source entries");
         w->xcap = cap < xcap_max ? cap : xcap_max;
         w->xlist = (uint32_t *)dmalloc(4 * (size_t)nseeds * (size_t)w->xcap, "x lists");
         w->xnode = (uint32_t *)dmalloc(4 * (size_t)nseeds * (size_t)w->xcap, "x lists");
@@ -1938,6 +1951,7 @@ static BArgs batch_setup(Graph &g, const SolveParams &p, BatchWork *w, const int
     // hub slab: the residuals of nodes of degree >= the tuning's hub_degree live in a dense
     // fixed-point array per seed (two banks, one per layer parity, for the layered kinds); ids of
     // slab entries follow the pool's slot ids, so both must fit 32 bits; at most kSlabMaxBytes
+    const bool katz_f = p.kind == GDE_KATZ && p.katz_minus_source;
     w->slab_on = false;
     SeedSlab sl{};
     const int banks = lay ? 2 : 1;
@@ -1985,11 +1999,15 @@ static BArgs batch_setup(Graph &g, const SolveParams &p, BatchWork *w, const int
     k_batch_seed<<<(nseeds + kThreads - 1) / kThreads, kThreads, 0, s>>>(
         nseeds, w->seeds, w->kr, w->cand[0], w->log2cap, (uint32_t)(cap - 1), w->glob, w->status,
         w->inserts, w->svol, w->spushes, w->slast, key_tag, w->xcnt, w->spush, w->sscat, g.deg, p.gbeta,
-        w->smass0, sl);
+        w->smass0, sl, katz_f ? w->xsrc : nullptr);
     GDE_CUDA(cudaGetLastError());
     g.prof.launched();
 
     BArgs a = bargs_base(g, w, cap, list_cap, nseeds, key_tag, key_idmask);
+    if (katz_f) {
+        a.xsrc = w->xsrc;
+        a.seed_ids = w->seeds;
+    }
     if (w->slab_on) {
         a.colp = g.colq;  // hub words carry the hub's rank
         a.slab = w->slab;
@@ -2091,6 +2109,9 @@ static void batch_solve_once(Graph &g, const SolveParams &p, const int32_t *seed
     }
     if (w->slab_on) {
         ta.slab_x = w->slab_x; ta.slab_base = w->slab_base; ta.H = g.hub_n; ta.hub_node = g.hub_node;
+    }
+    if (p.kind == GDE_KATZ && p.katz_minus_source) {
+        ta.xsrc = w->xsrc; ta.seed_ids = w->seeds;
     }
     const int pt = g.prof.start(kProfBatchTopk, s);
     k_batch_topk<<<nseeds, kThreads, 0, s>>>(ta);
@@ -2937,7 +2958,9 @@ struct BatchSession {
     std::vector<unsigned long long> h_kr, h_xkr, h_slab;  // host copies of the tables after the last step
     std::vector<float> h_xs, h_xxs, h_slab_x;
     std::vector<int32_t> h_status;
+    std::vector<double> h_xsrc;
     std::vector<std::vector<int32_t>> pushed;     // per seed: the nodes pushed in the last round
+    std::vector<int32_t> seeds_host;
 };
 
 static float host_bits_to_float(uint32_t b) {
@@ -2956,6 +2979,10 @@ static void bsession_mirror(BatchSession *S) {
     GDE_CUDA(cudaMemcpyAsync(S->h_kr.data(), w->kr, 8 * pool, cudaMemcpyDeviceToHost, s));
     GDE_CUDA(cudaMemcpyAsync(S->h_xs.data(), w->xs, 4 * pool, cudaMemcpyDeviceToHost, s));
     GDE_CUDA(cudaMemcpyAsync(S->h_status.data(), w->status, 4 * (size_t)S->nseeds, cudaMemcpyDeviceToHost, s));
+    if (S->p.kind == GDE_KATZ && S->p.katz_minus_source) {
+        S->h_xsrc.resize((size_t)S->nseeds);
+        GDE_CUDA(cudaMemcpyAsync(S->h_xsrc.data(), w->xsrc, 8 * (size_t)S->nseeds, cudaMemcpyDeviceToHost, s));
+    }
     if (w->slab_on) {
         // the bank the next round reads (the layered kinds keep two)
         const size_t sp = (size_t)S->nseeds * (size_t)w->slab_H;
@@ -3025,6 +3052,7 @@ BatchSession *bsession_begin(Graph &g, const SolveParams &p, const int32_t *seed
         S->col0 = g.col;
         S->nnz0 = g.nnz;
         S->pushed.assign((size_t)nseeds, std::vector<int32_t>());
+        S->seeds_host.assign(seeds_host, seeds_host + nseeds);
         bsession_mirror(S);
     } catch (...) {
         bsession_free(S);
@@ -3120,6 +3148,7 @@ gde_status bsession_read(BatchSession *S, int32_t j, float *x, double *r, int32_
             x[key & S->key_idmask] = S->h_xxs[xb + (uint64_t)i];
         }
     }
+    if (x && S->p.kind == GDE_KATZ && S->p.katz_minus_source) x[S->seeds_host[(size_t)j]] = (float)S->h_xsrc[(size_t)j];
     const std::vector<int32_t> &pl = S->pushed[(size_t)j];
     if (pushed) std::copy(pl.begin(), pl.end(), pushed);
     if (n_pushed) *n_pushed = (int64_t)pl.size();

@@ -189,6 +189,7 @@ struct SolveParams {
     cudaStream_t stream;
     double gbeta;      // GDE_GPPR: b of M = D^-b A D^(b-1) (the engines run PPR on y = S r, S = max(d,1)^b)
     std::vector<double> series;  // GDE_SERIES: c_0..c_N (the layered system's coefficients)
+    int katz_minus_source;       // Katz: output f_Katz = x - e_s (source entry from an FP64 word)
 };
 
 // the heat kernel and the general series share the layered engine

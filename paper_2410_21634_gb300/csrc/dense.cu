@@ -70,6 +70,10 @@ struct DenseWork {
     int64_t *hub_vstart = nullptr;
     Ctl *ctl = nullptr;
     Ctl *hctl = nullptr;  // pinned
+    // Katz: the source entry x_s - 1 in FP64 (starts at -1, gains every residual pushed at s),
+    // so that f_Katz = x - e_s keeps full precision at s (no cancellation against the unit)
+    double *xsrc = nullptr;
+    int32_t seed = -1;
     Bins bins;
     // deterministic scatter (sort + segmented reduce), allocated on first use
     void *wbuf = nullptr;            // real[n]
@@ -176,6 +180,8 @@ template <typename real> struct FrontierArgs {
     double cx;            // x_u += cx * rho  (PPR alpha, else 1)
     double coef;          // PPR 1-alpha, Katz beta, HK fl(tau/(t+1))
     double gbeta;         // generalised propagation: x_u += (cx * rho) / S_u (0: plain PPR)
+    double *xsrc;         // Katz: x_seed - 1 in FP64, or NULL
+    int32_t seed;
     int propagate;
     int32_t t1, t2;
     int64_t *b_beg[3];
@@ -225,6 +231,7 @@ __global__ void __launch_bounds__(kThreads) k_frontier(FrontierArgs<real> a) {
                 a.x[u] = radd<real>(a.x[u], from_f64<real>(__dmul_rn(a.cx, rho64)));
             else
                 a.x[u] = radd<real>(a.x[u], rho);
+            if (KIND == GDE_KATZ && a.xsrc && u == a.seed) *a.xsrc = __dadd_rn(*a.xsrc, rho64);
             append_u32(&a.ctl->n_active, a.active, u, a.cap, &a.ctl->overflow);
             my_active += 1;
             my_vol += (unsigned long long)d;
@@ -516,6 +523,7 @@ DenseWork *dense_work_create(Graph &g, int precision) {
         }
         w->hub_vstart = (int64_t *)dmalloc(8 * n, "hub offsets");
         w->ctl = (Ctl *)dmalloc(sizeof(Ctl), "counters");
+        w->xsrc = (double *)dmalloc(sizeof(double), "source entry");
         GDE_CUDA(cudaMallocHost((void **)&w->hctl, sizeof(Ctl)));
     } catch (...) {
         dense_work_destroy(w);
@@ -569,12 +577,21 @@ void dense_work_destroy(DenseWork *w) {
     }
     dfree(w->hub_vstart);
     dfree(w->ctl);
+    dfree(w->xsrc);
     dfree(w->wbuf);
     for (int k = 0; k < 2; k++) { dfree(w->sact[k]); dfree(w->pkey[k]); dfree(w->pval[k]); }
     dfree(w->vdeg); dfree(w->vstart); dfree(w->dscratch); dfree(w->dtotal);
     if (w->htotal) cudaFreeHost(w->htotal);
     if (w->hctl) cudaFreeHost(w->hctl);
     delete w;
+}
+
+__global__ void k_set_source(double *xsrc) { *xsrc = -1.0; }
+
+// the output's source entry f_Katz,s = x_s - 1, from the FP64 source word
+template <typename real>
+__global__ void k_patch_source(real *dst, int32_t seed, const double *xsrc) {
+    dst[seed] = from_f64<real>(*xsrc);
 }
 
 template <typename real>
@@ -597,6 +614,12 @@ static void begin_impl(Graph &g, DenseWork *w, const SolveParams &p, int32_t see
         g.prof.launched();
     }
     GDE_CUDA(cudaGetLastError());
+    w->seed = seed;
+    if (p.kind == GDE_KATZ) {
+        k_set_source<<<1, 1, 0, p.stream>>>(w->xsrc);
+        GDE_CUDA(cudaGetLastError());
+        g.prof.launched();
+    }
     w->kind = p.kind;
     w->t = 0;
     w->ncand = 1;
@@ -629,7 +652,7 @@ static int64_t round_impl(Graph &g, DenseWork *w, const SolveParams &p, RoundInf
     fa.rcur = KIND == GDE_HK ? (real *)w->rl[cur] : nullptr;
     fa.propagate = last_layer ? 0 : 1;
     if (KIND == GDE_PPR) { fa.cx = p.param; fa.coef = 1.0 - p.param; fa.gbeta = p.gbeta; }
-    else if (KIND == GDE_KATZ) { fa.cx = 1.0; fa.coef = p.param; }
+    else if (KIND == GDE_KATZ) { fa.cx = 1.0; fa.coef = p.param; fa.xsrc = w->xsrc; fa.seed = w->seed; }
     else {
         fa.cx = 1.0;
         fa.coef = layer_ratio(p, t);
@@ -768,6 +791,22 @@ void dense_read(Graph &g, DenseWork *w, const SolveParams &p, void *x, void *r, 
     const size_t bytes = w->rsz * (size_t)g.n;
     const cudaMemcpyKind k = device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (x && g.n) GDE_CUDA(cudaMemcpyAsync(x, w->x, bytes, k, p.stream));
+    if (x && g.n && p.kind == GDE_KATZ && p.katz_minus_source) {
+        // x - e_s: the source entry from the FP64 source word
+        if (device_ptrs) {
+            if (p.precision == GDE_FP64)
+                k_patch_source<double><<<1, 1, 0, p.stream>>>((double *)x, w->seed, w->xsrc);
+            else
+                k_patch_source<float><<<1, 1, 0, p.stream>>>((float *)x, w->seed, w->xsrc);
+            GDE_CUDA(cudaGetLastError());
+        } else {
+            double v = 0.0;
+            GDE_CUDA(cudaMemcpyAsync(&v, w->xsrc, sizeof v, cudaMemcpyDeviceToHost, p.stream));
+            GDE_CUDA(cudaStreamSynchronize(p.stream));
+            if (p.precision == GDE_FP64) ((double *)x)[w->seed] = v;
+            else ((float *)x)[w->seed] = (float)v;
+        }
+    }
     if (r && g.n) {
         if (layered(p.kind)) {
             // after round t-1 the current layer is t
@@ -809,6 +848,14 @@ void dense_output(Graph &g, DenseWork *w, const SolveParams &p, void *dst_dev) {
                                                                       (float *)dst_dev, scale, apply);
     GDE_CUDA(cudaGetLastError());
     g.prof.launched();
+    if (p.kind == GDE_KATZ && p.katz_minus_source) {
+        if (p.precision == GDE_FP64)
+            k_patch_source<double><<<1, 1, 0, p.stream>>>((double *)dst_dev, w->seed, w->xsrc);
+        else
+            k_patch_source<float><<<1, 1, 0, p.stream>>>((float *)dst_dev, w->seed, w->xsrc);
+        GDE_CUDA(cudaGetLastError());
+        g.prof.launched();
+    }
 }
 
 }  // namespace gde

@@ -55,9 +55,14 @@ def near_threshold(r, thr):
 
 
 def run(G, g, kind, param, eps, seed, precision="fp64", hk_mode=0, max_rounds=100000,
-        check_every=1):
+        check_every=1, katz_minus_source=0):
+    """katz_minus_source=1 (Katz): the device reads back f_Katz = x - e_s, its source entry
+    from the engine's FP64 source word; the oracle runs on x = f + e_s, and the source entry
+    f_s is compared on its own at 1e-5 relative every round (it is small, so the eps d_u mask
+    of the other entries would skip it)."""
     import paper_2410_21634_gb300 as gde
-    S = gde.Session(G, kind, param, eps, seed, precision=precision, hk_threshold=hk_mode)
+    S = gde.Session(G, kind, param, eps, seed, precision=precision, hk_threshold=hk_mode,
+                    katz_minus_source=katz_minus_source)
     d = g.degrees().astype(np.float64)
     x, r, _ = S.read()
     t = 0
@@ -68,6 +73,8 @@ def run(G, g, kind, param, eps, seed, precision="fp64", hk_mode=0, max_rounds=10
     try:
         while t < max_rounds:
             xo = x.astype(np.float64)
+            if katz_minus_source:
+                xo[seed] += 1.0  # the engine's x_s = 1 + f_s
             ro = r.astype(np.float64)
             rn = np.zeros(g.n) if kind == "hk" else None
             if kind == "hk":
@@ -92,6 +99,11 @@ def run(G, g, kind, param, eps, seed, precision="fp64", hk_mode=0, max_rounds=10
             r_or = rn if kind == "hk" else ro
             xd = x.astype(np.float64)
             rd = r.astype(np.float64)
+            if katz_minus_source:
+                xo[seed] -= 1.0  # compare f = x - e_s
+                if xo[seed] != 0.0:
+                    rel_s = abs(xd[seed] - xo[seed]) / abs(xo[seed])
+                    assert rel_s <= FP32_REL, f"round {t}: source entry f_s rel {rel_s:.3g}"
             if precision == "fp64":
                 ex, er = _rel_l1(xd, xo), _rel_l1(rd, r_or)
                 assert ex <= FP64_REL_L1, f"round {t}: x rel L1 {ex}"
@@ -147,7 +159,8 @@ def _oracle_round(g, kind, param, eps, xo, ro, t, hk_mode, coef):
     return oracle.localgd_round(g, kind, param, eps, xo, ro, t=t), None, eps, eps
 
 
-def run_batched(G, g, kind, param, eps, seeds, hk_mode=0, coef=None, widen=False, max_rounds=100000):
+def run_batched(G, g, kind, param, eps, seeds, hk_mode=0, coef=None, widen=False, max_rounds=100000,
+                katz_minus_source=0):
     """Lock-step comparison of the batched FP32 engine (every seed of the batch advanced by one
     persistent launch per round) with the FP64 oracle.  At every round t and for every seed j:
     the device state (x^t, r^t) of seed j is widened exactly to FP64, the oracle runs round t
@@ -162,7 +175,7 @@ def run_batched(G, g, kind, param, eps, seeds, hk_mode=0, coef=None, widen=False
     Returns a report: rounds, compared entries, worst relative errors, widened entries and
     rounds skipped for near-threshold differences."""
     import paper_2410_21634_gb300 as gde
-    kw = {"hk_threshold": hk_mode}
+    kw = {"hk_threshold": hk_mode, "katz_minus_source": katz_minus_source}
     if coef is not None:
         kw["series_coef"] = np.asarray(coef, dtype=np.float64)
     S = gde.BatchSession(G, kind, param, eps, seeds, **kw)
@@ -182,9 +195,13 @@ def run_batched(G, g, kind, param, eps, seeds, hk_mode=0, coef=None, widen=False
             for j in range(ns):
                 x, r = state[j]
                 xo = x.astype(np.float64)
+                if katz_minus_source:
+                    xo[seeds[j]] += 1.0  # the engine's x_s = 1 + f_s
                 ro = r.astype(np.float64)
                 r0 = ro.copy()
                 rr, rn, et, en = _oracle_round(g, oracle_kind, param, eps, xo, ro, t, hk_mode, coef)
+                if katz_minus_source:
+                    xo[seeds[j]] -= 1.0
                 pre.append((xo, rn if layered else ro, rr, r0, et * d))
             ncand = S.step()
             for j in range(ns):
@@ -200,6 +217,11 @@ def run_batched(G, g, kind, param, eps, seeds, hk_mode=0, coef=None, widen=False
                 rep["pushes"] += len(pushed)
                 xd = x.astype(np.float64)
                 rd = r.astype(np.float64)
+                if katz_minus_source and xo[seeds[j]] != 0.0:
+                    sj = seeds[j]
+                    rel_s = abs(xd[sj] - xo[sj]) / abs(xo[sj])
+                    assert rel_s <= FP32_REL, f"seed {j} round {t}: source entry f_s rel {rel_s:.3g}"
+                    rep["max_rel_source"] = max(rep.get("max_rel_source", 0.0), rel_s)
                 big = (np.abs(r_or) >= ed) & (r_or != 0)
                 if big.any():
                     rel = np.abs(rd[big] - r_or[big]) / np.abs(r_or[big])
@@ -231,6 +253,8 @@ def run_batched(G, g, kind, param, eps, seeds, hk_mode=0, coef=None, widen=False
                     for j in range(ns):
                         x, r = state[j]
                         xo, ro = x.astype(np.float64), r.astype(np.float64)
+                        if katz_minus_source:
+                            xo[seeds[j]] += 1.0
                         r0 = ro.copy()
                         rr, _, et, _ = _oracle_round(g, oracle_kind, param, eps, xo, ro, t, hk_mode, coef)
                         assert rr.n_active == 0 or np.all(near_threshold(r0[rr.active], et * d[rr.active])), \
