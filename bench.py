@@ -66,9 +66,13 @@ def parse():
                     help="batched hub-slab degree threshold (0: the library default, -1: no slab)")
     ap.add_argument("--budget-gb", type=float, default=0.0,
                     help="hash accumulator budget (0: the library default)")
-    ap.add_argument("--serve-seconds", type=float, default=2.0,
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="seconds of the serving stream measured after the batched bench (0: skip)")
     ap.add_argument("--no-gd", action="store_true", help="skip the global GD vs LocalGD comparison")
+    ap.add_argument("--no-c2", action="store_true",
+                    help="skip the plain FP64 sweep on R-MAT 22 (PPR, Katz, heat kernel over eps)")
+    ap.add_argument("--no-c3", action="store_true",
+                    help="skip the FP32-vs-FP64 precision comparison on Chung-Lu 2^24")
     ap.add_argument("--no-kinds", action="store_true", help="skip the batched heat-kernel line")
     ap.add_argument("--no-random-probe", action="store_true",
                     help="skip the random-access calibration of device memory")
@@ -442,6 +446,110 @@ def run_gd_compare(gde, g=None):
                         f"8 seeds at degree quantiles, one gde_solve per seed", "rows": rows}
 
 
+def run_c2(gde, g=None, nseeds=64):
+    """Plain FP64 LocalGD, one seed per gde_solve, on R-MAT scale 22 (edge factor 16, int32 CSR):
+    PPR alpha=0.1, Katz beta=0.5/lambda_max, heat kernel tau=5 (Taylor layers to 1e-12), at
+    eps in {1e-4, 1e-5, 1e-6, 1e-7}, 64 seeds at degree quantiles.  Per row: seeds/s, ms per
+    seed and GTEPS (sum_t vol(S_t) over the wall time of the 64 solves, device output)."""
+    import torch
+
+    import synth
+    if g is None:
+        g = synth.workload_graph("rmat22")
+    lam, _ = synth.lambda_max(g, rel_tol=1e-9, max_iter=2000)
+    G = gde.Graph.from_synth(g)
+    seeds = synth.seeds_quantile(g, nseeds)
+    out = torch.zeros((1, g.n), dtype=torch.float64, device="cuda")
+    rows = []
+    for kind, param in (("ppr", 0.1), ("katz", 0.5 / lam), ("hk", 5.0)):
+        for eps in (1e-4, 1e-5, 1e-6, 1e-7):
+            gde.solve(G, kind, param, eps, torch.tensor(seeds[:1], dtype=torch.int32, device="cuda"), out)
+            torch.cuda.synchronize()
+            vol = rounds = 0
+            t0 = time.perf_counter()
+            for sd in seeds:
+                _, st = gde.solve(G, kind, param, eps, torch.tensor([int(sd)], dtype=torch.int32, device="cuda"), out)
+                vol += st[0]["active_volume"]
+                rounds += st[0]["rounds"]
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            rows.append({"kind": kind, "param": param, "eps": eps, "seeds_per_s": len(seeds) / dt,
+                         "ms_per_seed": 1e3 * dt / len(seeds), "gteps": vol / dt / 1e9,
+                         "rounds_mean": rounds / len(seeds), "volume_mean": vol / len(seeds)})
+    G.close()
+    return {"workload": f"R-MAT scale 22 ({g.n} nodes, {g.nnz} CSR entries, edge factor 16, int32 CSR), "
+                        f"plain FP64 LocalGD, one gde_solve per seed, {nseeds} seeds at degree quantiles, "
+                        f"lambda_max = {lam:.6g}", "rows": rows}
+
+
+def run_c3(gde, g=None, nseeds=64, sample=8):
+    """FP32 vs FP64 on Chung-Lu n=2^24 (mean degree 20, exponent 2.1, int64 offsets / int32
+    columns): PPR alpha=0.15 and the heat kernel tau=10 at eps=1e-7, plain engine, 64 seeds at
+    degree quantiles.  Per precision: seeds/s and GTEPS over the 64 solves.  Per result on
+    `sample` of the seeds, the FP32 answer against the FP64 answer of the same seed (the FP64
+    engine equals the FP64 oracle to 1e-9 relative L1 on this graph: tests/test_gpu_fullsize.py):
+    relative L1 error, the largest absolute error, the largest relative error over entries
+    >= eps d_u, and whether every entry lies inside the method's error band (both answers
+    satisfy 0 <= f - x < eps d_u for the exact f, so they differ by less than eps d_u)."""
+    import numpy as np
+    import torch
+
+    import synth
+    if g is None:
+        g = synth.workload_graph("chung_lu_2p24")
+    G = gde.Graph.from_synth(g)
+    seeds = synth.seeds_quantile(g, nseeds)
+    pick = seeds[np.linspace(0, nseeds - 1, sample).round().astype(int)]
+    d = g.degrees().astype(np.float64)
+    band = 1e-7 * np.maximum(d, 1.0)
+    rows = []
+    eps = 1e-7
+    for kind, param in (("ppr", 0.15), ("hk", 10.0)):
+        times = {}
+        for precision, dt_t in (("fp64", torch.float64), ("fp32", torch.float32)):
+            out = torch.zeros((1, g.n), dtype=dt_t, device="cuda")
+            gde.solve(G, kind, param, eps, torch.tensor(seeds[:1], dtype=torch.int32, device="cuda"), out,
+                      precision=precision)
+            torch.cuda.synchronize()
+            vol = 0
+            t0 = time.perf_counter()
+            for sd in seeds:
+                _, st = gde.solve(G, kind, param, eps, torch.tensor([int(sd)], dtype=torch.int32, device="cuda"),
+                                  out, precision=precision)
+                vol += st[0]["active_volume"]
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            times[precision] = {"seeds_per_s": len(seeds) / dt, "gteps": vol / dt / 1e9}
+        errs = []
+        o64 = torch.zeros((1, g.n), dtype=torch.float64, device="cuda")
+        o32 = torch.zeros((1, g.n), dtype=torch.float32, device="cuda")
+        for sd in pick:
+            sdt = torch.tensor([int(sd)], dtype=torch.int32, device="cuda")
+            gde.solve(G, kind, param, eps, sdt, o64, precision="fp64")
+            gde.solve(G, kind, param, eps, sdt, o32, precision="fp32")
+            ref = o64[0].cpu().numpy()
+            x = o32[0].double().cpu().numpy()
+            diff = np.abs(x - ref)
+            big = np.abs(ref) >= eps * d
+            errs.append({"seed": int(sd), "degree": int(d[sd]),
+                         "rel_l1": float(diff.sum() / np.abs(ref).sum()),
+                         "max_abs": float(diff.max()),
+                         "max_rel_entries_ge_eps_d": float((diff[big] / np.abs(ref[big])).max()) if big.any() else 0.0,
+                         "within_eps_band": bool(np.all(diff < band + 1e-12))})
+        rows.append({"kind": kind, "param": param, "eps": eps,
+                     "fp64": times["fp64"], "fp32": times["fp32"],
+                     "fp32_speedup": times["fp32"]["seeds_per_s"] / times["fp64"]["seeds_per_s"],
+                     "fp32_vs_fp64_max_rel_l1": max(e["rel_l1"] for e in errs),
+                     "fp32_vs_fp64_max_rel_entries_ge_eps_d": max(e["max_rel_entries_ge_eps_d"] for e in errs),
+                     "fp32_all_within_eps_band": all(e["within_eps_band"] for e in errs),
+                     "per_result": errs})
+    G.close()
+    return {"workload": f"Chung-Lu n=2^24 ({g.n} nodes, {g.nnz} CSR entries, mean degree 20, exponent 2.1, "
+                        f"int64 offsets, int32 columns), plain engine, {nseeds} seeds at degree quantiles; "
+                        f"errors of the FP32 answers on {sample} of them against the FP64 answers",
+            "rows": rows}
+
+
 PROBE_GRID = 152 * 8
 PROBE_ACCESSES = 1 << 30
 
@@ -562,7 +670,14 @@ def main():
     k_ms = prof["batch_rounds_ms"] / launches
     # candidates tested per launch: the kernel's round log of the last solve (all steps are the
     # same solve)
-    cands = float(G.profile_rounds()[:, 0].sum())
+    rlog = G.profile_rounds()
+    cands = float(rlog[:, 0].sum())
+    # device time of the last solve's rounds: frontier phase (S_t, pushes placed) vs scatter
+    t_end, t_a = rlog[:, 3], rlog[:, 4]
+    t_prev = np.concatenate(([0.0], t_end[:-1]))
+    phases = {"frontier_ms": float((t_a - t_prev).sum() / 1e6), "scatter_ms": float((t_end - t_a).sum() / 1e6),
+              "rounds": int(rlog.shape[0]),
+              "heavy_rounds_ms": [round(float(x) / 1e6, 3) for x in (t_end - t_prev)[:4]]}
     alg_bytes = (BYTES_PER_EDGE * prof["edges"] + BYTES_PER_PUSH * prof["pushes"]) / launches \
         + BYTES_PER_CAND * cands
     achieved = alg_bytes / (k_ms / 1e3) / 1e9
@@ -586,6 +701,7 @@ def main():
                                f"{BYTES_PER_CAND} B per candidate",
                 "edges_per_launch": prof["edges"] / launches, "pushes_per_launch": prof["pushes"] / launches,
                 "candidates_per_launch": cands,
+                "phases_last_launch": phases,
                 "frac_kernel_model": kernel_bytes / (k_ms / 1e3) / 1e9 / peak,
                 "traffic_over_alg": traffic / alg_bytes if traffic else None,
                 "share_of_step": prof["batch_rounds_ms"] / ms if ms > 0 else None}
@@ -651,9 +767,21 @@ def main():
         G.close()  # release the batched pool first
         serving = run_serving(gde, args.serve_seconds, SERVE_SLOTS, SERVE_ROUNDS_PER_STEP)
     gd_compare = None
+    g22 = None
+    if (not args.no_gd or not args.no_c2) and rank == 0 and ws == 1:
+        import synth
+        g22 = synth.workload_graph("rmat22")
     if not args.no_gd and rank == 0 and ws == 1:
         G.close()
-        gd_compare = run_gd_compare(gde)
+        gd_compare = run_gd_compare(gde, g22)
+    c2 = None
+    if not args.no_c2 and rank == 0 and ws == 1:
+        G.close()
+        c2 = run_c2(gde, g22)
+    c3 = None
+    if not args.no_c3 and rank == 0 and ws == 1:
+        G.close()
+        c3 = run_c3(gde)
     line = {
         "metric": METRIC, "value": value, "unit": "seeds/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
@@ -676,6 +804,8 @@ def main():
         "batched_kinds": kinds,
         "serving": serving,
         "global_gd_vs_localgd": gd_compare,
+        "c2_plain_fp64_rmat22": c2,
+        "c3_fp32_vs_fp64_chung_lu_2p24": c3,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

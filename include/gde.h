@@ -328,6 +328,24 @@ gde_status gde_topk_f32_noalloc(const float *x, int64_t n, int32_t k, int32_t *o
 gde_status gde_probe_random_access(void *buf, uint64_t bytes, int64_t nops, int32_t mode, int32_t grid,
                                    int32_t reps, int32_t l2_fetch_bytes, void *cuda_stream, double *ms_out);
 
+/*
+ * Fault injection for failure-detection tests (no counterpart in the paper).  Nothing faults,
+ * traps or hangs on the device: a failure is injected on the host, or a bounded device-side
+ * wait is made to run out, and the call reports a status while the context stays usable.
+ *   gde_test_fail_alloc     the nth device allocation of this library from now on (any thread)
+ *                           fails as cudaMalloc's out-of-memory would: the call that makes it
+ *                           returns GDE_ENOMEM and writes no output; 0 disarms, nth < 0 is
+ *                           GDE_EINVAL.  Process-wide; for tests only.
+ *   gde_test_barrier_fault  later batched launches on g (solves, stepping sessions, servers)
+ *                           wait at most limit_ns at each grid barrier of the persistent round
+ *                           kernel (0: the default, 20 s), and block `block` of the launch leaves
+ *                           at its barrier number `barrier` (0 = first) without arriving, as a
+ *                           block that died would; the others' waits run out and the call
+ *                           returns GDE_ETIMEOUT.  block < 0 turns the fault off.
+ */
+gde_status gde_test_fail_alloc(int64_t nth);
+gde_status gde_test_barrier_fault(gde_graph *g, int64_t limit_ns, int32_t block, int32_t barrier);
+
 /* Thread-local description of the last failure of this thread ("" if none). */
 const char *gde_last_error(void);
 

@@ -35,7 +35,7 @@ EXPORTED = ["gde_solve_opts_init", "gde_graph_create", "gde_graph_destroy", "gde
             "gde_server_clock", "gde_server_create", "gde_server_destroy", "gde_server_submit",
             "gde_server_insert_edges", "gde_server_step", "gde_server_poll", "gde_server_info",
             "gde_probe_random_access", "gde_bsession_begin", "gde_bsession_step", "gde_bsession_read",
-            "gde_bsession_end"]
+            "gde_bsession_end", "gde_test_fail_alloc", "gde_test_barrier_fault"]
 
 
 class GdeError(RuntimeError):
@@ -141,6 +141,10 @@ def load(path: str | None = None):
     lib.gde_bsession_end.argtypes = [vp]
     for name in ("gde_bsession_begin", "gde_bsession_step", "gde_bsession_read", "gde_bsession_end"):
         getattr(lib, name).restype = ctypes.c_int
+    lib.gde_test_fail_alloc.argtypes = [I64]
+    lib.gde_test_fail_alloc.restype = ctypes.c_int
+    lib.gde_test_barrier_fault.argtypes = [vp, I64, I32, I32]
+    lib.gde_test_barrier_fault.restype = ctypes.c_int
     lib.gde_topk_f32_noalloc.argtypes = [vp, I64, I32, vp, vp, vp]
     lib.gde_topk_f32_noalloc.restype = ctypes.c_int
     lib.gde_profile_rounds.argtypes = [vp, vp, I64, ctypes.POINTER(I64)]
@@ -329,6 +333,11 @@ class Graph:
                                    ctypes.byref(o), ctypes.byref(t), ctypes.byref(ms)))
         return {f: getattr(t, f) for f, _ in t._fields_}, ms.value
 
+    def test_barrier_fault(self, limit_ns: int = 0, block: int = -1, barrier: int = 0):
+        """gde_test_barrier_fault: bounded grid-barrier waits of limit_ns and a block that leaves
+        at one barrier (tests only; block < 0 turns it off)."""
+        _check(load().gde_test_barrier_fault(self._h, int(limit_ns), int(block), int(barrier)))
+
     def close(self):
         if getattr(self, "_h", None):
             load().gde_graph_destroy(self._h)
@@ -401,6 +410,12 @@ def topk_noalloc(x, k: int, out_ids, out_vals, stream=None):
             stream = torch.cuda.current_stream(x.device).cuda_stream
         _check(load().gde_topk_f32_noalloc(_ptr(x)[0], int(x.numel()), int(k), _ptr(out_ids)[0],
                                            _ptr(out_vals)[0], stream))
+
+
+def test_fail_alloc(nth: int):
+    """gde_test_fail_alloc: the nth device allocation from now fails with GDE_ENOMEM (0 disarms;
+    tests only)."""
+    _check(load().gde_test_fail_alloc(int(nth)))
 
 
 PROBE_MODES = {"load": 0, "load_atomic": 1, "atomic": 2}

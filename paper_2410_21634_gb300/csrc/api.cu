@@ -1,5 +1,6 @@
 // C ABI entry points (include/gde.h): argument checks, graph store lifetime, the
 // single-seed solve loop and the stepping interface.
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -15,9 +16,19 @@ static thread_local std::string g_last_error;
 void set_error(const std::string &msg) { g_last_error = msg; }
 void clear_error() { g_last_error.clear(); }
 
+// Test fault injection (gde_test_fail_alloc): the n-th device allocation from the arming
+// fails as cudaMalloc's out-of-memory would (0: disarmed).  Process-wide.
+static std::atomic<long long> g_fail_alloc_in{0};
+
 void *dmalloc(size_t bytes, const char *what) {
     void *p = nullptr;
     if (bytes == 0) bytes = 16;
+    if (g_fail_alloc_in.load() > 0 && g_fail_alloc_in.fetch_sub(1) == 1) {
+        char buf[256];
+        snprintf(buf, sizeof(buf), "cudaMalloc(%zu bytes) for %s failed: injected allocation failure", bytes, what);
+        set_error(buf);
+        throw Fail{GDE_ENOMEM};
+    }
     cudaError_t e = cudaMalloc(&p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();  // clear the sticky-free allocation error
@@ -699,6 +710,25 @@ gde_status gde_session_end(gde_session *s) {
     }
     delete s;
     return GDE_OK;
+}
+
+gde_status gde_test_fail_alloc(int64_t nth) {
+    API_BEGIN
+    GDE_REQUIRE(nth >= 0, GDE_EINVAL, "nth must be >= 0");
+    g_fail_alloc_in.store((long long)nth);
+    API_END
+}
+
+gde_status gde_test_barrier_fault(gde_graph *h, int64_t limit_ns, int32_t block, int32_t barrier) {
+    API_BEGIN
+    GDE_REQUIRE(h != nullptr, GDE_EINVAL, "graph is NULL");
+    GDE_REQUIRE(limit_ns >= 0, GDE_EINVAL, "limit_ns must be >= 0");
+    Graph &g = h->g;
+    std::lock_guard<std::mutex> lock(g.mu);
+    g.dbg_bar_limit_ns = (unsigned long long)limit_ns;
+    g.dbg_fail_block = block < 0 ? -1 : block;
+    g.dbg_fail_barrier = block < 0 ? -1 : barrier;
+    API_END
 }
 
 gde_status gde_bsession_begin(gde_graph *h, gde_kind kind, double param, double eps, const int32_t *seeds,

@@ -235,8 +235,14 @@ __device__ __forceinline__ float *r_of(unsigned long long *kr, uint64_t slot) {
 }
 
 // Grid-wide barrier for a cooperative launch (all blocks co-resident).  Returns false if the
-// wait exceeded the time limit or another block recorded an error; the caller then returns.
-__device__ bool grid_sync(BGlobal *g, unsigned nblocks) {
+// wait exceeded the time limit (limit_ns) or another block recorded an error; the caller then
+// returns.  Fault injection for tests: the block fail_block leaves the kernel at its
+// fail_barrier-th barrier (counted from 0 in *nbar) without arriving, as a block that died
+// would; the others' bounded waits then run out and the launch reports GDE_ETIMEOUT.
+__device__ bool grid_sync(BGlobal *g, unsigned nblocks, unsigned long long limit_ns, int fail_block,
+                          int fail_barrier, int *nbar) {
+    const int k = (*nbar)++;
+    if ((int)blockIdx.x == fail_block && k == fail_barrier) return false;
     __syncthreads();
     __shared__ int s_ok;
     if (threadIdx.x == 0) {
@@ -252,7 +258,7 @@ __device__ bool grid_sync(BGlobal *g, unsigned nblocks) {
             const unsigned long long t0 = globaltimer();
             while (ld_acquire_u32(&g->bar_gen) == gen) {
                 if (ld_acquire_u32(&g->error) != 0) { ok = 0; break; }
-                if (globaltimer() - t0 > kBarrierLimitNs) {
+                if (globaltimer() - t0 > limit_ns) {
                     atomicCAS(&g->error, 0u, (unsigned)GDE_ETIMEOUT);
                     ok = 0;
                     break;
@@ -340,6 +346,11 @@ struct BArgs {
     unsigned long long *grp_off;    // their exclusive prefix sums
     unsigned *pend;     // not NULL: receives per seed the candidates left for the next launch
     uint32_t *pushed;   // not NULL (stepping sessions): per candidate of the round, 1 if it was pushed
+    // test fault injection: grid-barrier wait limit (0: kBarrierLimitNs) and a block that leaves
+    // at one barrier without arriving (fail_block < 0: none)
+    unsigned long long bar_limit_ns;
+    int32_t fail_block;
+    int32_t fail_barrier;
     // hub slab (non-layered kinds without per-slot parameters; slab == NULL: off).  A column
     // word whose degree code is >= hub_code names a hub by its rank (colq); the hub's residual
     // of seed j is the fixed-point integer slab[j * H + rank] (value = count * 2^qexp: sums of
@@ -695,6 +706,8 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
     const int64_t gw = (int64_t)wid * gridDim.x + blockIdx.x;
     BGlobal *G = a.glob;
     const unsigned long long t_start = globaltimer();
+    const unsigned long long bar_limit = a.bar_limit_ns ? a.bar_limit_ns : kBarrierLimitNs;
+    int nbar = 0;  // grid barriers passed by this block
     __shared__ uint32_t s_stage[kWarps][kStage];
     __shared__ unsigned s_nstage[kWarps];
     uint32_t *sbuf = s_stage[wid];
@@ -926,7 +939,7 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
                 if (lane == 0 && dm > 0) atomicMax(&ctl->dmax_push, dm);
             }
         }
-        if (!grid_sync(G, nblocks)) return;
+        if (!grid_sync(G, nblocks, bar_limit, a.fail_block, a.fail_barrier, &nbar)) return;
         const bool direct = ncand <= kDirectCand && __ldcg(&ctl->dmax_push) <= kDirectMaxDeg;
         if (!direct) {
 
@@ -968,7 +981,7 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
                 if (threadIdx.x == 0) ctl->units_total = tot;
             }
         }
-        if (!grid_sync(G, nblocks)) return;
+        if (!grid_sync(G, nblocks, bar_limit, a.fail_block, a.fail_barrier, &nbar)) return;
 
         // ---------------- phase A2: place the pushes seed by seed ----------------
         for (int64_t ci = tid; ci < ncand; ci += nthreads) {
@@ -1014,7 +1027,7 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
                 }
             }
         }
-        if (!grid_sync(G, nblocks)) return;
+        if (!grid_sync(G, nblocks, bar_limit, a.fail_block, a.fail_barrier, &nbar)) return;
         }  // !direct
         if (tid == 0 && lt < kLogCap) a.log[lt].tA_ns = globaltimer() - t_start;
         const unsigned long long tb0 = globaltimer();
@@ -1251,7 +1264,7 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
                 atomicMax(&a.log[lt].busy_max_ns, bm);
             }
         }
-        if (!grid_sync(G, nblocks)) return;
+        if (!grid_sync(G, nblocks, bar_limit, a.fail_block, a.fail_barrier, &nbar)) return;
         const unsigned next = __ldcg(&ctl->cand_out);
         const unsigned ovf = __ldcg(&ctl->overflow);
         if (tid == 0) {
@@ -1815,6 +1828,9 @@ static BArgs bargs_base(Graph &g, BatchWork *w, int64_t cap, int64_t list_cap, i
     a.glob = w->glob; a.log = w->log;
     const Bins &bins = g.bins;
     a.t1 = bins.t1; a.t2 = bins.t2; a.chunk = bins.chunk; a.schedule = bins.schedule;
+    a.bar_limit_ns = g.dbg_bar_limit_ns;
+    a.fail_block = g.dbg_fail_block;
+    a.fail_barrier = g.dbg_fail_barrier;
     return a;
 }
 

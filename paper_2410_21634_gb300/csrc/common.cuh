@@ -39,7 +39,7 @@ struct Fail {
         }                                                                           \
     } while (0)
 
-// device allocation that throws GDE_ENOMEM
+// device allocation that throws GDE_ENOMEM (also when the test injector says this one fails)
 void *dmalloc(size_t bytes, const char *what);
 void dfree(void *p);
 
@@ -123,6 +123,10 @@ struct Graph {
     bool symmetric = false;    // A = A^T verified at creation (insertions keep it)
     Profiler prof;
     Bins bins;                 // launch shape used by later solves
+    // test fault injection of the batched round kernel (gde_test_barrier_fault)
+    unsigned long long dbg_bar_limit_ns = 0;  // 0: the default limit
+    int32_t dbg_fail_block = -1;
+    int32_t dbg_fail_barrier = -1;
 };
 
 // row validation result bits

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def test_bench_line_contract():
     cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--graph", "rmat20", "--seeds", "64", "--steps", "3",
            "--warmup", "3", "--no-plain", "--no-cpu", "--no-autotune", "--serve-seconds", "0", "--no-gd",
-           "--no-kinds", "--probe-gb", "1"]
+           "--no-kinds", "--no-c2", "--no-c3", "--probe-gb", "1"]
     out = subprocess.run(cmd, capture_output=True, text=True, timeout=900, cwd=ROOT)
     assert out.returncode == 0, out.stderr[-3000:]
     lines = [ln for ln in out.stdout.splitlines() if ln.strip()]
