@@ -102,7 +102,7 @@ constexpr unsigned kDirectCand = 1u << GDE_DIRECT_CAND_LOG2;
 constexpr unsigned kDirectMaxDeg = 1u << GDE_DIRECT_DEG_LOG2;
 
 #ifndef GDE_SEED_GROUP
-#define GDE_SEED_GROUP 8
+#define GDE_SEED_GROUP 2
 #endif
 constexpr int kSeedGroup = GDE_SEED_GROUP;  // seeds whose bins are scattered together (schedule 3)
 

@@ -112,7 +112,7 @@ def test_injected_allocation_failure_batched(gde, c1, nth):
         failed = False
     except gde.GdeError as e:
         failed = True
-        assert e.value.status == gde.ENOMEM and "injected" in str(e.value)
+        assert e.status == gde.ENOMEM and "injected" in str(e)
         assert np.all(ids == -7) and np.all(vals == -1.0), "output written on failure"
     finally:
         gde.test_fail_alloc(0)

@@ -64,7 +64,8 @@ def test_katz_minus_source_output(gde, c1, frac):
     G = gde.Graph.from_synth(c1)
     out_f = np.zeros((len(seeds), c1.n), dtype=np.float32)
     out_x = np.zeros((len(seeds), c1.n), dtype=np.float32)
-    st, _ = gde.solve(G, "katz", beta, 1e-7, seeds, out_f, precision="fp32", deterministic=1, katz_minus_source=1)
+    st, stats = gde.solve(G, "katz", beta, 1e-7, seeds, out_f, precision="fp32", deterministic=1,
+                          katz_minus_source=1)
     assert st == gde.OK
     st, _ = gde.solve(G, "katz", beta, 1e-7, seeds, out_x, precision="fp32", deterministic=1)
     assert st == gde.OK
@@ -72,7 +73,9 @@ def test_katz_minus_source_output(gde, c1, frac):
         other = np.arange(c1.n) != s
         assert np.array_equal(out_x[i, other], out_f[i, other])
         assert out_f[i, s] > 0
-        assert abs(float(out_x[i, s]) - 1.0 - float(out_f[i, s])) <= 2.0 ** -23
+        # the FP32 x_s gains one rounding of up to half an ulp of 1 per push of s; the source
+        # word does not, which is what keeps f_s to FP32 relative precision
+        assert abs(float(out_x[i, s]) - 1.0 - float(out_f[i, s])) <= (stats[i]["rounds"] + 1) * 2.0 ** -24
     G.close()
 
 
