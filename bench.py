@@ -268,13 +268,9 @@ def run_serving(gde, seconds, slots, rounds_per_step, g=None, beta=None, budget_
     if beta is None:
         beta = 0.5 / synth.lambda_max(g)[0]
     G = gde.Graph.from_synth(g, check_symmetric=True)  # lets insertions keep the packed columns
-    if budget_gb <= 0:
-        # tables of 2n slots (the most a query can touch is n nodes, so no table passes half load)
-        # (slot indices are 32-bit: slots * cap <= 2^32)
-        cap = min(1 << int(np.ceil(np.log2(2 * g.n))), (1 << 32) // slots)
-        budget = slots * cap * 12
-    else:
-        budget = int(budget_gb * (1 << 30))
+    # the table pool: 2^31 table slots at 20 bytes (40 GB); queries take power-of-two runs of
+    # 64K-slot pages as they are admitted, up to 2n slots each
+    budget = int(budget_gb * (1 << 30)) if budget_gb > 0 else (1 << 31) * 20
     S = gde.Server(G, slots=slots, rounds_per_step=rounds_per_step, eps=SERVE["eps"], mem_budget_bytes=budget,
                    defer_volume=defer_volume)
     arrivals = synth.poisson_arrivals(SERVE["rate_qps"], seconds, seed=7)
@@ -351,7 +347,13 @@ def run_serving(gde, seconds, slots, rounds_per_step, g=None, beta=None, budget_
         "elapsed_s": elapsed, "edge_batches": info["edge_batches"], "steps": steps,
         "rounds": info["rounds"], "slots": slots, "rounds_per_step": rounds_per_step,
         "defer_volume": defer_volume if defer_volume != 0 else 1 << 23,
-        "slot_cap": info["cap"], "pool_gb": round(budget / 2**30, 1), "pushed_edges": info["volume"],
+        "admission": {"budget_gb": round(budget / 2**30, 1), "pool_pages": info["pool_pages"],
+                      "page_slots": info["page_slots"], "largest_table_slots": info["cap"],
+                      "peak_resident_queries": info["peak_resident"],
+                      "peak_gb_in_tables": round(info["peak_pages"] * info["page_slots"] * 20 / 2**30, 2),
+                      "readmissions": info["readmissions"],
+                      "evictions": info["evictions"], "slots": slots},
+        "pushed_edges": info["volume"],
         "step_seconds": {k: round(info[k], 4) for k in ("t_graph", "t_correct", "t_admit", "t_rounds", "t_results")}, "pushed_edges_first_answers": int(vol),
     }
 

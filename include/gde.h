@@ -404,10 +404,18 @@ gde_status gde_bsession_end(gde_bsession *s);
 
 /*
  * Serving (continuous batching of PPR and Katz queries on a graph that receives edge
- * insertions; the dynamic setting of Section 4).  A server owns a pool of `slots` resident
- * queries, each a per-query hash table of FP32 x and r in device memory (12 bytes per
- * table slot; the pool holds mem_budget_bytes, default 16 GB, so slots * cap * 12 <= budget
- * with cap a power of two <= 2 n).
+ * insertions; the dynamic setting of Section 4).  A server owns up to `slots` resident
+ * queries, each with a hash table of FP32 x and r in device memory, taken from a pool of
+ * mem_budget_bytes (default 16 GB; 20 bytes per table slot: key and residual 8, x 4, x-list 8).
+ * The pool is cut into pages of 2^16 table slots (fewer for graphs with n < 2^15); a query's
+ * table is a power-of-two run of pages (a buddy allocator), at most 2n slots.  Queries are
+ * admitted in arrival order while a slot and their table fit, so the number resident at once
+ * follows their memory, not a fixed count.  A new query's table starts at the largest size
+ * that the last 16 answered queries of its kind, tolerance class and seed-degree bucket
+ * (floor(log2(d_s + 1))) needed to hold their keys at an eighth load (the nearest lower bucket's
+ * when its own has none yet; one page at first); a query whose table overflows is started
+ * again, ahead of the queue and with its arrival time kept, with a table four times larger (up
+ * to the largest), and only overflowing the largest table answers GDE_ENOMEM.
  *   gde_server_submit        queues a query (qid chosen by the caller; kind GDE_PPR with
  *                            param = alpha in (0,1), or GDE_KATZ with param = beta > 0;
  *                            eps_class picks one of the server's tolerances; flags
@@ -443,12 +451,12 @@ typedef struct gde_server gde_server;
 #define GDE_SERVE_TRACK 1u  /* gde_server_submit: keep the query as a standing query */
 
 typedef struct {
-    int32_t slots;            /* resident queries (default 256) */
+    int32_t slots;            /* resident queries at most (default 256) */
     int32_t rounds_per_step;  /* LocalGD rounds per device step (default 4) */
     int32_t topk;             /* entries per result, 1..64 (default 64) */
     int32_t n_eps;            /* tolerance classes, 1..4 (default 1) */
     double eps[4];            /* their tolerances (default eps[0] = 1e-6) */
-    int64_t mem_budget_bytes; /* hash pool bytes, 0 = 16 GB */
+    int64_t mem_budget_bytes; /* table pool bytes (20 per table slot), 0 = 16 GB */
     int64_t defer_volume;     /* a query whose last step pushed more edges than this runs one
                                  round per step (its rounds are unchanged, only spread out) so
                                  the other queries' rounds in a step are not each held up by
@@ -472,13 +480,21 @@ typedef struct {
     int64_t steps;            /* device steps so far */
     int64_t rounds;           /* LocalGD rounds run by the pool so far */
     int64_t edge_batches;     /* insertion batches applied */
-    int64_t cap;              /* hash slots per query table */
+    int64_t cap;              /* hash slots of the largest query table */
     int64_t volume;           /* edges pushed by the pool so far (all queries, all rounds) */
     double t_graph;           /* seconds spent in steps on: graph updates (CSR rebuild), */
     double t_correct;         /*   warm-start corrections of resident queries, */
     double t_admit;           /*   admissions, */
     double t_rounds;          /*   LocalGD rounds (the persistent launches), */
     double t_results;         /*   convergence checks and top-k of answered queries */
+    int64_t pool_pages;       /* pages of the table pool (the memory budget) */
+    int64_t pages_used;       /* pages held by resident queries now */
+    int64_t page_slots;       /* table slots per page */
+    int32_t peak_resident;    /* most queries resident at once so far */
+    int32_t pad;
+    int64_t readmissions;     /* queries started again with a larger table after an overflow */
+    int64_t evictions;        /* standing queries whose slot or pages went to new queries */
+    int64_t peak_pages;       /* most pages held by resident queries at once so far */
 } gde_server_info_t;
 
 void gde_server_opts_init(gde_server_opts *o);

@@ -101,7 +101,10 @@ class ServerInfo(ctypes.Structure):
                 ("queued", ctypes.c_int32), ("steps", ctypes.c_int64), ("rounds", ctypes.c_int64),
                 ("edge_batches", ctypes.c_int64), ("cap", ctypes.c_int64), ("volume", ctypes.c_int64),
                 ("t_graph", ctypes.c_double), ("t_correct", ctypes.c_double), ("t_admit", ctypes.c_double),
-                ("t_rounds", ctypes.c_double), ("t_results", ctypes.c_double)]
+                ("t_rounds", ctypes.c_double), ("t_results", ctypes.c_double), ("pool_pages", ctypes.c_int64),
+                ("pages_used", ctypes.c_int64), ("page_slots", ctypes.c_int64), ("peak_resident", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("readmissions", ctypes.c_int64), ("evictions", ctypes.c_int64),
+                ("peak_pages", ctypes.c_int64)]
 
 
 _lib = None

@@ -30,6 +30,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <set>
 #include <vector>
 
 #include "common.cuh"
@@ -58,6 +59,9 @@ struct SlotParam {
     uint32_t tag;    // the slot's key tag (shifted above the id bits): a server retags a slot
                      // for every query, so the previous query's keys read as free
     uint32_t flags;  // kSlotDefer: the slot runs only the first round of a launch
+    uint64_t base;   // the slot's table: slots [base, base + 2^log2cap) of the paged pool, whose
+    uint32_t log2cap;  // x-list occupies the same range of the x-list arrays
+    uint32_t pad;
 };
 
 // A slot whose last launch pushed many edges (a query in its heavy rounds) runs one round
@@ -346,6 +350,10 @@ struct BArgs {
     unsigned long long *grp_off;    // their exclusive prefix sums
     unsigned *pend;     // not NULL: receives per seed the candidates left for the next launch
     uint32_t *pushed;   // not NULL (stepping sessions): per candidate of the round, 1 if it was pushed
+    // paged pool (a server; NULL otherwise): slot ids name their query through the owner of
+    // their page, page_owner[slot >> pg_bits], instead of slot >> log2cap
+    const int32_t *page_owner;
+    int pg_bits;
     // test fault injection: grid-barrier wait limit (0: kBarrierLimitNs) and a block that leaves
     // at one barrier without arriving (fail_block < 0: none)
     unsigned long long bar_limit_ns;
@@ -492,6 +500,8 @@ struct SlotMeta {
     int cls;
     uint32_t tag;
     uint32_t bank;  // hub slab bank the scatter writes (layered kinds: the next layer's parity)
+    uint32_t mask;  // the seed's table: slots [base, base + mask + 1)
+    uint64_t base;
 };
 
 // the keys round t's scatter writes: the next layer's (layered kinds) or the solve's
@@ -500,18 +510,16 @@ __device__ __forceinline__ uint32_t write_tag(const BArgs &a, int64_t t) {
     return LAYERED ? a.key_tag + (uint32_t)(t + 1) * a.tag_step : a.key_tag;
 }
 
-template <bool LAYERED>
+// PAGED: a server's pool, whose slots carry their own parameters and table (SlotParam) and
+// name their query through the page owner table; else the batch layout (seed j's table is
+// [j << log2cap, (j + 1) << log2cap), one parameter set for all seeds)
+template <bool LAYERED, bool PAGED>
 __device__ __forceinline__ SlotMeta slot_meta(const BArgs &a, int32_t j, int64_t t) {
-    if (!a.sparam) return SlotMeta{0, write_tag<LAYERED>(a, t), LAYERED ? (uint32_t)((t + 1) & 1) : 0u};
+    if (!PAGED) return SlotMeta{0, write_tag<LAYERED>(a, t), LAYERED ? (uint32_t)((t + 1) & 1) : 0u, 0u, 0ull};
     const SlotParam &sp = a.sparam[j];
-    return SlotMeta{sp.cls, sp.tag, 0u};
+    return SlotMeta{sp.cls, sp.tag, 0u, (uint32_t)((1ull << sp.log2cap) - 1), sp.base};
 }
 
-// Insert-or-add w at node v of seed j's table.  The probe starts at a 4-slot bucket (one
-// 32-byte sector) chosen by mix32(v) and continues linearly bucket by bucket; slots are
-// examined in order, so the first empty slot ends the search (keys are never removed).  A
-// residual that crosses its threshold from below (exactly once: contributions are positive)
-// is staged as a candidate of the next round.  Returns 1 if v was a new key.
 // Adds count wq to hub `rank` of seed j's slab (one integer atomic: the slab has a fixed
 // place for every hub, so there is no probe).  PPR and Katz: a count that crosses the hub's
 // threshold (exactly once: counts only grow) is staged as a candidate of the next round.  The
@@ -536,17 +544,24 @@ __device__ __forceinline__ void slab_add(const BArgs &a, int32_t j, uint32_t cod
     if (nv >= kSlabLimit) atomicExch(a.status + j, kSeedOverflow);
 }
 
-template <bool LAYERED>
+// Insert-or-add w at node v of seed j's table.  The probe starts at a 4-slot bucket (one
+// 32-byte sector) chosen by mix32(v) and continues linearly bucket by bucket; slots are
+// examined in order, so the first empty slot ends the search (keys are never removed).  A
+// residual that crosses its threshold from below (exactly once: contributions are positive)
+// is staged as a candidate of the next round.  Returns 1 if v was a new key (a server's pool
+// also counts its queries' keys, which sizes the tables of later queries).
+template <bool LAYERED, bool PAGED>
 __device__ __forceinline__ unsigned bscatter(const BArgs &a, int32_t j, SlotMeta m, uint32_t packed, float w,
                                              unsigned long long wq, uint32_t *sbuf, unsigned *sn) {
-    if (a.slab) {
+    if (!PAGED && a.slab) {
         const uint32_t code = packed >> a.idbits;
         if (code >= a.hub_code) {
             slab_add<LAYERED>(a, j, code, packed & a.idmask, m.bank, wq, sbuf, sn);
             return 0;
         }
     }
-    const uint64_t base = (uint64_t)j << a.log2cap;
+    const uint64_t base = PAGED ? m.base : (uint64_t)j << a.log2cap;
+    const uint32_t tmask = PAGED ? m.mask : a.mask;
     const int32_t v = (int32_t)(packed & a.idmask);
     const uint32_t kcur = (uint32_t)v | m.tag;
     const int cls = m.cls;
@@ -559,9 +574,9 @@ __device__ __forceinline__ unsigned bscatter(const BArgs &a, int32_t j, SlotMeta
     } else {
         tb.lo = tb.hi = thr32c[v];
     }
-    const uint32_t sector_mask = a.mask >= 3 ? 3u : a.mask;
-    uint32_t h = mix32((uint32_t)v) & a.mask & ~sector_mask;
-    for (uint32_t probes = 0; probes <= a.mask && probes < kMaxProbe;) {
+    const uint32_t sector_mask = tmask >= 3 ? 3u : tmask;
+    uint32_t h = mix32((uint32_t)v) & tmask & ~sector_mask;
+    for (uint32_t probes = 0; probes <= tmask && probes < kMaxProbe;) {
         unsigned long long w0, w1, w2, w3;
         if (sector_mask == 3u) {
             const ulonglong2 lo = __ldcg(reinterpret_cast<const ulonglong2 *>(a.kr + base + h));
@@ -587,12 +602,16 @@ __device__ __forceinline__ unsigned bscatter(const BArgs &a, int32_t j, SlotMeta
                 const unsigned long long prev = atomicCAS(a.kr + slot, wk, slot_word(kcur, w));
                 if (prev == wk) {
                     if (crossed<LAYERED>(thr32c, v, tb, 0.0f, w)) stage_push(sbuf, sn, (uint32_t)slot);
+                    if (PAGED) {  // one atomic per group of lanes of the same query
+                        const unsigned peers = __match_any_sync(__activemask(), j);
+                        if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(a.inserts + j, (unsigned)__popc(peers));
+                    }
                     return 1;
                 }
                 wk = prev;  // lost the race: look at what was written into this slot
             }
         }
-        h = (h + sector_mask + 1) & a.mask;
+        h = (h + sector_mask + 1) & tmask;
     }
     atomicExch(a.status + j, kSeedOverflow);  // table full
     return 0;
@@ -694,7 +713,7 @@ __device__ __forceinline__ int64_t hub_chunk(int64_t vh, int64_t nwarps, int64_t
 #ifndef GDE_ROUNDS_MIN_BLOCKS
 #define GDE_ROUNDS_MIN_BLOCKS 6  // 40 registers, 48 warps per SM (the kernel is latency-bound)
 #endif
-template <bool LAYERED>
+template <bool LAYERED, bool PAGED>
 __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_rounds(BArgs a) {
     const unsigned nblocks = gridDim.x;
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -778,9 +797,10 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
             // a hub slab entry (slab_base + j * H + rank) or a hash slot (j << log2cap | i)
             const bool hub = a.slab && slot >= a.slab_base;
             const uint64_t hidx = hub ? (uint64_t)(slot - a.slab_base) : 0ull;
-            const int32_t j = hub ? (int32_t)(hidx / (uint64_t)a.H) : (int32_t)(slot >> a.log2cap);
+            const int32_t j = hub ? (int32_t)(hidx / (uint64_t)a.H)
+                                  : (PAGED ? __ldg(a.page_owner + (slot >> a.pg_bits)) : (int32_t)(slot >> a.log2cap));
             if (a.pushed) a.pushed[ci] = 0u;
-            if (__ldcg(a.status + j) != kSeedOk) { __stcg(a.tmp_deg + ci, 0); continue; }
+            if (j < 0 || __ldcg(a.status + j) != kSeedOk) { __stcg(a.tmp_deg + ci, 0); continue; }
             int32_t v;
             float rho = 0.0f;
             if (hub) {
@@ -793,9 +813,15 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
             double cx = a.cx, coef = a.coef;
             bool divide = a.kind != GDE_KATZ;
             int cls = 0;
-            if (a.sparam) {
+            // the seed's x-list: a fixed stretch per seed, or (a server's paged pool) the range of
+            // its table, whose x entries cannot outnumber its slots
+            uint64_t xlbase = (uint64_t)j * a.xcap;
+            unsigned xlcap = a.xcap;
+            if (PAGED) {
                 const SlotParam sp = a.sparam[j];
                 cx = sp.cx; coef = sp.coef; divide = sp.divide != 0; cls = sp.cls;
+                xlbase = sp.base;
+                xlcap = 1u << sp.log2cap;
                 if ((sp.flags & kSlotDefer) && t != a.t0) {
                     // sits this round out: the candidate carries over to the next round
                     bappend(&ctl->cand_out, a.cand[p ^ 1], slot, a.list_cap, &ctl->overflow);
@@ -898,9 +924,9 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
                 unsigned xb = 0;
                 if (lane == xl) xb = atomicAdd(a.xcnt + j, (unsigned)__popc(xpeers));
                 xb = __shfl_sync(xpeers, xb, xl) + __popc(xpeers & ((1u << lane) - 1u));
-                if (xb < a.xcap) {
-                    __stcg(a.xlist + (uint64_t)j * a.xcap + xb, (uint32_t)xslot);
-                    __stcg(a.xnode + (uint64_t)j * a.xcap + xb, (uint32_t)v);
+                if (xb < xlcap) {
+                    __stcg(a.xlist + xlbase + xb, (uint32_t)xslot);
+                    __stcg(a.xnode + xlbase + xb, (uint32_t)v);
                 }
             }
             if (d == 0) { __stcg(a.tmp_deg + ci, 0); continue; }
@@ -1072,7 +1098,7 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
                 float hw = __ldcg(a.b_w[2] + h);
                 unsigned long long hwq = a.slab ? slab_count(a, hw) : 0ull;
                 int32_t hj = __ldcg(a.b_seed[2] + h);
-                SlotMeta hm = slot_meta<LAYERED>(a, hj, t);
+                SlotMeta hm = slot_meta<LAYERED, PAGED>(a, hj, t);
                 for (int64_t eb = e0; eb < e1; eb += 32) {
                     const int64_t e = eb + lane;
                     if (e < e1) {
@@ -1084,9 +1110,9 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
                             hw = __ldcg(a.b_w[2] + h);
                             hwq = a.slab ? slab_count(a, hw) : 0ull;
                             hj = __ldcg(a.b_seed[2] + h);
-                            hm = slot_meta<LAYERED>(a, hj, t);
+                            hm = slot_meta<LAYERED, PAGED>(a, hj, t);
                         }
-                        bscatter<LAYERED>(a, hj, hm, push_col(a, hb + (e - hs)), hw, hwq, sbuf, sn);
+                        bscatter<LAYERED, PAGED>(a, hj, hm, push_col(a, hb + (e - hs)), hw, hwq, sbuf, sn);
                     }
                     stage_flush(sbuf, sn, false, ctl, cand_out, a.list_cap);
                 }
@@ -1106,10 +1132,10 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
                 const float w = __ldcg(a.b_w[1] + i);
                 const unsigned long long wq = a.slab ? slab_count(a, w) : 0ull;
                 const int32_t j = __ldcg(a.b_seed[1] + i);
-                const SlotMeta m = slot_meta<LAYERED>(a, j, t);
+                const SlotMeta m = slot_meta<LAYERED, PAGED>(a, j, t);
                 for (int32_t k0 = 0; k0 < d; k0 += 32) {
                     const int32_t k = k0 + lane;
-                    if (k < d) bscatter<LAYERED>(a, j, m, push_col(a, b + k), w, wq, sbuf, sn);
+                    if (k < d) bscatter<LAYERED, PAGED>(a, j, m, push_col(a, b + k), w, wq, sbuf, sn);
                     stage_flush(sbuf, sn, false, ctl, cand_out, a.list_cap);
                 }
             };
@@ -1127,10 +1153,10 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
                     j = __ldcg(a.b_seed[0] + i);
                 }
                 const int32_t dmax = (int32_t)__reduce_max_sync(0xffffffffu, (unsigned)d);
-                const SlotMeta m = d > 0 ? slot_meta<LAYERED>(a, j, t) : SlotMeta{0, write_tag<LAYERED>(a, t), 0u};
+                const SlotMeta m = d > 0 ? slot_meta<LAYERED, PAGED>(a, j, t) : SlotMeta{0, write_tag<LAYERED>(a, t), 0u, 0u, 0ull};
                 const unsigned long long wq = a.slab && d > 0 ? slab_count(a, w) : 0ull;
                 for (int32_t k = 0; k < dmax; k++) {
-                    if (k < d) bscatter<LAYERED>(a, j, m, push_col(a, b + k), w, wq, sbuf, sn);
+                    if (k < d) bscatter<LAYERED, PAGED>(a, j, m, push_col(a, b + k), w, wq, sbuf, sn);
                     stage_flush(sbuf, sn, false, ctl, cand_out, a.list_cap);
                 }
             };
@@ -1145,10 +1171,10 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
                     const float w = __ldcg(a.tmp_w + ci);
                     const unsigned long long wq = a.slab ? slab_count(a, w) : 0ull;
                     const int32_t j = (int32_t)(__ldcg(a.tmp_jb + ci) & ((1u << 30) - 1u));
-                    const SlotMeta m = slot_meta<LAYERED>(a, j, t);
+                    const SlotMeta m = slot_meta<LAYERED, PAGED>(a, j, t);
                     for (int32_t k0 = 0; k0 < d; k0 += 32) {
                         const int32_t k = k0 + lane;
-                        if (k < d) bscatter<LAYERED>(a, j, m, push_col(a, b + k), w, wq, sbuf, sn);
+                        if (k < d) bscatter<LAYERED, PAGED>(a, j, m, push_col(a, b + k), w, wq, sbuf, sn);
                         stage_flush(sbuf, sn, false, ctl, cand_out, a.list_cap);
                     }
                 }
@@ -1286,7 +1312,11 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
     }
     if (a.pend && last_p >= 0) {
         const uint32_t *left = a.cand[last_p ^ 1];
-        for (int64_t i = tid; i < (int64_t)last_next; i += nthreads) atomicAdd(a.pend + (__ldcg(left + i) >> a.log2cap), 1u);
+        for (int64_t i = tid; i < (int64_t)last_next; i += nthreads) {
+            const uint32_t slot = __ldcg(left + i);
+            const int32_t j = PAGED ? a.page_owner[slot >> a.pg_bits] : (int32_t)(slot >> a.log2cap);
+            if (j >= 0) atomicAdd(a.pend + j, 1u);
+        }
     }
 }
 
@@ -1662,10 +1692,11 @@ static BatchWork *batch_work_alloc(int64_t nseeds, int64_t cap, int64_t list_cap
         w->glob = (BGlobal *)dmalloc(sizeof(BGlobal), "batch control");
         w->log = (RoundLog *)dmalloc(sizeof(RoundLog) * kLogCap, "round log");
         int per_sm = 0;
-        GDE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_rounds<false>, kThreads, 0));
-        int per_sm_layered = 0;
-        GDE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_layered, k_batch_rounds<true>, kThreads, 0));
-        if (per_sm_layered < per_sm) per_sm = per_sm_layered;  // one grid serves both
+        GDE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_rounds<false, false>, kThreads, 0));
+        int per_sm_layered = 0, per_sm_paged = 0;
+        GDE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_layered, k_batch_rounds<true, false>, kThreads, 0));
+        GDE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_paged, k_batch_rounds<false, true>, kThreads, 0));
+        per_sm = std::min(per_sm, std::min(per_sm_layered, per_sm_paged));  // one grid serves all
         int dev = 0, sms = 0;
         GDE_CUDA(cudaGetDevice(&dev));
         GDE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -1849,8 +1880,9 @@ static void launch_rounds(Graph &g, BatchWork *w, const BArgs &a, cudaStream_t s
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     const int pr = g.prof.start(kProfBatchRounds, s);
-    if (a.layer_eps) GDE_CUDA(cudaLaunchKernelEx(&cfg, k_batch_rounds<true>, a));
-    else GDE_CUDA(cudaLaunchKernelEx(&cfg, k_batch_rounds<false>, a));
+    if (a.layer_eps) GDE_CUDA(cudaLaunchKernelEx(&cfg, k_batch_rounds<true, false>, a));
+    else if (a.page_owner) GDE_CUDA(cudaLaunchKernelEx(&cfg, k_batch_rounds<false, true>, a));
+    else GDE_CUDA(cudaLaunchKernelEx(&cfg, k_batch_rounds<false, false>, a));
     g.prof.launched();
     g.prof.stop(pr, s);
 }
@@ -2207,10 +2239,26 @@ static void batch_solve_once(Graph &g, const SolveParams &p, const int32_t *seed
 // candidate list and every table where the previous launch stopped.  Slots carry their own
 // kind, coefficient and tolerance class.
 
+// Memory: the pool is a paged array of table slots (12 bytes each, plus 8 bytes of x-list) of
+// the server's memory budget.  A query's table is a power-of-two run of 2^order pages taken
+// from a buddy allocator, so queries are admitted while their tables fit rather than by a
+// fixed slot count, and a query that outgrows its table is started again with a larger one.
+// Its x-list occupies the same range of the x-list arrays (a table cannot hold more x entries
+// than slots).  A slot id names its query through the owner of its page.
+
 struct ServePool {
     BatchWork *w = nullptr;
-    int32_t slots = 0;
-    int64_t cap = 0, list_cap = 0;
+    int32_t slots = 0;           // query slots (concurrent queries at most)
+    int64_t list_cap = 0;
+    int pg_bits = 16;            // table slots per page: 2^pg_bits
+    int64_t pages = 0;           // a power of two
+    int max_order = 0;           // largest table: 2^max_order pages
+    int64_t pages_used = 0;
+    std::vector<std::set<int64_t>> free_blocks;  // per order: first pages of free blocks
+    std::vector<int32_t> h_owner;  // per page: its query slot, or -1
+    int32_t *d_owner = nullptr;
+    bool owner_dirty = true;
+    std::vector<int> order;        // per slot: its table's order, or -1 (no table)
     int ncls = 0;
     double eps[kMaxCls] = {};
     float *thr = nullptr;        // ncls arrays of n thresholds
@@ -2218,10 +2266,7 @@ struct ServePool {
     SlotParam *d_param = nullptr;
     std::vector<SlotParam> h_param;
     uint32_t key_idmask = 0;
-    int key_idbits = 0;
-    uint32_t max_tag = 0;
-    std::vector<uint32_t> epoch;  // per slot: the tag of its current query (0: never used)
-    uint32_t *d_tags = nullptr;
+    uint32_t tag = 0;            // key tag of every table (tables are cleared at admission)
     int64_t T = 0;               // the next round to run
     int64_t volume = 0;          // edges pushed so far
     unsigned *pend = nullptr;    // per-slot candidates of the next round
@@ -2239,38 +2284,36 @@ struct ServePool {
     bool pend_valid = false;       // cleared by anything that changes the candidate list
 };
 
-// device view of one slot table's probing, shared by the admission and correction kernels
+// device view of the pool's tables, shared by the admission and correction kernels
 struct SlotTable {
     unsigned long long *kr;
     float *xs;
-    int log2cap;
-    uint32_t mask;
     uint32_t key_idmask;
 };
 
-// slot of node v in table j, or -1 (the probe stops at the first free slot)
-__device__ int64_t slot_find(const SlotTable &t, int32_t j, uint32_t tag, uint32_t v) {
-    const uint64_t base = (uint64_t)j << t.log2cap;
+// slot of node v in the table [base, base + mask + 1), or -1 (the probe stops at the first
+// free slot)
+__device__ int64_t slot_find(const SlotTable &t, uint64_t base, uint32_t mask, uint32_t tag, uint32_t v) {
     const uint32_t kcur = v | tag;
-    const uint32_t sector_mask = t.mask >= 3 ? 3u : t.mask;
-    uint32_t h = mix32(v) & t.mask & ~sector_mask;
-    for (uint32_t probes = 0; probes <= t.mask && probes < kMaxProbe; probes++) {
+    const uint32_t sector_mask = mask >= 3 ? 3u : mask;
+    uint32_t h = mix32(v) & mask & ~sector_mask;
+    for (uint32_t probes = 0; probes <= mask && probes < kMaxProbe; probes++) {
         const uint32_t key = (uint32_t)(ld_relaxed_u64(t.kr + base + h) & 0xFFFFFFFFull);
         if (key == kcur) return (int64_t)(base + h);
         if (key == kEmpty || (key & ~t.key_idmask) != tag) return -1;
-        h = (h + 1) & t.mask;
+        h = (h + 1) & mask;
     }
     return -1;
 }
 
-// insert-or-add w at node v of table j; returns the slot (and the residual after the add in
-// *nv), or -1 if the table is full
-__device__ int64_t slot_add(const SlotTable &t, int32_t j, uint32_t tag, uint32_t v, float w, float *nv) {
-    const uint64_t base = (uint64_t)j << t.log2cap;
+// insert-or-add w at node v of the table [base, base + mask + 1); returns the slot (and the
+// residual after the add in *nv), or -1 if the table is full
+__device__ int64_t slot_add(const SlotTable &t, uint64_t base, uint32_t mask, uint32_t tag, uint32_t v, float w,
+                            float *nv) {
     const uint32_t kcur = v | tag;
-    const uint32_t sector_mask = t.mask >= 3 ? 3u : t.mask;
-    uint32_t h = mix32(v) & t.mask & ~sector_mask;
-    for (uint32_t probes = 0; probes <= t.mask && probes < kMaxProbe; probes++) {
+    const uint32_t sector_mask = mask >= 3 ? 3u : mask;
+    uint32_t h = mix32(v) & mask & ~sector_mask;
+    for (uint32_t probes = 0; probes <= mask && probes < kMaxProbe; probes++) {
         const uint64_t slot = base + h;
         unsigned long long wk = ld_relaxed_u64(t.kr + slot);
         for (;;) {
@@ -2287,7 +2330,7 @@ __device__ int64_t slot_add(const SlotTable &t, int32_t j, uint32_t tag, uint32_
             }
             wk = prev;
         }
-        h = (h + 1) & t.mask;
+        h = (h + 1) & mask;
     }
     return -1;
 }
@@ -2298,37 +2341,25 @@ __device__ __forceinline__ void list_append(uint32_t *cand, unsigned *count, uns
     if (pos < cap) cand[pos] = slot; else atomicCAS(error, 0u, (unsigned)GDE_ENOMEM);
 }
 
-__global__ void k_serve_clear(int64_t n_entries, const int32_t *slots, int log2cap, int64_t cap,
-                              unsigned long long *kr, float *xs) {
-    const unsigned long long empty = (unsigned long long)kEmpty;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_entries;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t slot = ((uint64_t)slots[i / cap] << log2cap) + (uint64_t)(i % cap);
-        kr[slot] = empty;
-        xs[slot] = 0.0f;
-    }
-}
-
-// one block per reused slot: zero the x entries its previous query set (its x-list; the whole
-// x range if the list overflowed)
-__global__ void k_serve_xzero(const int32_t *slots, const uint32_t *xlist, const unsigned *xcnt, int64_t xcap,
-                              float *xs, int log2cap, int64_t cap) {
-    const int32_t j = slots[blockIdx.x];
-    const unsigned nx = xcnt[j];
-    const uint64_t base = (uint64_t)j << log2cap;
-    if ((int64_t)nx <= xcap) {
-        for (unsigned i = threadIdx.x; i < nx; i += blockDim.x) xs[xlist[(uint64_t)j * xcap + i]] = 0.0f;
-    } else {
-        for (int64_t i = threadIdx.x; i < cap; i += blockDim.x) xs[base + i] = 0.0f;
+// blockIdx.y: the i-th admitted slot; its table [base, base + 2^log2cap) is emptied (keys free,
+// x zero) by gridDim.x blocks
+__global__ void k_serve_clear(const int32_t *slots, const SlotParam *sparam, unsigned long long *kr, float *xs) {
+    const SlotParam sp = sparam[slots[blockIdx.y]];
+    const int64_t cap = (int64_t)1 << sp.log2cap;
+    const unsigned long long empty = (unsigned long long)kEmpty;  // r = 0.0f in the high half
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cap; i += (int64_t)gridDim.x * blockDim.x) {
+        kr[sp.base + (uint64_t)i] = empty;
+        xs[sp.base + (uint64_t)i] = 0.0f;
     }
 }
 
 struct AdmitArgs {
     SlotTable t;
+    const SlotParam *sparam;
     int32_t n;
     const int32_t *slots;
     const int32_t *seeds;
-    const uint32_t *tags;     // the admitted queries' key tags
+    uint32_t tag;
     uint32_t *cand;
     unsigned *count;
     unsigned list_cap;
@@ -2343,17 +2374,19 @@ struct AdmitArgs {
     double *sscat;
 };
 
-// unit residual at the seed of each admitted slot (under the slot's new tag every older key
-// reads as free, so the seed takes the first slot of its probe), per-slot counters reset, the
-// seed's slot listed for the next round
+// unit residual at the seed of each admitted slot (its table was just emptied, so the seed
+// takes the first slot of its probe), per-slot counters reset, the seed's slot listed for the
+// next round
 __global__ void k_serve_seed(AdmitArgs a) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     const int32_t j = a.slots[i];
+    const SlotParam sp = a.sparam[j];
+    const uint32_t mask = (uint32_t)((1ull << sp.log2cap) - 1);
     const uint32_t s = (uint32_t)a.seeds[i];
-    const uint32_t sector_mask = a.t.mask >= 3 ? 3u : a.t.mask;
-    const uint64_t slot = ((uint64_t)j << a.t.log2cap) + (mix32(s) & a.t.mask & ~sector_mask);
-    a.t.kr[slot] = ((unsigned long long)__float_as_uint(1.0f) << 32) | (unsigned long long)(s | a.tags[i]);
+    const uint32_t sector_mask = mask >= 3 ? 3u : mask;
+    const uint64_t slot = sp.base + (mix32(s) & mask & ~sector_mask);
+    a.t.kr[slot] = ((unsigned long long)__float_as_uint(1.0f) << 32) | (unsigned long long)(s | a.tag);
     a.status[j] = kSeedOk;
     a.inserts[j] = 1;
     a.xcnt[j] = 0;
@@ -2400,7 +2433,8 @@ __global__ void k_serve_correct(CorrectArgs a) {
     const int64_t ri = i % a.rows;
     const int32_t u = a.row[ri];
     const SlotParam sp = a.sparam[j];
-    const int64_t su = slot_find(a.t, j, sp.tag, (uint32_t)u);
+    const uint32_t mask = (uint32_t)((1ull << sp.log2cap) - 1);
+    const int64_t su = slot_find(a.t, sp.base, mask, sp.tag, (uint32_t)u);
     if (su < 0) return;
     const float x = a.t.xs[su];
     if (x == 0.0f) return;
@@ -2428,7 +2462,7 @@ __global__ void k_serve_correct(CorrectArgs a) {
     for (int32_t e = 0; e < k; e++) {
         const int32_t v = a.added[st + e];
         float nv = 0.0f;
-        const int64_t sv = slot_add(a.t, j, sp.tag, (uint32_t)v, give, &nv);
+        const int64_t sv = slot_add(a.t, sp.base, mask, sp.tag, (uint32_t)v, give, &nv);
         if (sv < 0) {
             atomicExch(a.status + j, kSeedOverflow);
             continue;
@@ -2437,11 +2471,13 @@ __global__ void k_serve_correct(CorrectArgs a) {
     }
 }
 
-__global__ void k_serve_pending(const unsigned *count, unsigned list_cap, const uint32_t *cand, int log2cap,
-                                unsigned *pend) {
+__global__ void k_serve_pending(const unsigned *count, unsigned list_cap, const uint32_t *cand,
+                                const int32_t *page_owner, int pg_bits, unsigned *pend) {
     const unsigned n = min(*count, list_cap);
-    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        atomicAdd(pend + (cand[i] >> log2cap), 1u);
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int32_t j = page_owner[cand[i] >> pg_bits];
+        if (j >= 0) atomicAdd(pend + j, 1u);
+    }
 }
 
 static unsigned *next_count(ServePool *P) {
@@ -2452,9 +2488,16 @@ static unsigned *next_count(ServePool *P) {
 
 static SlotTable slot_table(ServePool *P) {
     SlotTable t;
-    t.kr = P->w->kr; t.xs = P->w->xs; t.log2cap = P->w->log2cap; t.mask = (uint32_t)(P->cap - 1);
+    t.kr = P->w->kr; t.xs = P->w->xs;
     t.key_idmask = P->key_idmask;
     return t;
+}
+
+static void serve_sync_owner(ServePool *P) {
+    if (!P->owner_dirty) return;
+    GDE_CUDA(cudaMemcpyAsync(P->d_owner, P->h_owner.data(), 4 * (size_t)P->pages, cudaMemcpyHostToDevice, P->s));
+    GDE_CUDA(cudaStreamSynchronize(P->s));  // the host table may change before the next launch
+    P->owner_dirty = false;
 }
 
 static void serve_check_error(ServePool *P) {
@@ -2472,18 +2515,21 @@ static void serve_check_error(ServePool *P) {
 }
 
 // Top-k of served queries in two passes, so a query with a large support is ranked by many
-// blocks: block (i, c) ranks part c of query i's x-list (or of its whole table if the list
-// overflowed) into a partial top-64, then one block per query merges its parts.
+// blocks: block (i, c) ranks part c of query i's x-list into a partial top-64, then one block
+// per query merges its parts.
 constexpr int kServeTopkParts = 16;
 
-__global__ void __launch_bounds__(kThreads) k_serve_topk_partial(TopkArgs a, unsigned long long *partial) {
+__global__ void __launch_bounds__(kThreads) k_serve_topk_partial(TopkArgs a, const SlotParam *sparam,
+                                                                 unsigned long long *partial) {
     const int qi = blockIdx.x / kServeTopkParts, part = blockIdx.x % kServeTopkParts;
     const int j = a.slots[qi];
+    const SlotParam sp = sparam[j];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const uint64_t base = (uint64_t)j << a.log2cap;
+    const int64_t cap = (int64_t)1 << sp.log2cap;
     const unsigned nx = a.xcnt[j];
-    const bool use_list = nx <= a.xcap;
-    const int64_t n = use_list ? (int64_t)nx : a.cap;
+    // the x-list has room for every slot of the table; a count past it would scan the table
+    const bool use_list = (int64_t)nx <= cap;
+    const int64_t n = use_list ? (int64_t)nx : cap;
     const int64_t per = (n + kServeTopkParts - 1) / kServeTopkParts;
     const int64_t lo = (int64_t)part * per, hi = min(lo + per, n);
     unsigned long long ta = 0, tb = 0;
@@ -2491,8 +2537,8 @@ __global__ void __launch_bounds__(kThreads) k_serve_topk_partial(TopkArgs a, uns
         const int64_t i = i0 + lane;
         unsigned long long key = 0;
         if (i < hi) {
-            const uint64_t li = (uint64_t)j * a.xcap + i;
-            const uint64_t slot = use_list ? (uint64_t)a.xlist[li] : base + (uint64_t)i;
+            const uint64_t li = sp.base + (uint64_t)i;
+            const uint64_t slot = use_list ? (uint64_t)a.xlist[li] : sp.base + (uint64_t)i;
             const float x = a.xs[slot];
             if (x > 0.0f) {
                 const uint32_t v = use_list ? a.xnode[li] : (uint32_t)(a.kr[slot] & 0xFFFFFFFFull) & a.key_idmask;
@@ -2548,27 +2594,52 @@ ServePool *serve_pool_create(Graph &g, int32_t slots, int64_t budget, const doub
     for (int c = 0; c < ncls; c++) GDE_REQUIRE(eps[c] > 0.0, GDE_EINVAL, "tolerances must be > 0");
     GDE_REQUIRE(g.n < ((int64_t)1 << 31) - 1, GDE_EINVAL, "graph too large for 32-bit keys");
     if (budget <= 0) budget = (int64_t)16 << 30;
-    int64_t cap = floor_pow2(budget / (12 * (int64_t)slots));
-    // (at most 2^31 slots per table: slot indices are 32-bit and carry the seed above log2(cap))
+    // a table never needs more than 2n slots (at most n keys: half load); pages of 2^16 slots,
+    // smaller for small graphs so that one page is not already larger than that
     const int64_t cap_max = std::min<int64_t>(ceil_pow2(2 * (g.n > 0 ? g.n : 1)), (int64_t)1 << 31);
-    if (cap > cap_max) cap = cap_max;
-    GDE_REQUIRE(cap >= 64 || cap == cap_max, GDE_ENOMEM, "memory budget too small for the slots");
-    GDE_REQUIRE((int64_t)slots * cap <= ((int64_t)1 << 32), GDE_EINVAL, "pool exceeds 2^32 slots (32-bit slot indices)");
+    int pg = 16;
+    while (pg > 6 && ((int64_t)1 << pg) > cap_max) pg--;
+    const int64_t page_bytes = ((int64_t)1 << pg) * 20;  // kr 8 + x 4 + x-list 8 per table slot
+    // the budget, but no more than `slots` queries with the largest tables could hold
+    const int64_t pages_need = ceil_pow2((int64_t)slots * (cap_max >> pg));
+    int64_t pages = std::min<int64_t>(floor_pow2(std::max<int64_t>(budget / page_bytes, 1)), pages_need);
+    // slot ids are 32-bit: pages * 2^pg <= 2^32
+    while ((pages << pg) > ((int64_t)1 << 32)) pages >>= 1;
+    int max_order = 0;
+    while (((int64_t)1 << (max_order + 1)) <= pages && ((int64_t)1 << (pg + max_order + 1)) <= cap_max) max_order++;
     // a served stream mixes queries whose rounds touch millions of nodes, and a resumed state
     // cannot be re-run after an overflow: the lists get room for 2^26 candidates up front
-    int64_t list_cap = (int64_t)1 << 26;
-    if (list_cap > (int64_t)slots * cap) list_cap = (int64_t)slots * cap;
+    int64_t list_cap = std::min<int64_t>((int64_t)1 << 26, pages << pg);
     ServePool *P = new ServePool();
     try {
         P->slots = slots;
-        P->cap = cap;
         P->list_cap = list_cap;
+        P->pg_bits = pg;
+        P->pages = pages;
+        P->max_order = max_order;
+        int lp = 0;
+        while (((int64_t)1 << lp) < pages) lp++;
+        P->free_blocks.assign((size_t)lp + 1, std::set<int64_t>());
+        P->free_blocks[(size_t)lp].insert(0);
+        P->h_owner.assign((size_t)pages, -1);
+        P->order.assign((size_t)slots, -1);
         P->ncls = ncls;
         for (int c = 0; c < ncls; c++) P->eps[c] = eps[c];
         P->s = g.stream;
-        // x-lists of up to 2^22 entries: a served query's support stays listed, so its top-k
-        // and the zeroing at the slot's next admission touch only that support
-        P->w = batch_work_alloc(slots, cap, list_cap, (int64_t)1 << 22);
+        // per-slot arrays and the candidate / bin lists come from a batch workspace; the tables
+        // and x-lists are the paged pool's own
+        P->w = batch_work_alloc(slots, 1, list_cap, 1);
+        const size_t total = (size_t)pages << pg;
+        dfree(P->w->kr); P->w->kr = nullptr;
+        dfree(P->w->xs); P->w->xs = nullptr;
+        dfree(P->w->xlist); P->w->xlist = nullptr;
+        dfree(P->w->xnode); P->w->xnode = nullptr;
+        P->w->kr = (unsigned long long *)dmalloc(8 * total, "served tables");
+        P->w->xs = (float *)dmalloc(4 * total, "served tables");
+        P->w->xlist = (uint32_t *)dmalloc(4 * total, "served x-lists");
+        P->w->xnode = (uint32_t *)dmalloc(4 * total, "served x-lists");
+        P->w->pool = (int64_t)total;
+        P->d_owner = (int32_t *)dmalloc(4 * (size_t)pages, "page owners");
         P->thr = (float *)dmalloc(4 * (size_t)ncls * (size_t)(g.n > 0 ? g.n : 1), "class thresholds");
         P->d_param = (SlotParam *)dmalloc(sizeof(SlotParam) * (size_t)slots, "slot parameters");
         P->h_param.assign((size_t)slots, SlotParam{0.15, 0.85, 1, 0});
@@ -2577,27 +2648,21 @@ ServePool *serve_pool_create(Graph &g, int32_t slots, int64_t budget, const doub
         P->pend = (unsigned *)dmalloc(4 * (size_t)slots, "pending counts");
         P->d_list = (int32_t *)dmalloc(4 * (size_t)slots, "slot list");
         P->d_seeds = (int32_t *)dmalloc(4 * (size_t)slots, "slot seeds");
-        P->d_tags = (uint32_t *)dmalloc(4 * (size_t)slots, "slot tags");
-        P->epoch.assign((size_t)slots, 0u);
         P->d_ids = (int32_t *)dmalloc(4 * 64 * (size_t)slots, "slot top-k");
         P->d_vals = (float *)dmalloc(4 * 64 * (size_t)slots, "slot top-k");
         P->d_partial = (unsigned long long *)dmalloc(8 * 64 * (size_t)kServeTopkParts * (size_t)slots, "top-k parts");
         int key_idbits = 1;
         while (((int64_t)1 << key_idbits) < g.n) key_idbits++;
-        const int tag_bits = 32 - key_idbits < 8 ? 32 - key_idbits : 8;
-        const uint32_t max_tag = tag_bits >= 2 ? (1u << tag_bits) - 2u : 0u;
-        P->key_idbits = key_idbits;
-        P->max_tag = max_tag;
         P->key_idmask = (uint32_t)(((uint64_t)1 << key_idbits) - 1);
+        P->tag = key_idbits < 32 ? (1u << key_idbits) : 0u;
         cudaStream_t s = P->s;
-        k_batch_clear<<<kSMs * 8, kThreads, 0, s>>>(P->w->pool, P->w->kr, P->w->xs);
-        GDE_CUDA(cudaGetLastError());
         GDE_CUDA(cudaMemsetAsync(P->w->glob, 0, sizeof(BGlobal), s));
         GDE_CUDA(cudaMemsetAsync(P->w->seg_cnt, 0, 4 * 3 * (size_t)slots, s));
         GDE_CUDA(cudaMemsetAsync(P->w->seg_hvol, 0, 8 * (size_t)slots, s));
         GDE_CUDA(cudaMemsetAsync(P->w->status, 0, 4 * (size_t)slots, s));
         GDE_CUDA(cudaMemsetAsync(P->w->xcnt, 0, 4 * (size_t)slots, s));
         GDE_CUDA(cudaStreamSynchronize(s));
+        serve_sync_owner(P);
     } catch (...) {
         serve_pool_destroy(P);
         throw;
@@ -2609,12 +2674,61 @@ void serve_pool_destroy(ServePool *P) {
     if (!P) return;
     if (P->s) cudaStreamSynchronize(P->s);
     batch_free(P->w);
-    dfree(P->thr); dfree(P->d_param); dfree(P->pend); dfree(P->d_list); dfree(P->d_seeds); dfree(P->d_tags);
+    dfree(P->thr); dfree(P->d_param); dfree(P->pend); dfree(P->d_list); dfree(P->d_seeds); dfree(P->d_owner);
     dfree(P->d_ids); dfree(P->d_vals); dfree(P->d_partial);
     delete P;
 }
 
-int64_t serve_pool_cap(const ServePool *P) { return P->cap; }
+int64_t serve_pool_cap(const ServePool *P) { return (int64_t)1 << (P->pg_bits + P->max_order); }
+int serve_pool_max_order(const ServePool *P) { return P->max_order; }
+int64_t serve_pool_page_slots(const ServePool *P) { return (int64_t)1 << P->pg_bits; }
+int64_t serve_pool_pages(const ServePool *P) { return P->pages; }
+int64_t serve_pool_pages_used(const ServePool *P) { return P->pages_used; }
+int serve_pool_order(const ServePool *P, int32_t slot) { return P->order[(size_t)slot]; }
+
+// Buddy allocation of 2^ord pages for query slot j (host bookkeeping; the device owner table
+// follows before the next launch).  Returns false when no block of that size is free.
+bool serve_pool_reserve(ServePool *P, int32_t j, int ord) {
+    GDE_REQUIRE(j >= 0 && j < P->slots && P->order[(size_t)j] < 0, GDE_EINVAL, "slot busy or out of range");
+    GDE_REQUIRE(ord >= 0 && ord <= P->max_order, GDE_EINVAL, "table order out of range");
+    int o = ord;
+    while (o < (int)P->free_blocks.size() && P->free_blocks[(size_t)o].empty()) o++;
+    if (o >= (int)P->free_blocks.size()) return false;
+    int64_t page = *P->free_blocks[(size_t)o].begin();
+    P->free_blocks[(size_t)o].erase(P->free_blocks[(size_t)o].begin());
+    while (o > ord) {  // split: keep the lower half, free the upper
+        o--;
+        P->free_blocks[(size_t)o].insert(page + ((int64_t)1 << o));
+    }
+    for (int64_t q = page; q < page + ((int64_t)1 << ord); q++) P->h_owner[(size_t)q] = j;
+    P->owner_dirty = true;
+    P->pages_used += (int64_t)1 << ord;
+    P->order[(size_t)j] = ord;
+    SlotParam &sp = P->h_param[(size_t)j];
+    sp.base = (uint64_t)page << P->pg_bits;
+    sp.log2cap = (uint32_t)(P->pg_bits + ord);
+    return true;
+}
+
+void serve_pool_release(ServePool *P, int32_t j) {
+    const int ord = P->order[(size_t)j];
+    if (ord < 0) return;
+    int64_t page = (int64_t)(P->h_param[(size_t)j].base >> P->pg_bits);
+    for (int64_t q = page; q < page + ((int64_t)1 << ord); q++) P->h_owner[(size_t)q] = -1;
+    P->owner_dirty = true;
+    P->pages_used -= (int64_t)1 << ord;
+    P->order[(size_t)j] = -1;
+    int o = ord;
+    while (o + 1 < (int)P->free_blocks.size()) {  // merge with the free buddy
+        const int64_t buddy = page ^ ((int64_t)1 << o);
+        auto it = P->free_blocks[(size_t)o].find(buddy);
+        if (it == P->free_blocks[(size_t)o].end()) break;
+        P->free_blocks[(size_t)o].erase(it);
+        page = std::min(page, buddy);
+        o++;
+    }
+    P->free_blocks[(size_t)o].insert(page);
+}
 
 void serve_pool_set_defer(ServePool *P, int64_t v) { P->defer_vol = v; }
 
@@ -2640,57 +2754,45 @@ void serve_pool_admit(Graph &g, ServePool *P, int32_t n, const int32_t *slots, c
     cudaStream_t s = P->s;
     for (int32_t i = 0; i < n; i++) {
         GDE_REQUIRE(slots[i] >= 0 && slots[i] < P->slots, GDE_EINVAL, "slot out of range");
+        GDE_REQUIRE(P->order[(size_t)slots[i]] >= 0, GDE_EINVAL, "slot has no table reserved");
         GDE_REQUIRE(seeds[i] >= 0 && seeds[i] < g.n, GDE_EINVAL, "seed out of range");
         GDE_REQUIRE(cls[i] >= 0 && cls[i] < P->ncls, GDE_EINVAL, "tolerance class out of range");
         SlotParam &sp = P->h_param[(size_t)slots[i]];
         if (kinds[i] == GDE_PPR) {
             GDE_REQUIRE(params[i] > 0.0 && params[i] < 1.0, GDE_EINVAL, "PPR alpha must be in (0,1)");
-            sp = SlotParam{params[i], 1.0 - params[i], 1, cls[i]};
+            sp.cx = params[i]; sp.coef = 1.0 - params[i]; sp.divide = 1;
         } else {
             GDE_REQUIRE(kinds[i] == GDE_KATZ && params[i] > 0.0, GDE_EINVAL, "a server serves PPR and Katz");
-            sp = SlotParam{1.0, params[i], 0, cls[i]};
+            sp.cx = 1.0; sp.coef = params[i]; sp.divide = 0;
         }
-    }
-    // new key tag per admitted slot; a slot whose tag would wrap is cleared and starts over,
-    // a reused slot only has its previous query's x zeroed
-    std::vector<int32_t> wrap, reuse;
-    std::vector<uint32_t> tags((size_t)n);
-    for (int32_t i = 0; i < n; i++) {
-        uint32_t &e = P->epoch[(size_t)slots[i]];
-        const bool used = e != 0;
-        e++;
-        if (e > P->max_tag || P->max_tag == 0) {
-            wrap.push_back(slots[i]);
-            e = P->max_tag >= 1 ? 1u : 0u;
-        } else if (used) {
-            reuse.push_back(slots[i]);
-        }
-        tags[(size_t)i] = e << P->key_idbits;
-        P->h_param[(size_t)slots[i]].tag = tags[(size_t)i];
-        P->h_param[(size_t)slots[i]].flags = 0;
+        sp.cls = cls[i];
+        sp.tag = P->tag;
+        sp.flags = 0;
         P->last_vol[(size_t)slots[i]] = 0;
         P->heavy[(size_t)slots[i]] = 0;
     }
+    serve_sync_owner(P);
     GDE_CUDA(cudaMemcpyAsync(P->d_param, P->h_param.data(), sizeof(SlotParam) * (size_t)P->slots,
                              cudaMemcpyHostToDevice, s));
-    if (!reuse.empty()) {
-        GDE_CUDA(cudaMemcpyAsync(P->d_list, reuse.data(), 4 * reuse.size(), cudaMemcpyHostToDevice, s));
-        k_serve_xzero<<<(unsigned)reuse.size(), kThreads, 0, s>>>(P->d_list, P->w->xlist, P->w->xcnt, P->w->xcap,
-                                                                  P->w->xs, P->w->log2cap, P->cap);
-        GDE_CUDA(cudaGetLastError());
-    }
-    if (!wrap.empty()) {
-        GDE_CUDA(cudaMemcpyAsync(P->d_seeds, wrap.data(), 4 * wrap.size(), cudaMemcpyHostToDevice, s));
-        k_serve_clear<<<kSMs * 8, kThreads, 0, s>>>((int64_t)wrap.size() * P->cap, P->d_seeds, P->w->log2cap,
-                                                   P->cap, P->w->kr, P->w->xs);
-        GDE_CUDA(cudaGetLastError());
-    }
     GDE_CUDA(cudaMemcpyAsync(P->d_list, slots, 4 * (size_t)n, cudaMemcpyHostToDevice, s));
     GDE_CUDA(cudaMemcpyAsync(P->d_seeds, seeds, 4 * (size_t)n, cudaMemcpyHostToDevice, s));
-    GDE_CUDA(cudaMemcpyAsync(P->d_tags, tags.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, s));
+    // empty the admitted tables (a page may have belonged to any earlier query), then seed them
+    int bx = 1;
+    for (int32_t i = 0; i < n; i++) {
+        const int64_t cap = (int64_t)1 << P->h_param[(size_t)slots[i]].log2cap;
+        const int64_t want = (cap + (int64_t)kThreads * 16 - 1) / ((int64_t)kThreads * 16);
+        if (want > bx) bx = (int)std::min<int64_t>(want, 1024);
+    }
+    for (int32_t i0 = 0; i0 < n; i0 += 32768) {  // gridDim.y stays below its limit of 65535
+        const int32_t m = std::min<int32_t>(32768, n - i0);
+        k_serve_clear<<<dim3((unsigned)bx, (unsigned)m), kThreads, 0, s>>>(P->d_list + i0, P->d_param, P->w->kr,
+                                                                            P->w->xs);
+        GDE_CUDA(cudaGetLastError());
+    }
     AdmitArgs a{};
     a.t = slot_table(P);
-    a.n = n; a.slots = P->d_list; a.seeds = P->d_seeds; a.tags = P->d_tags;
+    a.sparam = P->d_param;
+    a.n = n; a.slots = P->d_list; a.seeds = P->d_seeds; a.tag = P->tag;
     a.cand = P->w->cand[P->T & 1]; a.count = next_count(P); a.list_cap = (unsigned)P->list_cap;
     a.error = &P->w->glob->error;
     a.status = P->w->status; a.inserts = P->w->inserts; a.svol = P->w->svol; a.spushes = P->w->spushes;
@@ -2722,6 +2824,7 @@ void serve_pool_correct(Graph &g, ServePool *P, const EdgeBatch &eb, int32_t nre
 int64_t serve_pool_run(Graph &g, ServePool *P, int64_t rounds) {
     P->pend_valid = false;
     serve_ensure_graph_state(g, P);
+    serve_sync_owner(P);
     BatchWork *w = P->w;
     // heavy slots (by their volume in the last launch) run one round of this launch
     bool changed = false;
@@ -2735,7 +2838,9 @@ int64_t serve_pool_run(Graph &g, ServePool *P, int64_t rounds) {
     if (changed)
         GDE_CUDA(cudaMemcpyAsync(P->d_param, P->h_param.data(), sizeof(SlotParam) * (size_t)P->slots,
                                  cudaMemcpyHostToDevice, P->s));
-    BArgs a = bargs_base(g, w, P->cap, P->list_cap, P->slots, 1u << P->key_idbits, P->key_idmask);
+    BArgs a = bargs_base(g, w, 1, P->list_cap, P->slots, P->tag, P->key_idmask);
+    a.page_owner = P->d_owner;
+    a.pg_bits = P->pg_bits;
     a.thr32 = P->thr;
     a.thr_stride = g.n;
     a.eps = P->eps[0];
@@ -2777,9 +2882,10 @@ void serve_pool_pending(Graph &g, ServePool *P, unsigned *pend_host) {
         std::copy(P->h_pend.begin(), P->h_pend.end(), pend_host);
         return;
     }
+    serve_sync_owner(P);
     GDE_CUDA(cudaMemsetAsync(P->pend, 0, 4 * (size_t)P->slots, P->s));
     k_serve_pending<<<kSMs * 2, kThreads, 0, P->s>>>(next_count(P), (unsigned)P->list_cap, P->w->cand[P->T & 1],
-                                                      P->w->log2cap, P->pend);
+                                                      P->d_owner, P->pg_bits, P->pend);
     GDE_CUDA(cudaGetLastError());
     g.prof.launched();
     GDE_CUDA(cudaMemcpyAsync(pend_host, P->pend, 4 * (size_t)P->slots, cudaMemcpyDeviceToHost, P->s));
@@ -2787,18 +2893,17 @@ void serve_pool_pending(Graph &g, ServePool *P, unsigned *pend_host) {
 }
 
 void serve_pool_results(Graph &g, ServePool *P, int32_t n, const int32_t *slots, int k, int32_t *ids,
-                        float *vals, int32_t *status, int64_t *volume, int32_t *last_round) {
+                        float *vals, int32_t *status, int64_t *volume, int32_t *last_round, int64_t *support) {
     if (n <= 0) return;
     GDE_REQUIRE(k >= 1 && k <= kTopMax, GDE_EINVAL, "topk must be in [1, 64]");
     cudaStream_t s = P->s;
     GDE_CUDA(cudaMemcpyAsync(P->d_list, slots, 4 * (size_t)n, cudaMemcpyHostToDevice, s));
     TopkArgs ta{};
-    ta.kr = P->w->kr; ta.xs = P->w->xs; ta.log2cap = P->w->log2cap; ta.cap = P->cap; ta.k = k;
+    ta.kr = P->w->kr; ta.xs = P->w->xs; ta.k = k;
     ta.key_idmask = P->key_idmask; ta.xlist = P->w->xlist; ta.xnode = P->w->xnode; ta.xcnt = P->w->xcnt;
-    ta.xcap = (unsigned)P->w->xcap;
     ta.out_ids = P->d_ids; ta.out_vals = P->d_vals; ta.ssupport = P->w->inserts;
     ta.slots = P->d_list; ta.keep = 1;
-    k_serve_topk_partial<<<(unsigned)(n * kServeTopkParts), kThreads, 0, s>>>(ta, P->d_partial);
+    k_serve_topk_partial<<<(unsigned)(n * kServeTopkParts), kThreads, 0, s>>>(ta, P->d_param, P->d_partial);
     GDE_CUDA(cudaGetLastError());
     k_serve_topk_final<<<(unsigned)n, kThreads, 0, s>>>(k, P->d_partial, P->d_ids, P->d_vals);
     GDE_CUDA(cudaGetLastError());
@@ -2807,15 +2912,18 @@ void serve_pool_results(Graph &g, ServePool *P, int32_t n, const int32_t *slots,
     GDE_CUDA(cudaMemcpyAsync(vals, P->d_vals, 4 * (size_t)n * k, cudaMemcpyDeviceToHost, s));
     std::vector<int32_t> st((size_t)P->slots), last((size_t)P->slots);
     std::vector<unsigned long long> vol((size_t)P->slots);
+    std::vector<unsigned> keys((size_t)P->slots);
     GDE_CUDA(cudaMemcpyAsync(st.data(), P->w->status, 4 * (size_t)P->slots, cudaMemcpyDeviceToHost, s));
     GDE_CUDA(cudaMemcpyAsync(last.data(), P->w->slast, 4 * (size_t)P->slots, cudaMemcpyDeviceToHost, s));
     GDE_CUDA(cudaMemcpyAsync(vol.data(), P->w->svol, 8 * (size_t)P->slots, cudaMemcpyDeviceToHost, s));
+    GDE_CUDA(cudaMemcpyAsync(keys.data(), P->w->inserts, 4 * (size_t)P->slots, cudaMemcpyDeviceToHost, s));
     GDE_CUDA(cudaStreamSynchronize(s));
     for (int32_t i = 0; i < n; i++) {
         const size_t j = (size_t)slots[i];
         status[i] = st[j] == kSeedOk ? GDE_OK : GDE_ENOMEM;
         volume[i] = (int64_t)vol[j];
         last_round[i] = last[j];
+        if (support) support[i] = (int64_t)keys[j];  // keys its table holds
     }
 }
 

@@ -282,7 +282,17 @@ void serve_pool_correct(Graph &g, ServePool *P, const EdgeBatch &eb, int32_t nre
 int64_t serve_pool_run(Graph &g, ServePool *P, int64_t rounds);
 void serve_pool_pending(Graph &g, ServePool *P, unsigned *pend_host);
 void serve_pool_results(Graph &g, ServePool *P, int32_t n, const int32_t *slots, int k, int32_t *ids,
-                        float *vals, int32_t *status, int64_t *volume, int32_t *last_round);
+                        float *vals, int32_t *status, int64_t *volume, int32_t *last_round, int64_t *support);
+// the paged pool: a query slot's table is 2^order pages (serve_pool_page_slots() slots each)
+// taken by serve_pool_reserve (false: no free block that large) and given back by
+// serve_pool_release; order <= serve_pool_max_order()
+bool serve_pool_reserve(ServePool *P, int32_t slot, int order);
+void serve_pool_release(ServePool *P, int32_t slot);
+int serve_pool_max_order(const ServePool *P);
+int serve_pool_order(const ServePool *P, int32_t slot);
+int64_t serve_pool_page_slots(const ServePool *P);
+int64_t serve_pool_pages(const ServePool *P);
+int64_t serve_pool_pages_used(const ServePool *P);
 void batch_solve(Graph &g, const SolveParams &p, const int32_t *seeds_dev, int32_t nseeds, int k,
                  int64_t mem_budget, int32_t *ids_dev, float *vals_dev, gde_stats *stats_host,
                  int32_t *overflow_seeds_host, int32_t *n_overflow);

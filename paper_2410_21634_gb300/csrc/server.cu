@@ -1,14 +1,18 @@
 // Serving loop over a serving pool (continuous batching of PPR/Katz queries on a changing
-// graph, Section 4): queries wait in a FIFO and are admitted into free slots between device
-// steps; a step runs a bounded number of LocalGD rounds for every resident query at once, so a
-// query that arrives while others are on the GPU joins them at the next step; a query whose
-// slot has no candidate left has converged and its top-k is emitted; edge-insertion batches
-// are applied between steps, after which every resident query is corrected (warm start) and
-// runs on from its corrected state.  A one-shot query leaves its slot at its answer; a standing
+// graph, Section 4): queries wait in a FIFO and are admitted between device steps while their
+// accumulator tables fit the pool's memory (a table is a power-of-two run of pages; its first
+// size comes from what recent queries of the same kind and tolerance needed); a step runs a
+// bounded number of LocalGD rounds for every resident query at once, so a query that arrives
+// while others are on the GPU joins them at the next step; a query whose slot has no candidate
+// left has converged and its top-k is emitted; a query whose table overflowed is started again,
+// ahead of the queue, with a table four times larger; edge-insertion batches are applied
+// between steps, after which every resident query is corrected (warm start) and runs on from
+// its corrected state.  A one-shot query leaves its slot (and pages) at its answer; a standing
 // query stays resident, tracking the graph (re-answered as an update after every batch), until
-// its slot is needed (oldest answer first).
+// its slot or memory is needed (oldest answer first).
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <deque>
 #include <mutex>
 #include <vector>
@@ -38,6 +42,7 @@ struct Query {
     int32_t seed;
     bool track;
     double t_submit;
+    int order = -1;  // table size to start with (2^order pages); -1: the class estimate
 };
 
 struct Slot {
@@ -67,7 +72,52 @@ struct gde_server {
     int64_t steps = 0;
     int64_t edge_batches = 0;
     double t_phase[5] = {0, 0, 0, 0, 0};  // graph, correct, admit, rounds, results (seconds)
+    int32_t peak_resident = 0;
+    int64_t peak_pages = 0;
+    int64_t readmissions = 0;
+    int64_t evictions = 0;
+    // Table sizes that recent queries needed, per (kind, tolerance class, seed degree bucket
+    // floor(log2(d_s + 1))): the table order holding their keys at an eighth load at most, the last
+    // kNeedWindow answered queries (or an overflow) of each bucket.  A new query starts at the
+    // largest order of its bucket, else of the nearest lower-degree bucket that has one.
+    static constexpr int kBuckets = 32;
+    static constexpr size_t kNeedWindow = 16;
+    std::deque<int> needed[2][4][kBuckets];
+    std::vector<int32_t> deg;  // seed degrees (as of creation: the buckets are a guide only)
 };
+
+namespace {
+
+int degree_bucket(const gde_server *S, int32_t seed) {
+    int b = 0;
+    while (b + 1 < gde_server::kBuckets && ((int64_t)2 << b) <= (int64_t)S->deg[(size_t)seed] + 1) b++;
+    return b;
+}
+
+int start_order(gde_server *S, const Query &q) {
+    if (q.order >= 0) return q.order;
+    const int kind = q.kind == GDE_KATZ ? 1 : 0;
+    for (int b = degree_bucket(S, q.seed); b >= 0; b--) {
+        const std::deque<int> &h = S->needed[kind][q.cls][b];
+        if (!h.empty()) return *std::max_element(h.begin(), h.end());
+    }
+    return 0;
+}
+
+void note_needed(gde_server *S, const Query &q, int order) {
+    std::deque<int> &h = S->needed[q.kind == GDE_KATZ ? 1 : 0][q.cls][degree_bucket(S, q.seed)];
+    h.push_back(order);
+    if (h.size() > gde_server::kNeedWindow) h.pop_front();
+}
+
+// the smallest table order whose slots hold `keys` at an eighth load (short probes)
+int order_for_keys(int64_t keys, int64_t page_slots, int max_order) {
+    int o = 0;
+    while (o < max_order && (page_slots << o) < 8 * keys) o++;
+    return o;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -105,6 +155,8 @@ gde_status gde_server_create(gde_graph *g, const gde_server_opts *o, gde_server 
         S->pool = serve_pool_create(G, op.slots, op.mem_budget_bytes, op.eps, op.n_eps);
         serve_pool_set_defer(S->pool, op.defer_volume == 0 ? ((int64_t)1 << 23) : op.defer_volume);
         S->slots.resize((size_t)op.slots);
+        S->deg.resize((size_t)G.n);
+        if (G.n > 0) GDE_CUDA(cudaMemcpy(S->deg.data(), G.deg, 4 * (size_t)G.n, cudaMemcpyDeviceToHost));
     } catch (...) {
         if (S->pool) serve_pool_destroy(S->pool);
         delete S;
@@ -208,29 +260,40 @@ gde_status gde_server_step(gde_server *S, int32_t *running, int32_t *queued) {
         edge_batch_free(eb);
     }
 
-    // 2. admission: free slots first, then the slots answered longest ago
+    // 2. admission in arrival order, while a slot and the query's table fit: free slots and
+    //    free pages first, then the slots and pages of standing queries answered longest ago
     {
         std::lock_guard<std::mutex> lock(S->mu);
         if (!S->queue.empty()) {
-            std::vector<int32_t> free_slots, answered;
-            for (int32_t j = 0; j < nslots; j++) {
-                const Slot &sl = S->slots[(size_t)j];
-                if (sl.state == kFree) free_slots.push_back(j);
-                else if (sl.state == kAnswered) answered.push_back(j);
-            }
-            std::sort(answered.begin(), answered.end(), [&](int32_t a, int32_t b) {
-                return S->slots[(size_t)a].t_answer < S->slots[(size_t)b].t_answer;
-            });
-            free_slots.insert(free_slots.end(), answered.begin(), answered.end());
-            size_t take = std::min(free_slots.size(), S->queue.size());
             std::vector<int32_t> sl_ids, seeds, cls;
             std::vector<gde_kind> kinds;
             std::vector<double> params;
             const double now = server_clock();
-            for (size_t i = 0; i < take; i++) {
+            auto evict_oldest = [&]() -> int32_t {
+                int32_t best = -1;
+                for (int32_t j = 0; j < nslots; j++) {
+                    const Slot &sl = S->slots[(size_t)j];
+                    if (sl.state == kAnswered && (best < 0 || sl.t_answer < S->slots[(size_t)best].t_answer)) best = j;
+                }
+                if (best >= 0) {
+                    serve_pool_release(P, best);
+                    S->slots[(size_t)best].state = kFree;
+                    S->evictions++;
+                }
+                return best;
+            };
+            while (!S->queue.empty()) {
                 const Query q = S->queue.front();
+                int32_t j = -1;
+                for (int32_t c = 0; c < nslots && j < 0; c++)
+                    if (S->slots[(size_t)c].state == kFree) j = c;
+                if (j < 0) j = evict_oldest();
+                if (j < 0) break;  // every slot runs a query
+                const int ord = std::min(start_order(S, q), serve_pool_max_order(P));
+                bool ok = serve_pool_reserve(P, j, ord);
+                while (!ok && evict_oldest() >= 0) ok = serve_pool_reserve(P, j, ord);
+                if (!ok) break;  // waits until running queries give memory back
                 S->queue.pop_front();
-                const int32_t j = free_slots[i];
                 Slot &sl = S->slots[(size_t)j];
                 sl.state = kRunning;
                 sl.q = q;
@@ -242,14 +305,20 @@ gde_status gde_server_step(gde_server *S, int32_t *running, int32_t *queued) {
                 params.push_back(q.param);
                 cls.push_back(q.cls);
             }
-            if (take) {
+            if (!sl_ids.empty()) {
                 const double ta = server_clock();
-                serve_pool_admit(G, P, (int32_t)take, sl_ids.data(), seeds.data(), kinds.data(), params.data(),
-                                 cls.data());
+                serve_pool_admit(G, P, (int32_t)sl_ids.size(), sl_ids.data(), seeds.data(), kinds.data(),
+                                 params.data(), cls.data());
                 GDE_CUDA(cudaStreamSynchronize(G.stream));
                 S->t_phase[2] += server_clock() - ta;
             }
         }
+    }
+    {
+        int32_t resident = 0;
+        for (const Slot &sl : S->slots) resident += sl.state != kFree;
+        S->peak_resident = std::max(S->peak_resident, resident);
+        S->peak_pages = std::max(S->peak_pages, serve_pool_pages_used(P));
     }
 
     // 3. a bounded number of rounds for every resident query
@@ -271,12 +340,32 @@ gde_status gde_server_step(gde_server *S, int32_t *running, int32_t *queued) {
             const int32_t nf = (int32_t)fin.size();
             std::vector<int32_t> ids((size_t)nf * k), st((size_t)nf), last((size_t)nf);
             std::vector<float> vals((size_t)nf * k);
-            std::vector<int64_t> vol((size_t)nf);
-            serve_pool_results(G, P, nf, fin.data(), k, ids.data(), vals.data(), st.data(), vol.data(), last.data());
+            std::vector<int64_t> vol((size_t)nf), support((size_t)nf);
+            serve_pool_results(G, P, nf, fin.data(), k, ids.data(), vals.data(), st.data(), vol.data(), last.data(),
+                               support.data());
             const double now = server_clock();
             std::lock_guard<std::mutex> lock(S->mu);
+            std::vector<Query> again;
             for (int32_t i = 0; i < nf; i++) {
-                Slot &sl = S->slots[(size_t)fin[(size_t)i]];
+                const int32_t j = fin[(size_t)i];
+                Slot &sl = S->slots[(size_t)j];
+                const int ord = serve_pool_order(P, j);
+                if (st[(size_t)i] != GDE_OK && !sl.answered_once && ord < serve_pool_max_order(P)) {
+                    // its table overflowed: start it again with a table four times larger, ahead
+                    // of the queue (its latency still counts from its arrival); its bucket learns
+                    // that it needed more
+                    Query q = sl.q;
+                    q.order = std::min(ord + 2, serve_pool_max_order(P));
+                    note_needed(S, q, q.order);
+                    again.push_back(q);
+                    serve_pool_release(P, j);
+                    sl.state = kFree;
+                    S->readmissions++;
+                    continue;
+                }
+                if (st[(size_t)i] == GDE_OK && !sl.answered_once)
+                    note_needed(S, sl.q, order_for_keys(support[(size_t)i], serve_pool_page_slots(P),
+                                                        serve_pool_max_order(P)));
                 gde_server_result r{};
                 r.qid = sl.q.qid;
                 r.status = st[(size_t)i];
@@ -293,12 +382,14 @@ gde_status gde_server_step(gde_server *S, int32_t *running, int32_t *queued) {
                 S->done.push_back(r);
                 if (r.status != GDE_OK || !sl.q.track) {
                     sl.state = kFree;  // answered one-shot (or failed) queries leave their slot
+                    serve_pool_release(P, j);
                 } else {
                     sl.state = kAnswered;
                     sl.answered_once = true;
                     sl.t_answer = now;
                 }
             }
+            for (auto it = again.rbegin(); it != again.rend(); ++it) S->queue.push_front(*it);
         }
         S->t_phase[4] += server_clock() - tq;
     }
@@ -346,6 +437,13 @@ gde_status gde_server_info(gde_server *S, gde_server_info_t *info) {
     info->t_admit = S->t_phase[2];
     info->t_rounds = S->t_phase[3];
     info->t_results = S->t_phase[4];
+    info->pool_pages = serve_pool_pages(S->pool);
+    info->pages_used = serve_pool_pages_used(S->pool);
+    info->page_slots = serve_pool_page_slots(S->pool);
+    info->peak_resident = S->peak_resident;
+    info->readmissions = S->readmissions;
+    info->evictions = S->evictions;
+    info->peak_pages = S->peak_pages;
     API_END
 }
 

@@ -273,3 +273,47 @@ def test_deferred_heavy_queries(gde, g0, defer):
         # deferral spreads a query's rounds over more steps without changing them
         assert np.allclose(a["vals"], b["vals"], rtol=1e-5, atol=0)
     S.close()
+
+
+def test_admission_by_memory_and_readmission(gde):
+    """A pool of eight 64K-slot pages (20 bytes per slot) on Chung-Lu n = 2^17 (tables of 1, 2
+    or 4 pages): queries are admitted while their tables fit, so no more than eight run at
+    once whatever the slot count; a Katz query from the largest hub touches more nodes than a
+    one-page table holds, overflows and is started again with a table four times larger; every
+    answer matches the oracle, and the pool is empty at the end."""
+    g = synth.chung_lu(1 << 17, 8.0, 2.3, seed=41)
+    d = g.degrees()
+    G = gde.Graph.from_synth(g)
+    pages = 8
+    S = gde.Server(G, slots=64, rounds_per_step=2, eps=(1e-5, 1e-7), mem_budget_bytes=pages * (1 << 16) * 20)
+    inf = S.info()
+    assert inf["pool_pages"] == pages and inf["page_slots"] == 1 << 16 and inf["cap"] == 1 << 18
+    beta = beta_of(g)
+    hub = int(np.argmax(d))
+    qs = [(0, "katz", beta, 1, hub)]
+    seeds = synth.seeds_by_degree(g, 23, seed=42)
+    for i, s in enumerate(seeds):
+        qs.append((i + 1, "ppr", 0.15, 0, int(s)))
+    for q in qs:
+        S.submit(*q)
+    first, peak = {}, 0
+    for _ in range(100000):
+        running, queued = S.step()
+        inf = S.info()
+        peak = max(peak, inf["running"])
+        assert inf["pages_used"] <= pages
+        for r in S.poll():
+            if not r["update"]:
+                first[r["qid"]] = r
+        if running == 0 and queued == 0:
+            break
+    inf = S.info()
+    assert sorted(first) == list(range(len(qs)))
+    assert all(r["status"] == gde.OK for r in first.values())
+    assert peak <= pages and inf["peak_resident"] <= pages
+    assert inf["readmissions"] >= 1 and inf["pages_used"] == 0
+    for q in qs[:6]:
+        ref = oracle.localgd(g, q[1], q[2], (1e-5, 1e-7)[q[3]], q[4]).x
+        check_answer(g, first[q[0]], ref, (1e-5, 1e-7)[q[3]])
+    S.close()
+    G.close()
