@@ -196,8 +196,10 @@ struct BatchWork {
     // hub slab: per seed, H fixed-point residuals (value = count * 2^qexp) and H float x values
     unsigned long long *slab = nullptr;
     float *slab_x = nullptr;
-    int64_t slab_seeds = 0, slab_H = 0;
+    int64_t slab_seeds = 0, slab_H = 0;  // capacity: seeds (per bank) and hubs a seed
+    int slab_banks = 0;                  // capacity: banks
     bool slab_x_dirty = true;  // slab_x must be zeroed before the next solve
+    bool slab_dirty = true;    // slab counts must be zeroed before the next solve
     double *xsrc = nullptr;    // Katz with f_Katz output: per seed x_s - 1 in FP64
     bool slab_on = false;      // the last set-up used the slab
     uint32_t slab_base = 0;
@@ -2006,20 +2008,37 @@ static BArgs batch_setup(Graph &g, const SolveParams &p, BatchWork *w, const int
     if (slab_hubs(g, p, nseeds, cap, s) > 0) {
         const int64_t H = g.hub_n;
         const size_t bank = (size_t)nseeds * (size_t)H;
-        if (!w->slab || w->slab_seeds < (int64_t)nseeds * banks || w->slab_H != H) {
+        if (!w->slab || w->slab_seeds < (int64_t)nseeds || w->slab_banks < banks || w->slab_H != H) {
+            // grow to cover both this solve and the last allocation (PPR and the layered kinds
+            // alternate without reallocating when H is unchanged)
+            int64_t cs = w->slab && w->slab_H == H ? std::max<int64_t>(w->slab_seeds, nseeds) : nseeds;
+            int cb = w->slab && w->slab_H == H ? std::max(w->slab_banks, banks) : banks;
+            if ((uint64_t)cs * (uint64_t)H * (8ull * (uint64_t)cb + 4ull) > kSlabMaxBytes) {
+                cs = nseeds;
+                cb = banks;
+            }
             dfree(w->slab); w->slab = nullptr;
             dfree(w->slab_x); w->slab_x = nullptr;
             w->slab_seeds = w->slab_H = 0;
-            w->slab = (unsigned long long *)dmalloc(8 * bank * (size_t)banks, "hub slab");
-            w->slab_x = (float *)dmalloc(4 * bank, "hub slab x");
-            w->slab_seeds = (int64_t)nseeds * banks;
+            w->slab_banks = 0;
+            w->slab = (unsigned long long *)dmalloc(8 * (size_t)cs * (size_t)H * (size_t)cb, "hub slab");
+            w->slab_x = (float *)dmalloc(4 * (size_t)cs * (size_t)H, "hub slab x");
+            w->slab_seeds = cs;
+            w->slab_banks = cb;
             w->slab_H = H;
             w->slab_x_dirty = true;
+            w->slab_dirty = true;
         }
-        // residual counts start at zero every solve; x is zeroed by the top-k through the x-lists
-        GDE_CUDA(cudaMemsetAsync(w->slab, 0, 8 * bank * (size_t)banks, s));
-        if (w->slab_x_dirty) GDE_CUDA(cudaMemsetAsync(w->slab_x, 0, 4 * bank, s));
+        // residual counts start at zero: PPR and Katz leave the remainders of touched hubs behind
+        // (one memset per solve), while a completed layered solve leaves every bank empty (its
+        // frontier takes every entry it lists), so only a new slab or a failed, capped or
+        // overflowed layered solve needs one; x is zeroed by the top-k through the x-lists.  A
+        // dirty array is zeroed whole: a solve may use more seeds or banks than the one before
+        const size_t cap_entries = (size_t)w->slab_seeds * (size_t)H;
+        if (w->slab_dirty) GDE_CUDA(cudaMemsetAsync(w->slab, 0, 8 * cap_entries * (size_t)w->slab_banks, s));
+        if (w->slab_x_dirty) GDE_CUDA(cudaMemsetAsync(w->slab_x, 0, 4 * cap_entries, s));
         w->slab_x_dirty = true;  // until this solve's top-k has run
+        w->slab_dirty = true;    // until this solve has completed
         // fixed-point scale 2^qexp: the finest whose counts (below the 2^62 overflow mark) hold
         // 64 times the largest residual the solve can reach: the source mass for PPR and Katz
         // (the generalised propagation's source is d_s^b), the largest layer mass
@@ -2228,6 +2247,9 @@ static void batch_solve_once(Graph &g, const SolveParams &p, const int32_t *seed
         }
     }
     if (n_overflow) *n_overflow = nof;
+    // a layered solve's frontier took every slab entry it listed, unless a seed overflowed (its
+    // candidates are skipped) or the round cap stopped the solve with entries still listed
+    if (w->slab_on && lay && nof == 0 && !capped) w->slab_dirty = false;
 }
 
 // ============================================================ serving pool ====

@@ -152,3 +152,44 @@ def test_isolated_duplicate_and_padding(gde):
     st, stats, ids, vals = run_batched(gde, G, "series", 0.0, 1e-4, seeds[:1], k=8, series_coef=c)
     assert st == gde.OK and ids[0, 0] == 6 and vals[0, 0] == pytest.approx(0.5, rel=1e-6)
     G.close()
+
+
+def test_capped_and_overflowed_solves_leave_a_clean_slab(gde, rmat16):
+    """The hub slab is zeroed by the top-k (PPR) or by the layered frontier taking every entry;
+    a solve stopped by the round cap, or with an overflowed seed, leaves entries behind and the
+    next solve must start from zero counts anyway."""
+    g = rmat16
+    G = gde.Graph.from_synth(g)
+    seeds = synth.seeds_mixed(g, 8, 8, seed=17)
+    st, stats, ids, vals = run_batched(gde, G, "hk", 5.0, 1e-6, seeds, max_rounds=3)
+    assert st == gde.ENOTCONV
+    st, stats, ids, vals = run_batched(gde, G, "ppr", 0.1, 1e-6, seeds, max_rounds=2)
+    assert st == gde.ENOTCONV
+    # a budget so small that some seeds overflow their tables and are re-batched
+    run_batched(gde, G, "hk", 5.0, 1e-6, seeds, mem_budget_bytes=16 * 18 * 4096)
+    for kind, param in (("hk", 5.0), ("ppr", 0.1), ("hk", 5.0)):
+        st, stats, ids, vals = run_batched(gde, G, kind, param, 1e-6, seeds)
+        assert st == gde.OK
+        for i in (0, 9, 15):
+            ref = oracle.localgd(g, kind, param, 1e-6, int(seeds[i]))
+            check_topk(g, ids[i], vals[i], ref.x, 1e-6)
+    G.close()
+
+
+def test_slab_capacity_across_kinds_and_batch_sizes(gde, rmat16):
+    """The hub slab is reused across solves: two banks for the layered kinds, one for PPR and
+    Katz, a seed count that changes from batch to batch.  A layered batch of 4, a PPR batch of
+    24, then layered batches of 24 and 4: every batch must start from zero counts and zero x
+    wherever it reads, however the one before used the arrays."""
+    g = rmat16
+    G = gde.Graph.from_synth(g)
+    small = synth.seeds_mixed(g, 2, 2, seed=23)
+    big = synth.seeds_mixed(g, 12, 12, seed=29)
+    for kind, param, seeds in (("hk", 5.0, small), ("ppr", 0.1, big), ("hk", 5.0, big),
+                               ("ppr", 0.1, small), ("hk", 5.0, small)):
+        st, stats, ids, vals = run_batched(gde, G, kind, param, 1e-6, seeds)
+        assert st == gde.OK
+        for i in (0, len(seeds) - 1):
+            ref = oracle.localgd(g, kind, param, 1e-6, int(seeds[i]))
+            check_topk(g, ids[i], vals[i], ref.x, 1e-6)
+    G.close()
