@@ -19,8 +19,13 @@ LIB = os.path.join(OUT, "libgde.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# Device code keeps nvcc's default contraction: every expression whose rounding is part of the
+# result (thresholds fl(fl(theta eps) d), push weights, shares, fixed-point scales and counts)
+# is written with explicit round-to-nearest intrinsics (__dmul_rn, __ddiv_rn, __fadd_rn, ...),
+# which are never fused.  Host code is compiled without contraction: it computes thresholds
+# and per-layer constants that the kernels compare against.
 NVCC_FLAGS = ARCH + [
-    "-O3", "-lineinfo", "-std=c++17", "--fmad=false",
+    "-O3", "-lineinfo", "-std=c++17",
     "-Xcompiler", "-fPIC,-O2,-ffp-contract=off",
     "-I", INCLUDE, "-I", CSRC,
 ]

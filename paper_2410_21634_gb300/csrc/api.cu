@@ -303,6 +303,7 @@ gde_status gde_graph_destroy(gde_graph *h) {
     dfree(g.colp);
     hubs_free(g);
     for (void *q : g.stage_buf) dfree(q);
+    dfree(g.topk_part);
     if (g.stream) cudaStreamDestroy(g.stream);
     delete h;
     return GDE_OK;
@@ -472,7 +473,7 @@ gde_status gde_solve(gde_graph *h, gde_kind kind, double param, double eps, cons
                 void *dst = vec ? vec : (char *)out_x + rsz * (size_t)g.n * i;
                 dense_output(g, w, p, dst);
                 if (k > 0) {
-                    topk_dense_f32((const float *)vec, g.n, k, ids_dev + (size_t)i * k,
+                    topk_dense_f32(g, (const float *)vec, g.n, k, ids_dev + (size_t)i * k,
                                    vals_dev + (size_t)i * k, p.stream);
                 } else if (!dev && g.n > 0) {
                     GDE_CUDA(cudaMemcpyAsync((char *)out_x + rsz * (size_t)g.n * i, vec, rsz * (size_t)g.n,

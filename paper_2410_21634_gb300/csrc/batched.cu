@@ -1594,22 +1594,15 @@ __global__ void __launch_bounds__(kThreads) k_topk_dense_final(int64_t nparts, c
     }
 }
 
-void topk_dense_f32(const float *x_dev, int64_t n, int k, int32_t *ids_dev, float *vals_dev,
+void topk_dense_f32(Graph &g, const float *x_dev, int64_t n, int k, int32_t *ids_dev, float *vals_dev,
                     cudaStream_t s) {
     GDE_REQUIRE(k >= 1 && k <= kTopMax, GDE_EINVAL, "topk must be in [1, 64]");
     const int parts = kSMs * 2;
-    unsigned long long *partial = (unsigned long long *)dmalloc(8 * 64 * (size_t)parts, "top-k partials");
-    try {
-        k_topk_dense_partial<<<parts, kThreads, 0, s>>>(n, x_dev, partial);
-        GDE_CUDA(cudaGetLastError());
-        k_topk_dense_final<<<1, kThreads, 0, s>>>(parts, partial, k, ids_dev, vals_dev);
-        GDE_CUDA(cudaGetLastError());
-        GDE_CUDA(cudaStreamSynchronize(s));
-    } catch (...) {
-        dfree(partial);
-        throw;
-    }
-    dfree(partial);
+    if (!g.topk_part) g.topk_part = (unsigned long long *)dmalloc(8 * 64 * (size_t)parts, "top-k partials");
+    k_topk_dense_partial<<<parts, kThreads, 0, s>>>(n, x_dev, g.topk_part);
+    GDE_CUDA(cudaGetLastError());
+    k_topk_dense_final<<<1, kThreads, 0, s>>>(parts, g.topk_part, k, ids_dev, vals_dev);
+    GDE_CUDA(cudaGetLastError());
 }
 
 // =============================================================== host ====

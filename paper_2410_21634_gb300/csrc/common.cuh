@@ -102,6 +102,7 @@ struct Graph {
     // takes its buffers in a fixed order, growing one only when a larger call needs it)
     std::vector<void *> stage_buf;
     std::vector<size_t> stage_cap;
+    unsigned long long *topk_part = nullptr;  // dense top-k partial lists, allocated on first use
     // Hubs of the batched engine: the nodes of degree >= hub_min_deg ranked by degree
     // (descending, then id).  colq is the packed column array with each hub's rank in place of
     // its id (the degree code above it says which words name hubs: code >= hub_code).  Built on
@@ -312,7 +313,8 @@ gde_status bsession_read(BatchSession *S, int32_t j, float *x, double *r, int32_
 int64_t bsession_round(const BatchSession *S);
 void bsession_destroy(BatchSession *S);
 // top-k (x desc, id asc) of a dense float vector on the device
-void topk_dense_f32(const float *x_dev, int64_t n, int k, int32_t *ids_dev, float *vals_dev,
+// (enqueued on s; the partial lists live in g.topk_part, kept between calls)
+void topk_dense_f32(Graph &g, const float *x_dev, int64_t n, int k, int32_t *ids_dev, float *vals_dev,
                     cudaStream_t s);
 // the two kernels of that top-k: per-block top-64 lists into `partial` (64 keys per block),
 // then one block merges gridDim-many lists into the first k entries
