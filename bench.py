@@ -570,7 +570,13 @@ def random_access_ceiling(gde, dev, gb=16.0, l2_fetch=0):
     for name in ("load", "load_atomic", "atomic"):
         ms = gde.probe_random_access(buf, PROBE_ACCESSES, name, grid=PROBE_GRID, reps=3, l2_fetch_bytes=l2_fetch)
         out[f"{name}_gaccess_per_s"] = PROBE_ACCESSES / (ms / 1e3) / 1e9
-    del buf
+    # the same accesses over the first 32 MB only (L2-resident): the rate of the hits
+    l2buf = buf[: 32 << 20]
+    out["l2_resident_mb"] = 32
+    for name in ("load", "load_atomic", "atomic"):
+        ms = gde.probe_random_access(l2buf, PROBE_ACCESSES, name, grid=PROBE_GRID, reps=3)
+        out[f"l2_resident_{name}_gaccess_per_s"] = PROBE_ACCESSES / (ms / 1e3) / 1e9
+    del buf, l2buf
     torch.cuda.empty_cache()
     return out
 
