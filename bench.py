@@ -362,9 +362,11 @@ def run_batched_kinds(gde, G, g, seeds_np, dev, sample=32):
     """The batched engine on the other kinds of the paper, on the benchmark's graph and seeds:
     Katz (beta = 0.5 / lambda_max, eps = 1e-7) and the heat kernel (tau = 5, Taylor layers,
     eps = 1e-6), both with 64 GB of tables (a Katz hub seed and the first heat-kernel layers
-    touch more nodes than PPR).  Each row: batched FP32 seeds/s and GTEPS (CUDA events around
-    3 solves after one warm-up), and the plain FP64 one-seed-per-launch path on `sample` of
-    the seeds (half uniform, half hubs)."""
+    touch more nodes than PPR).  Each kind runs on a graph object of its own, autotuned for
+    that kind first (the launch shape that suits PPR does not suit the layered heat kernel).
+    Each row: batched FP32 seeds/s and GTEPS (CUDA events around 3 solves after one warm-up),
+    and the plain FP64 one-seed-per-launch path on `sample` of the seeds (half uniform, half
+    hubs)."""
     import numpy as np
     import torch
 
@@ -377,13 +379,15 @@ def run_batched_kinds(gde, G, g, seeds_np, dev, sample=32):
     vals = torch.zeros((nseeds, TOPK), dtype=torch.float32, device=dev)
     for kind, param, eps, budget_gb in (("katz", 0.5 / lam, 1e-7, 64.0), ("hk", 5.0, 1e-6, 64.0)):
         budget = int(budget_gb * (1 << 30))
+        Gk = gde.Graph.from_synth(g)
+        tuning, _ = Gk.autotune(kind, param, eps, seeds, topk=TOPK, mem_budget_bytes=budget)
 
         def solve():
-            return gde.solve(G, kind, param, eps, seeds, vals, ids, precision="fp32", topk=TOPK, batched=1,
+            return gde.solve(Gk, kind, param, eps, seeds, vals, ids, precision="fp32", topk=TOPK, batched=1,
                              mem_budget_bytes=budget)
         solve()
         torch.cuda.synchronize()
-        G.profile_enable(True)
+        Gk.profile_enable(True)
         stream = torch.cuda.current_stream()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -392,25 +396,27 @@ def run_batched_kinds(gde, G, g, seeds_np, dev, sample=32):
             st, stats = solve()
         e1.record(stream)
         torch.cuda.synchronize()
-        prof = G.profile_read()
-        G.profile_enable(False)
+        prof = Gk.profile_read()
+        Gk.profile_enable(False)
         sec = e0.elapsed_time(e1) / 1e3 / reps
         overflow = sum(1 for x in stats if x["fallback"])
         half = nseeds // 2
         smp = np.concatenate([seeds_np[: sample // 2], seeds_np[half: half + sample // 2]])
         out = torch.zeros((1, g.n), dtype=torch.float64, device=dev)
-        gde.solve(G, kind, param, eps, torch.tensor([int(smp[0])], dtype=torch.int32, device=dev), out)
+        gde.solve(Gk, kind, param, eps, torch.tensor([int(smp[0])], dtype=torch.int32, device=dev), out)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for sd in smp:
-            gde.solve(G, kind, param, eps, torch.tensor([int(sd)], dtype=torch.int32, device=dev), out)
+            gde.solve(Gk, kind, param, eps, torch.tensor([int(sd)], dtype=torch.int32, device=dev), out)
         torch.cuda.synchronize()
         plain = len(smp) / (time.perf_counter() - t0)
         rows.append({"kind": kind, "param": param, "eps": eps, "seeds": nseeds, "budget_gb": budget_gb,
                      "batched_fp32_seeds_per_s": nseeds / sec, "ms_per_solve": sec * 1e3,
                      "gteps": prof["edges"] / reps / sec / 1e9, "fallback_seeds": overflow,
                      "plain_fp64_seeds_per_s": plain, "plain_sample": len(smp),
-                     "speedup_vs_plain_fp64": nseeds / sec / plain})
+                     "speedup_vs_plain_fp64": nseeds / sec / plain,
+                     "tuning": {k: v for k, v in tuning.items() if k != "blocks_per_sm" or v}})
+        Gk.close()
     return {"graph": g.name, "lambda_max": lam, "rows": rows}
 
 

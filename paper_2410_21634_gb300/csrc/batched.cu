@@ -446,6 +446,26 @@ __device__ __forceinline__ void stage_flush(uint32_t *buf, unsigned *n, bool for
     __syncwarp();
 }
 
+#ifndef GDE_PREFETCH
+#define GDE_PREFETCH 1  // stream a seed group's hub slab into L2 ahead of its scatter
+#endif
+constexpr int kPrefetch = GDE_PREFETCH;
+constexpr int64_t kPrefetchAhead = 1;  // groups ahead (2 crowds L2: slower)
+constexpr int kPrefetchShift = 3;      // a seed's slab is streamed when its hub pushes are >= hubs / 8
+constexpr uint32_t kPrefetchChunk = 8192;  // bytes a bulk L2 prefetch instruction covers
+
+// Whole warp: stream [p, p + bytes) of global memory into L2 with bulk prefetches (no
+// completion to wait for; the lines are simply present when the scatter reaches them).  The
+// range is shrunk to 16-byte boundaries inside it, as the bulk copy requires.
+__device__ __forceinline__ void l2_prefetch_range(const void *p, uint64_t bytes, int lane) {
+    const uint64_t a0 = ((uint64_t)p + 15ull) & ~15ull;
+    const uint64_t a1 = ((uint64_t)p + bytes) & ~15ull;
+    for (uint64_t q = a0 + (uint64_t)lane * kPrefetchChunk; q < a1; q += 32ull * kPrefetchChunk) {
+        const uint32_t n = (uint32_t)(a1 - q < kPrefetchChunk ? a1 - q : kPrefetchChunk);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(q), "r"(n) : "memory");
+    }
+}
+
 struct ThrBounds {
     float lo, hi;  // lo <= thr_v <= hi; lo == hi means exact
 };
@@ -1200,6 +1220,26 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
                     }
                     const int64_t j0 = glo * kSeedGroup, j1 = j0 + kSeedGroup < ns ? j0 + kSeedGroup : ns;
                     int64_t r = (int64_t)(u - __ldcg(a.grp_off + glo));
+                    if (kPrefetch && !PAGED && a.slab && r == 0) {
+                        // the first unit of a group: stream the next group's hub slabs into L2
+                        // (the first group also its own) while this one is scattered, for the
+                        // seeds whose hub pushes this round are at least an eighth as many as
+                        // hubs (their scatter touches a large share of the slab's sectors; a
+                        // random miss costs several times a streamed sector; streaming every
+                        // seed's slab wastes the bandwidth and crowds L2).  Streaming the tables
+                        // as well gained nothing: their keys are sparser.
+                        for (int64_t gp = glo == 0 ? 0 : glo + kPrefetchAhead; gp <= glo + kPrefetchAhead && gp < ngroups; gp++) {
+                            const int64_t q1 = min(gp * kSeedGroup + kSeedGroup, ns);
+                            for (int64_t jq = gp * kSeedGroup; jq < q1; jq++) {
+                                const int64_t hv = (jq + 1 < ns ? (int64_t)__ldcg(a.vol_off + jq + 1) : VH) -
+                                                   (int64_t)__ldcg(a.vol_off + jq);
+                                if ((hv << kPrefetchShift) >= (int64_t)a.H) {
+                                    const uint64_t bank = LAYERED ? (uint64_t)((t + 1) & 1) : 0ull;
+                                    l2_prefetch_range(a.slab + bank * a.slab_bank + (uint64_t)jq * a.H, 8ull * a.H, lane);
+                                }
+                            }
+                        }
+                    }
                     const int64_t hv0 = (int64_t)__ldcg(a.vol_off + j0);
                     const int64_t hv1 = j1 < ns ? (int64_t)__ldcg(a.vol_off + j1) : VH;
                     const int64_t nch = (hv1 - hv0 + chunk - 1) / chunk;
@@ -2000,7 +2040,6 @@ static BArgs batch_setup(Graph &g, const SolveParams &p, BatchWork *w, const int
     const int banks = lay ? 2 : 1;
     if (slab_hubs(g, p, nseeds, cap, s) > 0) {
         const int64_t H = g.hub_n;
-        const size_t bank = (size_t)nseeds * (size_t)H;
         if (!w->slab || w->slab_seeds < (int64_t)nseeds || w->slab_banks < banks || w->slab_H != H) {
             // grow to cover both this solve and the last allocation (PPR and the layered kinds
             // alternate without reallocating when H is unchanged)
