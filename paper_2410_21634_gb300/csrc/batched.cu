@@ -202,6 +202,12 @@ struct BatchWork {
     bool slab_dirty = true;    // slab counts must be zeroed before the next solve
     double *xsrc = nullptr;    // Katz with f_Katz output: per seed x_s - 1 in FP64
     bool slab_on = false;      // the last set-up used the slab
+    // the counts of a PPR or Katz solve are dead once its round kernel has finished: they are
+    // zeroed on a side stream that overlaps the solve's top-k and read-back, and the next
+    // set-up waits for z_done on its own stream
+    cudaStream_t zs = nullptr;
+    cudaEvent_t z_start = nullptr, z_done = nullptr;
+    bool z_pending = false;
     uint32_t slab_base = 0;
     int qexp = 0;
 };
@@ -1657,7 +1663,11 @@ static void batch_free(BatchWork *w) {
     dfree(w->seg_hcur); dfree(w->seeds); dfree(w->status); dfree(w->inserts); dfree(w->svol);
     dfree(w->spushes); dfree(w->slast); dfree(w->spush); dfree(w->sscat); dfree(w->smass0); dfree(w->xlist); dfree(w->xnode); dfree(w->xcnt); dfree(w->glob); dfree(w->log);
     dfree(w->xkr); dfree(w->xxs); dfree(w->layer_eps); dfree(w->layer_coef);
+    if (w->zs) cudaStreamSynchronize(w->zs);
     dfree(w->slab); dfree(w->slab_x); dfree(w->xsrc);
+    if (w->z_start) cudaEventDestroy(w->z_start);
+    if (w->z_done) cudaEventDestroy(w->z_done);
+    if (w->zs) cudaStreamDestroy(w->zs);
     delete w;
 }
 
@@ -2038,6 +2048,11 @@ static BArgs batch_setup(Graph &g, const SolveParams &p, BatchWork *w, const int
     w->slab_on = false;
     SeedSlab sl{};
     const int banks = lay ? 2 : 1;
+    if (w->z_pending) {
+        // the last solve's slab zeroing (side stream) completes before this solve touches it
+        GDE_CUDA(cudaStreamWaitEvent(s, w->z_done, 0));
+        w->z_pending = false;
+    }
     if (slab_hubs(g, p, nseeds, cap, s) > 0) {
         const int64_t H = g.hub_n;
         if (!w->slab || w->slab_seeds < (int64_t)nseeds || w->slab_banks < banks || w->slab_H != H) {
@@ -2049,6 +2064,7 @@ static BArgs batch_setup(Graph &g, const SolveParams &p, BatchWork *w, const int
                 cs = nseeds;
                 cb = banks;
             }
+            if (w->z_done) GDE_CUDA(cudaEventSynchronize(w->z_done));
             dfree(w->slab); w->slab = nullptr;
             dfree(w->slab_x); w->slab_x = nullptr;
             w->slab_seeds = w->slab_H = 0;
@@ -2195,6 +2211,22 @@ static void batch_solve_once(Graph &g, const SolveParams &p, const int32_t *seed
     BArgs a = batch_setup(g, p, w, seeds_dev, nseeds, cap, list_cap, &key_tag, &key_idmask);
     (void)key_tag;
     launch_rounds(g, w, a, s);
+    if (w->slab_on && !lay) {
+        // PPR and Katz leave residual counts behind; nothing reads them after the round
+        // kernel, so they are zeroed now, beside the top-k, instead of before the next solve
+        if (!w->zs) {
+            GDE_CUDA(cudaStreamCreateWithFlags(&w->zs, cudaStreamNonBlocking));
+            GDE_CUDA(cudaEventCreateWithFlags(&w->z_start, cudaEventDisableTiming));
+            GDE_CUDA(cudaEventCreateWithFlags(&w->z_done, cudaEventDisableTiming));
+        }
+        GDE_CUDA(cudaEventRecord(w->z_start, s));
+        GDE_CUDA(cudaStreamWaitEvent(w->zs, w->z_start, 0));
+        GDE_CUDA(cudaMemsetAsync(w->slab, 0, 8 * (size_t)w->slab_seeds * (size_t)w->slab_H * (size_t)w->slab_banks,
+                                 w->zs));
+        GDE_CUDA(cudaEventRecord(w->z_done, w->zs));
+        w->z_pending = true;
+        w->slab_dirty = false;
+    }
 
     TopkArgs ta{};
     ta.kr = w->kr; ta.xs = w->xs; ta.log2cap = w->log2cap; ta.cap = cap; ta.k = k;
