@@ -311,7 +311,10 @@ gde_status gde_topk_f32_noalloc(const float *x, int64_t n, int32_t k, int32_t *o
  * different salt per launch) and, by mode:
  *   0  reads the sector (two 16-byte loads that bypass L1, as the scatter's probe does),
  *   1  reads it, then atomically adds 1.0f to an FP32 word in it (the insert-or-add pattern),
- *   2  atomically adds 1.0f to its first FP32 value without reading it first.
+ *   2  atomically adds 1.0f to an FP32 value in it without reading it first,
+ *   3  the same add with its result unused (a reduction: nothing returns to the SM),
+ *   4  atomically adds 1 to its first 64-bit integer (the hub-slab insert), result used,
+ *   5  the same 64-bit add with its result unused.
  *   buf        device pointer, 256-byte aligned; its contents are zeroed and then overwritten
  *   bytes      size of buf (>= 64); the probe uses the largest power-of-two number of sectors
  *              that fits, so pass a buffer well above the L2 size to measure device memory

@@ -421,14 +421,14 @@ def test_fail_alloc(nth: int):
     _check(load().gde_test_fail_alloc(int(nth)))
 
 
-PROBE_MODES = {"load": 0, "load_atomic": 1, "atomic": 2}
+PROBE_MODES = {"load": 0, "load_atomic": 1, "atomic": 2, "red": 3, "atomic64": 4, "red64": 5}
 
 
 def probe_random_access(buf, nops: int, mode="load_atomic", grid: int = 152 * 8, reps: int = 3,
                         l2_fetch_bytes: int = 0, stream=None) -> float:
     """gde_probe_random_access: mean ms of one launch of `nops` random 32-byte sector accesses
     over the contiguous CUDA tensor `buf` (its contents are overwritten).  mode: "load",
-    "load_atomic" or "atomic" (or 0, 1, 2)."""
+    "load_atomic", "atomic", "red", "atomic64" or "red64" (or 0 .. 5)."""
     if not _is_cuda_tensor(buf):
         raise ValueError("probe_random_access takes a CUDA tensor")
     m = PROBE_MODES.get(mode, mode)

@@ -2,8 +2,9 @@
 // many random 32-byte sectors per second the memory system can serve, not by streaming
 // bandwidth: a copy moves whole lines in order, a hash-table insert touches one sector at an
 // unpredictable address.  This probe measures that rate with the scatter's own access forms
-// (two 16-byte L1-bypassing loads of one sector, then an FP32 atomic add into it), so the
-// roofline of the round kernel can be read against both ceilings.
+// (two 16-byte L1-bypassing loads of one sector, then an FP32 atomic add into it; a 64-bit
+// integer add alone, as into the hub slab; each add with and without its result used), so
+// the roofline of the round kernel can be read against both ceilings.
 #include "common.cuh"
 
 namespace gde {
@@ -22,17 +23,22 @@ __global__ void __launch_bounds__(kThreads) k_probe_random(unsigned long long *b
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nops; i += (int64_t)gridDim.x * blockDim.x) {
         unsigned long long *p = buf + 4 * (probe_mix((uint64_t)i + salt) & smask);
         unsigned long long w = 0ull;
-        if (mode != 2) {
+        if (mode <= 1) {
             const ulonglong2 lo = __ldcg(reinterpret_cast<const ulonglong2 *>(p));
             const ulonglong2 hi = __ldcg(reinterpret_cast<const ulonglong2 *>(p + 2));
             w = lo.x ^ lo.y ^ hi.x ^ hi.y;
         }
         if (mode == 0) {
             acc += w;
-        } else {
-            // the word the read picked (mode 1) or the sector's first word (mode 2)
+        } else if (mode <= 3) {
+            // the word the read picked (mode 1) or the sector's first word (modes 2 and 3)
             float *f = reinterpret_cast<float *>(p + (w & 3ull)) + 1;
-            acc += (unsigned long long)atomicAdd(f, 1.0f);
+            if (mode == 3) atomicAdd(f, 1.0f);
+            else acc += (unsigned long long)atomicAdd(f, 1.0f);
+        } else if (mode == 4) {
+            acc += atomicAdd(p, 1ull);
+        } else {
+            atomicAdd(p, 1ull);
         }
     }
     // keeps the loads live; the sink is written only if the sum hits this one value
@@ -56,7 +62,7 @@ extern "C" gde_status gde_probe_random_access(void *buf, uint64_t bytes, int64_t
         GDE_REQUIRE(((uintptr_t)buf & 255u) == 0, GDE_EINVAL, "gde_probe_random_access: buf must be 256-byte aligned");
         GDE_REQUIRE(bytes >= 64, GDE_EINVAL, "gde_probe_random_access: bytes must be at least 64");
         GDE_REQUIRE(nops >= 1, GDE_EINVAL, "gde_probe_random_access: nops must be >= 1");
-        GDE_REQUIRE(mode >= 0 && mode <= 2, GDE_EINVAL, "gde_probe_random_access: mode is 0, 1 or 2");
+        GDE_REQUIRE(mode >= 0 && mode <= 5, GDE_EINVAL, "gde_probe_random_access: mode is 0 .. 5");
         GDE_REQUIRE(grid >= 1 && grid <= 65535, GDE_EINVAL, "gde_probe_random_access: grid in [1, 65535]");
         GDE_REQUIRE(reps >= 1 && reps <= 1000, GDE_EINVAL, "gde_probe_random_access: reps in [1, 1000]");
         GDE_REQUIRE(l2_fetch_bytes == 0 || l2_fetch_bytes == 32 || l2_fetch_bytes == 64 || l2_fetch_bytes == 128,

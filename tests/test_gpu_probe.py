@@ -15,7 +15,7 @@ def gde():
     return m
 
 
-@pytest.mark.parametrize("mode", ["load_atomic", "atomic"])
+@pytest.mark.parametrize("mode", ["load_atomic", "atomic", "red"])
 def test_every_access_counted(gde, mode):
     import torch
     buf = torch.empty(64 << 20, dtype=torch.uint8, device="cuda")
@@ -26,6 +26,17 @@ def test_every_access_counted(gde, mode):
     # the adds go to the upper FP32 half of 8-byte words; each word stays far below 2^24
     assert float(f[1::2].double().sum()) == (reps + 1) * nops
     assert float(f[0::2].double().abs().sum()) == 0.0
+
+
+@pytest.mark.parametrize("mode", ["atomic64", "red64"])
+def test_every_64bit_add_counted(gde, mode):
+    import torch
+    buf = torch.empty(64 << 20, dtype=torch.uint8, device="cuda")
+    nops, reps = 1 << 20, 2
+    assert gde.probe_random_access(buf, nops, mode, grid=152 * 4, reps=reps) > 0
+    q = buf.view(torch.int64)
+    assert int(q.sum()) == (reps + 1) * nops
+    assert int(q.view(-1, 4)[:, 1:].abs().sum()) == 0  # only the first word of a sector
 
 
 def test_loads_leave_buffer_zero(gde):
@@ -45,7 +56,7 @@ def test_fetch_granularity_limit_accepted(gde):
 def test_bad_arguments(gde):
     import torch
     buf = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
-    for kw in (dict(mode=3), dict(grid=0), dict(reps=0), dict(l2_fetch_bytes=48), dict(nops=0)):
+    for kw in (dict(mode=6), dict(mode=-1), dict(grid=0), dict(reps=0), dict(l2_fetch_bytes=48), dict(nops=0)):
         args = dict(nops=1024, mode="load", grid=8, reps=1, l2_fetch_bytes=0)
         args.update(kw)
         with pytest.raises(gde.GdeError) as e:
