@@ -267,7 +267,7 @@ gde_status gde_get_tuning(const gde_graph *g, gde_tuning *t);
  * Autotuner of the batched push: one pass of coordinate descent over t1, t2, chunk,
  * schedule, blocks_per_sm and (unless the slab is off) hub_degree in {64, 128, 160} (in that
  * order; each tried over a fixed candidate list with the others held), timing batched solves
- * of `seeds` (kind/param/eps/opts as for gde_solve;
+ * of `seeds` (any kind the batched engine serves, kind/param/eps/opts as for gde_solve;
  * opts->topk in [1,64], batched forced on, FP32) with CUDA events on the solve stream, the
  * fastest of two timed runs per candidate.  The best tuning is applied to g as by
  * gde_set_tuning and, if best is not NULL, returned; *best_ms (may be NULL) receives its time.

@@ -575,7 +575,8 @@ gde_status gde_autotune(gde_graph *h, gde_kind kind, double param, double eps, c
     Graph &g = h->g;
     std::lock_guard<std::mutex> lock(g.mu);
     SolveParams p = make_params(g, kind, param, eps, o);
-    GDE_REQUIRE(kind == GDE_PPR || kind == GDE_KATZ, GDE_EINVAL, "the batched push serves PPR and Katz");
+    GDE_REQUIRE(kind == GDE_PPR || kind == GDE_KATZ || kind == GDE_GPPR || kind == GDE_HK || kind == GDE_SERIES,
+                GDE_EINVAL, "unknown kind");
     const bool dev = (o.flags & GDE_DEVICE_PTRS) != 0;
     std::vector<void *> owned;
     auto alloc = [&](size_t bytes, const char *what) {

@@ -238,6 +238,22 @@ def test_autotune_picks_a_valid_tuning(gde, rmat16):
         check_topk(g, ids[i], vals[i], ref.x, 1e-6)
 
 
+def test_autotune_layered_kind(gde, rmat16):
+    """The autotuner times any batched kind: a heat-kernel batch tunes, and its solves stay
+    correct with the tuning it applied."""
+    g = rmat16
+    G = gde.Graph.from_synth(g)
+    seeds = synth.seeds_mixed(g, 8, 8, seed=19)
+    best, ms = G.autotune("hk", 5.0, 1e-6, seeds, topk=K)
+    assert ms > 0 and G.get_tuning() == best
+    st, stats, ids, vals = run_batched(gde, G, "hk", 5.0, 1e-6, seeds)
+    assert st == gde.OK
+    for i in (0, 15):
+        ref = oracle.localgd(g, "hk", 5.0, 1e-6, int(seeds[i]))
+        check_topk(g, ids[i], vals[i], ref.x, 1e-6)
+    G.close()
+
+
 def test_many_seeds_small_graph(gde, c1):
     """5,000 seeds on a 10^4-node graph (more seeds than nodes, repeats included): the
     per-seed segments, lists and tables at a seed count well past the benchmark's."""
