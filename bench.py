@@ -711,11 +711,13 @@ def main():
         tj = json.load(open(tp))
         src = open(os.path.join(ROOT, "paper_2410_21634_gb300", "csrc", "batched.cu"), "rb").read()
         tuned = {k: v for k, v in G.get_tuning().items() if k != "blocks_per_sm"}
-        if (tj.get("kernel") == "k_batch_rounds" and tj.get("source_sha256") == hashlib.sha256(src).hexdigest()
-                and tj.get("tuning") == tuned):
-            traffic = tj["bytes_per_edge"] * prof["edges"] / launches
-            traffic_note = (f"{tj['bytes_per_edge']:.2f} B per pushed edge from one ncu capture on {tj['graph']} "
-                            f"with {tj['seeds']} seeds (profiles/traffic.json), times this launch's pushed edges")
+        if tj.get("kernel") == "k_batch_rounds" and tj.get("source_sha256") == hashlib.sha256(src).hexdigest():
+            for c in tj.get("captures", []):
+                if c.get("tuning") == tuned:
+                    traffic = c["bytes_per_edge"] * prof["edges"] / launches
+                    traffic_note = (f"{c['bytes_per_edge']:.2f} B per pushed edge from one ncu capture on "
+                                    f"{tj['graph']} with {tj['seeds']} seeds and this launch's tuning "
+                                    f"(profiles/traffic.json), times this launch's pushed edges")
     roofline = {"bound": "hbm", "kernel": "k_batch_rounds", "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                 "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
