@@ -65,6 +65,36 @@ class Stats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class StatsList:
+    """The per-seed gde_stats of one solve, read from the C array as they are used: item i is a
+    dict of seed i's fields (a batch's 1,024 dicts would cost a millisecond to build up front,
+    in the time between two solves)."""
+
+    def __init__(self, arr, n: int):
+        self._arr = arr
+        self._n = n
+
+    def __len__(self):
+        return self._n
+
+    def __getitem__(self, i):
+        if isinstance(i, slice):
+            return [self[k] for k in range(*i.indices(self._n))]
+        i = int(i)
+        if i < 0:
+            i += self._n
+        if not 0 <= i < self._n:
+            raise IndexError("seed index out of range")
+        return self._arr[i].as_dict()
+
+    def __iter__(self):
+        for i in range(self._n):
+            yield self._arr[i].as_dict()
+
+    def __repr__(self):
+        return repr(list(self))
+
+
 class Profile(ctypes.Structure):
     _fields_ = [("batch_rounds_ms", ctypes.c_double), ("batch_clear_ms", ctypes.c_double),
                 ("batch_topk_ms", ctypes.c_double), ("dense_frontier_ms", ctypes.c_double),
@@ -362,7 +392,7 @@ class Graph:
 def solve(graph: Graph, kind, param: float, eps: float, seeds, out_x, out_ids=None,
           stats: bool = True, **opt_kw):
     """gde_solve.  seeds/out_x/out_ids: numpy arrays (host) or CUDA tensors (device).
-    Returns (status, list of per-seed stats dicts)."""
+    Returns (status, per-seed stats: a sequence of dicts, StatsList)."""
     lib = load()
     ps, ds = _ptr(seeds)
     px, dx = _ptr(out_x)
@@ -379,7 +409,7 @@ def solve(graph: Graph, kind, param: float, eps: float, seeds, out_x, out_ids=No
                        ctypes.byref(o), px, pi, ctypes.cast(st_arr, ctypes.c_void_p) if stats else None)
     if st not in (OK, ENOTCONV):
         _check(st)
-    return st, ([st_arr[i].as_dict() for i in range(nseeds)] if stats else [])
+    return st, (StatsList(st_arr, nseeds) if stats else [])
 
 
 def _check_topk_noalloc_args(x, k, out_ids, out_vals):
