@@ -1550,21 +1550,51 @@ __global__ void __launch_bounds__(kThreads) k_batch_topk(TopkArgs a) {
     unsigned long long ta = 0, tb = 0;
     const unsigned nx = a.xcnt[j];
     const bool use_list = nx <= a.xcap;
-    // an overflowed x-list: the whole table, then the seed's slab entries
     const int64_t n = use_list ? (int64_t)nx : a.cap + (a.slab_x ? a.H : 0);
     unsigned support = 0;
-    for (int64_t i0 = (int64_t)wid * 32; i0 < n; i0 += kThreads) {
+    // x-list entries 4 a lane at a time: the four x loads (random) are in flight together
+    constexpr int kU = 4;
+    const int64_t nl = use_list ? n : 0;
+    for (int64_t i0 = (int64_t)wid * 32 * kU; i0 < nl; i0 += kThreads * kU) {
+        float *xp[kU];
+        uint32_t v[kU];
+        float x[kU];
+#pragma unroll
+        for (int u = 0; u < kU; u++) {
+            const int64_t i = i0 + u * 32 + lane;
+            xp[u] = nullptr;
+            v[u] = 0u;
+            if (i < nl) {
+                const uint64_t li = (uint64_t)j * a.xcap + i;
+                const uint32_t id = a.xlist[li];
+                xp[u] = a.slab_x && id >= a.slab_base ? a.slab_x + (id - a.slab_base) : a.xs + id;
+                v[u] = a.xnode[li];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kU; u++) x[u] = xp[u] ? *xp[u] : 0.0f;
+#pragma unroll
+        for (int u = 0; u < kU; u++) {
+            unsigned long long key = 0;
+            if (x[u] > 0.0f) {
+                if (!a.keep) *xp[u] = 0.0f;
+                support++;
+                float xv = x[u];
+                if (a.xsrc && (int32_t)v[u] == a.seed_ids[j]) xv = __double2float_rn(a.xsrc[j]);
+                if (xv > 0.0f)
+                    key = ((unsigned long long)__float_as_uint(xv) << 32) | (unsigned long long)(0xFFFFFFFFu - v[u]);
+            }
+            top64_insert(ta, tb, key, lane);
+        }
+    }
+    // an overflowed x-list: the whole table, then the seed's slab entries
+    for (int64_t i0 = (int64_t)wid * 32; i0 < n && !use_list; i0 += kThreads) {
         const int64_t i = i0 + lane;
         unsigned long long key = 0;
         if (i < n) {
-            const uint64_t li = (uint64_t)j * a.xcap + i;
             float *xp;
             uint32_t v;
-            if (use_list) {
-                const uint32_t id = a.xlist[li];
-                xp = a.slab_x && id >= a.slab_base ? a.slab_x + (id - a.slab_base) : a.xs + id;
-                v = a.xnode[li];
-            } else if (i < a.cap) {
+            if (i < a.cap) {
                 xp = a.xs + base + (uint64_t)i;
                 v = (uint32_t)(a.kr[base + (uint64_t)i] & 0xFFFFFFFFull) & a.key_idmask;
             } else {
