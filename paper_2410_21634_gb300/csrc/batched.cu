@@ -945,12 +945,22 @@ __global__ void __launch_bounds__(kThreads, GDE_ROUNDS_MIN_BLOCKS) k_batch_round
                 const unsigned am = __activemask();
                 const unsigned peers = __match_any_sync(am, j);
                 const unsigned dsum = __reduce_add_sync(peers, (unsigned)dvol);
-                double psum = 0.0, ssum = 0.0;
-                const double scat = d > 0 ? __dmul_rn((double)w, (double)d) : 0.0;
-                for (unsigned m = peers; m; m &= m - 1) {
-                    const int src = __ffs(m) - 1;
-                    psum += __shfl_sync(peers, rho64, src);
-                    ssum += __shfl_sync(peers, scat, src);
+                double psum = rho64, ssum = d > 0 ? __dmul_rn((double)w, (double)d) : 0.0;
+                if (peers == 0xffffffffu) {
+                    // the whole warp on one seed (the usual case: candidates come seed-grouped)
+                    for (int o = 16; o >= 1; o >>= 1) {
+                        psum += __shfl_xor_sync(0xffffffffu, psum, o);
+                        ssum += __shfl_xor_sync(0xffffffffu, ssum, o);
+                    }
+                } else {
+                    const double mp = psum, ms = ssum;
+                    psum = 0.0;
+                    ssum = 0.0;
+                    for (unsigned m = peers; m; m &= m - 1) {
+                        const int src = __ffs(m) - 1;
+                        psum += __shfl_sync(peers, mp, src);
+                        ssum += __shfl_sync(peers, ms, src);
+                    }
                 }
                 if (lane == __ffs(peers) - 1) {
                     atomicAdd(a.svol + j, (unsigned long long)dsum);
