@@ -238,8 +238,9 @@ gde_status gde_profile_rounds(gde_graph *g, double *out, int64_t cap, int64_t *r
  * limit); schedule orders the batched scatter: 1 hands hub chunks to warps in bin order (the
  * bins are laid out seed by seed, so the warps in flight share a few seeds' tables in L2), 2
  * additionally orders medium and small entries, 3 strides every bin statically, 4 scatters
- * the bins group by group of 2 seeds (a seed's table enters L2 once per round; schedule
- * values are stored minus one; 0 keeps the current setting).  Values <= 0 keep the current
+ * the bins seed by seed (a seed's table enters L2 once per round, its hub slab streamed in
+ * ahead; schedule values are stored minus one; 0 keeps the current setting).  Values <= 0
+ * keep the current
  * setting.  Applies to later solves on g.
  */
 typedef struct {

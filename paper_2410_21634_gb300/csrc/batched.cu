@@ -106,7 +106,7 @@ constexpr unsigned kDirectCand = 1u << GDE_DIRECT_CAND_LOG2;
 constexpr unsigned kDirectMaxDeg = 1u << GDE_DIRECT_DEG_LOG2;
 
 #ifndef GDE_SEED_GROUP
-#define GDE_SEED_GROUP 2
+#define GDE_SEED_GROUP 1
 #endif
 constexpr int kSeedGroup = GDE_SEED_GROUP;  // seeds whose bins are scattered together (schedule 3)
 
@@ -456,7 +456,7 @@ __device__ __forceinline__ void stage_flush(uint32_t *buf, unsigned *n, bool for
 #define GDE_PREFETCH 1  // stream a seed group's hub slab into L2 ahead of its scatter
 #endif
 constexpr int kPrefetch = GDE_PREFETCH;
-constexpr int64_t kPrefetchAhead = 1;  // groups ahead (2 crowds L2: slower)
+constexpr int64_t kPrefetchAhead = 1;  // groups ahead (2 or 3 crowd L2: slower)
 constexpr int kPrefetchShift = 3;      // a seed's slab is streamed when its hub pushes are >= hubs / 8
 constexpr uint32_t kPrefetchChunk = 8192;  // bytes a bulk L2 prefetch instruction covers
 
