@@ -1522,6 +1522,9 @@ __device__ __forceinline__ void top64_insert(unsigned long long &a, unsigned lon
     b = merge32_desc(lo, lane);
 }
 
+constexpr int kTopkThreads = 512;
+constexpr int kTopkWarps = kTopkThreads / 32;
+
 struct TopkArgs {
     const unsigned long long *kr;
     float *xs;                  // read, then zeroed for the next solve
@@ -1552,7 +1555,9 @@ struct TopkArgs {
 // One block per seed: the top-k of (x desc, id asc) over the slots of the seed's x-list (every
 // node with nonzero x), which are zeroed for the next solve.  If the list overflowed, the whole
 // table is scanned instead.
-__global__ void __launch_bounds__(kThreads) k_batch_topk(TopkArgs a) {
+// one block of kTopkThreads per seed: the seeds with the longest x-lists set the kernel's time, so
+// wide blocks (512 threads: 0.94 ms for the benchmark's batch, 1.02 ms at 256, 1.14 ms at 128)
+__global__ void __launch_bounds__(kTopkThreads, 2) k_batch_topk(TopkArgs a) {
     const int j = a.slots ? a.slots[blockIdx.x] : (int)blockIdx.x;
     const int64_t orow = blockIdx.x;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -1565,7 +1570,7 @@ __global__ void __launch_bounds__(kThreads) k_batch_topk(TopkArgs a) {
     // x-list entries 4 a lane at a time: the four x loads (random) are in flight together
     constexpr int kU = 4;
     const int64_t nl = use_list ? n : 0;
-    for (int64_t i0 = (int64_t)wid * 32 * kU; i0 < nl; i0 += kThreads * kU) {
+    for (int64_t i0 = (int64_t)wid * 32 * kU; i0 < nl; i0 += kTopkThreads * kU) {
         float *xp[kU];
         uint32_t v[kU];
         float x[kU];
@@ -1598,7 +1603,7 @@ __global__ void __launch_bounds__(kThreads) k_batch_topk(TopkArgs a) {
         }
     }
     // an overflowed x-list: the whole table, then the seed's slab entries
-    for (int64_t i0 = (int64_t)wid * 32; i0 < n && !use_list; i0 += kThreads) {
+    for (int64_t i0 = (int64_t)wid * 32; i0 < n && !use_list; i0 += kTopkThreads) {
         const int64_t i = i0 + lane;
         unsigned long long key = 0;
         if (i < n) {
@@ -1622,19 +1627,19 @@ __global__ void __launch_bounds__(kThreads) k_batch_topk(TopkArgs a) {
         }
         top64_insert(ta, tb, key, lane);
     }
-    __shared__ unsigned long long s_a[kWarps][32], s_b[kWarps][32];
-    __shared__ unsigned s_k[kWarps];
+    __shared__ unsigned long long s_a[kTopkWarps][32], s_b[kTopkWarps][32];
+    __shared__ unsigned s_k[kTopkWarps];
     s_a[wid][lane] = ta;
     s_b[wid][lane] = tb;
     support = bwarp_sum(support);
     if (lane == 0) s_k[wid] = support;
     __syncthreads();
     if (wid == 0) {
-        for (int ww = 1; ww < kWarps; ww++) {
+        for (int ww = 1; ww < kTopkWarps; ww++) {
             top64_insert(ta, tb, s_a[ww][lane], lane);
             top64_insert(ta, tb, s_b[ww][lane], lane);
         }
-        unsigned kk = lane < kWarps ? s_k[lane] : 0u;
+        unsigned kk = lane < kTopkWarps ? s_k[lane] : 0u;
         kk = bwarp_sum(kk);
         if (lane == 0) a.ssupport[j] = kk;
         const int k = a.k;
@@ -2315,7 +2320,7 @@ static void batch_solve_once(Graph &g, const SolveParams &p, const int32_t *seed
         ta.xsrc = w->xsrc; ta.seed_ids = w->seeds;
     }
     const int pt = g.prof.start(kProfBatchTopk, s);
-    k_batch_topk<<<nseeds, kThreads, 0, s>>>(ta);
+    k_batch_topk<<<nseeds, kTopkThreads, 0, s>>>(ta);
     GDE_CUDA(cudaGetLastError());
     g.prof.launched();
     g.prof.stop(pt, s);
