@@ -185,11 +185,12 @@ def test_full_size_rmat24_sampled(gde):
     g = synth.workload_graph("rmat24")
     seeds = synth.seeds_mixed(g, 512, 512, seed=4)
     G = gde.Graph.from_synth(g)
-    # the tuning the benchmark's autotuner settles on for this batch
-    G.set_tuning(t1=16, t2=128, chunk=1024, schedule=2)
+    # the tuning the benchmark's autotuner settles on for this batch (seed-by-seed order, hub
+    # threshold 128; 160 selects the same hubs on this graph)
+    G.set_tuning(t1=32, t2=128, chunk=512, schedule=4, hub_degree=128)
     st, stats, ids, vals = run_batched(gde, G, "ppr", 0.1, 1e-7, seeds)
     assert st == gde.OK and not any(s["fallback"] for s in stats)
-    sample = [0, 1, 511, 512, 700, 1023]
+    sample = [0, 1, 255, 511, 512, 700, 900, 1023]
     xs, info = oracle.localgd_many(g, "ppr", 0.1, 1e-7, seeds[sample])
     for n, i in enumerate(sample):
         check_topk(g, ids[i], vals[i], xs[n], 1e-7)
