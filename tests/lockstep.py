@@ -160,7 +160,7 @@ def _oracle_round(g, kind, param, eps, xo, ro, t, hk_mode, coef):
 
 
 def run_batched(G, g, kind, param, eps, seeds, hk_mode=0, coef=None, widen=False, max_rounds=100000,
-                katz_minus_source=0):
+                katz_minus_source=0, mem_budget_bytes=0):
     """Lock-step comparison of the batched FP32 engine (every seed of the batch advanced by one
     persistent launch per round) with the FP64 oracle.  At every round t and for every seed j:
     the device state (x^t, r^t) of seed j is widened exactly to FP64, the oracle runs round t
@@ -176,6 +176,8 @@ def run_batched(G, g, kind, param, eps, seeds, hk_mode=0, coef=None, widen=False
     rounds skipped for near-threshold differences."""
     import paper_2410_21634_gb300 as gde
     kw = {"hk_threshold": hk_mode, "katz_minus_source": katz_minus_source}
+    if mem_budget_bytes:
+        kw["mem_budget_bytes"] = int(mem_budget_bytes)
     if coef is not None:
         kw["series_coef"] = np.asarray(coef, dtype=np.float64)
     S = gde.BatchSession(G, kind, param, eps, seeds, **kw)

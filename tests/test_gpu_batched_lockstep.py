@@ -181,3 +181,21 @@ def test_batched_session_runs_the_solve(gde, rmat16):
     assert max(s["rounds"] for s in stats) == rounds + 1
     S.close()
     G.close()
+
+
+@pytest.mark.slow
+def test_batched_lockstep_full_size_rmat24(gde):
+    """Round by round on the benchmark's graph (R-MAT scale 24, hubs of degree up to ~400K)
+    with the benchmark's launch shape, PPR alpha=0.1, eps=1e-7: four uniform and four top-1%
+    seeds of the benchmark's batch, every entry >= eps d_u within 1e-5 of the FP64 oracle's
+    round from the same state, every round of the solve."""
+    g = synth.workload_graph("rmat24")
+    batch = synth.seeds_mixed(g, 512, 512, seed=4)
+    seeds = batch[[0, 1, 2, 3, 512, 513, 514, 515]]
+    G = gde.Graph.from_synth(g)
+    G.set_tuning(t1=32, t2=128, chunk=512, schedule=4, hub_degree=128)
+    rep = run_batched(G, g, "ppr", 0.1, 1e-7, seeds, mem_budget_bytes=512 << 20)
+    _report("full size R-MAT 24", rep)
+    assert rep["rounds"] >= 8 and rep["entries"] > 10**5
+    assert rep["max_rel_r"] <= 1e-5 and rep["max_rel_x"] <= 1e-5
+    G.close()
