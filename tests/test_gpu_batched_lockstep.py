@@ -199,3 +199,23 @@ def test_batched_lockstep_full_size_rmat24(gde):
     assert rep["rounds"] >= 8 and rep["entries"] > 10**5
     assert rep["max_rel_r"] <= 1e-5 and rep["max_rel_x"] <= 1e-5
     G.close()
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("kind,param,eps", [("katz", 0.9, 1e-7), ("hk", 5.0, 1e-6)])
+def test_batched_lockstep_full_size_rmat24_katz_hk(gde, kind, param, eps):
+    """The benchmark's other kinds on its graph, round by round: Katz (beta = 0.9 / lambda_max,
+    the power iteration's estimate) and the heat kernel (tau = 5, error-bound threshold), two
+    uniform and two top-1% seeds of the benchmark's batch, at the plain 1e-5 bar."""
+    g = synth.workload_graph("rmat24")
+    if kind == "katz":
+        lam, _ = synth.lambda_max(g, rel_tol=1e-4, max_iter=200)
+        param = param / lam
+    batch = synth.seeds_mixed(g, 512, 512, seed=4)
+    seeds = batch[[0, 1, 512, 513]]
+    G = gde.Graph.from_synth(g)
+    G.set_tuning(t1=32, t2=128, chunk=512, schedule=4, hub_degree=64)
+    rep = run_batched(G, g, kind, param, eps, seeds, mem_budget_bytes=2 << 30)
+    _report(f"full size R-MAT 24 {kind}", rep)
+    assert rep["max_rel_r"] <= 1e-5 and rep["max_rel_x"] <= 1e-5
+    G.close()
