@@ -460,9 +460,9 @@ constexpr int64_t kPrefetchAhead = 1;  // groups ahead (2 or 3 crowd L2: slower)
 constexpr int kPrefetchShift = 3;      // a seed's slab is streamed when its hub pushes are >= hubs / 8
 constexpr uint32_t kPrefetchChunk = 8192;  // bytes a bulk L2 prefetch instruction covers
 
-// Whole warp: stream [p, p + bytes) of global memory into L2 with bulk prefetches (no
-// completion to wait for; the lines are simply present when the scatter reaches them).  The
-// range is shrunk to 16-byte boundaries inside it, as the bulk copy requires.
+// Whole warp: stream [p, p + bytes) of global memory into L2 with bulk prefetches (a hint with
+// no completion to wait for: lines that arrive before the scatter reaches them save it a random
+// miss).  The range is shrunk to 16-byte boundaries inside it, as the bulk copy requires.
 __device__ __forceinline__ void l2_prefetch_range(const void *p, uint64_t bytes, int lane) {
     const uint64_t a0 = ((uint64_t)p + 15ull) & ~15ull;
     const uint64_t a1 = ((uint64_t)p + bytes) & ~15ull;
