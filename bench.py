@@ -565,6 +565,28 @@ PROBE_GRID = 152 * 8
 PROBE_ACCESSES = 1 << 30
 
 
+def traffic_from_capture(traffic_json, kernel_source, tuning, edges_per_launch):
+    """DRAM bytes of one round-kernel launch, from the ncu capture of the same kernel source and
+    launch shape on a small case of the workload (bytes per pushed edge) times this launch's
+    pushed edges.  (None, None) when the file is missing, the source changed since the capture,
+    or no capture has this tuning (blocks_per_sm aside: the grid follows the occupancy)."""
+    import hashlib
+    if not os.path.exists(traffic_json):
+        return None, None
+    tj = json.load(open(traffic_json))
+    src = open(kernel_source, "rb").read()
+    if tj.get("kernel") != "k_batch_rounds" or tj.get("source_sha256") != hashlib.sha256(src).hexdigest():
+        return None, None
+    tuned = {k: v for k, v in tuning.items() if k != "blocks_per_sm"}
+    for c in tj.get("captures", []):
+        if c.get("tuning") == tuned:
+            note = (f"{c['bytes_per_edge']:.2f} B per pushed edge from one ncu capture on {tj['graph']} with "
+                    f"{tj['seeds']} seeds and this launch's tuning (profiles/traffic.json), times this "
+                    f"launch's pushed edges")
+            return c["bytes_per_edge"] * edges_per_launch, note
+    return None, None
+
+
 def random_access_ceiling(gde, dev, gb=16.0, l2_fetch=0):
     """Random 32-byte sector rates of device memory (gde_probe_random_access) over a buffer far
     above the L2 size: reads, read + FP32 atomic add (the scatter's insert-or-add), and atomics
@@ -702,22 +724,11 @@ def main():
     achieved = alg_bytes / (k_ms / 1e3) / 1e9
     kernel_bytes = (KERNEL_BYTES_PER_EDGE * prof["edges"] + KERNEL_BYTES_PER_PUSH * prof["pushes"]) / launches
     traffic, traffic_note = None, None
-    tp = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tp) and g.name == "rmat24" and nseeds == 1024:
-        # DRAM bytes per pushed edge from an ncu capture of the same kernel source and tuning on
-        # a small case of the workload, scaled by this launch's pushed edges (only valid for the
-        # kernel source it was taken on)
-        import hashlib
-        tj = json.load(open(tp))
-        src = open(os.path.join(ROOT, "paper_2410_21634_gb300", "csrc", "batched.cu"), "rb").read()
-        tuned = {k: v for k, v in G.get_tuning().items() if k != "blocks_per_sm"}
-        if tj.get("kernel") == "k_batch_rounds" and tj.get("source_sha256") == hashlib.sha256(src).hexdigest():
-            for c in tj.get("captures", []):
-                if c.get("tuning") == tuned:
-                    traffic = c["bytes_per_edge"] * prof["edges"] / launches
-                    traffic_note = (f"{c['bytes_per_edge']:.2f} B per pushed edge from one ncu capture on "
-                                    f"{tj['graph']} with {tj['seeds']} seeds and this launch's tuning "
-                                    f"(profiles/traffic.json), times this launch's pushed edges")
+    if g.name == "rmat24" and nseeds == 1024:
+        traffic, traffic_note = traffic_from_capture(
+            os.path.join(ROOT, "profiles", "traffic.json"),
+            os.path.join(ROOT, "paper_2410_21634_gb300", "csrc", "batched.cu"),
+            G.get_tuning(), prof["edges"] / launches)
     roofline = {"bound": "hbm", "kernel": "k_batch_rounds", "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                 "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
